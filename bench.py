@@ -1,0 +1,336 @@
+"""Throughput benchmark: PD and FD L-MMSE equalization on GB300.
+
+One step = PD equalization and FD equalization of the same batch (B=256
+antennas, U=16 users, C=8 clusters, 1200 subcarriers x 14 OFDM symbols, 16-QAM,
+i.i.d. Rayleigh, 10 dB, LLRs on): every stage of the hot path runs once per
+architecture.  The metric counts equalized symbols (subcarrier x symbol x user)
+of both architectures per second.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "equalized symbols/s (subcarrier x symbol x user), PD + FD L-MMSE"
+UNIT = "symbols/s"
+WORKLOAD = dict(B=256, U=16, C=8, n_sc=1200, n_sym=14, bits=4, snr_db=10.0)
+# Paper, Table I (L-MMSE, B=256, C=8 on 8 V100): PD 0.856 ms, FD 0.751 ms for
+# 16*1200*14 symbols each; symbols/s of one PD + one FD pass of the batch.
+PAPER_SYMBOLS_PER_S = 2 * 16 * 1200 * 14 / (0.856e-3 + 0.751e-3)
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def input_bytes(B, U, n_sc, n_sym):
+    """HBM bytes the local preprocessing must read: H and y (complex64)."""
+    return n_sc * 8 * (B * U + B * n_sym)
+
+
+def solve_flops(U, n_sym, C):
+    """Real flops of one subcarrier's solve stage: per system Cholesky 4U^3/3,
+    L^{-1} 4U^3/3, two triangular products with n_sym right-hand sides 8U^2 n_sym."""
+    return C * (8.0 * U ** 3 / 3.0 + 8.0 * U * U * n_sym)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _time_oracle(n_sc_total_budget_s: float):
+    """Oracle-only timing on pre-generated chunks (generation excluded)."""
+    from oracle import lmmse
+    from paper_1808_04473_gb300 import synth
+    w = WORKLOAD
+    chunk = 40
+    p = synth.make_problem(w["B"], w["U"], w["C"], chunk, w["n_sym"], snr_db=w["snr_db"], bits=w["bits"], seed=99)
+    done, spent = 0, 0.0
+    while spent < n_sc_total_budget_s:
+        t = time.perf_counter()
+        lmmse.equalize_pd(p.H, p.y, p.N0, p.Es, p.C)
+        lmmse.equalize_fd(p.H, p.y, p.N0, p.Es, p.C)
+        spent += time.perf_counter() - t
+        done += chunk
+    symbols = 2 * w["U"] * w["n_sym"] * done
+    return symbols / spent, done, spent
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    budget = max(2.0, min(30.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        _time_oracle(min(1.0, budget))
+    rates, samples, spent_all = [], 0, 0.0
+    for _ in range(args.steps):
+        r, n, s = _time_oracle(budget)
+        rates.append(r)
+        samples += n
+        spent_all += s
+    value = statistics.median(rates)
+    w = WORKLOAD
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * 2 * w["U"] * w["n_sym"] * w["n_sc"] / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD",
+                   "sample": "FP64 oracle on 40-subcarrier chunks per timed step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{samples} subcarriers over {args.steps} steps ({spent_all:.1f} s of oracle time)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ffeq", choices=["ffeq", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1808_04473_gb300 import build as fbuild
+    from paper_1808_04473_gb300 import ffeq, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    fbuild.build()
+    ffeq.lib()
+
+    w = WORKLOAD
+    B, U, C, n_sc, n_sym, bits = w["B"], w["U"], w["C"], w["n_sc"], w["n_sym"], w["bits"]
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=w["snr_db"], bits=bits, seed=12345 + rank)
+    in_bytes = p.H.nbytes + p.y.nbytes
+    n_sets = max(2, -(-4 * L2_BYTES // in_bytes))          # rotate inputs: working set > 4x L2
+    H0 = torch.from_numpy(p.H).to(dev)
+    y0 = torch.from_numpy(p.y).to(dev)
+    Hs = [H0] + [H0.clone() for _ in range(n_sets - 1)]
+    ys = [y0] + [y0.clone() for _ in range(n_sets - 1)]
+
+    plans = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, llr_bits=bits) for a in (ffeq.PD, ffeq.FD)}
+    outs = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
+                    s2=torch.empty((n_sc, U), dtype=torch.float32, device=dev),
+                    llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32, device=dev))
+            for a in plans}
+    ws_bytes = {a: ffeq.ffeq_workspace_size(pl) for a, pl in plans.items()}
+    ws = {a: torch.empty(ws_bytes[a], dtype=torch.uint8, device=dev) for a in plans}
+    stream = torch.cuda.current_stream(dev)
+
+    # One step: for PD then FD, the local preprocessing kernel and the fusion /
+    # equalization kernel, each bracketed by CUDA events on the launching stream.
+    def step(i, evs=None):
+        for a in (ffeq.PD, ffeq.FD):
+            o = outs[a]
+            if evs is not None:
+                evs[2 * a].record(stream)
+            ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], stream)
+            if evs is not None:
+                evs[2 * a + 1].record(stream)
+            ffeq.ffeq_fuse_equalize(plans[a], ws[a], ws_bytes[a], p.N0, p.Es, o["z"], o["s2"], o["llr"], None,
+                                    stream)
+        if evs is not None:
+            evs[4].record(stream)
+
+    for i in range(args.warmup):
+        step(i % n_sets)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        for k in range(K):
+            step(k % n_sets, ev[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = start.elapsed_time(end)
+    kern = {name: statistics.mean(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K))
+            for j, name in enumerate(["pd_local", "pd_fuse", "fd_local", "fd_fuse"])}
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    assert ffeq.ffeq_device_status() == 0
+    for a in plans:
+        assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
+
+    symbols_per_step = 2 * U * n_sc * n_sym
+    value = world * symbols_per_step * K / (elapsed_ms * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    Hh = torch.from_numpy(p.H).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    stage_bytes = max(ffeq.ffeq_host_staging_size(pl) for pl in plans.values())
+    staging = torch.empty(stage_bytes, dtype=torch.uint8, device=dev)
+    host_out = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64).pin_memory(),
+                        s2=torch.empty((n_sc, U), dtype=torch.float32).pin_memory(),
+                        llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32).pin_memory())
+                for a in plans}
+
+    def host_step():
+        for a in (ffeq.PD, ffeq.FD):
+            o = host_out[a]
+            ffeq.ffeq_equalize_host(plans[a], Hh, yh, p.N0, p.Es, o["z"], o["s2"], o["llr"], None, staging,
+                                    stage_bytes, stream)
+
+    for _ in range(2):
+        host_step()
+    Ke = max(3, min(K, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        host_step()
+    e2e_s = (time.perf_counter() - t0) / Ke
+    e2e_value = world * symbols_per_step / e2e_s
+    h2d = 2 * in_bytes
+    d2h = 2 * (outs[0]["z"].numel() * 8 + outs[0]["s2"].numel() * 4 + outs[0]["llr"].numel() * 4)
+
+    # ---- roofline of the dominant kernel
+    hbm_peak, peak_src = _peaks()
+    dom = max(kern, key=kern.get)
+    dom_ms = kern[dom]
+    if dom.endswith("local"):
+        alg = input_bytes(B, U, n_sc, n_sym)
+        achieved = alg / (dom_ms * 1e-3) / 1e9
+        roof = {"kernel": f"gram_fp32_kernel ({dom[:2].upper()} local preprocessing)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg}
+    else:
+        flops = solve_flops(U, n_sym, C if dom.startswith("fd") else 1) * n_sc
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        peak = FP32_ALU_TFLOPS
+        roof = {"kernel": f"solve_fuse_kernel ({dom[:2].upper()})", "bound": "alu", "achieved": achieved,
+                "peak": peak, "peak_source": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz", "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "algorithmic_flops_per_launch": flops}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_SYMBOLS_PER_S, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD, LLRs",
+                   "precision": "fp32", "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
+                   "parallelism": f"replicas x{world}"},
+        "kernels_ms": kern,
+        "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / ((kern["pd_local"] + kern["pd_fuse"]) * 1e-3),
+                                   "fd": U * n_sc * n_sym / ((kern["fd_local"] + kern["fd_fuse"]) * 1e-3)},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * K,
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, s = _time_oracle(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} subcarriers of the same workload, PD+FD, {s:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

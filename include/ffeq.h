@@ -1,0 +1,166 @@
+/*
+ * ffeq.h -- C ABI of the GB300 (sm_103a) decentralized feedforward equalizer.
+ *
+ * The library computes, for every subcarrier of a massive MU-MIMO uplink
+ * (Sec. II-A, Eq. 1: y = H s0 + n), the partially decentralized (PD) or
+ * fully decentralized (FD) L-MMSE equalizer of Jeon, Li, Cavallaro and Studer,
+ * "Decentralized Equalization with Feedforward Architectures for Massive
+ * MU-MIMO":
+ *
+ *   per cluster c (contiguous antenna block, Sec. II-B):
+ *       G_c = H_c^H H_c,   y_c^MRC = H_c^H y_c                    (Sec. II-C)
+ *   PD: G = sum_c G_c, y^MRC = sum_c y_c^MRC                       (Eq. fullMRC)
+ *       z = (G + rho I)^{-1} y^MRC, rho = N0/Es                     (Sec. III-A)
+ *   FD: z_c = (G_c + rho I)^{-1} y_c^MRC per cluster, then
+ *       z_u = sum_c nu_{c,u} z_{c,u},  nu = sigma_c^-2 / sum sigma^-2 (Eq. fusionrule,
+ *       Lemma 1 Eq. opt_fusion), sigma^2 = (sum_c sigma_c^-2)^-1     (Thm. 3)
+ *   error variances sigma^2 and max-log LLRs of the decoupled channel (Eq. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are interleaved float32 pairs (re, im) ("cf32", 8 bytes).
+ *   H      cf32 [n_sc][U][B]       row u = the B antenna gains of user u
+ *                                  (column-major layout of the paper's B x U H)
+ *   y      cf32 [n_sc][n_sym][B]   receive vectors, one per OFDM symbol
+ *   z      cf32 [n_sc][n_sym][U]   equalized symbols
+ *   sigma2 f32  [n_sc][U]          post-equalization error variance (real)
+ *   llr    f32  [n_sc][n_sym][U][llr_bits]   optional max-log LLRs
+ *   info   i32  [n_sc] (PD) or [n_sc][C] (FD)  optional: 0, or k (1-based) when
+ *                                  the k-th Cholesky pivot of G + rho I (or of
+ *                                  G_c + rho I) was not positive; the outputs of
+ *                                  that subcarrier are then NaN.
+ * Clusters are C contiguous blocks of S = B/C antennas (B % C == 0).
+ * Device pointers must be 8-byte aligned; 16-byte aligned H and y with even B
+ * take the bulk-copy (TMA) staging path.
+ *
+ * Estimates (the paper types sigma^2 as complex; it is real here):
+ *   FFEQ_LITERAL   z = (G + rho I)^{-1} y^MRC and the error variance of Sec. III-A,
+ *                  diag(A G A^H N0 + (AG - I)(AG - I)^H Es) = N0 diag(A),
+ *                  A = (G + rho I)^{-1}; FD fuses these pairs.
+ *   FFEQ_UNBIASED  z / mu, sigma^2 / mu with mu_u = [A G]_uu = 1 - rho A_uu, the
+ *                  unbiased decoupled model z_u = s_u + e_u that Lemma 1 assumes;
+ *                  FD fuses the unbiased per-cluster pairs.
+ *   N0 == 0 is zero forcing; fusion weights then use the N0 -> 0 limit.
+ *   A user with mu <= 0 (e.g. an all-zero channel column) gets weight 0; if
+ *   every cluster gives it weight 0 its z is 0 and its sigma^2 is +inf.
+ *
+ * LLRs (the paper names them, Sec. II-A, but gives no formula): square QAM,
+ * L = 2^(llr_bits/2) odd-integer levels per axis scaled to energy Es; labels are
+ * the binary-reflected Gray code of the in-phase level index (MSB first)
+ * followed by that of the quadrature index; LLR_b = (min_{a: b=1}|z-a|^2 -
+ * min_{a: b=0}|z-a|^2) / sigma^2 (positive favours bit 0).
+ *
+ * Errors: every entry point validates its arguments before launching and
+ * returns a status; nothing is allocated inside the equalize calls (the caller
+ * owns all device memory, including the workspace).  Kernels bound every wait;
+ * a wait that runs out records FFEQ_ERR_TIMEOUT in a device status word that
+ * ffeq_device_status() reads.
+ */
+#ifndef FFEQ_H
+#define FFEQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFEQ_OK = 0,
+  FFEQ_ERR_INVALID_ARG = 1,   /* a size, pointer or enum is out of range */
+  FFEQ_ERR_UNSUPPORTED = 2,   /* valid problem this build cannot run (e.g. U > 32) */
+  FFEQ_ERR_CUDA = 3,          /* a CUDA runtime call failed; see ffeq_last_cuda_error() */
+  FFEQ_ERR_TIMEOUT = 4        /* a bounded device wait ran out (read by ffeq_device_status) */
+} ffeq_status;
+
+typedef enum { FFEQ_PD = 0, FFEQ_FD = 1 } ffeq_arch;
+typedef enum { FFEQ_FP32 = 0 } ffeq_precision;
+typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
+
+/* Problem statement (Sec. II-A, II-B, VI): B antennas, U users, C clusters,
+ * n_sc subcarriers, n_sym OFDM symbols sharing one channel per subcarrier. */
+typedef struct {
+  int B, U, C;
+  int n_sc, n_sym;
+  int arch;        /* ffeq_arch */
+  int precision;   /* ffeq_precision */
+  int estimate;    /* ffeq_estimate */
+  int llr_bits;    /* 0 (no LLRs), 2, 4, 6 or 8 */
+} ffeq_problem;
+
+typedef struct ffeq_plan ffeq_plan;
+
+/* Validate *p and create a plan (host memory only; no device allocation).
+ * Limits of this build: 1 <= U <= 32, 1 <= n_sym <= 16, B % C == 0, the
+ * staged subcarrier (U + n_sym) * (B + 2) * 8 bytes (plus split-K partials
+ * when the clusters are fewer than 8) must fit in 200 KiB, and the C local
+ * systems of one FD subcarrier must fit one CTA (C * U padded <= 512).
+ * Returns FFEQ_ERR_INVALID_ARG or FFEQ_ERR_UNSUPPORTED otherwise. */
+ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p);
+
+/* Destroy a plan (NULL is ignored). */
+void ffeq_plan_destroy(ffeq_plan* plan);
+
+/* Device workspace bytes ffeq_equalize needs: the per-(subcarrier, cluster)
+ * local Gram matrices and MRC outputs, n_sc * Ceff * (U + n_sym) * U * 8 bytes
+ * with Ceff = C (FD) or 1 (PD).  Owned by the caller, 16-byte aligned. */
+ffeq_status ffeq_workspace_size(const ffeq_plan* plan, size_t* bytes);
+
+/* Equalize on the device (Sec. II-C/D, III-A, IV-A; see the header comment).
+ * H, y, z, sigma2 are device pointers; llr and info are device pointers or NULL.
+ * N0 >= 0 and Es > 0 (finite).  workspace is a device buffer of at least
+ * ffeq_workspace_size bytes; calls that share a workspace must be ordered on
+ * one stream.  stream is a cudaStream_t (NULL = legacy default stream).
+ * Asynchronous: returns after the launches (a contraction kernel, then a
+ * solve/fusion kernel started by programmatic dependent launch); results are
+ * ready when the stream reaches them. */
+ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es,
+                          void* z, float* sigma2, float* llr, int* info,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* The two stages of ffeq_equalize, for callers that schedule them apart.
+ *
+ * ffeq_local_preprocess: local preprocessing of every cluster (Sec. II-C):
+ *   G_c = H_c^H H_c and y_c^MRC = H_c^H y_c, summed over clusters for PD
+ *   (Eq. fullMRC), written to the workspace as [n_sc][Ceff][U + n_sym][U]
+ *   complex with D[v][u] = G[u][v] (v < U) and D[U + n][u] = y^MRC_u(n).
+ * ffeq_fuse_equalize: the central (PD) or per-cluster (FD) L-MMSE equalization
+ *   from the workspace, optimal fusion (FD) and the soft outputs.
+ * Same argument rules as ffeq_equalize; the workspace written by the first
+ * must be read by the second on the same stream. */
+ffeq_status ffeq_local_preprocess(const ffeq_plan* plan, const void* H, const void* y,
+                                  void* workspace, size_t workspace_bytes, void* stream);
+ffeq_status ffeq_fuse_equalize(const ffeq_plan* plan, const void* workspace, size_t workspace_bytes,
+                               float N0, float Es, void* z, float* sigma2, float* llr, int* info,
+                               void* stream);
+
+/* Device staging bytes ffeq_equalize_host needs (inputs, outputs and workspace). */
+ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes);
+
+/* Same computation on HOST buffers: copies H and y to the caller's device
+ * staging buffer, runs ffeq_equalize, copies z, sigma2 (and llr, info when not
+ * NULL) back, and synchronizes the stream before returning.  Host buffers should
+ * be page-locked for full copy bandwidth.  staging is a device pointer of at
+ * least ffeq_host_staging_size bytes, 256-byte aligned. */
+ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const void* y_host,
+                               float N0, float Es, void* z_host, float* sigma2_host,
+                               float* llr_host, int* info_host,
+                               void* staging, size_t staging_bytes, void* stream);
+
+/* Read (and, if clear != 0, reset) the device status word written by bounded
+ * waits: FFEQ_OK or FFEQ_ERR_TIMEOUT.  Synchronous with respect to the device. */
+ffeq_status ffeq_device_status(int* code, int clear);
+
+/* Human-readable status; the last CUDA error string seen by the library. */
+const char* ffeq_status_string(ffeq_status s);
+const char* ffeq_last_cuda_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int ffeq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFEQ_H */

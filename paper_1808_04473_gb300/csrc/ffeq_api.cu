@@ -1,0 +1,266 @@
+// C ABI of the equalizer (see include/ffeq.h): plans, argument validation,
+// launches and the host-buffer wrapper.  Nothing here allocates device memory.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "ffeq.h"
+#include "ffeq_internal.h"
+
+struct ffeq_plan {
+  ffeq_problem p;
+  int Ceff;              // clusters kept apart: C (FD) or 1 (PD: summed on chip)
+  size_t workspace;      // bytes of the [n_sc][Ceff][U+n_sym][U] complex workspace
+};
+
+namespace {
+
+thread_local char g_last_cuda_error[256] = "no error";
+
+ffeq_status cuda_fail(cudaError_t e) {
+  std::strncpy(g_last_cuda_error, cudaGetErrorString(e), sizeof(g_last_cuda_error) - 1);
+  return FFEQ_ERR_CUDA;
+}
+
+constexpr size_t kSmemLimit = 200 * 1024;
+constexpr size_t kSolveSmemLimit = 227 * 1024;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+struct Sizes {
+  size_t H, y, z, s2, llr, info;
+};
+
+Sizes buffer_sizes(const ffeq_problem& p) {
+  Sizes s;
+  const size_t nsc = static_cast<size_t>(p.n_sc);
+  s.H = nsc * p.U * p.B * 8;
+  s.y = nsc * p.n_sym * p.B * 8;
+  s.z = nsc * p.n_sym * p.U * 8;
+  s.s2 = nsc * p.U * 4;
+  s.llr = nsc * p.n_sym * p.U * p.llr_bits * 4;
+  s.info = nsc * (p.arch == FFEQ_FD ? p.C : 1) * 4;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ffeq_version(void) { return 100; }
+
+const char* ffeq_status_string(ffeq_status s) {
+  switch (s) {
+    case FFEQ_OK: return "ok";
+    case FFEQ_ERR_INVALID_ARG: return "invalid argument";
+    case FFEQ_ERR_UNSUPPORTED: return "unsupported problem size for this build";
+    case FFEQ_ERR_CUDA: return "CUDA runtime error";
+    case FFEQ_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* ffeq_last_cuda_error(void) { return g_last_cuda_error; }
+
+ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
+  if (!out || !p) return FFEQ_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (p->B <= 0 || p->U <= 0 || p->C <= 0 || p->n_sc < 0 || p->n_sym <= 0) return FFEQ_ERR_INVALID_ARG;
+  if (p->B % p->C != 0) return FFEQ_ERR_INVALID_ARG;
+  if (p->arch != FFEQ_PD && p->arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
+  if (p->precision != FFEQ_FP32) return FFEQ_ERR_INVALID_ARG;
+  if (p->estimate != FFEQ_UNBIASED && p->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
+  if (p->llr_bits != 0 && p->llr_bits != 2 && p->llr_bits != 4 && p->llr_bits != 6 && p->llr_bits != 8)
+    return FFEQ_ERR_INVALID_ARG;
+  if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
+  const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
+  if (ffeq::gram_fp32_smem_bytes(p->B, p->U, p->n_sym, Ceff) > kSmemLimit) return FFEQ_ERR_UNSUPPORTED;
+  const int spc = ffeq::solve_subcarriers_per_cta(p->U, Ceff);
+  if (spc * Ceff * ffeq::padded_users(p->U) > 512 || ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
+    return FFEQ_ERR_UNSUPPORTED;
+  ffeq_plan* plan = new (std::nothrow) ffeq_plan;
+  if (!plan) return FFEQ_ERR_INVALID_ARG;
+  plan->p = *p;
+  plan->Ceff = Ceff;
+  plan->workspace = static_cast<size_t>(p->n_sc) * Ceff * (p->U + p->n_sym) * p->U * 8;
+  *out = plan;
+  return FFEQ_OK;
+}
+
+void ffeq_plan_destroy(ffeq_plan* plan) { delete plan; }
+
+ffeq_status ffeq_workspace_size(const ffeq_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return FFEQ_ERR_INVALID_ARG;
+  *bytes = plan->workspace;
+  return FFEQ_OK;
+}
+
+namespace {
+
+ffeq_status check_common(const ffeq_plan* plan, const void* workspace, size_t workspace_bytes) {
+  if (!plan) return FFEQ_ERR_INVALID_ARG;
+  if (plan->p.n_sc == 0) return FFEQ_OK;
+  if (!workspace || workspace_bytes < plan->workspace || !aligned(workspace, 16)) return FFEQ_ERR_INVALID_ARG;
+  return FFEQ_OK;
+}
+
+ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y, void* workspace,
+                             cudaStream_t st) {
+  const ffeq_problem& p = plan->p;
+  if (!H || !y || !aligned(H, 8) || !aligned(y, 8)) return FFEQ_ERR_INVALID_ARG;
+  ffeq::GramParams gp;
+  gp.H = static_cast<const float2*>(H);
+  gp.y = static_cast<const float2*>(y);
+  gp.D = static_cast<float2*>(workspace);
+  gp.status = ffeq::device_status_ptr();
+  gp.B = p.B;
+  gp.U = p.U;
+  gp.Ceff = plan->Ceff;
+  gp.n_sc = p.n_sc;
+  gp.n_sym = p.n_sym;
+  gp.bulk = (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
+  const cudaError_t e = ffeq::launch_gram_fp32(gp, st);
+  return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+}
+
+ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0, float Es, void* z,
+                          float* sigma2, float* llr, int* info, cudaStream_t st) {
+  const ffeq_problem& p = plan->p;
+  if (!(N0 >= 0.f) || !std::isfinite(N0) || !(Es > 0.f) || !std::isfinite(Es)) return FFEQ_ERR_INVALID_ARG;
+  if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
+  if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
+  if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
+  ffeq::SolveParams sp;
+  sp.D = static_cast<const float2*>(workspace);
+  sp.z = static_cast<float2*>(z);
+  sp.sigma2 = sigma2;
+  sp.llr = p.llr_bits ? llr : nullptr;
+  sp.info = info;
+  sp.U = p.U;
+  sp.Ceff = plan->Ceff;
+  sp.n_sc = p.n_sc;
+  sp.n_sym = p.n_sym;
+  sp.spc = ffeq::solve_subcarriers_per_cta(p.U, plan->Ceff);
+  sp.unbiased = p.estimate == FFEQ_UNBIASED;
+  sp.llr_bits = p.llr_bits;
+  sp.N0 = N0;
+  sp.rho = static_cast<float>(static_cast<double>(N0) / static_cast<double>(Es));
+  if (p.llr_bits) {
+    const double L = static_cast<double>(1 << (p.llr_bits / 2));
+    sp.llr_scale = static_cast<float>(std::sqrt(static_cast<double>(Es) / (2.0 * (L * L - 1.0) / 3.0)));
+  } else {
+    sp.llr_scale = 0.f;
+  }
+  const cudaError_t e = ffeq::launch_solve(sp, st);
+  return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+}
+
+bool bad_scalars(float N0, float Es) {
+  return !(N0 >= 0.f) || !std::isfinite(N0) || !(Es > 0.f) || !std::isfinite(Es);
+}
+
+}  // namespace
+
+ffeq_status ffeq_local_preprocess(const ffeq_plan* plan, const void* H, const void* y, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+  ffeq_status r = check_common(plan, workspace, workspace_bytes);
+  if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
+  return local_preprocess(plan, H, y, workspace, static_cast<cudaStream_t>(stream));
+}
+
+ffeq_status ffeq_fuse_equalize(const ffeq_plan* plan, const void* workspace, size_t workspace_bytes, float N0,
+                               float Es, void* z, float* sigma2, float* llr, int* info, void* stream) {
+  if (plan && bad_scalars(N0, Es)) return FFEQ_ERR_INVALID_ARG;
+  ffeq_status r = check_common(plan, workspace, workspace_bytes);
+  if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
+  return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, static_cast<cudaStream_t>(stream));
+}
+
+ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
+                          float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (plan && bad_scalars(N0, Es)) return FFEQ_ERR_INVALID_ARG;
+  ffeq_status r = check_common(plan, workspace, workspace_bytes);
+  if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
+  const ffeq_problem& p = plan->p;
+  // Validate every pointer before the first launch.
+  if (!H || !y || !aligned(H, 8) || !aligned(y, 8)) return FFEQ_ERR_INVALID_ARG;
+  if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
+  if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
+  if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  r = local_preprocess(plan, H, y, workspace, st);
+  if (r != FFEQ_OK) return r;
+  return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st);
+}
+
+ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return FFEQ_ERR_INVALID_ARG;
+  const Sizes s = buffer_sizes(plan->p);
+  size_t ws = 0;
+  ffeq_workspace_size(plan, &ws);
+  *bytes = align_up(s.H) + align_up(s.y) + align_up(s.z) + align_up(s.s2) + align_up(s.llr) +
+           align_up(s.info) + align_up(ws);
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const void* y_host, float N0, float Es,
+                               void* z_host, float* sigma2_host, float* llr_host, int* info_host, void* staging,
+                               size_t staging_bytes, void* stream) {
+  if (!plan) return FFEQ_ERR_INVALID_ARG;
+  const ffeq_problem& p = plan->p;
+  size_t need = 0;
+  ffeq_host_staging_size(plan, &need);
+  if (p.n_sc == 0) return FFEQ_OK;
+  if (!H_host || !y_host || !z_host || !sigma2_host || !staging) return FFEQ_ERR_INVALID_ARG;
+  if (staging_bytes < need || !aligned(staging, kAlign)) return FFEQ_ERR_INVALID_ARG;
+  if (p.llr_bits && !llr_host) return FFEQ_ERR_INVALID_ARG;
+  const Sizes s = buffer_sizes(p);
+  char* base = static_cast<char*>(staging);
+  char* dH = base;
+  char* dy = dH + align_up(s.H);
+  char* dz = dy + align_up(s.y);
+  char* ds2 = dz + align_up(s.z);
+  char* dllr = ds2 + align_up(s.s2);
+  char* dinfo = dllr + align_up(s.llr);
+  char* dws = dinfo + align_up(s.info);
+  size_t ws = 0;
+  ffeq_workspace_size(plan, &ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dH, H_host, s.H, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(dy, y_host, s.y, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e);
+  const ffeq_status r = ffeq_equalize(plan, dH, dy, N0, Es, dz, reinterpret_cast<float*>(ds2),
+                                      p.llr_bits ? reinterpret_cast<float*>(dllr) : nullptr,
+                                      info_host ? reinterpret_cast<int*>(dinfo) : nullptr, ws ? dws : nullptr, ws,
+                                      stream);
+  if (r != FFEQ_OK) return r;
+  if ((e = cudaMemcpyAsync(z_host, dz, s.z, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(sigma2_host, ds2, s.s2, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e);
+  if (p.llr_bits && (e = cudaMemcpyAsync(llr_host, dllr, s.llr, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e);
+  if (info_host && (e = cudaMemcpyAsync(info_host, dinfo, s.info, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_device_status(int* code, int clear) {
+  if (!code) return FFEQ_ERR_INVALID_ARG;
+  int* d = ffeq::device_status_ptr();
+  if (!d) return cuda_fail(cudaGetLastError());
+  cudaError_t e = cudaMemcpy(code, d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (clear) {
+    const int zero = 0;
+    e = cudaMemcpy(d, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return FFEQ_OK;
+}
+
+}  // extern "C"

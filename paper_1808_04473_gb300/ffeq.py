@@ -1,0 +1,211 @@
+"""Thin ctypes binding over the C ABI of ``libffeq.so`` (``include/ffeq.h``).
+
+Every function here marshals arguments and calls the library entry point of the
+same name; all arithmetic runs in the CUDA kernels.  There is no fallback: if
+the library has not been built, or a call fails, an exception is raised.
+
+Tensors are ``torch`` tensors (device memory and streams come from PyTorch);
+complex arrays are ``torch.complex64``.  ``equalize`` is a convenience wrapper
+that allocates the outputs and calls ``ffeq_plan_create`` + ``ffeq_equalize``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PD, FD = 0, 1
+FP32 = 0
+UNBIASED, LITERAL = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffeq.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "ffeq.h")
+
+_STATUS = {0: "FFEQ_OK", 1: "FFEQ_ERR_INVALID_ARG", 2: "FFEQ_ERR_UNSUPPORTED", 3: "FFEQ_ERR_CUDA",
+           4: "FFEQ_ERR_TIMEOUT"}
+
+
+class FfeqError(RuntimeError):
+    """A non-OK status returned by the library."""
+
+    def __init__(self, func: str, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{func} -> {_STATUS.get(status, status)}{': ' + detail if detail else ''}")
+
+
+class ffeq_problem(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("U", ctypes.c_int), ("C", ctypes.c_int), ("n_sc", ctypes.c_int),
+                ("n_sym", ctypes.c_int), ("arch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("estimate", ctypes.c_int), ("llr_bits", ctypes.c_int)]
+
+
+_lib = None
+_vp, _sz, _f, _i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
+_SIGS = {
+    "ffeq_version": ([], _i),
+    "ffeq_status_string": ([_i], ctypes.c_char_p),
+    "ffeq_last_cuda_error": ([], ctypes.c_char_p),
+    "ffeq_plan_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_problem)], _i),
+    "ffeq_plan_destroy": ([_vp], None),
+    "ffeq_workspace_size": ([_vp, ctypes.POINTER(_sz)], _i),
+    "ffeq_equalize": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_local_preprocess": ([_vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_fuse_equalize": ([_vp, _vp, _sz, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
+    "ffeq_host_staging_size": ([_vp, ctypes.POINTER(_sz)], _i),
+    "ffeq_equalize_host": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_device_status": ([ctypes.POINTER(_i), _i], _i),
+}
+
+
+def lib():
+    """Load ``libffeq.so`` once (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in ``include/ffeq.h``."""
+    text = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"\b(ffeq_[a-z_]+)\s*\(", text)))
+
+
+def _check(func: str, status: int):
+    if status != 0:
+        detail = lib().ffeq_last_cuda_error().decode() if status == 3 else ""
+        raise FfeqError(func, status, detail)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to libffeq must be contiguous")
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):                       # numpy array (host buffers)
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libffeq must be C-contiguous")
+        return t.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(t)!r}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """Owner of an ``ffeq_plan*`` (destroyed with the object)."""
+
+    def __init__(self, handle: int, problem: ffeq_problem):
+        self.handle = handle
+        self.problem = problem
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.ffeq_plan_destroy(self.handle)
+            self.handle = None
+
+
+def ffeq_version() -> int:
+    return lib().ffeq_version()
+
+
+def ffeq_plan_create(B: int, U: int, C: int, n_sc: int, n_sym: int, arch: int = PD, precision: int = FP32,
+                     estimate: int = UNBIASED, llr_bits: int = 0) -> Plan:
+    p = ffeq_problem(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits)
+    h = _vp()
+    _check("ffeq_plan_create", lib().ffeq_plan_create(ctypes.byref(h), ctypes.byref(p)))
+    return Plan(h.value, p)
+
+
+def ffeq_workspace_size(plan: Plan) -> int:
+    n = _sz()
+    _check("ffeq_workspace_size", lib().ffeq_workspace_size(plan.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ffeq_host_staging_size(plan: Plan) -> int:
+    n = _sz()
+    _check("ffeq_host_staging_size", lib().ffeq_host_staging_size(plan.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ffeq_equalize(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=None, info=None, workspace=None,
+                  workspace_bytes: int = 0, stream=None) -> None:
+    _check("ffeq_equalize", lib().ffeq_equalize(
+        plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
+        _ptr(workspace), workspace_bytes, _stream(stream)))
+
+
+def ffeq_local_preprocess(plan: Plan, H, y, workspace, workspace_bytes: int, stream=None) -> None:
+    _check("ffeq_local_preprocess", lib().ffeq_local_preprocess(
+        plan.handle, _ptr(H), _ptr(y), _ptr(workspace), workspace_bytes, _stream(stream)))
+
+
+def ffeq_fuse_equalize(plan: Plan, workspace, workspace_bytes: int, N0: float, Es: float, z, sigma2, llr=None,
+                       info=None, stream=None) -> None:
+    _check("ffeq_fuse_equalize", lib().ffeq_fuse_equalize(
+        plan.handle, _ptr(workspace), workspace_bytes, float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr),
+        _ptr(info), _stream(stream)))
+
+
+def ffeq_equalize_host(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=None, info=None, staging=None,
+                       staging_bytes: int = 0, stream=None) -> None:
+    _check("ffeq_equalize_host", lib().ffeq_equalize_host(
+        plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
+        _ptr(staging), staging_bytes, _stream(stream)))
+
+
+def ffeq_device_status(clear: bool = True) -> int:
+    code = _i()
+    _check("ffeq_device_status", lib().ffeq_device_status(ctypes.byref(code), int(clear)))
+    return code.value
+
+
+def ffeq_status_string(status: int) -> str:
+    return lib().ffeq_status_string(status).decode()
+
+
+# --------------------------------------------------------------------- convenience
+
+def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int = UNBIASED, llr_bits: int = 0,
+             with_info: bool = False, stream=None) -> dict:
+    """Allocate outputs on ``H.device`` and run one equalization (returns torch tensors)."""
+    import torch
+    if H.dtype != torch.complex64 or y.dtype != torch.complex64:
+        raise TypeError("H and y must be complex64")
+    if not H.is_cuda or not y.is_cuda:
+        raise ValueError("H and y must be CUDA tensors (there is no CPU path)")
+    n_sc, U, B = H.shape
+    n_sym = y.shape[1]
+    if tuple(y.shape) != (n_sc, n_sym, B):
+        raise ValueError("y must be [n_sc][n_sym][B]")
+    plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, FP32, estimate, llr_bits)
+    dev = H.device
+    out = {"z": torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
+           "sigma2": torch.empty((n_sc, U), dtype=torch.float32, device=dev)}
+    if llr_bits:
+        out["llr"] = torch.empty((n_sc, n_sym, U, llr_bits), dtype=torch.float32, device=dev)
+    if with_info:
+        out["info"] = torch.empty((n_sc, C if arch == FD else 1), dtype=torch.int32, device=dev)
+    ws_bytes = ffeq_workspace_size(plan)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev) if ws_bytes else None
+    ffeq_equalize(plan, H, y, N0, Es, out["z"], out["sigma2"], out.get("llr"), out.get("info"), ws, ws_bytes,
+                  stream)
+    return out

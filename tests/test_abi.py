@@ -1,0 +1,108 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every symbol
+declared in include/ffeq.h, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_1808_04473_gb300 import build as fbuild
+from paper_1808_04473_gb300 import ffeq
+
+
+@pytest.fixture(scope="module")
+def built():
+    fbuild.build()
+    return ffeq.lib()
+
+
+def test_library_exports_every_header_symbol(built):
+    names = ffeq.header_symbols()
+    assert "ffeq_equalize" in names and "ffeq_plan_create" in names
+    for n in names:
+        assert hasattr(built, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", ffeq.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_version_and_status_strings(built):
+    assert ffeq.ffeq_version() >= 100
+    assert ffeq.ffeq_status_string(0) == "ok"
+    assert "invalid" in ffeq.ffeq_status_string(1)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(B=0, U=4, C=1), 1), (dict(B=32, U=4, C=3), 1), (dict(B=32, U=0, C=2), 1),
+    (dict(B=32, U=4, C=2, arch=7), 1), (dict(B=32, U=4, C=2, estimate=5), 1),
+    (dict(B=32, U=4, C=2, llr_bits=3), 1), (dict(B=32, U=4, C=2, precision=9), 1),
+    (dict(B=32, U=33, C=2), 2), (dict(B=32, U=4, C=2, n_sym=17), 2), (dict(B=8192, U=32, C=2), 2),
+])
+def test_plan_validation(built, kw, status):
+    args = dict(B=32, U=4, C=2, n_sc=8, n_sym=1)
+    args.update(kw)
+    with pytest.raises(ffeq.FfeqError) as e:
+        ffeq.ffeq_plan_create(**args)
+    assert e.value.status == status
+
+
+def test_equalize_rejects_bad_arguments_without_cuda(built):
+    plan = ffeq.ffeq_plan_create(32, 4, 2, 8, 1)
+    fake = 1 << 20                                  # never dereferenced: validation fails first
+    for N0, Es in ((-1.0, 1.0), (1.0, 0.0), (float("nan"), 1.0), (1.0, float("inf"))):
+        with pytest.raises(ffeq.FfeqError) as e:
+            ffeq.ffeq_equalize(plan, fake, fake, N0, Es, fake, fake, workspace=fake, workspace_bytes=1 << 30,
+                               stream=0)
+        assert e.value.status == 1
+    with pytest.raises(ffeq.FfeqError):
+        ffeq.ffeq_equalize(plan, None, fake, 1.0, 1.0, fake, fake, workspace=fake, workspace_bytes=1 << 30,
+                           stream=0)
+    with pytest.raises(ffeq.FfeqError):                                         # misaligned H
+        ffeq.ffeq_equalize(plan, fake + 4, fake, 1.0, 1.0, fake, fake, workspace=fake, workspace_bytes=1 << 30,
+                           stream=0)
+    need = ffeq.ffeq_workspace_size(plan)
+    with pytest.raises(ffeq.FfeqError):                                         # workspace too small
+        ffeq.ffeq_equalize(plan, fake, fake, 1.0, 1.0, fake, fake, workspace=fake, workspace_bytes=need - 1,
+                           stream=0)
+    llr_plan = ffeq.ffeq_plan_create(32, 4, 2, 8, 1, llr_bits=4)
+    with pytest.raises(ffeq.FfeqError):
+        ffeq.ffeq_equalize(llr_plan, fake, fake, 1.0, 1.0, fake, fake, llr=None, workspace=fake,
+                           workspace_bytes=1 << 30, stream=0)
+    empty = ffeq.ffeq_plan_create(32, 4, 2, 0, 1)                                # n_sc = 0 is a no-op
+    ffeq.ffeq_equalize(empty, None, None, 1.0, 1.0, None, None, stream=0)
+
+
+def test_staging_size_accounts_for_every_buffer(built):
+    plan = ffeq.ffeq_plan_create(256, 16, 8, 1200, 14, arch=ffeq.FD, llr_bits=4)
+    n = ffeq.ffeq_host_staging_size(plan)
+    ws = 1200 * 8 * (16 + 14) * 16 * 8
+    assert ffeq.ffeq_workspace_size(plan) == ws
+    need = 1200 * 16 * 256 * 8 + 1200 * 14 * 256 * 8 + 1200 * 14 * 16 * 8 + 1200 * 16 * 4 + \
+        1200 * 14 * 16 * 4 * 4 + 1200 * 8 * 4 + ws
+    assert need <= n <= need + 8 * 256
+    pd = ffeq.ffeq_plan_create(256, 16, 8, 1200, 14, arch=ffeq.PD)
+    assert ffeq.ffeq_workspace_size(pd) == 1200 * (16 + 14) * 16 * 8
+
+
+def test_plan_struct_layout_matches_header(built):
+    assert ctypes.sizeof(ffeq.ffeq_problem) == 9 * 4
+    text = open(ffeq.HEADER_PATH).read()
+    body = text[text.index("typedef struct {"):text.index("} ffeq_problem;")]
+    fields = [f for line in body.splitlines()[1:] for f in line.split(";")[0].replace("int", "").split(",")
+              if f.strip() and not f.strip().startswith("/*")]
+    assert [f.strip() for f in fields] == [n for n, _ in ffeq.ffeq_problem._fields_]
+
+
+def test_oracle_and_cuda_sources_are_independent(repo_root):
+    """The oracle never imports the CUDA path, and the package never imports the oracle."""
+    for dirpath, _, files in os.walk(os.path.join(repo_root, "oracle")):
+        for f in files:
+            if f.endswith(".py"):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "paper_1808_04473_gb300" not in src and "ffeq" not in src.replace("ffeq_", ""), f
+    pkg = os.path.join(repo_root, "paper_1808_04473_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f

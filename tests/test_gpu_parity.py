@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance (FP32 path): per subcarrier, ||z_gpu - z_oracle||_2 / ||z_oracle||_2
+<= 1e-5, and the same for sigma^2 and the LLRs of that subcarrier.  Inputs are
+the same seeded complex64 arrays for both sides.
+"""
+import numpy as np
+import pytest
+
+from oracle import llr as ollr
+from oracle import lmmse
+from paper_1808_04473_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04473_gb300 import build as fbuild
+    from paper_1808_04473_gb300 import ffeq
+    fbuild.build()
+    ffeq.lib()
+    return ffeq
+
+
+def _gpu(ff, p, arch, estimate, llr_bits=0, with_info=True, H=None, y=None, N0=None):
+    dev = torch.device("cuda:0")
+    Ht = torch.from_numpy(p.H if H is None else H).to(dev)
+    yt = torch.from_numpy(p.y if y is None else y).to(dev)
+    out = ff.equalize(Ht, yt, p.N0 if N0 is None else N0, p.Es, p.C, arch=arch, estimate=estimate,
+                      llr_bits=llr_bits, with_info=with_info)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _oracle(p, arch, estimate, H=None, y=None, N0=None, idx=None):
+    H = p.H if H is None else H
+    y = p.y if y is None else y
+    if idx is not None:
+        H, y = H[idx], y[idx]
+    f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
+    return f(H, y, p.N0 if N0 is None else N0, p.Es, p.C, "unbiased" if estimate == 0 else "literal")
+
+
+def _rel_per_sc(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+
+
+def _check(g, o, p, bits=0, tol=TOL, idx=None):
+    z = g["z"] if idx is None else g["z"][idx]
+    s2 = g["sigma2"] if idx is None else g["sigma2"][idx]
+    ez = _rel_per_sc(z, o["z"])
+    es = _rel_per_sc(s2, o["sigma2"])
+    assert ez.max() <= tol, f"z rel err {ez.max():.3g}"
+    assert es.max() <= tol, f"sigma2 rel err {es.max():.3g}"
+    if bits:
+        L = g["llr"] if idx is None else g["llr"][idx]
+        Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], bits, p.Es)
+        el = _rel_per_sc(L, Lo)
+        assert el.max() <= tol, f"llr rel err {el.max():.3g}"
+    return ez.max()
+
+
+CASES = [
+    # B, U, C, n_sc, n_sym, bits, snr_db, Es
+    (32, 4, 2, 64, 1, 2, 10.0, 1.0),        # small PD/FD case (QPSK, 10 dB)
+    (64, 16, 4, 37, 14, 4, 10.0, 1.0),      # several tiles, ragged subcarrier count
+    (48, 7, 3, 5, 3, 4, 5.0, 2.0),          # odd U, C=3, Es != 1
+    (256, 16, 8, 24, 14, 4, 20.0, 1.0),     # per-subcarrier shape of the throughput workload
+    (256, 32, 16, 12, 14, 6, 15.0, 1.0),    # S=16 < U=32: rank-deficient local Gram matrices
+    (33, 5, 3, 9, 2, 2, 8.0, 1.0),          # odd B: plain-load staging path
+    (128, 1, 4, 10, 1, 2, 0.0, 1.0),        # single user
+    (64, 32, 1, 10, 16, 8, 12.0, 1.0),      # U=32, n_sym=16 (maxima), C=1, 256-QAM LLRs
+    (40, 20, 5, 7, 4, 4, 6.0, 0.5),         # S=8 < U=20, C=5 (split-K with 3 spare warps)
+    (96, 12, 12, 6, 5, 6, 18.0, 1.0),       # C=12: two rounds of clusters
+]
+
+
+@pytest.mark.parametrize("B,U,C,n_sc,n_sym,bits,snr,Es", CASES)
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+@pytest.mark.parametrize("estimate", [0, 1], ids=["unbiased", "literal"])
+def test_parity_small(ff, B, U, C, n_sc, n_sym, bits, snr, Es, arch, estimate):
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=snr, bits=bits, seed=B * 131 + U * 7 + C, Es=Es)
+    g = _gpu(ff, p, arch, estimate, llr_bits=bits)
+    o = _oracle(p, arch, estimate)
+    _check(g, o, p, bits)
+    assert (g["info"] == 0).all()
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_parity_correlated_channel(ff, arch):
+    """Receive-side exponential correlation r = 0.7 (ill-conditioned local Gram matrices)."""
+    p = synth.make_problem(256, 32, 16, 8, 14, snr_db=15.0, bits=6, seed=77, corr_r=0.7)
+    g = _gpu(ff, p, arch, 0, llr_bits=6)
+    o = _oracle(p, arch, 0)
+    _check(g, o, p, 6)
+
+
+def test_pd_ignores_partition_and_equals_fd_at_c1(ff):
+    p = synth.make_problem(64, 8, 1, 16, 3, seed=3)
+    base = _gpu(ff, p, 0, 0)
+    for C in (2, 4, 8, 16):
+        q = synth.make_problem(64, 8, C, 16, 3, seed=3)
+        g = _gpu(ff, q, 0, 0)
+        assert np.array_equal(g["z"], base["z"]) and np.array_equal(g["sigma2"], base["sigma2"])
+    fd = _gpu(ff, p, 1, 0)
+    assert np.array_equal(fd["z"], base["z"]) and np.array_equal(fd["sigma2"], base["sigma2"])
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_noiseless_zero_forcing(ff, arch):
+    p = synth.make_problem(128, 8, 4, 32, 6, noiseless=True, seed=4, bits=4)
+    g = _gpu(ff, p, arch, 0)
+    assert np.abs(g["z"] - p.s).max() < 1e-4
+    assert (g["sigma2"] == 0).all()
+
+
+def test_singular_zero_forcing_reports_pivot(ff):
+    p = synth.make_problem(16, 4, 2, 3, 2, noiseless=True, seed=10)
+    H = p.H.copy()
+    H[1, 2, :] = 0.0
+    for arch in (0, 1):
+        g = _gpu(ff, p, arch, 0, H=H, N0=0.0)
+        o = _oracle(p, arch, 0, H=H, N0=0.0)
+        assert np.array_equal(g["info"].reshape(o["info"].shape), o["info"])
+        assert np.isnan(g["z"][1]).all() and np.isnan(g["sigma2"][1]).all()
+        assert np.isfinite(g["z"][[0, 2]]).all()
+
+
+def test_zero_channel_column_gets_zero_weight(ff):
+    p = synth.make_problem(16, 3, 2, 2, 2, seed=11)
+    H = p.H.copy()
+    H[0, 1, :8] = 0.0            # invisible to cluster 0 only: FD weight 0 there
+    H[1, 2, :] = 0.0             # invisible everywhere: z = 0, sigma^2 = inf
+    for arch in (0, 1):
+        g = _gpu(ff, p, arch, 0, H=H)
+        o = _oracle(p, arch, 0, H=H)
+        assert np.isinf(g["sigma2"][1, 2]) and np.isinf(o["sigma2"][1, 2])
+        assert (g["z"][1, :, 2] == 0).all()
+        keep = np.ones_like(o["sigma2"], bool)
+        keep[1, 2] = False
+        np.testing.assert_allclose(g["sigma2"][keep], o["sigma2"][keep], rtol=TOL)
+        np.testing.assert_allclose(g["z"][0], o["z"][0], rtol=TOL, atol=TOL)
+
+
+def test_empty_and_single_subcarrier(ff):
+    p = synth.make_problem(32, 4, 2, 1, 1, seed=12)
+    for arch in (0, 1):
+        _check(_gpu(ff, p, arch, 0), _oracle(p, arch, 0), p)
+    dev = torch.device("cuda:0")
+    plan = ff.ffeq_plan_create(32, 4, 2, 0, 1)
+    ff.ffeq_equalize(plan, None, None, 1.0, 1.0, None, None)
+
+
+def test_host_buffer_entry_point_matches_device_path(ff):
+    p = synth.make_problem(64, 16, 4, 40, 14, seed=13, bits=4)
+    plan = ff.ffeq_plan_create(64, 16, 4, 40, 14, arch=ff.FD, llr_bits=4)
+    nbytes = ff.ffeq_host_staging_size(plan)
+    staging = torch.empty(nbytes, dtype=torch.uint8, device="cuda:0")
+    Hh = torch.from_numpy(p.H).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    z = torch.empty((40, 14, 16), dtype=torch.complex64).pin_memory()
+    s2 = torch.empty((40, 16), dtype=torch.float32).pin_memory()
+    L = torch.empty((40, 14, 16, 4), dtype=torch.float32).pin_memory()
+    info = torch.empty((40, 4), dtype=torch.int32).pin_memory()
+    ff.ffeq_equalize_host(plan, Hh, yh, p.N0, p.Es, z, s2, L, info, staging, nbytes)
+    g = _gpu(ff, p, 1, 0, llr_bits=4)
+    assert np.array_equal(z.numpy(), g["z"]) and np.array_equal(s2.numpy(), g["sigma2"])
+    assert np.array_equal(L.numpy(), g["llr"]) and (info.numpy() == 0).all()
+    assert ff.ffeq_device_status() == 0
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_full_size_throughput_workload_sampled(ff, arch):
+    """B=256, U=16, C=8, 1200 subcarriers x 14 symbols, 16-QAM, in the benchmark's launch.
+
+    The oracle checks 48 sampled subcarriers; every output must be finite."""
+    p = synth.make_problem(256, 16, 8, 1200, 14, snr_db=10.0, bits=4, seed=2024)
+    g = _gpu(ff, p, arch, 0, llr_bits=4)
+    idx = np.random.default_rng(5).choice(1200, 48, replace=False)
+    o = _oracle(p, arch, 0, idx=idx)
+    _check(g, o, p, 4, idx=idx)
+    assert np.isfinite(g["z"]).all() and np.isfinite(g["llr"]).all() and (g["info"] == 0).all()
+
+
+def test_full_size_correlated_workload_sampled(ff):
+    """B=256, U=32, C=16, 3300 x 14, 64-QAM, r=0.7, 15 dB (FD and PD), sampled."""
+    p = synth.make_problem(256, 32, 16, 3300, 14, snr_db=15.0, bits=6, seed=7, corr_r=0.7)
+    idx = np.random.default_rng(6).choice(3300, 24, replace=False)
+    for arch in (0, 1):
+        g = _gpu(ff, p, arch, 0, llr_bits=6)
+        _check(g, _oracle(p, arch, 0, idx=idx), p, 6, idx=idx)
+        assert np.isfinite(g["z"]).all()
