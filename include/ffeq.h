@@ -148,6 +148,22 @@ ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const 
                                float* llr_host, int* info_host,
                                void* staging, size_t staging_bytes, void* stream);
 
+/* Equalize without any device allocation (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory, such as a real-time
+ * receive chain that must stay out of the CUDA allocator on its per-slot path,
+ * or a plug-in that owns no device memory besides the buffers it is given).
+ * Same computation and arguments as ffeq_equalize, minus the workspace: it
+ * uses a 64 MiB array compiled into the library, one per device, which every
+ * GPU that loads the library holds until the process exits.  Problems whose
+ * ffeq_workspace_size exceeds 64 MiB return FFEQ_ERR_UNSUPPORTED.  The first
+ * call on a device looks up that device's array address (cudaGetSymbolAddress)
+ * and so must come before any stream capture on that device.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialized by the caller; nothing in it needs clearing between
+ * calls.  It calls no cudaMalloc, cudaFree or allocating library routine. */
+ffeq_status ffeq_equalize_noalloc(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es,
+                                  void* z, float* sigma2, float* llr, int* info, void* stream);
+
 /* Read (and, if clear != 0, reset) the device status word written by bounded
  * waits: FFEQ_OK or FFEQ_ERR_TIMEOUT.  Synchronous with respect to the device. */
 ffeq_status ffeq_device_status(int* code, int clear);

@@ -54,6 +54,7 @@ _SIGS = {
     "ffeq_fuse_equalize": ([_vp, _vp, _sz, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
     "ffeq_host_staging_size": ([_vp, ctypes.POINTER(_sz)], _i),
     "ffeq_equalize_host": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_equalize_noalloc": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
     "ffeq_device_status": ([ctypes.POINTER(_i), _i], _i),
 }
 
@@ -170,6 +171,17 @@ def ffeq_equalize_host(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=No
     _check("ffeq_equalize_host", lib().ffeq_equalize_host(
         plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
         _ptr(staging), staging_bytes, _stream(stream)))
+
+
+def ffeq_equalize_noalloc(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=None, info=None,
+                          stream=None) -> None:
+    """``ffeq_equalize`` for callers that cannot allocate device memory: no workspace
+    argument, the library's fixed 64 MiB per-device array is used instead (calls
+    must not overlap on the GPU; the first call on a device must precede any
+    stream capture)."""
+    _check("ffeq_equalize_noalloc", lib().ffeq_equalize_noalloc(
+        plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
+        _stream(stream)))
 
 
 def ffeq_device_status(clear: bool = True) -> int:
