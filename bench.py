@@ -168,6 +168,8 @@ def main():
     ap.add_argument("--impl", default="ffeq", choices=["ffeq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"],
+                    help="arithmetic of the local preprocessing (solve and fusion are FP32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -204,7 +206,9 @@ def main():
     Hs = [H0] + [H0.clone() for _ in range(n_sets - 1)]
     ys = [y0] + [y0.clone() for _ in range(n_sets - 1)]
 
-    plans = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, llr_bits=bits) for a in (ffeq.PD, ffeq.FD)}
+    prec = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3}[args.precision]
+    plans = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=prec, llr_bits=bits)
+             for a in (ffeq.PD, ffeq.FD)}
     outs = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
                     s2=torch.empty((n_sc, U), dtype=torch.float32, device=dev),
                     llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32, device=dev))
@@ -295,7 +299,7 @@ def main():
     if dom.endswith("local"):
         alg = input_bytes(B, U, n_sc, n_sym)
         achieved = alg / (dom_ms * 1e-3) / 1e9
-        roof = {"kernel": f"gram_fp32_kernel ({dom[:2].upper()} local preprocessing)", "bound": "hbm",
+        roof = {"kernel": f"gram_kernel<{args.precision}> ({dom[:2].upper()} local preprocessing)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg}
     else:
@@ -308,9 +312,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": value / PAPER_SYMBOLS_PER_S, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": value / PAPER_SYMBOLS_PER_S,
+        "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32"}[args.precision], "data": "synthetic",
         "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD, LLRs",
-                   "precision": "fp32", "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
+                   "precision": args.precision, "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
                    "parallelism": f"replicas x{world}"},
         "kernels_ms": kern,
         "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / ((kern["pd_local"] + kern["pd_fuse"]) * 1e-3),

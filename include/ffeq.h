@@ -75,7 +75,14 @@ typedef enum {
 } ffeq_status;
 
 typedef enum { FFEQ_PD = 0, FFEQ_FD = 1 } ffeq_arch;
-typedef enum { FFEQ_FP32 = 0 } ffeq_precision;
+/* Arithmetic of the local preprocessing (G_c, y_c^MRC); the solve and fusion
+ * are FP32 in every mode.
+ *   FFEQ_FP32    FP32 on the CUDA cores.
+ *   FFEQ_TF32X3  tensor cores, each FP32 operand split into TF32 hi + lo, three
+ *                products accumulated in FP32 (about FP32 accuracy).
+ *   FFEQ_BF16X3  tensor cores, BF16 hi + lo split, three products, FP32
+ *                accumulation (mixed precision: ~16 significand bits per operand). */
+typedef enum { FFEQ_FP32 = 0, FFEQ_TF32X3 = 1, FFEQ_BF16X3 = 2 } ffeq_precision;
 typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
 
 /* Problem statement (Sec. II-A, II-B, VI): B antennas, U users, C clusters,
@@ -92,10 +99,11 @@ typedef struct {
 typedef struct ffeq_plan ffeq_plan;
 
 /* Validate *p and create a plan (host memory only; no device allocation).
- * Limits of this build: 1 <= U <= 32, 1 <= n_sym <= 16, B % C == 0, the
+ * Limits of this build: 1 <= U <= 32, 1 <= n_sym <= 16, B % C == 0, one
  * staged subcarrier (U + n_sym) * (B + 2) * 8 bytes (plus split-K partials
- * when the clusters are fewer than 8) must fit in 200 KiB, and the C local
- * systems of one FD subcarrier must fit one CTA (C * U padded <= 512).
+ * when fewer than 8 clusters are kept apart) must fit in 227 KiB of shared
+ * memory, and the C local systems of one FD subcarrier must fit one CTA
+ * (C * U padded <= 512).
  * Returns FFEQ_ERR_INVALID_ARG or FFEQ_ERR_UNSUPPORTED otherwise. */
 ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p);
 

@@ -23,7 +23,6 @@ ffeq_status cuda_fail(cudaError_t e) {
   return FFEQ_ERR_CUDA;
 }
 
-constexpr size_t kSmemLimit = 200 * 1024;
 constexpr size_t kSolveSmemLimit = 227 * 1024;
 constexpr size_t kAlign = 256;
 
@@ -72,15 +71,17 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (p->B <= 0 || p->U <= 0 || p->C <= 0 || p->n_sc < 0 || p->n_sym <= 0) return FFEQ_ERR_INVALID_ARG;
   if (p->B % p->C != 0) return FFEQ_ERR_INVALID_ARG;
   if (p->arch != FFEQ_PD && p->arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
-  if (p->precision != FFEQ_FP32) return FFEQ_ERR_INVALID_ARG;
+  if (p->precision != FFEQ_FP32 && p->precision != FFEQ_TF32X3 && p->precision != FFEQ_BF16X3)
+    return FFEQ_ERR_INVALID_ARG;
   if (p->estimate != FFEQ_UNBIASED && p->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
   if (p->llr_bits != 0 && p->llr_bits != 2 && p->llr_bits != 4 && p->llr_bits != 6 && p->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
   if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
-  if (ffeq::gram_fp32_smem_bytes(p->B, p->U, p->n_sym, Ceff) > kSmemLimit) return FFEQ_ERR_UNSUPPORTED;
+  if (ffeq::gram_stages(p->precision, p->B, p->U, p->n_sym, Ceff, false) < 1) return FFEQ_ERR_UNSUPPORTED;
   const int spc = ffeq::solve_subcarriers_per_cta(p->U, Ceff);
-  if (spc * Ceff * ffeq::padded_users(p->U) > 512 || ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
+  if (spc * Ceff * ffeq::padded_users(p->U) * (Ceff == 1 && ffeq::padded_users(p->U) == 16 ? 2 : 1) > 512 ||
+      ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
   ffeq_plan* plan = new (std::nothrow) ffeq_plan;
   if (!plan) return FFEQ_ERR_INVALID_ARG;
@@ -123,7 +124,9 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.n_sc = p.n_sc;
   gp.n_sym = p.n_sym;
   gp.bulk = (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
-  const cudaError_t e = ffeq::launch_gram_fp32(gp, st);
+  gp.stages = ffeq::gram_stages(p.precision, p.B, p.U, p.n_sym, plan->Ceff, gp.bulk != 0);
+  const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
+                                                 : ffeq::launch_gram_tc(gp, p.precision, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
 }
 

@@ -107,11 +107,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // Wait for phase `parity` of `bar` with an iteration limit.  On time-out the
 // device status word gets `code` and false is returned; callers then leave
 // without touching the staged data.
-constexpr long kWaitLimit = 1L << 24;
+// Each try_wait suspends the thread for a bounded, hardware-defined time, so the
+// loop spins without sleeping; after kWaitLimit attempts (seconds) it gives up.
+constexpr long kWaitLimit = 1L << 26;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code) {
   for (long it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it > 32) __nanosleep(128);
   }
   if (status) atomicExch(status, code);
   return false;

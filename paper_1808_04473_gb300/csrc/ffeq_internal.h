@@ -19,6 +19,7 @@ struct GramParams {
   int* status;        // device status word
   int B, U, Ceff, n_sc, n_sym;
   int bulk;           // 1: stage rows with cp.async.bulk (16-byte aligned rows)
+  int stages;         // subcarriers staged ahead (1 without bulk copies)
 };
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
@@ -38,8 +39,13 @@ struct SolveParams {
 
 // Padded user count (8, 16 or 32) used for register tiles.
 int padded_users(int U);
-size_t gram_fp32_smem_bytes(int B, int U, int n_sym, int Ceff);
+// Subcarriers the contraction kernel of `precision` can stage ahead (0: one
+// subcarrier does not fit in shared memory).
+int gram_stages(int precision, int B, int U, int n_sym, int Ceff, bool bulk);
+int gram_tc_stages(int B, int U, int n_sym, int Ceff, bool bulk);
 cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream);
+// Tensor-core split-precision contraction (precision FFEQ_TF32X3 or FFEQ_BF16X3).
+cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream);
 int solve_subcarriers_per_cta(int U, int Ceff);
 size_t solve_smem_bytes(int U, int Ceff);
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream);

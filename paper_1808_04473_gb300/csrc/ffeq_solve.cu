@@ -2,12 +2,19 @@
 //
 // Input: the workspace written by the contraction kernel, one matrix
 // D = [G ; (y^MRC)^T] of (U + n_sym) x U complex per (subcarrier, cluster):
-// G[u][v] = D[v][u], y^MRC_u(n) = D[U+n][u].  One group of UP lanes (UP = U
-// padded to 8/16/32; lane i = user i) equalizes one matrix:
-//   * Cholesky G + rho I = L L^H in registers (rho = N0/Es, Sec. III-A);
-//   * column i of L^{-1} by right-looking substitution; A_ii = ||L^{-1} e_i||^2
-//     is the i-th diagonal entry of A = (G + rho I)^{-1};
-//   * z = A y^MRC = L^{-H} (L^{-1} y^MRC) for all n_sym right-hand sides.
+// G[u][v] = D[v][u], y^MRC_u(n) = D[U+n][u].  Column i of D is therefore row i of
+// the augmented system [G + rho I | y^MRC] (rho = N0/Es, Sec. III-A), up to the
+// added rho.  One group of UP lanes (UP = U padded to 8/16/32; lane i = user i)
+// keeps its row in registers and runs a Gauss-Jordan sweep: at step k the pivot
+// row is scaled by 1/p_k, broadcast through shared memory, and eliminated from
+// every other row, while the pivot column is replaced by the inverse.  After U
+// steps the left block holds A = (G + rho I)^{-1} and the right block holds
+// z = A y^MRC for all n_sym right-hand sides.  The pivots p_k are the Schur
+// complements of the Hermitian positive definite matrix, i.e. the squared
+// diagonal of its Cholesky factor: a pivot that is not positive marks a failed
+// factorization at the same index k.  Every lane does the same (U + n_sym)
+// complex updates per step (no triangular idle lanes).
+//
 // A CTA holds the C clusters of one subcarrier (FD) or several subcarriers (PD)
 // and fuses per user with the optimal weights (Eq. fusionrule, Lemma 1):
 //     z_u = sum_c (z_{c,u}/A_{c,uu}) / sum_c (g_{c,u}/A_{c,uu}),
@@ -26,54 +33,69 @@ namespace {
 
 template <int UP>
 struct SolveLayout {
-  // Per matrix: L / L^{-1} (UP x (UP+1)), right-hand sides (UP x kNsymMax),
-  // fusion denominators (UP); padded so matrices start 64 bytes apart mod 128.
-  static constexpr int kL = UP * (UP + 1);
-  static constexpr int kB = UP * kNsymMax;
-  static constexpr int kMat = ((kL + kB + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
+  // Per matrix: pivot-row broadcast buffer (UP + kNsymMax complex), fusion
+  // numerators [kNsymMax][UP] complex and denominators [UP] floats; padded so
+  // consecutive matrices start 64 bytes apart modulo 128.
+  static constexpr int kRow = UP + kNsymMax;
+  static constexpr int kNum = kNsymMax * UP;
+  static constexpr int kMat = ((kRow + kNum + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
 };
 
-__device__ __forceinline__ float2 shfl2w(float2 v, int src, int width) {
-  return make_float2(__shfl_sync(kFullMask, v.x, src, width), __shfl_sync(kFullMask, v.y, src, width));
-}
-
-// Max-log LLRs of one Gray-labelled PAM axis (labels and sign as in ffeq.h).
-__device__ __forceinline__ void axis_llr(float x, float s2, float scale, int h, float* out) {
-  const int L = 1 << h;
-  float m0[4], m1[4];
+// Max-log LLRs of one Gray-labelled PAM axis with H bits (labels and sign as in
+// ffeq.h): for each bit, the squared distance to the nearest level carrying a 1
+// minus that to the nearest level carrying a 0, over sigma^2.
+template <int H>
+__device__ __forceinline__ void axis_llr(float x, float s2, float scale, float* out) {
+  constexpr int L = 1 << H;
+  float m0[H], m1[H];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) m0[t] = m1[t] = INFINITY;
+  for (int t = 0; t < H; ++t) m0[t] = m1[t] = INFINITY;
+#pragma unroll
   for (int l = 0; l < L; ++l) {
-    const float a = scale * static_cast<float>(2 * l - (L - 1));
-    const float d = (x - a) * (x - a);
+    const float e = x - scale * static_cast<float>(2 * l - (L - 1));
+    const float d = e * e;
     const int g = l ^ (l >> 1);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (t < h) {
-        if ((g >> (h - 1 - t)) & 1) m1[t] = fminf(m1[t], d);
-        else m0[t] = fminf(m0[t], d);
-      }
+    for (int t = 0; t < H; ++t) {
+      if ((g >> (H - 1 - t)) & 1) m1[t] = fminf(m1[t], d);
+      else m0[t] = fminf(m0[t], d);
     }
   }
   const bool s2inf = isinf(s2);
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    if (t < h) {
-      const float diff = m1[t] - m0[t];
-      float v = diff / s2;
-      if (s2inf || (s2 == 0.f && diff == 0.f)) v = 0.f;
-      out[t] = v;
-    }
+  for (int t = 0; t < H; ++t) {
+    const float diff = m1[t] - m0[t];
+    float v = diff / s2;
+    if (s2inf || (s2 == 0.f && diff == 0.f)) v = 0.f;
+    out[t] = v;
   }
 }
 
-template <int UP>
+__device__ __forceinline__ void symbol_llr(float2 z, float s2, float scale, int h, float* out) {
+  switch (h) {
+    case 1: axis_llr<1>(z.x, s2, scale, out); axis_llr<1>(z.y, s2, scale, out + 1); break;
+    case 2: axis_llr<2>(z.x, s2, scale, out); axis_llr<2>(z.y, s2, scale, out + 2); break;
+    case 3: axis_llr<3>(z.x, s2, scale, out); axis_llr<3>(z.y, s2, scale, out + 3); break;
+    default: axis_llr<4>(z.x, s2, scale, out); axis_llr<4>(z.y, s2, scale, out + 4); break;
+  }
+}
+
+// LPR lanes per row: with LPR = 2 the two lanes of row i hold halves of its
+// augmented row (columns [0, W/2) and [W/2, W)), halving the work per lane and
+// step; the pivot column k < UP always lies in the first half.
+template <int UP, int LPR>
 __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   using Lay = SolveLayout<UP>;
+  constexpr int GS = UP * LPR;                // lanes per matrix
+  constexpr int W = UP + kNsymMax;            // augmented row width (RHS columns beyond n_sym unused)
+  constexpr int WH = W / LPR;                 // columns per lane
+  static_assert(UP <= WH, "pivot columns must lie in the first half of a row");
   const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, spc = p.spc;
   const int nmat = spc * Ceff;
-  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int g = threadIdx.x / GS, gl = threadIdx.x % GS;
+  const int i = gl % UP;
+  const int h = LPR == 1 ? 0 : gl / UP;        // which half of the row this lane holds
   int* fail_sc = reinterpret_cast<int*>(smem);                       // [spc]
   float2* base = reinterpret_cast<float2*>(smem + 256);
   const int sc0 = blockIdx.x * spc;
@@ -85,132 +107,140 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   const int scl = gm / Ceff, c = gm % Ceff;
   const int sc = sc0 + scl;
   const bool valid = g < nmat && sc < p.n_sc;
-  float2* Ls = base + gm * Lay::kMat;
-  float2* Bs = Ls + Lay::kL;
-  float* Dn = reinterpret_cast<float*>(Bs + Lay::kB);
+  float2* rowbuf = base + gm * Lay::kMat;
+  float2* Fz = rowbuf + Lay::kRow;
+  float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
   const size_t matSize = static_cast<size_t>(U + NS) * U;
   const float2* Dg = p.D + (static_cast<size_t>(valid ? sc : 0) * Ceff + c) * matSize;
 
   // Wait for the contraction grid (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
-  // ---- load row i of M = G + rho I and the right-hand sides b[i][n]
-  float2 a[UP];
+  // ---- this lane's columns of row i of [G + rho I | y^MRC] (padding: identity, zero RHS)
+  // Loads are unconditional (clamped to valid addresses) so they all issue before
+  // the first use; padding values are selected afterwards.
+  float2 aug[WH];
+  const int ic = i < U ? i : 0;
+#pragma unroll
+  for (int j = 0; j < WH; ++j) {
+    const int col = h * WH + j;
+    const int row = col < UP ? (col < U ? col : 0) : (col - UP < NS ? U + col - UP : 0);
+    aug[j] = Dg[row * U + ic];
+  }
   float gii = 1.f;
 #pragma unroll
-  for (int j = 0; j < UP; ++j) {
-    float2 v = make_float2(i == j ? 1.f : 0.f, 0.f);
-    if (valid && i < U && j < U) {
-      v = Dg[j * U + i];
-      if (i == j) {
-        gii = v.x;
-        v = make_float2(v.x + p.rho, 0.f);
-      }
+  for (int j = 0; j < WH; ++j) {
+    const int col = h * WH + j;
+    const bool real = valid && i < U && (col < UP ? col < U : col - UP < NS);
+    float2 v = real ? aug[j] : make_float2(col == i ? 1.f : 0.f, 0.f);
+    if (col == i && real) {
+      gii = v.x;
+      v = make_float2(v.x + p.rho, 0.f);
     }
-    a[j] = v;
-  }
-  if (g < nmat) {
-#pragma unroll
-    for (int n = 0; n < kNsymMax; ++n)
-      if (n < NS) Bs[i * kNsymMax + n] = (valid && i < U) ? Dg[(U + n) * U + i] : make_float2(0.f, 0.f);
+    aug[j] = v;
   }
 
-  // ---- Cholesky: lane i keeps row i of L in a[0..i]
+  // ---- Gauss-Jordan sweep
   int fail = 0;
+  if constexpr (LPR == 1) {
+    // Column-rotating form: every step shifts the row left by one, so the pivot
+    // column is always aug[0] and the new inverse column is appended at aug[W-1].
+    // All register indices are compile-time constants while k stays a runtime
+    // loop (one step of code).  After UP steps: aug[0..kNsymMax) = z (RHS block),
+    // aug[kNsymMax + j] = A[i][j].
+#pragma unroll 1
+    for (int k = 0; k < UP; ++k) {
+      const float piv = __shfl_sync(kFullMask, aug[0].x, k, GS);
+      const bool ok = piv > 0.f;
+      if (!ok && fail == 0) fail = k + 1;
+      const float r = 1.f / (ok ? piv : 1.f);
+      if (i == k && g < nmat) {
+        // Scaled pivot row in the rotated layout: [aug[1..W-1] * r, r].
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+          const float2 v0 = j + 1 < W ? cscale(aug[j + 1], r) : make_float2(r, 0.f);
+          const float2 v1 = j + 2 < W ? cscale(aug[j + 2], r) : make_float2(r, 0.f);
+          *reinterpret_cast<float4*>(rowbuf + j) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        }
+      }
+      __syncwarp();
+      const float2 f = aug[0];
+      if (i == k) {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+          const float4 q = *reinterpret_cast<const float4*>(rowbuf + j);
+          aug[j] = make_float2(q.x, q.y);
+          aug[j + 1] = make_float2(q.z, q.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+          const float4 q = *reinterpret_cast<const float4*>(rowbuf + j);
+          aug[j] = j + 1 < W ? cfms(f, make_float2(q.x, q.y), aug[j + 1]) : make_float2(-f.x * r, -f.y * r);
+          aug[j + 1] = j + 2 < W ? cfms(f, make_float2(q.z, q.w), aug[j + 2]) : make_float2(-f.x * r, -f.y * r);
+        }
+      }
+      __syncwarp();
+    }
+  } else {
   static_for<UP>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    const float piv = __shfl_sync(kFullMask, a[k].x, k, UP);
+    const float piv = __shfl_sync(kFullMask, aug[k].x, k, GS);
+    const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
     const bool ok = piv > 0.f;
     if (!ok && fail == 0) fail = k + 1;
-    const float d = sqrtf(ok ? piv : 1.f);
-    const float inv = 1.f / d;
-    if (i == k) a[k] = make_float2(d, 0.f);
-    else if (i > k) a[k] = cscale(a[k], inv);
+    const float r = 1.f / (ok ? piv : 1.f);
+    if (i == k) {
 #pragma unroll
-    for (int j = k + 1; j < UP; ++j) {
-      const float2 ljk = shfl2w(a[k], j, UP);
-      if (i >= j) a[j] = cfms_bconj(a[k], ljk, a[j]);
-    }
-  });
-  if (g < nmat) {
+      for (int j = 0; j < WH; ++j) aug[j] = (h == 0 && j == k) ? make_float2(r, 0.f) : cscale(aug[j], r);
+      if (g < nmat) {
 #pragma unroll
-    for (int j = 0; j < UP; ++j)
-      if (j <= i) Ls[i * (UP + 1) + j] = a[j];
-  }
-  __syncwarp();
-
-  // ---- column i of L^{-1} (right-looking forward substitution on e_i)
-  float2 x[UP];
-#pragma unroll
-  for (int r = 0; r < UP; ++r) x[r] = make_float2(r == i ? 1.f : 0.f, 0.f);
-  static_for<UP>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    const float inv = 1.f / Ls[k * (UP + 1) + k].x;
-    x[k] = cscale(x[k], inv);
-#pragma unroll
-    for (int r = k + 1; r < UP; ++r) x[r] = cfms(Ls[r * (UP + 1) + k], x[k], x[r]);
-  });
-  float Aii = 0.f;
-#pragma unroll
-  for (int r = 0; r < UP; ++r) Aii += cabs2(x[r]);
-  __syncwarp();
-  // L^{-1} row-major into Ls (lane i writes column i).
-  if (g < nmat) {
-#pragma unroll
-    for (int r = 0; r < UP; ++r) Ls[r * (UP + 1) + i] = x[r];
-  }
-  __syncwarp();
-
-  // ---- w = L^{-1} b (lane i: row i), then z = L^{-H} w
-  float2 acc[kNsymMax];
-#pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) acc[n] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < UP; ++j) {
-    const float2 l = Ls[i * (UP + 1) + j];
-#pragma unroll
-    for (int n = 0; n < kNsymMax; n += 2) {
-      if (n < NS) {
-        const float4 bb = *reinterpret_cast<const float4*>(Bs + j * kNsymMax + n);
-        acc[n] = cfma(l, make_float2(bb.x, bb.y), acc[n]);
-        acc[n + 1] = cfma(l, make_float2(bb.z, bb.w), acc[n + 1]);
+        for (int j = 0; j < WH; j += 2)
+          if (h * WH + j < UP + NS)
+            *reinterpret_cast<float4*>(rowbuf + h * WH + j) =
+                make_float4(aug[j].x, aug[j].y, aug[j + 1].x, aug[j + 1].y);
       }
     }
-  }
-  __syncwarp();
-  if (g < nmat) {
+    __syncwarp();
+    if (i != k) {
+      const float2* rb = rowbuf + h * WH;
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n)
-      if (n < NS) Bs[i * kNsymMax + n] = acc[n];
-  }
-  __syncwarp();
-#pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) acc[n] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < UP; ++k) {
-    const float2 l = x[k];
-#pragma unroll
-    for (int n = 0; n < kNsymMax; n += 2) {
-      if (n < NS) {
-        const float4 ww = *reinterpret_cast<const float4*>(Bs + k * kNsymMax + n);
-        acc[n] = cfma_conj(l, make_float2(ww.x, ww.y), acc[n]);
-        acc[n + 1] = cfma_conj(l, make_float2(ww.z, ww.w), acc[n + 1]);
+      for (int j = 0; j < WH; j += 2) {
+        if (h * WH + j < UP + NS) {
+          const float4 q = *reinterpret_cast<const float4*>(rb + j);
+          aug[j] = (h == 0 && j == k) ? make_float2(-f.x * r, -f.y * r) : cfms(f, make_float2(q.x, q.y), aug[j]);
+          aug[j + 1] = (h == 0 && j + 1 == k) ? make_float2(-f.x * r, -f.y * r)
+                                              : cfms(f, make_float2(q.z, q.w), aug[j + 1]);
+        }
       }
     }
+    __syncwarp();
+  });
+
   }
 
-  // ---- fusion terms of this matrix
-  const float invA = 1.f / Aii;
+  // ---- fusion terms of this matrix: A_ii on the first-half lane of row i
+  // (column i before rotation; column kNsymMax + i after the rotating sweep)
+  constexpr int kA = LPR == 1 ? kNsymMax : 0;   // first column of A in this lane's registers
+  constexpr int kZ = LPR == 1 ? 0 : UP;         // first RHS column (global column index)
+  float Ai = 1.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j)
+    if (j == i) Ai = aug[kA + j].x;
+  Ai = __shfl_sync(kFullMask, Ai, i, GS);
+  const float invA = 1.f / Ai;
   // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
   // mu = 0 exactly, which the subtraction would only reach up to rounding.
-  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - p.rho * Aii, 0.f);
-  __syncwarp();
+  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - p.rho * Ai, 0.f);
   if (g < nmat) {
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n)
-      if (n < NS) Bs[i * kNsymMax + n] = cscale(acc[n], invA);
-    Dn[i] = (p.unbiased ? mu : 1.f) * invA;
-    if (i == 0 && valid) {
+    for (int j = 0; j < WH; ++j) {
+      const int n = h * WH + j - kZ;
+      if (n >= 0 && n < NS && (LPR != 1 || j < kNsymMax))
+        Fz[n * UP + i] = cscale(aug[j], invA);   // [n][u]: the epilogue reads along u
+    }
+    if (h == 0) Dn[i] = (p.unbiased ? mu : 1.f) * invA;
+    if (gl == 0 && valid) {
       if (p.info) p.info[static_cast<size_t>(sc) * Ceff + c] = fail;
       if (fail) atomicOr(&fail_sc[scl], 1);
     }
@@ -219,7 +249,7 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
 
   // ---- per subcarrier: sum over clusters, outputs
   const int per = U * NS;
-  const int bits = p.llr_bits, h = bits / 2;
+  const int bits = p.llr_bits, hb = bits / 2;
   for (int e = threadIdx.x; e < spc * per; e += blockDim.x) {
     const int s = e / per, r = e - s * per;
     const int n = r / U, u = r - n * U;
@@ -228,9 +258,9 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     float2 nm = make_float2(0.f, 0.f);
     float dn = 0.f;
     for (int cc = 0; cc < Ceff; ++cc) {
-      const float2* Lm = base + (s * Ceff + cc) * Lay::kMat;
-      nm = cadd(nm, (Lm + Lay::kL)[u * kNsymMax + n]);
-      dn += reinterpret_cast<const float*>(Lm + Lay::kL + Lay::kB)[u];
+      const float2* Lm = base + (s * Ceff + cc) * Lay::kMat + Lay::kRow;
+      nm = cadd(nm, Lm[n * UP + u]);
+      dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
     }
     float2 zz;
     float s2;
@@ -248,26 +278,22 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     const size_t zi = (static_cast<size_t>(k) * NS + n) * U + u;
     p.z[zi] = zz;
     if (n == 0) p.sigma2[static_cast<size_t>(k) * U + u] = s2;
-    if (bits) {
-      float* out = p.llr + zi * bits;
-      axis_llr(zz.x, s2, p.llr_scale, h, out);
-      axis_llr(zz.y, s2, p.llr_scale, h, out + h);
-    }
+    if (bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * bits);
   }
 }
 
-template <int UP>
+template <int UP, int LPR>
 cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   using Lay = SolveLayout<UP>;
   const int nmat = p.spc * p.Ceff;
-  const int threads = ((nmat * UP + 31) / 32) * 32;
+  const int threads = ((nmat * UP * LPR + 31) / 32) * 32;
   const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
   static int configured[64] = {0};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(solve_fuse_kernel<UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    err = cudaFuncSetAttribute(solve_fuse_kernel<UP, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
@@ -281,13 +307,19 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP>, p);
+  return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP, LPR>, p);
 }
 
 }  // namespace
 
+// PD (one system per subcarrier) with U <= 16: a full warp per system (two
+// lanes per row) and 4 subcarriers per CTA, for more warps in flight; FD: the C
+// systems of one subcarrier in one CTA, UP lanes each.
+static int lanes_per_row(int U, int Ceff) { return (Ceff == 1 && padded_users(U) == 16) ? 2 : 1; }
+
 int solve_subcarriers_per_cta(int U, int Ceff) {
-  return Ceff == 1 ? (padded_users(U) >= 32 ? 4 : 128 / padded_users(U)) : 1;
+  if (Ceff != 1) return 1;
+  return 128 / (padded_users(U) * lanes_per_row(U, Ceff));
 }
 
 size_t solve_smem_bytes(int U, int Ceff) {
@@ -304,9 +336,9 @@ size_t solve_smem_bytes(int U, int Ceff) {
 
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream) {
   switch (padded_users(p.U)) {
-    case 8: return launch_up<8>(p, stream);
-    case 16: return launch_up<16>(p, stream);
-    default: return launch_up<32>(p, stream);
+    case 8: return launch_up<8, 1>(p, stream);
+    case 16: return lanes_per_row(p.U, p.Ceff) == 2 ? launch_up<16, 2>(p, stream) : launch_up<16, 1>(p, stream);
+    default: return launch_up<32, 1>(p, stream);
   }
 }
 

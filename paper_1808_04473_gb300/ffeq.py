@@ -15,7 +15,7 @@ import os
 import re
 
 PD, FD = 0, 1
-FP32 = 0
+FP32, TF32X3, BF16X3 = 0, 1, 2
 UNBIASED, LITERAL = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -197,7 +197,7 @@ def ffeq_status_string(status: int) -> str:
 # --------------------------------------------------------------------- convenience
 
 def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int = UNBIASED, llr_bits: int = 0,
-             with_info: bool = False, stream=None) -> dict:
+             with_info: bool = False, stream=None, precision: int = FP32) -> dict:
     """Allocate outputs on ``H.device`` and run one equalization (returns torch tensors)."""
     import torch
     if H.dtype != torch.complex64 or y.dtype != torch.complex64:
@@ -208,7 +208,7 @@ def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int =
     n_sym = y.shape[1]
     if tuple(y.shape) != (n_sc, n_sym, B):
         raise ValueError("y must be [n_sc][n_sym][B]")
-    plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, FP32, estimate, llr_bits)
+    plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits)
     dev = H.device
     out = {"z": torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
            "sigma2": torch.empty((n_sc, U), dtype=torch.float32, device=dev)}
