@@ -47,14 +47,38 @@ def _peaks():
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def _source_digest():
+    """Digest of the CUDA sources: DRAM counters taken from another build are stale."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1808_04473_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """Per-launch DRAM bytes (read + write) from the committed ncu summary, if it
+    was taken on the current sources; otherwise {} (the JSON reports null)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return {}
+    return d.get("kernels", {}) if d.get("source_digest") == _source_digest() else {}
+
+
 def input_bytes(B, U, n_sc, n_sym):
     """HBM bytes the local preprocessing must read: H and y (complex64)."""
     return n_sc * 8 * (B * U + B * n_sym)
 
 
 def solve_flops(U, n_sym, C):
-    """Real flops of one subcarrier's solve stage: per system Cholesky 4U^3/3,
-    L^{-1} 4U^3/3, two triangular products with n_sym right-hand sides 8U^2 n_sym."""
+    """Algorithmic real flops of one subcarrier's solve stage (independent of the
+    method used): per system a Cholesky factorization 4U^3/3, the diagonal of the
+    inverse 4U^3/3 and two triangular solves with n_sym right-hand sides 8U^2 n_sym."""
     return C * (8.0 * U ** 3 / 3.0 + 8.0 * U * U * n_sym)
 
 
@@ -74,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -163,12 +187,12 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ffeq", choices=["ffeq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"],
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"],
                     help="arithmetic of the local preprocessing (solve and fusion are FP32)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -206,60 +230,77 @@ def main():
     Hs = [H0] + [H0.clone() for _ in range(n_sets - 1)]
     ys = [y0] + [y0.clone() for _ in range(n_sets - 1)]
 
-    prec = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3}[args.precision]
-    plans = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=prec, llr_bits=bits)
-             for a in (ffeq.PD, ffeq.FD)}
+    PREC = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3}
     outs = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
                     s2=torch.empty((n_sc, U), dtype=torch.float32, device=dev),
                     llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32, device=dev))
-            for a in plans}
-    ws_bytes = {a: ffeq.ffeq_workspace_size(pl) for a, pl in plans.items()}
-    ws = {a: torch.empty(ws_bytes[a], dtype=torch.uint8, device=dev) for a in plans}
+            for a in (ffeq.PD, ffeq.FD)}
     stream = torch.cuda.current_stream(dev)
 
-    # One step: for PD then FD, the local preprocessing kernel and the fusion /
-    # equalization kernel, each bracketed by CUDA events on the launching stream.
-    def step(i, evs=None):
-        for a in (ffeq.PD, ffeq.FD):
-            o = outs[a]
-            if evs is not None:
-                evs[2 * a].record(stream)
-            ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], stream)
-            if evs is not None:
-                evs[2 * a + 1].record(stream)
-            ffeq.ffeq_fuse_equalize(plans[a], ws[a], ws_bytes[a], p.N0, p.Es, o["z"], o["s2"], o["llr"], None,
-                                    stream)
-        if evs is not None:
-            evs[4].record(stream)
+    def make_plans(precision):
+        pl = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=PREC[precision], llr_bits=bits)
+              for a in (ffeq.PD, ffeq.FD)}
+        nb = {a: ffeq.ffeq_workspace_size(x) for a, x in pl.items()}
+        return pl, nb, {a: torch.empty(nb[a], dtype=torch.uint8, device=dev) for a in pl}
 
-    for i in range(args.warmup):
-        step(i % n_sets)
-    torch.cuda.synchronize()
+    def timed(precision, K, warmup, sampler=None):
+        """K steps; one step = for PD then FD, the local preprocessing kernel and the
+        fusion / equalization kernel, each bracketed by CUDA events on the launching stream."""
+        plans, ws_bytes, ws = make_plans(precision)
 
-    K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
+        def step(i, evs=None):
+            for a in (ffeq.PD, ffeq.FD):
+                o = outs[a]
+                if evs is not None:
+                    evs[2 * a].record(stream)
+                ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], stream)
+                if evs is not None:
+                    evs[2 * a + 1].record(stream)
+                ffeq.ffeq_fuse_equalize(plans[a], ws[a], ws_bytes[a], p.N0, p.Es, o["z"], o["s2"], o["llr"],
+                                        None, stream)
+            if evs is not None:
+                evs[4].record(stream)
+
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler is not None:          # clocks: sampled from the warm-up through the timed region
+            sampler.__enter__()
+        for i in range(warmup):
+            step(i % n_sets)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         start.record(stream)
         for k in range(K):
             step(k % n_sets, ev[k])
         end.record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    elapsed_ms = start.elapsed_time(end)
-    kern = {name: statistics.mean(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K))
-            for j, name in enumerate(["pd_local", "pd_fuse", "fd_local", "fd_fuse"])}
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    assert ffeq.ffeq_device_status() == 0
-    for a in plans:
-        assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
+        if sampler is not None:
+            sampler.__exit__(None, None, None)
+        if world > 1:
+            dist.barrier()
+        ms = start.elapsed_time(end)
+        kern = {name: statistics.mean(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K))
+                for j, name in enumerate(["pd_local", "pd_fuse", "fd_local", "fd_fuse"])}
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        assert ffeq.ffeq_device_status() == 0
+        for a in outs:
+            assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
+        return ms, kern, plans
+
+    K = args.steps
+    clk = ClockSampler(local_rank)
+    elapsed_ms, kern, plans = timed(args.precision, K, args.warmup, clk)
+    fp32_cmp = None
+    if args.precision != "fp32":
+        Kc = max(5, K // 4)
+        ms32, kern32, _ = timed("fp32", Kc, args.warmup)
+        fp32_cmp = {"value": world * 2 * U * n_sc * n_sym * Kc / (ms32 * 1e-3), "ms_per_step": ms32 / Kc,
+                    "steps": Kc, "kernels_ms": kern32}
 
     symbols_per_step = 2 * U * n_sc * n_sym
     value = world * symbols_per_step * K / (elapsed_ms * 1e-3)
@@ -292,23 +333,29 @@ def main():
     h2d = 2 * in_bytes
     d2h = 2 * (outs[0]["z"].numel() * 8 + outs[0]["s2"].numel() * 4 + outs[0]["llr"].numel() * 4)
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (and of the Gram stage)
     hbm_peak, peak_src = _peaks()
-    dom = max(kern, key=kern.get)
-    dom_ms = kern[dom]
-    if dom.endswith("local"):
+    traffic = _ncu_traffic()
+
+    def gram_roof(name):
         alg = input_bytes(B, U, n_sc, n_sym)
-        achieved = alg / (dom_ms * 1e-3) / 1e9
-        roof = {"kernel": f"gram_kernel<{args.precision}> ({dom[:2].upper()} local preprocessing)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg}
+        achieved = alg / (kern[name] * 1e-3) / 1e9
+        kname = f"gram_kernel<{args.precision}> ({name[:2].upper()} local preprocessing)"
+        return {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "peak_source": f"{peak_src} (STREAM-style copy)", "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic.get(f"{args.precision}:{name}"), "algorithmic_bytes_per_launch": alg,
+                "kernel_ms": kern[name]}
+
+    dom = max(kern, key=kern.get)
+    if dom.endswith("local"):
+        roof = gram_roof(dom)
     else:
         flops = solve_flops(U, n_sym, C if dom.startswith("fd") else 1) * n_sc
-        achieved = flops / (dom_ms * 1e-3) / 1e12
-        peak = FP32_ALU_TFLOPS
+        achieved = flops / (kern[dom] * 1e-3) / 1e12
         roof = {"kernel": f"solve_fuse_kernel ({dom[:2].upper()})", "bound": "alu", "achieved": achieved,
-                "peak": peak, "peak_source": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz", "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "algorithmic_flops_per_launch": flops}
+                "peak": FP32_ALU_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic.get(f"{args.precision}:{dom}"),
+                "algorithmic_flops_per_launch": flops, "kernel_ms": kern[dom]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -321,6 +368,8 @@ def main():
         "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / ((kern["pd_local"] + kern["pd_fuse"]) * 1e-3),
                                    "fd": U * n_sc * n_sym / ((kern["fd_local"] + kern["fd_fuse"]) * 1e-3)},
         "roofline": roof,
+        "roofline_gram_stage": {"pd": gram_roof("pd_local"), "fd": gram_roof("fd_local")},
+        "fp32_same_gpu": fp32_cmp,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * K,
     }
