@@ -10,6 +10,8 @@ Modules
             (Sec. II-B..D, Sec. III-A, Sec. IV-A, Lemma 1, Thm. 3).
 ``llr``     max-log soft outputs for square QAM (the paper names LLRs but gives
             no formula; the reading is stated in that module).
+``adjoint`` the differentiable FD form (per-cluster regularizers, free fusion
+            weights) and its closed-form gradients, checked by finite differences.
 ``theory``  large-system closed forms and fixed points (Thm. 1, Cor. 1,
             Lemma 2, Lemma 4, Lemma 5, Lemma 7) and the Sec. VI message sizes.
 
@@ -18,4 +20,4 @@ given (they are upcast once), loops over subcarriers in plain Python and uses
 library primitives (``numpy.linalg.inv``, matrix products) only as steps of the
 paper's definitions, so it can be checked against the paper by eye.
 """
-from . import llr, lmmse, theory  # noqa: F401
+from . import adjoint, llr, lmmse, theory  # noqa: F401

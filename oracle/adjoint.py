@@ -1,0 +1,101 @@
+"""FP64 oracle: differentiable FD equalization and its adjoint.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper fixes the FD architecture (Sec. II-D, Sec. IV-A) with the L-MMSE
+regularizer rho = N0/Es (Sec. III-A) and fusion weights from Lemma 1.  Its
+trainable form -- per-cluster regularizers ``rho_c`` and explicit real fusion
+weights ``nu[c][u]`` shared by all subcarriers, tuned on a loss -- is not in the
+paper; reading taken here:
+
+    x_c = (G_c + rho_c I)^{-1} H_c^H y_c          (local estimate, per symbol)
+    z_u = sum_c nu[c][u] x_{c,u}                   (Eq. fusionrule with free weights)
+
+Complex gradients follow the convention ``g = dL/dRe + i dL/dIm`` of a real loss
+``L``.  With ``M_c = G_c + rho_c I`` (Hermitian), ``G_x,c = diag(nu_c) G_z`` and
+``G_b,c = M_c^{-1} G_x,c`` (matrices over the n_sym right-hand sides):
+
+    dL/dH_c   = Y_c G_b^H - H_c (G_b X_c^H + X_c G_b^H)      (B_c x U)
+    dL/dy_c   = H_c G_b                                      (B_c x n_sym)
+    dL/drho_c = -Re tr(G_b^H X_c)                           (summed over subcarriers)
+    dL/dnu[c][u] = sum_n Re(conj(g_z,u,n) x_c,u,n)           (summed over subcarriers)
+
+(from dX = M^{-1}(dB - dM X), dM = dH^H H + H^H dH + drho I, dB = dH^H Y + H^H dY).
+``finite_difference`` checks them against the definition of the derivative.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .lmmse import partition
+
+__all__ = ["fd_train_forward", "fd_train_backward", "finite_difference"]
+
+
+def _blocks(H, y, k, bounds):
+    Hm = np.asarray(H[k], dtype=np.complex128).T          # B x U
+    Ym = np.asarray(y[k], dtype=np.complex128).T          # B x n_sym
+    return [(Hm[b0:b1], Ym[b0:b1]) for (b0, b1) in bounds]
+
+
+def fd_train_forward(H, y, rho, nu):
+    """Return ``z`` ``[n_sc][n_sym][U]`` and the local estimates ``x`` ``[n_sc][C][n_sym][U]``."""
+    n_sc, U, B = H.shape
+    n_sym = y.shape[1]
+    C = len(rho)
+    bounds = partition(B, C)
+    z = np.zeros((n_sc, n_sym, U), np.complex128)
+    xs = np.zeros((n_sc, C, n_sym, U), np.complex128)
+    for k in range(n_sc):
+        for c, (Hc, Yc) in enumerate(_blocks(H, y, k, bounds)):
+            M = Hc.conj().T @ Hc + rho[c] * np.eye(U)
+            X = np.linalg.solve(M, Hc.conj().T @ Yc)             # U x n_sym
+            xs[k, c] = X.T
+            z[k] += (nu[c][:, None] * X).T
+    return z, xs
+
+
+def fd_train_backward(H, y, rho, nu, gz):
+    """Gradients of a real loss with ``dL/dz = gz`` (``[n_sc][n_sym][U]``, dL/dRe + i dL/dIm).
+
+    Returns ``(gH [n_sc][U][B], gy [n_sc][n_sym][B], grho [C], gnu [C][U])``.
+    """
+    n_sc, U, B = H.shape
+    n_sym = y.shape[1]
+    C = len(rho)
+    bounds = partition(B, C)
+    gH = np.zeros((n_sc, U, B), np.complex128)
+    gy = np.zeros((n_sc, n_sym, B), np.complex128)
+    grho = np.zeros(C)
+    gnu = np.zeros((C, U))
+    for k in range(n_sc):
+        Gz = np.asarray(gz[k], dtype=np.complex128).T             # U x n_sym
+        for c, (Hc, Yc) in enumerate(_blocks(H, y, k, bounds)):
+            M = Hc.conj().T @ Hc + rho[c] * np.eye(U)
+            X = np.linalg.solve(M, Hc.conj().T @ Yc)
+            Gx = nu[c][:, None] * Gz
+            Gb = np.linalg.solve(M, Gx)                           # M Hermitian: M^{-H} = M^{-1}
+            b0, b1 = bounds[c]
+            gH[k, :, b0:b1] = (Yc @ Gb.conj().T - Hc @ (Gb @ X.conj().T + X @ Gb.conj().T)).T
+            gy[k, :, b0:b1] = (Hc @ Gb).T
+            grho[c] += -np.real(np.trace(Gb.conj().T @ X))
+            gnu[c] += np.real(np.sum(np.conj(Gz) * X, axis=1))
+    return gH, gy, grho, gnu
+
+
+def finite_difference(f, x: np.ndarray, eps: float = 1e-6) -> np.ndarray:
+    """Central differences of the real scalar ``f`` at ``x``: ``dL/dRe + i dL/dIm`` for complex ``x``."""
+    x = np.array(x, dtype=np.complex128 if np.iscomplexobj(x) else np.float64)
+    g = np.zeros_like(x)
+    flat = x.reshape(-1)
+    gf = g.reshape(-1)
+    for i in range(flat.size):
+        for unit in ((1.0, 1j) if np.iscomplexobj(x) else (1.0,)):
+            old = flat[i]
+            flat[i] = old + eps * unit
+            fp = f(x)
+            flat[i] = old - eps * unit
+            fm = f(x)
+            flat[i] = old
+            gf[i] += unit * (fp - fm) / (2 * eps)
+    return g
