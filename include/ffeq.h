@@ -143,6 +143,33 @@ ffeq_status ffeq_fuse_equalize(const ffeq_plan* plan, const void* workspace, siz
                                float N0, float Es, void* z, float* sigma2, float* llr, int* info,
                                void* stream);
 
+/* Differentiable FD equalization (the paper's FD architecture, Sec. II-D /
+ * IV-A, with its regularizer and fusion weights made free parameters):
+ *   X_c = (G_c + rho_c I)^{-1} H_c^H Y_c     (per cluster, L-MMSE form of Sec. III-A)
+ *   z_u = sum_c nu[c][u] X_c[u]              (Eq. fusionrule with free weights)
+ * rho_c: f32 [C] (> 0), nu: f32 [C][U], both on the device and shared by all
+ * subcarriers.  The plan must be FD.  The workspace (ffeq_fd_train_workspace_size
+ * bytes, 256-byte aligned, owned by the caller) carries the local Gram matrices
+ * and the local estimates from the forward call to the backward call; the
+ * backward call recomputes the factorizations from them.
+ * ffeq_fd_train_backward takes gz = dL/dRe z + i dL/dIm z of a real loss L
+ * (cf32 [n_sc][n_sym][U]) and writes dL/dH (cf32 [n_sc][U][B]), dL/dy
+ * (cf32 [n_sc][n_sym][B]) in the same convention, and dL/drho (f32 [C]) and
+ * dL/dnu (f32 [C][U]) summed over all subcarriers:
+ *   dL/dH_c = Y_c G_b^H - H_c (G_b X_c^H + X_c G_b^H),  dL/dY_c = H_c G_b,
+ *   dL/drho_c = -sum Re tr(G_b^H X_c),  dL/dnu[c][u] = sum Re(conj(gz_u) X_c,u),
+ *   G_b = (G_c + rho_c I)^{-1} diag(nu_c) gz.
+ * The same H, y, rho_c, nu and workspace must be passed to both calls, in order
+ * on one stream.  Outputs of a subcarrier whose system is not positive definite
+ * are NaN.  Limits: C * U padded <= 512. */
+ffeq_status ffeq_fd_train_workspace_size(const ffeq_plan* plan, size_t* bytes);
+ffeq_status ffeq_fd_train_forward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
+                                  const float* nu, void* z, void* workspace, size_t workspace_bytes,
+                                  void* stream);
+ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
+                                   const float* nu, const void* gz, void* gH, void* gy, float* grho,
+                                   float* gnu, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Device staging bytes ffeq_equalize_host needs (inputs, outputs and workspace). */
 ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes);
 

@@ -201,6 +201,96 @@ ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, f
   return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st);
 }
 
+namespace {
+
+struct TrainLayoutBytes {
+  size_t D, X, Gb, W, P, total;
+};
+
+TrainLayoutBytes train_layout(const ffeq_plan* plan) {
+  const ffeq_problem& p = plan->p;
+  const size_t nsc = static_cast<size_t>(p.n_sc), C = static_cast<size_t>(p.C);
+  TrainLayoutBytes t;
+  t.D = align_up(plan->workspace);
+  t.X = align_up(nsc * C * p.n_sym * p.U * 8);
+  t.Gb = t.X;
+  t.W = align_up(nsc * C * p.U * p.U * 8);
+  t.P = align_up(nsc * C * (1 + p.U) * 4);
+  t.total = t.D + t.X + t.Gb + t.W + t.P;
+  return t;
+}
+
+ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c, const float* nu,
+                         void* workspace, size_t workspace_bytes, ffeq::TrainParams& tp) {
+  if (!plan) return FFEQ_ERR_INVALID_ARG;
+  const ffeq_problem& p = plan->p;
+  if (p.arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
+  if (ffeq::padded_users(p.U) * p.C > 512 || ffeq::train_smem_bytes(p.U, p.C) > kSolveSmemLimit)
+    return FFEQ_ERR_UNSUPPORTED;
+  const TrainLayoutBytes t = train_layout(plan);
+  if (p.n_sc == 0) return FFEQ_OK;
+  if (!H || !y || !rho_c || !nu || !workspace || workspace_bytes < t.total) return FFEQ_ERR_INVALID_ARG;
+  if (!aligned(H, 8) || !aligned(y, 8) || !aligned(rho_c, 4) || !aligned(nu, 4) || !aligned(workspace, 256))
+    return FFEQ_ERR_INVALID_ARG;
+  char* base = static_cast<char*>(workspace);
+  tp = ffeq::TrainParams{};
+  tp.H = static_cast<const float2*>(H);
+  tp.y = static_cast<const float2*>(y);
+  tp.D = reinterpret_cast<const float2*>(base);
+  tp.X = reinterpret_cast<float2*>(base + t.D);
+  tp.Gb = reinterpret_cast<float2*>(base + t.D + t.X);
+  tp.Wm = reinterpret_cast<float2*>(base + t.D + t.X + t.Gb);
+  tp.P = reinterpret_cast<float*>(base + t.D + t.X + t.Gb + t.W);
+  tp.rho_c = rho_c;
+  tp.nu = nu;
+  tp.B = p.B;
+  tp.U = p.U;
+  tp.C = p.C;
+  tp.n_sc = p.n_sc;
+  tp.n_sym = p.n_sym;
+  return FFEQ_OK;
+}
+
+}  // namespace
+
+ffeq_status ffeq_fd_train_workspace_size(const ffeq_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return FFEQ_ERR_INVALID_ARG;
+  *bytes = train_layout(plan).total;
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_fd_train_forward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
+                                  const float* nu, void* z, void* workspace, size_t workspace_bytes, void* stream) {
+  ffeq::TrainParams tp;
+  ffeq_status r = train_params(plan, H, y, rho_c, nu, workspace, workspace_bytes, tp);
+  if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
+  if (!z || !aligned(z, 8)) return FFEQ_ERR_INVALID_ARG;
+  tp.z = static_cast<float2*>(z);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  r = local_preprocess(plan, H, y, workspace, st);
+  if (r != FFEQ_OK) return r;
+  const cudaError_t e = ffeq::launch_train_forward(tp, st);
+  return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+}
+
+ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
+                                   const float* nu, const void* gz, void* gH, void* gy, float* grho, float* gnu,
+                                   void* workspace, size_t workspace_bytes, void* stream) {
+  ffeq::TrainParams tp;
+  ffeq_status r = train_params(plan, H, y, rho_c, nu, workspace, workspace_bytes, tp);
+  if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
+  if (!gz || !gH || !gy || !grho || !gnu) return FFEQ_ERR_INVALID_ARG;
+  if (!aligned(gz, 8) || !aligned(gH, 8) || !aligned(gy, 8) || !aligned(grho, 4) || !aligned(gnu, 4))
+    return FFEQ_ERR_INVALID_ARG;
+  tp.gz = static_cast<const float2*>(gz);
+  tp.gH = static_cast<float2*>(gH);
+  tp.gy = static_cast<float2*>(gy);
+  tp.grho = grho;
+  tp.gnu = gnu;
+  const cudaError_t e = ffeq::launch_train_backward(tp, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+}
+
 ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes) {
   if (!plan || !bytes) return FFEQ_ERR_INVALID_ARG;
   const Sizes s = buffer_sizes(plan->p);

@@ -37,6 +37,29 @@ struct SolveParams {
   float llr_scale;    // sqrt(Es / e_avg): amplitude of level +1
 };
 
+// Differentiable FD (per-cluster rho_c, free fusion weights nu) and its adjoint.
+struct TrainParams {
+  const float2* H;     // [n_sc][U][B]
+  const float2* y;     // [n_sc][n_sym][B]
+  const float2* D;     // workspace: local Gram matrices and MRC outputs (FD layout)
+  float2* X;           // workspace [n_sc][C][n_sym][U]: local estimates
+  float2* Gb;          // workspace [n_sc][C][n_sym][U]
+  float2* Wm;          // workspace [n_sc][C][U][U]
+  float* P;            // workspace [n_sc][C][1+U]: partial sums of dL/drho, dL/dnu
+  const float* rho_c;  // [C]
+  const float* nu;     // [C][U]
+  float2* z;           // forward output [n_sc][n_sym][U]
+  const float2* gz;    // backward input [n_sc][n_sym][U]
+  float2* gH;          // [n_sc][U][B]
+  float2* gy;          // [n_sc][n_sym][B]
+  float* grho;         // [C]
+  float* gnu;          // [C][U]
+  int B, U, C, n_sc, n_sym;
+};
+size_t train_smem_bytes(int U, int C);
+cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t stream);
+cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t stream);
+
 // Padded user count (8, 16 or 32) used for register tiles.
 int padded_users(int U);
 // Subcarriers the contraction kernel of `precision` can stage ahead (0: one

@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "ffeq_device.cuh"
+#include "ffeq_gj.cuh"
 #include "ffeq_internal.h"
 
 namespace ffeq {
@@ -143,45 +144,9 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   // ---- Gauss-Jordan sweep
   int fail = 0;
   if constexpr (LPR == 1) {
-    // Column-rotating form: every step shifts the row left by one, so the pivot
-    // column is always aug[0] and the new inverse column is appended at aug[W-1].
-    // All register indices are compile-time constants while k stays a runtime
-    // loop (one step of code).  After UP steps: aug[0..kNsymMax) = z (RHS block),
-    // aug[kNsymMax + j] = A[i][j].
-#pragma unroll 1
-    for (int k = 0; k < UP; ++k) {
-      const float piv = __shfl_sync(kFullMask, aug[0].x, k, GS);
-      const bool ok = piv > 0.f;
-      if (!ok && fail == 0) fail = k + 1;
-      const float r = 1.f / (ok ? piv : 1.f);
-      if (i == k && g < nmat) {
-        // Scaled pivot row in the rotated layout: [aug[1..W-1] * r, r].
-#pragma unroll
-        for (int j = 0; j < W; j += 2) {
-          const float2 v0 = j + 1 < W ? cscale(aug[j + 1], r) : make_float2(r, 0.f);
-          const float2 v1 = j + 2 < W ? cscale(aug[j + 2], r) : make_float2(r, 0.f);
-          *reinterpret_cast<float4*>(rowbuf + j) = make_float4(v0.x, v0.y, v1.x, v1.y);
-        }
-      }
-      __syncwarp();
-      const float2 f = aug[0];
-      if (i == k) {
-#pragma unroll
-        for (int j = 0; j < W; j += 2) {
-          const float4 q = *reinterpret_cast<const float4*>(rowbuf + j);
-          aug[j] = make_float2(q.x, q.y);
-          aug[j + 1] = make_float2(q.z, q.w);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < W; j += 2) {
-          const float4 q = *reinterpret_cast<const float4*>(rowbuf + j);
-          aug[j] = j + 1 < W ? cfms(f, make_float2(q.x, q.y), aug[j + 1]) : make_float2(-f.x * r, -f.y * r);
-          aug[j + 1] = j + 2 < W ? cfms(f, make_float2(q.z, q.w), aug[j + 2]) : make_float2(-f.x * r, -f.y * r);
-        }
-      }
-      __syncwarp();
-    }
+    // Column-rotating form (ffeq_gj.cuh): afterwards aug[0..kNsymMax) = z (RHS
+    // block) and aug[kNsymMax + j] = A[i][j].
+    fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, g < nmat);
   } else {
   static_for<UP>([&](auto kc) {
     constexpr int k = decltype(kc)::value;

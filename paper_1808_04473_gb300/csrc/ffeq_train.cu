@@ -1,0 +1,304 @@
+// Differentiable FD equalization: forward with per-cluster regularizers and
+// free fusion weights, and its hand-written adjoint.
+//
+// Forward (per subcarrier k, cluster c; n_sym right-hand sides):
+//   X_c = (G_c + rho_c I)^{-1} B_c,  B_c = H_c^H Y_c       (L-MMSE, Sec. III-A, with rho_c free)
+//   z_u = sum_c nu[c][u] X_c[u]                            (Eq. fusionrule with free weights)
+// Adjoint of a real loss with g_z = dL/dRe z + i dL/dIm z:
+//   G_x,c = diag(nu_c) G_z,   G_b,c = (G_c + rho_c I)^{-1} G_x,c
+//   dL/dH_c   = Y_c G_b^H - H_c W_c,   W_c = G_b X_c^H + X_c G_b^H
+//   dL/dY_c   = H_c G_b
+//   dL/drho_c = -sum_k Re tr(G_b^H X_c),  dL/dnu[c][u] = sum_k sum_n Re(conj(g_z,u,n) X_c,u,n)
+// (dX = M^{-1}(dB - dM X), dM = dH^H H + H^H dH + drho I, dB = dH^H Y + H^H dY.)
+// The factorization is recomputed in the backward pass (a Gauss-Jordan sweep on
+// [G_c + rho_c I | G_x,c]); the forward keeps the local Gram matrices and the
+// local estimates X_c in the workspace.
+//
+// Workspace: D [n_sc][C][U+n_sym][U] (contraction output, as ffeq_equalize),
+// X [n_sc][C][n_sym][U], Gb [n_sc][C][n_sym][U], W [n_sc][C][U][U] (complex) and
+// per-subcarrier partial sums P [n_sc][C][1+U] (float).
+#include <cmath>
+
+#include "ffeq_device.cuh"
+#include "ffeq_gj.cuh"
+#include "ffeq_internal.h"
+
+namespace ffeq {
+namespace {
+
+template <int UP>
+struct TrainLayout {
+  static constexpr int kW = UP + kNsymMax;   // augmented row width
+  // Per group: pivot-row buffer (kW) + two [kNsymMax][UP] blocks.
+  static constexpr int kGroup = kW + 2 * kNsymMax * UP + 8;
+};
+
+// Row i of [G_c + rho_c I | R] from the workspace D (padding: identity / zero).
+// rhs(n) supplies R[i][n] for n < NS.
+template <int UP, typename Rhs>
+__device__ __forceinline__ void load_row(float2 (&aug)[UP + kNsymMax], const float2* Dg, int U, int NS, int i,
+                                         bool valid, float rho, Rhs rhs) {
+  const int ic = i < U ? i : 0;
+#pragma unroll
+  for (int j = 0; j < UP; ++j) aug[j] = Dg[(j < U ? j : 0) * U + ic];
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    const bool real = valid && i < U && j < U;
+    float2 v = real ? aug[j] : make_float2(i == j ? 1.f : 0.f, 0.f);
+    if (real && i == j) v = make_float2(v.x + rho, 0.f);
+    aug[j] = v;
+  }
+#pragma unroll
+  for (int n = 0; n < kNsymMax; ++n) aug[UP + n] = (n < NS && valid && i < U) ? rhs(n) : make_float2(0.f, 0.f);
+}
+
+// Forward: one CTA per subcarrier, one group of UP lanes per cluster.
+template <int UP>
+__global__ void __launch_bounds__(512) train_forward_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = TrainLayout<UP>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  float2* rowbuf = reinterpret_cast<float2*>(smem + 16) + gm * Lay::kGroup;
+  float2* F = rowbuf + W;                       // [kNsymMax][UP]: nu * X of this cluster
+  int* fail_any = reinterpret_cast<int*>(smem);
+  if (threadIdx.x == 0) *fail_any = 0;
+  __syncthreads();
+
+  const size_t matSize = static_cast<size_t>(U + NS) * U;
+  const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
+  float2 aug[W];
+  const float rho = p.rho_c[gm];
+  load_row<UP>(aug, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
+  const int fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+  if (valid && i == 0 && fail) atomicOr(fail_any, 1);
+
+  const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
+  if (valid && i < U) {
+    float2* Xk = p.X + (static_cast<size_t>(k) * C + gm) * NS * U;
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) {
+      if (n < NS) {
+        Xk[n * U + i] = aug[n];
+        F[n * UP + i] = cscale(aug[n], w);
+      }
+    }
+  }
+  __syncthreads();
+  const bool bad = *fail_any != 0;
+  for (int e = threadIdx.x; e < U * NS; e += blockDim.x) {
+    const int u = e % U, n = e / U;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < C; ++c) acc = cadd(acc, (reinterpret_cast<float2*>(smem + 16) + c * Lay::kGroup + W)[n * UP + u]);
+    p.z[(static_cast<size_t>(k) * NS + n) * U + u] = bad ? make_float2(NAN, NAN) : acc;
+  }
+}
+
+// Backward, per cluster: G_b = (G_c + rho_c I)^{-1} diag(nu_c) G_z, the partial
+// sums of dL/drho_c and dL/dnu[c][.] for this subcarrier, and W_c.
+template <int UP>
+__global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = TrainLayout<UP>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  float2* rowbuf = reinterpret_cast<float2*>(smem + 16) + gm * Lay::kGroup;
+  float2* Gs = rowbuf + W;                      // [kNsymMax][UP]  G_b of this cluster
+  float2* Xs = Gs + kNsymMax * UP;              // [kNsymMax][UP]  X of this cluster
+
+  const size_t matSize = static_cast<size_t>(U + NS) * U;
+  const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
+  const float2* gz = p.gz + static_cast<size_t>(k) * NS * U;
+  const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
+  float2 aug[W];
+  load_row<UP>(aug, Dg, U, NS, i, valid, p.rho_c[gm], [&](int n) { return cscale(gz[n * U + i], w); });
+  gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+
+  // aug[0..NS) = row i of G_b; X row i from the forward pass.
+  const size_t off = (static_cast<size_t>(k) * C + gm) * NS * U;
+  float2 x[kNsymMax];
+  float prho = 0.f, pnu = 0.f;
+#pragma unroll
+  for (int n = 0; n < kNsymMax; ++n) {
+    x[n] = (n < NS && valid && i < U) ? p.X[off + n * U + i] : make_float2(0.f, 0.f);
+    const float2 gzv = (n < NS && valid && i < U) ? gz[n * U + i] : make_float2(0.f, 0.f);
+    prho -= aug[n].x * x[n].x + aug[n].y * x[n].y;          // Re(conj(G_b) X)
+    pnu += gzv.x * x[n].x + gzv.y * x[n].y;                 // Re(conj(g_z) X)
+  }
+#pragma unroll
+  for (int o = UP / 2; o > 0; o >>= 1) prho += __shfl_xor_sync(kFullMask, prho, o, UP);
+  float* P = p.P + (static_cast<size_t>(k) * C + gm) * (1 + U);
+  if (valid) {
+    if (i == 0) P[0] = prho;
+    if (i < U) P[1 + i] = pnu;
+  }
+  if (valid && i < U) {
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) {
+      if (n < NS) {
+        p.Gb[off + n * U + i] = aug[n];
+        Gs[n * UP + i] = aug[n];
+        Xs[n * UP + i] = x[n];
+      }
+    }
+  }
+  __syncwarp();
+  // W row i: W[i][v] = sum_n G_b[i][n] conj(X[v][n]) + X[i][n] conj(G_b[v][n]).
+  if (valid && i < U) {
+    float2* Wk = p.Wm + (static_cast<size_t>(k) * C + gm) * U * U + i * U;
+    for (int v = 0; v < U; ++v) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n = 0; n < kNsymMax; ++n) {
+        if (n < NS) {
+          const float2 xv = Xs[n * UP + v], gv = Gs[n * UP + v];
+          // G_b[i] conj(X[v]) + X[i] conj(G_b[v])
+          acc = cfma(aug[n], make_float2(xv.x, -xv.y), acc);
+          acc = cfma(x[n], make_float2(gv.x, -gv.y), acc);
+        }
+      }
+      Wk[v] = acc;
+    }
+  }
+}
+
+// Backward contraction: thread per antenna b (its columns of H and Y in
+// registers, read coalesced from HBM), cluster c = b / S:
+//   dL/dH[u][b] = sum_n Y[n][b] conj(G_b[n][u]) - sum_v H[v][b] W[v][u]
+//   dL/dY[n][b] = sum_u H[u][b] G_b[n][u]
+// with G_b and W of the subcarrier's clusters staged in shared memory.
+template <int UP>
+__global__ void __launch_bounds__(256) train_backward_contract_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int U = p.U, NS = p.n_sym, C = p.C, B = p.B, S = B / C;
+  const int k = blockIdx.x;
+  float2* Gs = reinterpret_cast<float2*>(smem);            // [C][NS][U]
+  float2* Ws = Gs + static_cast<size_t>(C) * NS * U;       // [C][U][U]
+  const float2* Gk = p.Gb + static_cast<size_t>(k) * C * NS * U;
+  const float2* Wk = p.Wm + static_cast<size_t>(k) * C * U * U;
+  for (int e = threadIdx.x; e < C * NS * U; e += blockDim.x) Gs[e] = Gk[e];
+  for (int e = threadIdx.x; e < C * U * U; e += blockDim.x) Ws[e] = Wk[e];
+  __syncthreads();
+  const float2* Hk = p.H + static_cast<size_t>(k) * U * B;
+  const float2* Yk = p.y + static_cast<size_t>(k) * NS * B;
+  float2* gHk = p.gH + static_cast<size_t>(k) * U * B;
+  float2* gyk = p.gy + static_cast<size_t>(k) * NS * B;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int c = b / S;
+    const float2* Gc = Gs + static_cast<size_t>(c) * NS * U;
+    const float2* Wc = Ws + static_cast<size_t>(c) * U * U;
+    float2 h[UP], yv[kNsymMax];
+#pragma unroll
+    for (int v = 0; v < UP; ++v) h[v] = v < U ? Hk[static_cast<size_t>(v) * B + b] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) yv[n] = n < NS ? Yk[static_cast<size_t>(n) * B + b] : make_float2(0.f, 0.f);
+    for (int u = 0; u < U; ++u) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n = 0; n < kNsymMax; ++n)
+        if (n < NS) acc = cfma_conj(Gc[n * U + u], yv[n], acc);       // Y[n][b] conj(G_b[n][u])
+#pragma unroll
+      for (int v = 0; v < UP; ++v)
+        if (v < U) acc = cfms(h[v], Wc[v * U + u], acc);              // - H[v][b] W[v][u]
+      gHk[static_cast<size_t>(u) * B + b] = acc;
+    }
+    for (int n = 0; n < NS; ++n) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < UP; ++u)
+        if (u < U) acc = cfma(h[u], Gc[n * U + u], acc);
+      gyk[static_cast<size_t>(n) * B + b] = acc;
+    }
+  }
+}
+
+// dL/drho_c and dL/dnu[c][u]: fixed-order sums of the per-subcarrier partials
+// (block j reduces column j of P [n_sc][C * (1 + U)]).
+__global__ void __launch_bounds__(256) train_reduce_kernel(const TrainParams p) {
+  __shared__ float red[256];
+  const int U = p.U, C = p.C, J = C * (1 + U);
+  const int j = blockIdx.x;
+  float acc = 0.f;
+  for (int k = threadIdx.x; k < p.n_sc; k += blockDim.x) acc += p.P[static_cast<size_t>(k) * J + j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int c = j / (1 + U), q = j % (1 + U);
+    if (q == 0) p.grho[c] = red[0];
+    else p.gnu[c * U + q - 1] = red[0];
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    static_cast<int>(smem));
+  return cudaSuccess;
+}
+
+template <int UP>
+cudaError_t launch_forward_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = 16 + static_cast<size_t>(p.C) * TrainLayout<UP>::kGroup * sizeof(float2);
+  cudaError_t e = set_smem(train_forward_kernel<UP>, smem);
+  if (e != cudaSuccess) return e;
+  train_forward_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int UP>
+cudaError_t launch_backward_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = 16 + static_cast<size_t>(p.C) * TrainLayout<UP>::kGroup * sizeof(float2);
+  cudaError_t e = set_smem(train_backward_solve_kernel<UP>, smem);
+  if (e != cudaSuccess) return e;
+  train_backward_solve_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem2 = (static_cast<size_t>(p.C) * p.n_sym * p.U + static_cast<size_t>(p.C) * p.U * p.U) *
+                       sizeof(float2);
+  if ((e = set_smem(train_backward_contract_kernel<UP>, smem2)) != cudaSuccess) return e;
+  train_backward_contract_kernel<UP><<<p.n_sc, 256, smem2, st>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_reduce_kernel<<<p.C * (1 + p.U), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t train_smem_bytes(int U, int C) {
+  switch (padded_users(U)) {
+    case 8: return 16 + static_cast<size_t>(C) * TrainLayout<8>::kGroup * sizeof(float2);
+    case 16: return 16 + static_cast<size_t>(C) * TrainLayout<16>::kGroup * sizeof(float2);
+    default: return 16 + static_cast<size_t>(C) * TrainLayout<32>::kGroup * sizeof(float2);
+  }
+}
+
+cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t st) {
+  switch (padded_users(p.U)) {
+    case 8: return launch_forward_up<8>(p, st);
+    case 16: return launch_forward_up<16>(p, st);
+    default: return launch_forward_up<32>(p, st);
+  }
+}
+
+cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t st) {
+  switch (padded_users(p.U)) {
+    case 8: return launch_backward_up<8>(p, st);
+    case 16: return launch_backward_up<16>(p, st);
+    default: return launch_backward_up<32>(p, st);
+  }
+}
+
+}  // namespace ffeq

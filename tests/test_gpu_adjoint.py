@@ -1,0 +1,119 @@
+"""GPU parity of the differentiable FD form and its hand-written adjoint.
+
+Forward against ``oracle.adjoint.fd_train_forward`` (bound 1e-5 relative per
+subcarrier, FP32 arithmetic); backward against the oracle's closed-form
+gradients, which are pinned by finite differences (bound 1e-3 relative to the
+largest gradient entry, the stated target of the adjoint); and the autograd
+wrapper against the direct C-ABI calls.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint
+from paper_1808_04473_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04473_gb300 import build as fbuild
+    from paper_1808_04473_gb300 import ffeq
+    fbuild.build()
+    ffeq.lib()
+    return ffeq
+
+
+def _setup(B, U, C, n_sc, n_sym, seed, snr=10.0):
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=snr, bits=2, seed=seed)
+    rng = np.random.default_rng(seed + 7)
+    rho = (p.N0 / p.Es) * rng.uniform(0.5, 2.0, C)
+    nu = rng.uniform(0.5, 1.5, (C, U)) / C
+    return p, rho.astype(np.float32), nu.astype(np.float32)
+
+
+def _run(ff, p, rho, nu, C, gz=None):
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(p.H).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    r = torch.from_numpy(rho).to(dev)
+    w = torch.from_numpy(nu).to(dev)
+    plan = ff.ffeq_plan_create(p.B, p.U, C, p.n_sc, p.n_sym, arch=ff.FD)
+    nb = ff.ffeq_fd_train_workspace_size(plan)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    z = torch.empty((p.n_sc, p.n_sym, p.U), dtype=torch.complex64, device=dev)
+    ff.ffeq_fd_train_forward(plan, H, y, r, w, z, ws, nb)
+    out = {"z": z}
+    if gz is not None:
+        g = torch.from_numpy(gz.astype(np.complex64)).to(dev)
+        out.update(gH=torch.empty_like(H), gy=torch.empty_like(y), grho=torch.empty_like(r), gnu=torch.empty_like(w))
+        ff.ffeq_fd_train_backward(plan, H, y, r, w, g, out["gH"], out["gy"], out["grho"], out["gnu"], ws, nb)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+@pytest.mark.parametrize("B,U,C,n_sc,n_sym", [(16, 3, 2, 7, 2), (64, 16, 4, 20, 3), (96, 12, 12, 5, 1),
+                                              (128, 16, 8, 33, 1), (256, 32, 16, 6, 14)])
+def test_forward_and_backward_match_the_oracle(ff, B, U, C, n_sc, n_sym):
+    p, rho, nu = _setup(B, U, C, n_sc, n_sym, seed=B + U + C)
+    z0, _ = adjoint.fd_train_forward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64))
+    gz = 2.0 * (z0 - p.s) / z0.size                     # MSE loss
+    g = _run(ff, p, rho, nu, C, gz)
+    ez = np.linalg.norm((g["z"] - z0).reshape(n_sc, -1), axis=1) / np.linalg.norm(z0.reshape(n_sc, -1), axis=1)
+    assert ez.max() <= 1e-5, ez.max()
+    gH, gy, grho, gnu = adjoint.fd_train_backward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64),
+                                                  gz.astype(np.complex64).astype(np.complex128))
+    for name, ref in (("gH", gH), ("gy", gy), ("grho", grho), ("gnu", gnu)):
+        assert _relmax(g[name], ref) <= 1e-3, (name, _relmax(g[name], ref))
+
+
+def test_rho_and_nu_gradients_match_fp64_finite_differences(ff):
+    """Direct check of the GPU gradients against central differences of the FP64 forward."""
+    p, rho, nu = _setup(32, 4, 2, 6, 2, seed=3)
+    r64, n64 = rho.astype(np.float64), nu.astype(np.float64)
+    loss = lambda r, w: float(np.mean(np.abs(adjoint.fd_train_forward(p.H, p.y, r, w)[0] - p.s) ** 2))
+    z0, _ = adjoint.fd_train_forward(p.H, p.y, r64, n64)
+    g = _run(ff, p, rho, nu, 2, 2.0 * (z0 - p.s) / z0.size)
+    fr = adjoint.finite_difference(lambda r: loss(r, n64), r64)
+    fn = adjoint.finite_difference(lambda w: loss(r64, w), n64)
+    assert _relmax(g["grho"], fr) <= 1e-3
+    assert _relmax(g["gnu"], fn) <= 1e-3
+
+
+def test_training_shaped_batch(ff):
+    """B=128, U=16, C=8 (S=16), 1024 subcarriers x 8 channel draws, QPSK, 10 dB."""
+    p, rho, nu = _setup(128, 16, 8, 8 * 1024, 1, seed=11)
+    z0, _ = adjoint.fd_train_forward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64))
+    gz = 2.0 * (z0 - p.s) / z0.size
+    g = _run(ff, p, rho, nu, 8, gz)
+    gH, gy, grho, gnu = adjoint.fd_train_backward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64),
+                                                  gz.astype(np.complex64).astype(np.complex128))
+    assert _relmax(g["z"], z0) <= 1e-5
+    for name, ref in (("gH", gH), ("gy", gy), ("grho", grho), ("gnu", gnu)):
+        assert _relmax(g[name], ref) <= 1e-3, (name, _relmax(g[name], ref))
+
+
+def test_autograd_function_matches_the_c_abi(ff):
+    from paper_1808_04473_gb300.autograd import fd_equalize
+    p, rho, nu = _setup(64, 8, 4, 16, 2, seed=21)
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(p.H).to(dev).requires_grad_(True)
+    y = torch.from_numpy(p.y).to(dev).requires_grad_(True)
+    r = torch.from_numpy(rho).to(dev).requires_grad_(True)
+    w = torch.from_numpy(nu).to(dev).requires_grad_(True)
+    s = torch.from_numpy(p.s.astype(np.complex64)).to(dev)
+    z = fd_equalize(H, y, r, w, 4)
+    loss = (z - s).abs().pow(2).mean()
+    loss.backward()
+    z0 = z.detach().cpu().numpy()
+    gz = 2.0 * (z0 - p.s) / z0.size
+    ref = _run(ff, p, rho, nu, 4, gz)
+    for t, name in ((H, "gH"), (y, "gy"), (r, "grho"), (w, "gnu")):
+        assert _relmax(t.grad.cpu().numpy(), ref[name]) <= 1e-5, name
