@@ -23,6 +23,14 @@ ffeq_status cuda_fail(cudaError_t e) {
   return FFEQ_ERR_CUDA;
 }
 
+}  // namespace
+
+namespace ffeq {
+int record_cuda_error(cudaError_t e) { return static_cast<int>(cuda_fail(e)); }
+}  // namespace ffeq
+
+namespace {
+
 constexpr size_t kSolveSmemLimit = 227 * 1024;
 constexpr size_t kAlign = 256;
 
@@ -113,7 +121,7 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
                              cudaStream_t st) {
   const ffeq_problem& p = plan->p;
   if (!H || !y || !aligned(H, 8) || !aligned(y, 8)) return FFEQ_ERR_INVALID_ARG;
-  ffeq::GramParams gp;
+  ffeq::GramParams gp{};
   gp.H = static_cast<const float2*>(H);
   gp.y = static_cast<const float2*>(y);
   gp.D = static_cast<float2*>(workspace);
@@ -124,7 +132,7 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.n_sc = p.n_sc;
   gp.n_sym = p.n_sym;
   gp.bulk = (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
-  gp.stages = ffeq::gram_stages(p.precision, p.B, p.U, p.n_sym, plan->Ceff, gp.bulk != 0);
+  ffeq::gram_configure(gp, p.precision);
   const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                                  : ffeq::launch_gram_tc(gp, p.precision, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
@@ -137,7 +145,7 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
   if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
   if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
-  ffeq::SolveParams sp;
+  ffeq::SolveParams sp{};
   sp.D = static_cast<const float2*>(workspace);
   sp.z = static_cast<float2*>(z);
   sp.sigma2 = sigma2;

@@ -44,18 +44,70 @@ __host__ __device__ inline GramSplit gram_split(int Ceff, int Mrows, int warps, 
   return g;
 }
 
-// Stage subcarrier k's U + n_sym rows into `dst` (row stride B + 2 complex),
-// completing on `bar` (one cp.async.bulk per row; issued by one warp).
-__device__ __forceinline__ void issue_rows(const GramParams& p, int k, float2* dst, uint64_t* bar, int lane) {
-  const int U = p.U, B = p.B, NS = p.n_sym, Mrows = U + NS, RS = B + 2;
-  const float2* Hk = p.H + static_cast<size_t>(k) * U * B;
-  const float2* Yk = p.y + static_cast<size_t>(k) * NS * B;
+// One unit of work: a subcarrier of a uniform problem, or one descriptor of an
+// uneven batch (sizes and pointers from the descriptor, checked against the
+// group's shared-memory capacities and the buffers' extents).
+struct GramUnit {
+  int B, U, NS, Ceff;
+  bool ok;
+  const float2* H;
+  const float2* y;
+  float2* D;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int warps, bool splitM) {
+  GramUnit u;
+  if constexpr (BATCH) {
+    const BatchDesc& d = p.desc[t];
+    u.B = d.B; u.U = d.U; u.NS = d.n_sym; u.Ceff = d.Ceff;
+    const int Mrows = u.U + u.NS;
+    // (d_off even: the paired float4 stores below need 16-byte aligned rows.)
+    bool ok = (d.d_off & 1) == 0 && u.U >= 1 && u.U <= p.UP && u.NS >= 1 && u.NS <= kNsymMax && u.B >= 1 && u.B <= (1 << 20) &&
+              u.Ceff >= 1 &&
+              u.B % u.Ceff == 0 && Mrows * (u.B + 2) <= p.stage_elems;
+    if (ok) {
+      const GramSplit sp = gram_split(u.Ceff, Mrows, warps, splitM);
+      ok = sp.slots <= p.n_slots && (sp.slots == 0 || Mrows * (p.UP + 1) <= p.slot_elems) &&
+           span_ok(d.h_off, static_cast<long long>(u.U) * u.B, p.lim.h) &&
+           span_ok(d.y_off, static_cast<long long>(u.NS) * u.B, p.lim.y) &&
+           span_ok(d.d_off, static_cast<long long>(u.Ceff) * Mrows * u.U, p.lim.d) &&
+           (!p.bulk || ((u.B & 1) == 0 && (d.h_off & 1) == 0 && (d.y_off & 1) == 0));
+    }
+    u.ok = ok;
+    u.H = p.H + d.h_off; u.y = p.y + d.y_off; u.D = p.D + d.d_off;
+  } else {
+    u.B = p.B; u.U = p.U; u.NS = p.n_sym; u.Ceff = p.Ceff;
+    u.ok = true;
+    u.H = p.H + static_cast<size_t>(t) * p.U * p.B;
+    u.y = p.y + static_cast<size_t>(t) * p.n_sym * p.B;
+    u.D = p.D + static_cast<size_t>(t) * p.Ceff * (p.U + p.n_sym) * p.U;
+  }
+  return u;
+}
+
+// Stage a unit's U + n_sym rows into `dst` (row stride B + 2 complex),
+// completing on `bar` (one cp.async.bulk per row; issued by one warp).  A unit
+// that failed its checks completes the phase with a plain arrive.
+__device__ __forceinline__ void issue_rows(const GramUnit& w, float2* dst, uint64_t* bar, int lane) {
+  if (!w.ok) {
+    if (lane == 0) mbar_arrive(bar);
+    return;
+  }
+  const int U = w.U, B = w.B, NS = w.NS, Mrows = U + NS, RS = B + 2;
   if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Mrows) * B * 8u);
   __syncwarp();
   for (int r = lane; r < Mrows; r += 32) {
-    const float2* src = r < U ? Hk + static_cast<size_t>(r) * B : Yk + static_cast<size_t>(r - U) * B;
+    const float2* src = r < U ? w.H + static_cast<size_t>(r) * B : w.y + static_cast<size_t>(r - U) * B;
     bulk_g2s(dst + r * RS, src, static_cast<uint32_t>(B) * 8u, bar);
   }
+}
+
+// Unit that follows unit t in slot order: static stride for uniform problems,
+// the work queue (units sorted by decreasing cost on the host) for batches.
+__device__ __forceinline__ int gram_next(const GramParams& p, int t, int nst) {
+  if (p.queue) return nst * gridDim.x + atomicAdd(p.queue, 1);
+  return t + nst * gridDim.x;
 }
 
 // Persistent: CTA b handles subcarriers b, b + gridDim.x, ...  With bulk
@@ -63,64 +115,78 @@ __device__ __forceinline__ void issue_rows(const GramParams& p, int k, float2* d
 // ones overlap the contraction of the current one.  Contract::run<UP> computes
 // one warp's share of D over antennas [k0, k1) and hands each (m, u) entry to
 // the output functor.
-template <int UP, class Contract>
+template <int UP, class Contract, bool BATCH>
 __global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const GramParams p) {
   constexpr int kWarps = Contract::kWarps;
   constexpr int kThreads = kWarps * 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);                 // [p.stages]
-  const int U = p.U, B = p.B, NS = p.n_sym;
-  const int Mrows = U + NS, RS = B + 2, SU = UP + 1;
+  int* ring = reinterpret_cast<int*>(smem + 64);                      // unit of each stage
+  constexpr int SU = UP + 1;
   const int nst = p.stages;
   float2* stage0 = reinterpret_cast<float2*>(smem + kGramHeaderBytes);
-  const int stageSize = Mrows * RS;
+  const int stageSize = p.stage_elems;         // capacity of one stage (float2)
   float2* slots = stage0 + nst * stageSize;    // split-K partials (only when P > 1)
-  const int slotSize = Mrows * SU;
+  const int slotSize = p.slot_elems;           // capacity of one partial slot (float2)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  const int Ceff = p.Ceff;
-  const int S = B / Ceff;
-  const GramSplit sp = gram_split(Ceff, Mrows, kWarps, Contract::kSplitM);
-  const int P = sp.P, nM = sp.nM;
-  const int nItems = Ceff * P * nM;
-  const bool vec = (B & 1) == 0;
-  const int matSize = Mrows * U;
+  const int n_units = p.n_units;
+  constexpr bool kSM = Contract::kSplitM;
 
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
+    for (int s = 0; s < nst; ++s) ring[s] = blockIdx.x + s * gridDim.x;
   }
   __syncthreads();
   // Prologue: fill the ring.
   if (p.bulk && warp == 0) {
     for (int s = 0; s < nst; ++s) {
-      const int k = blockIdx.x + s * gridDim.x;
-      if (k < p.n_sc) issue_rows(p, k, stage0 + s * stageSize, &full[s], lane);
+      const int t = blockIdx.x + s * gridDim.x;
+      if (t < n_units) {
+        const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM);
+        if (!w.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+        issue_rows(w, stage0 + s * stageSize, &full[s], lane);
+      } else if (BATCH && lane == 0) {
+        mbar_arrive(&full[s]);   // the batch loop reads the sentinel through this stage
+      }
     }
   }
 
-  int it = 0;
-  for (int k = blockIdx.x; k < p.n_sc; k += gridDim.x, ++it) {
+  for (int it = 0;; ++it) {
     const int s = it % nst;
     float2* Ws = stage0 + s * stageSize;
+    if (!BATCH && blockIdx.x + it * gridDim.x >= n_units) break;   // uniform: nothing was staged
     if (p.bulk) {
       if (!mbar_wait_bounded(&full[s], (it / nst) & 1, p.status, FFEQ_ERR_TIMEOUT)) {
         // Give every copy still in flight a bounded chance to land, then leave.
         for (int q = 0; q < nst; ++q) mbar_wait_bounded(&full[q], ((it + q) / nst) & 1, nullptr, 0);
         return;
       }
-    } else {
-      const float2* Hk = p.H + static_cast<size_t>(k) * U * B;
-      const float2* Yk = p.y + static_cast<size_t>(k) * NS * B;
-      for (int e = tid; e < Mrows * B; e += kThreads) {
-        const int r = e / B, b = e - r * B;
-        Ws[r * RS + b] = r < U ? Hk[static_cast<size_t>(r) * B + b] : Yk[static_cast<size_t>(r - U) * B + b];
+    }
+    // Batch: the unit handed out with this stage; uniform: static stride.
+    const int t = BATCH ? ring[s] : blockIdx.x + it * gridDim.x;
+    if (t >= n_units) break;
+    const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM);
+    const int U = w.U, B = w.B, NS = w.NS, Ceff = w.Ceff;
+    const int Mrows = U + NS, RS = B + 2, S = B / Ceff;
+    const GramSplit sp = gram_split(Ceff, Mrows, kWarps, kSM);
+    const int P = sp.P, nM = sp.nM;
+    const int nItems = w.ok ? Ceff * P * nM : 0;
+    const bool vec = (B & 1) == 0;
+    const int matSize = Mrows * U;
+    if (!p.bulk) {
+      if (!w.ok && tid == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+      if (w.ok) {
+        for (int e = tid; e < Mrows * B; e += kThreads) {
+          const int r = e / B, b = e - r * B;
+          Ws[r * RS + b] = r < U ? w.H[static_cast<size_t>(r) * B + b] : w.y[static_cast<size_t>(r - U) * B + b];
+        }
       }
       __syncthreads();
     }
-    float2* Dk = p.D + static_cast<size_t>(k) * Ceff * matSize;
+    float2* Dk = w.D;
     for (int item = warp; item < nItems; item += kWarps) {
-      const int mt = Contract::kSplitM ? item % nM : -1;
+      const int mt = kSM ? item % nM : -1;
       const int rest = item / nM;
       const int part = rest % P, c = rest / P;
       const int k0 = c * S + (part * S) / P, k1 = c * S + ((part + 1) * S) / P;
@@ -145,12 +211,28 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const Gr
                                    });
       }
     }
-    __syncthreads();   // stage s (and, with split K, the partial slots) complete
-    if (p.bulk && warp == 0) {
-      const int kn = k + nst * gridDim.x;
-      if (kn < p.n_sc) issue_rows(p, kn, Ws, &full[s], lane);
+    __syncthreads();   // stage s (and, with split K, the partial slots) complete; ring[s] read by all
+    if constexpr (BATCH) {
+      if (warp == 0) {
+        const int tn = lane == 0 ? gram_next(p, t, nst) : 0;
+        const int tnb = __shfl_sync(kFullMask, tn, 0);
+        if (lane == 0) ring[s] = tnb;
+        if (p.bulk) {
+          if (tnb < n_units) {
+            const GramUnit wn = gram_unit<BATCH>(p, tnb, kWarps, kSM);
+            if (!wn.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+            issue_rows(wn, Ws, &full[s], lane);
+          } else if (lane == 0) {
+            mbar_arrive(&full[s]);
+          }
+        }
+      }
+    } else {
+      // Uniform: a unit past the end is never waited on, so no arrival is needed.
+      const int tn = t + nst * gridDim.x;
+      if (p.bulk && warp == 0 && tn < n_units) issue_rows(gram_unit<BATCH>(p, tn, kWarps, kSM), Ws, &full[s], lane);
     }
-    if (P > 1) {
+    if (P > 1 && w.ok) {
       // Fixed-order reduction of the K-parts, written coalesced to the workspace.
       for (int e = tid; e < Ceff * matSize; e += kThreads) {
         const int c = e / matSize, r = e - c * matSize;
@@ -160,23 +242,31 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const Gr
         for (int q = 1; q < P; ++q) v = cadd(v, sl[q * slotSize]);
         Dk[e] = v;
       }
-      __syncthreads();   // slots free for the next subcarrier
     }
+    // Slots free for the next unit; batch without bulk staging: publishes ring[s].
+    if ((P > 1 && w.ok) || (BATCH && !p.bulk)) __syncthreads();
   }
   // Let the dependent solve kernel start its launch while this grid drains.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Shared-memory stages that fit (0 when one subcarrier does not fit) and bytes.
+// Shared-memory capacity of one stage and of one partial slot (float2) for a
+// problem of these sizes, and the number of slots its split needs.
 template <class Contract>
-int gram_stages_for(int B, int U, int n_sym, int Ceff, bool bulk) {
-  const size_t Mrows = static_cast<size_t>(U) + n_sym;
-  const size_t SU = static_cast<size_t>(padded_users(U)) + 1;
-  const GramSplit sp = gram_split(Ceff, static_cast<int>(Mrows), Contract::kWarps, Contract::kSplitM);
-  const size_t partials = static_cast<size_t>(sp.slots) * Mrows * SU * 8;
-  const size_t stage = Mrows * (static_cast<size_t>(B) + 2) * 8;
-  if (partials + kGramHeaderBytes >= kGramSmemBudget) return 0;
-  const size_t budget = kGramSmemBudget - kGramHeaderBytes - partials;
+void gram_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems, int& slots) {
+  const int Mrows = U + n_sym;
+  const GramSplit sp = gram_split(Ceff, Mrows, Contract::kWarps, Contract::kSplitM);
+  // Both rounded to an even count: stages and slots start 16-byte aligned.
+  stage_elems = (Mrows * (B + 2) + 1) & ~1;
+  slot_elems = (Mrows * (padded_users(U) + 1) + 1) & ~1;
+  slots = sp.slots;
+}
+
+// Stages that fit for the given capacities (0 when one unit does not fit).
+inline int gram_stages_fit(size_t stage_elems, size_t slot_bytes_total, bool bulk) {
+  const size_t stage = stage_elems * 8;
+  if (slot_bytes_total + kGramHeaderBytes >= kGramSmemBudget) return 0;
+  const size_t budget = kGramSmemBudget - kGramHeaderBytes - slot_bytes_total;
   if (stage > budget) return 0;
   const size_t fit = budget / stage;
   if (!bulk) return 1;
@@ -184,12 +274,15 @@ int gram_stages_for(int B, int U, int n_sym, int Ceff, bool bulk) {
 }
 
 template <class Contract>
-size_t gram_smem_for(int B, int U, int n_sym, int Ceff, int stages) {
-  const size_t Mrows = static_cast<size_t>(U) + n_sym;
-  const size_t SU = static_cast<size_t>(padded_users(U)) + 1;
-  const GramSplit sp = gram_split(Ceff, static_cast<int>(Mrows), Contract::kWarps, Contract::kSplitM);
-  return kGramHeaderBytes + static_cast<size_t>(stages) * Mrows * (static_cast<size_t>(B) + 2) * 8 +
-         static_cast<size_t>(sp.slots) * Mrows * SU * 8;
+int gram_stages_for(int B, int U, int n_sym, int Ceff, bool bulk) {
+  int st, sl, ns;
+  gram_capacity<Contract>(B, U, n_sym, Ceff, st, sl, ns);
+  return gram_stages_fit(st, static_cast<size_t>(ns) * sl * 8, bulk);
+}
+
+inline size_t gram_smem_bytes(const GramParams& p) {
+  return kGramHeaderBytes + static_cast<size_t>(p.stages) * p.stage_elems * 8 +
+         static_cast<size_t>(p.n_slots) * p.slot_elems * 8;
 }
 
 // Launch on min(n_sc, #SMs) persistent CTAs.
@@ -201,15 +294,24 @@ cudaError_t launch_gram_up(const GramParams& p, size_t smem, cudaStream_t stream
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(gram_kernel<UP, Contract>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    err = cudaFuncSetAttribute(gram_kernel<UP, Contract, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               227 * 1024);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(gram_kernel<UP, Contract, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               227 * 1024);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
   const int sms = dev < 64 ? num_sms[dev] : 152;
-  const int grid = p.n_sc < sms ? p.n_sc : sms;
-  gram_kernel<UP, Contract><<<grid, Contract::kWarps * 32, smem, stream>>>(p);
+  int grid = p.n_units < sms ? p.n_units : sms;
+  if (p.grid_cap > 0 && grid > p.grid_cap) grid = p.grid_cap;
+  if (p.desc) {
+    gram_kernel<UP, Contract, true><<<grid, Contract::kWarps * 32, smem, stream>>>(p);
+  } else {
+    gram_kernel<UP, Contract, false><<<grid, Contract::kWarps * 32, smem, stream>>>(p);
+  }
   return cudaGetLastError();
 }
 

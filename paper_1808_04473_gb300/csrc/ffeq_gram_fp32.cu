@@ -95,13 +95,37 @@ struct SimtFp32 {
 
 int padded_users(int U) { return U <= 8 ? 8 : (U <= 16 ? 16 : 32); }
 
+void gram_instance_capacity(int precision, int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems,
+                            int& slots) {
+  if (precision == FFEQ_FP32) {
+    gram_capacity<SimtFp32>(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
+  } else {
+    gram_tc_capacity(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
+  }
+}
+
+int gram_stages_fit_bytes(size_t stage_elems, size_t slot_bytes_total, bool bulk) {
+  return gram_stages_fit(stage_elems, slot_bytes_total, bulk);
+}
+
 int gram_stages(int precision, int B, int U, int n_sym, int Ceff, bool bulk) {
-  return precision == FFEQ_FP32 ? gram_stages_for<SimtFp32>(B, U, n_sym, Ceff, bulk)
-                                : gram_tc_stages(B, U, n_sym, Ceff, bulk);
+  int st, sl, ns;
+  gram_instance_capacity(precision, B, U, n_sym, Ceff, st, sl, ns);
+  return gram_stages_fit(st, static_cast<size_t>(ns) * sl * 8, bulk);
+}
+
+void gram_configure(GramParams& p, int precision) {
+  gram_instance_capacity(precision, p.B, p.U, p.n_sym, p.Ceff, p.stage_elems, p.slot_elems, p.n_slots);
+  p.stages = gram_stages_fit(p.stage_elems, static_cast<size_t>(p.n_slots) * p.slot_elems * 8, p.bulk != 0);
+  p.n_units = p.n_sc;
+  p.desc = nullptr;
+  p.queue = nullptr;
+  p.UP = padded_users(p.U);
+  p.lim = BatchLimits{};
 }
 
 cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream) {
-  const size_t smem = gram_smem_for<SimtFp32>(p.B, p.U, p.n_sym, p.Ceff, p.stages);
+  const size_t smem = gram_smem_bytes(p);
   switch (padded_users(p.U)) {
     case 8: return launch_gram_up<8, SimtFp32>(p, smem, stream);
     case 16: return launch_gram_up<16, SimtFp32>(p, smem, stream);

@@ -252,12 +252,12 @@ cudaError_t launch_mode(const GramParams& p, size_t smem, cudaStream_t stream) {
 
 }  // namespace
 
-int gram_tc_stages(int B, int U, int n_sym, int Ceff, bool bulk) {
-  return gram_stages_for<TensorSplit<kBf16x3>>(B, U, n_sym, Ceff, bulk);
+void gram_tc_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems, int& slots) {
+  gram_capacity<TensorSplit<kBf16x3>>(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
 }
 
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream) {
-  const size_t smem = gram_smem_for<TensorSplit<kBf16x3>>(p.B, p.U, p.n_sym, p.Ceff, p.stages);
+  const size_t smem = gram_smem_bytes(p);
   return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3>(p, smem, stream) : launch_mode<kBf16x3>(p, smem, stream);
 }
 

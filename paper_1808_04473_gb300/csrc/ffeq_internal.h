@@ -10,6 +10,33 @@ namespace ffeq {
 
 constexpr int kNsymMax = 16;   // OFDM symbols per subcarrier held in registers
 
+// One unit of an uneven batch: a single subcarrier of one instance (element
+// offsets into the batch's flat buffers: complex for H, y, z, D; float for
+// sigma2 and llr; int for info).  Built on the host, validated on the device.
+struct BatchDesc {
+  long long h_off, y_off, z_off, s2_off, llr_off, info_off, d_off;
+  int B, U, Ceff, n_sym;
+  float N0, rho, llr_scale;
+  int inst;             // index of the instance (diagnostics)
+};
+
+// Element counts of the batch buffers (for the device-side bounds checks).
+struct BatchLimits {
+  long long h, y, z, s2, llr, info, d;
+};
+
+// [off, off + n) lies in [0, extent), written so that no sum can overflow.
+__host__ __device__ inline bool span_ok(long long off, long long n, long long extent) {
+  return off >= 0 && n >= 0 && off <= extent && n <= extent - off;
+}
+
+// A solve tile: descriptors [first, first + count) share one CTA; slot s of the
+// tile's matrix slots holds cluster (map[s] & 0xff) of descriptor first + (map[s] >> 8).
+constexpr int kTileSlots = 64;
+struct SolveTile {
+  int first, count;
+};
+
 // Contraction kernel: H, y -> workspace D = [n_sc][Ceff][U + n_sym][U] complex,
 // D[m][u] = sum over the cluster's antennas of conj(H[u][b]) * [H; Y][m][b].
 struct GramParams {
@@ -19,7 +46,16 @@ struct GramParams {
   int* status;        // device status word
   int B, U, Ceff, n_sc, n_sym;
   int bulk;           // 1: stage rows with cp.async.bulk (16-byte aligned rows)
-  int stages;         // subcarriers staged ahead (1 without bulk copies)
+  int stages;         // units staged ahead (1 without bulk copies)
+  int stage_elems;    // capacity of one stage (float2)
+  int slot_elems;     // capacity of one split-K partial slot (float2)
+  int n_slots;        // partial slots in shared memory
+  int n_units;        // subcarriers (uniform) or batch units
+  const BatchDesc* desc;  // nullptr: uniform problem
+  int* queue;         // batch: work-queue counter (zero at launch)
+  int UP;             // batch: users padding of the group
+  BatchLimits lim;    // batch: buffer extents
+  int grid_cap;       // > 0: at most this many persistent CTAs
 };
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
@@ -35,6 +71,14 @@ struct SolveParams {
   int llr_bits;
   float N0, rho;      // rho = N0 / Es
   float llr_scale;    // sqrt(Es / e_avg): amplitude of level +1
+  // Uneven batch (desc != nullptr): one CTA per tile; per-unit sizes, offsets,
+  // N0, rho and llr_scale from the descriptors.
+  const BatchDesc* desc;
+  const SolveTile* tiles;
+  const unsigned short* slot_map;   // [n_tiles][kTileSlots]
+  int n_tiles, n_desc, threads;
+  BatchLimits lim;
+  int* status;
 };
 
 // Differentiable FD (per-cluster rho_c, free fusion weights nu) and its adjoint.
@@ -65,15 +109,26 @@ int padded_users(int U);
 // Subcarriers the contraction kernel of `precision` can stage ahead (0: one
 // subcarrier does not fit in shared memory).
 int gram_stages(int precision, int B, int U, int n_sym, int Ceff, bool bulk);
-int gram_tc_stages(int B, int U, int n_sym, int Ceff, bool bulk);
+void gram_tc_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems, int& slots);
+// Fill stage_elems / slot_elems / n_slots / stages of a uniform problem.
+void gram_configure(GramParams& p, int precision);
+// Capacities for an instance under `precision` (for batch sizing).
+void gram_instance_capacity(int precision, int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems,
+                            int& slots);
+int gram_stages_fit_bytes(size_t stage_elems, size_t slot_bytes_total, bool bulk);
 cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream);
 // Tensor-core split-precision contraction (precision FFEQ_TF32X3 or FFEQ_BF16X3).
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream);
 int solve_subcarriers_per_cta(int U, int Ceff);
 size_t solve_smem_bytes(int U, int Ceff);
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream);
+// Uneven batch: p.U holds the group's padded users (8/16/32), lpr its lanes per row.
+cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream);
+size_t solve_batch_smem_bytes(int UP, int lpr, int threads);
 
 // Address of the device status word on the current device (nullptr on error).
 int* device_status_ptr();
+// Remember the CUDA error string for ffeq_last_cuda_error(); returns FFEQ_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
 
 }  // namespace ffeq

@@ -81,10 +81,60 @@ __device__ __forceinline__ void symbol_llr(float2 z, float s2, float scale, int 
   }
 }
 
+// Outputs of an uneven-batch tile: for each descriptor, sum its Ceff matrix
+// slots (contiguous, in tile order) and write z, sigma^2 and LLRs at its offsets.
+template <int UP>
+__device__ void batch_epilogue(const SolveParams& p, const float2* base, const int* fail, int nslot) {
+  using Lay = SolveLayout<UP>;
+  const SolveTile tile = p.tiles[blockIdx.x];
+  const int bits = p.llr_bits, hb = bits / 2;
+  int slot0 = 0;
+  for (int j = 0; j < tile.count && tile.first >= 0 && tile.first + j < p.n_desc; ++j) {
+    const BatchDesc& d = p.desc[tile.first + j];
+    const int U = d.U, NS = d.n_sym, Ceff = d.Ceff;
+    const int per = U * NS;
+    const bool ok = U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kTileSlots &&
+                    slot0 + Ceff <= kTileSlots && slot0 + Ceff <= nslot && span_ok(d.z_off, per, p.lim.z) &&
+                    span_ok(d.s2_off, U, p.lim.s2) &&
+                    (!bits || span_ok(d.llr_off, static_cast<long long>(per) * bits, p.lim.llr));
+    if (!ok) {
+      if (threadIdx.x == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+      break;
+    }
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int n = e / U, u = e - n * U;
+      float2 nm = make_float2(0.f, 0.f);
+      float dn = 0.f;
+      for (int cc = 0; cc < Ceff; ++cc) {
+        const float2* Lm = base + (slot0 + cc) * Lay::kMat + Lay::kRow;
+        nm = cadd(nm, Lm[n * UP + u]);
+        dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
+      }
+      float2 zz;
+      float s2;
+      if (fail[j]) {
+        zz = make_float2(NAN, NAN);
+        s2 = NAN;
+      } else if (dn > 0.f) {
+        const float rr = 1.f / dn;
+        zz = cscale(nm, rr);
+        s2 = d.N0 * rr;
+      } else {
+        zz = make_float2(0.f, 0.f);
+        s2 = INFINITY;
+      }
+      p.z[d.z_off + e] = zz;
+      if (n == 0) p.sigma2[d.s2_off + u] = s2;
+      if (bits) symbol_llr(zz, s2, d.llr_scale, hb, p.llr + d.llr_off + static_cast<long long>(e) * bits);
+    }
+    slot0 += Ceff;
+  }
+}
+
 // LPR lanes per row: with LPR = 2 the two lanes of row i hold halves of its
 // augmented row (columns [0, W/2) and [W/2, W)), halving the work per lane and
 // step; the pivot column k < UP always lies in the first half.
-template <int UP, int LPR>
+template <int UP, int LPR, bool BATCH>
 __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   using Lay = SolveLayout<UP>;
@@ -92,30 +142,62 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   constexpr int W = UP + kNsymMax;            // augmented row width (RHS columns beyond n_sym unused)
   constexpr int WH = W / LPR;                 // columns per lane
   static_assert(UP <= WH, "pivot columns must lie in the first half of a row");
-  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, spc = p.spc;
-  const int nmat = spc * Ceff;
+  const int spc = p.spc;
+  constexpr bool batch = BATCH;
+  const int nmat = batch ? static_cast<int>(blockDim.x) / GS : spc * p.Ceff;
   const int g = threadIdx.x / GS, gl = threadIdx.x % GS;
   const int i = gl % UP;
   const int h = LPR == 1 ? 0 : gl / UP;        // which half of the row this lane holds
-  int* fail_sc = reinterpret_cast<int*>(smem);                       // [spc]
+  int* fail_sc = reinterpret_cast<int*>(smem);                       // [spc] or [tile count]
   float2* base = reinterpret_cast<float2*>(smem + 256);
   const int sc0 = blockIdx.x * spc;
 
-  if (threadIdx.x < spc) fail_sc[threadIdx.x] = 0;
+  if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
   __syncthreads();
-
-  const int gm = g < nmat ? g : nmat - 1;       // spare lanes shadow the last matrix
-  const int scl = gm / Ceff, c = gm % Ceff;
-  const int sc = sc0 + scl;
-  const bool valid = g < nmat && sc < p.n_sc;
-  float2* rowbuf = base + gm * Lay::kMat;
-  float2* Fz = rowbuf + Lay::kRow;
-  float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
-  const size_t matSize = static_cast<size_t>(U + NS) * U;
-  const float2* Dg = p.D + (static_cast<size_t>(valid ? sc : 0) * Ceff + c) * matSize;
 
   // Wait for the contraction grid (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  // ---- the system this lane group solves
+  const int gm = g < nmat ? g : nmat - 1;       // spare lanes shadow the last matrix
+  int U, NS, Ceff, scl, c, sc = 0;
+  float rho;
+  bool valid;
+  const float2* Dg;
+  int* info_at = nullptr;
+  if constexpr (!batch) {
+    U = p.U; NS = p.n_sym; Ceff = p.Ceff; rho = p.rho;
+    scl = gm / Ceff; c = gm % Ceff;
+    sc = sc0 + scl;
+    valid = g < nmat && sc < p.n_sc;
+    const size_t matSize = static_cast<size_t>(U + NS) * U;
+    Dg = p.D + (static_cast<size_t>(valid ? sc : 0) * Ceff + c) * matSize;
+    if (p.info) info_at = p.info + static_cast<size_t>(sc) * Ceff + c;
+  } else {
+    // Slot g of this tile: cluster c of its descriptor j (map checked against the tile and the buffers).
+    const SolveTile tile = p.tiles[blockIdx.x];
+    const unsigned m = g < kTileSlots ? p.slot_map[static_cast<size_t>(blockIdx.x) * kTileSlots + g] : 0xffffu;
+    const int j = static_cast<int>(m >> 8);
+    c = static_cast<int>(m & 0xffu);
+    scl = j;
+    const int dj = tile.first + j;
+    valid = m != 0xffffu && j < tile.count && j < kTileSlots && tile.first >= 0 && dj < p.n_desc;
+    const BatchDesc* d = valid ? p.desc + dj : p.desc;
+    U = d->U; NS = d->n_sym; Ceff = d->Ceff; rho = d->rho;
+    valid = valid && U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kTileSlots && c < Ceff;
+    const long long matSize = valid ? static_cast<long long>(U + NS) * U : 0;
+    valid = valid && span_ok(d->d_off, Ceff * matSize, p.lim.d) &&
+            (!p.info || span_ok(d->info_off, Ceff, p.lim.info));
+    if (!valid) {
+      U = UP; NS = 1; Ceff = 1; c = 0; rho = 1.f;
+      if (m != 0xffffu && gl == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+    }
+    Dg = p.D + (valid ? d->d_off + c * matSize : 0);
+    if (p.info && valid) info_at = p.info + d->info_off + c;
+  }
+  float2* rowbuf = base + gm * Lay::kMat;
+  float2* Fz = rowbuf + Lay::kRow;
+  float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
 
   // ---- this lane's columns of row i of [G + rho I | y^MRC] (padding: identity, zero RHS)
   // Loads are unconditional (clamped to valid addresses) so they all issue before
@@ -126,7 +208,11 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   for (int j = 0; j < WH; ++j) {
     const int col = h * WH + j;
     const int row = col < UP ? (col < U ? col : 0) : (col - UP < NS ? U + col - UP : 0);
-    aug[j] = Dg[row * U + ic];
+    if constexpr (batch) {
+      aug[j] = valid ? Dg[row * U + ic] : make_float2(0.f, 0.f);
+    } else {
+      aug[j] = Dg[row * U + ic];   // invalid groups read subcarrier 0 (in bounds)
+    }
   }
   float gii = 1.f;
 #pragma unroll
@@ -136,7 +222,7 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     float2 v = real ? aug[j] : make_float2(col == i ? 1.f : 0.f, 0.f);
     if (col == i && real) {
       gii = v.x;
-      v = make_float2(v.x + p.rho, 0.f);
+      v = make_float2(v.x + rho, 0.f);
     }
     aug[j] = v;
   }
@@ -196,7 +282,7 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   const float invA = 1.f / Ai;
   // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
   // mu = 0 exactly, which the subtraction would only reach up to rounding.
-  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - p.rho * Ai, 0.f);
+  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
   if (g < nmat) {
 #pragma unroll
     for (int j = 0; j < WH; ++j) {
@@ -206,14 +292,18 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     }
     if (h == 0) Dn[i] = (p.unbiased ? mu : 1.f) * invA;
     if (gl == 0 && valid) {
-      if (p.info) p.info[static_cast<size_t>(sc) * Ceff + c] = fail;
+      if (info_at) *info_at = fail;
       if (fail) atomicOr(&fail_sc[scl], 1);
     }
   }
   __syncthreads();
+  if constexpr (batch) {
+    batch_epilogue<UP>(p, base, fail_sc, nmat);
+    return;
+  }
 
   // ---- per subcarrier: sum over clusters, outputs
-  const int per = U * NS;
+  const int per = U * NS;   // uniform problem: every group has the problem's sizes
   const int bits = p.llr_bits, hb = bits / 2;
   for (int e = threadIdx.x; e < spc * per; e += blockDim.x) {
     const int s = e / per, r = e - s * per;
@@ -247,23 +337,24 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   }
 }
 
-template <int UP, int LPR>
+template <int UP, int LPR, bool BATCH>
 cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   using Lay = SolveLayout<UP>;
-  const int nmat = p.spc * p.Ceff;
-  const int threads = ((nmat * UP * LPR + 31) / 32) * 32;
+  constexpr bool batch = BATCH;
+  const int nmat = batch ? p.threads / (UP * LPR) : p.spc * p.Ceff;
+  const int threads = batch ? p.threads : ((nmat * UP * LPR + 31) / 32) * 32;
   const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
   static int configured[64] = {0};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(solve_fuse_kernel<UP, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    err = cudaFuncSetAttribute(solve_fuse_kernel<UP, LPR, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((p.n_sc + p.spc - 1) / p.spc);
+  cfg.gridDim = dim3(batch ? p.n_tiles : (p.n_sc + p.spc - 1) / p.spc);
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
@@ -272,7 +363,7 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP, LPR>, p);
+  return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP, LPR, BATCH>, p);
 }
 
 }  // namespace
@@ -301,10 +392,25 @@ size_t solve_smem_bytes(int U, int Ceff) {
 
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream) {
   switch (padded_users(p.U)) {
-    case 8: return launch_up<8, 1>(p, stream);
-    case 16: return lanes_per_row(p.U, p.Ceff) == 2 ? launch_up<16, 2>(p, stream) : launch_up<16, 1>(p, stream);
-    default: return launch_up<32, 1>(p, stream);
+    case 8: return launch_up<8, 1, false>(p, stream);
+    case 16: return lanes_per_row(p.U, p.Ceff) == 2 ? launch_up<16, 2, false>(p, stream)
+                                                    : launch_up<16, 1, false>(p, stream);
+    default: return launch_up<32, 1, false>(p, stream);
   }
+}
+
+cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream) {
+  switch (p.U) {
+    case 8: return lpr == 2 ? launch_up<8, 2, true>(p, stream) : launch_up<8, 1, true>(p, stream);
+    case 16: return lpr == 2 ? launch_up<16, 2, true>(p, stream) : launch_up<16, 1, true>(p, stream);
+    default: return launch_up<32, 1, true>(p, stream);
+  }
+}
+
+size_t solve_batch_smem_bytes(int UP, int lpr, int threads) {
+  const int nmat = threads / (UP * lpr);
+  size_t per = UP == 8 ? SolveLayout<8>::kMat : (UP == 16 ? SolveLayout<16>::kMat : SolveLayout<32>::kMat);
+  return 256 + static_cast<size_t>(nmat) * per * sizeof(float2);
 }
 
 }  // namespace ffeq

@@ -20,7 +20,9 @@ UNBIASED, LITERAL = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffeq.so")
-HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "ffeq.h")
+INCLUDE_DIR = os.path.join(os.path.dirname(_HERE), "include")
+HEADER_PATH = os.path.join(INCLUDE_DIR, "ffeq.h")
+HEADER_PATHS = [HEADER_PATH, os.path.join(INCLUDE_DIR, "ffeq_batch.h")]
 
 _STATUS = {0: "FFEQ_OK", 1: "FFEQ_ERR_INVALID_ARG", 2: "FFEQ_ERR_UNSUPPORTED", 3: "FFEQ_ERR_CUDA",
            4: "FFEQ_ERR_TIMEOUT"}
@@ -38,6 +40,20 @@ class ffeq_problem(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int), ("U", ctypes.c_int), ("C", ctypes.c_int), ("n_sc", ctypes.c_int),
                 ("n_sym", ctypes.c_int), ("arch", ctypes.c_int), ("precision", ctypes.c_int),
                 ("estimate", ctypes.c_int), ("llr_bits", ctypes.c_int)]
+
+
+class ffeq_instance(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("U", ctypes.c_int), ("C", ctypes.c_int), ("n_sc", ctypes.c_int),
+                ("n_sym", ctypes.c_int), ("N0", ctypes.c_float), ("Es", ctypes.c_float),
+                ("h_off", ctypes.c_longlong), ("y_off", ctypes.c_longlong), ("z_off", ctypes.c_longlong),
+                ("sigma2_off", ctypes.c_longlong), ("llr_off", ctypes.c_longlong), ("info_off", ctypes.c_longlong)]
+
+
+class ffeq_batch_config(ctypes.Structure):
+    _fields_ = [("arch", ctypes.c_int), ("precision", ctypes.c_int), ("estimate", ctypes.c_int),
+                ("llr_bits", ctypes.c_int), ("h_elems", ctypes.c_longlong), ("y_elems", ctypes.c_longlong),
+                ("z_elems", ctypes.c_longlong), ("sigma2_elems", ctypes.c_longlong),
+                ("llr_elems", ctypes.c_longlong), ("info_elems", ctypes.c_longlong)]
 
 
 _lib = None
@@ -59,6 +75,16 @@ _SIGS = {
     "ffeq_fd_train_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ffeq_equalize_noalloc": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
     "ffeq_device_status": ([ctypes.POINTER(_i), _i], _i),
+    "ffeq_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_batch_config), ctypes.POINTER(ffeq_instance),
+                           _i], _i),
+    "ffeq_batch_destroy": ([_vp], None),
+    "ffeq_batch_workspace_size": ([_vp, ctypes.POINTER(_sz)], _i),
+    "ffeq_batch_upload": ([_vp, _vp, _sz, _vp], _i),
+    "ffeq_batch_equalize": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_batch_autotune": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _i], _i),
+    "ffeq_batch_groups": ([_vp], _i),
+    "ffeq_batch_get_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
+    "ffeq_batch_set_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
 }
 
 
@@ -79,8 +105,8 @@ def lib():
 
 
 def header_symbols() -> list[str]:
-    """Names of the functions declared in ``include/ffeq.h``."""
-    text = open(HEADER_PATH).read()
+    """Names of the functions declared in ``include/ffeq.h`` and ``include/ffeq_batch.h``."""
+    text = "".join(open(h).read() for h in HEADER_PATHS)
     return sorted(set(re.findall(r"\b(ffeq_[a-z_]+)\s*\(", text)))
 
 
@@ -214,6 +240,101 @@ def ffeq_device_status(clear: bool = True) -> int:
 
 def ffeq_status_string(status: int) -> str:
     return lib().ffeq_status_string(status).decode()
+
+
+# --------------------------------------------------------------------- uneven batches
+
+class Batch:
+    """Owner of an ``ffeq_batch*`` (destroyed with the object)."""
+
+    def __init__(self, handle: int, config: ffeq_batch_config, instances):
+        self.handle = handle
+        self.config = config
+        self.instances = instances
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.ffeq_batch_destroy(self.handle)
+            self.handle = None
+
+
+def ffeq_batch_create(config: ffeq_batch_config, instances) -> Batch:
+    """``instances``: a sequence of ``ffeq_instance`` (copied into a C array)."""
+    arr = (ffeq_instance * max(1, len(instances)))(*instances)
+    h = _vp()
+    _check("ffeq_batch_create", lib().ffeq_batch_create(ctypes.byref(h), ctypes.byref(config), arr,
+                                                        len(instances)))
+    return Batch(h.value, config, list(instances))
+
+
+def ffeq_batch_workspace_size(batch: Batch) -> int:
+    n = _sz()
+    _check("ffeq_batch_workspace_size", lib().ffeq_batch_workspace_size(batch.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ffeq_batch_upload(batch: Batch, workspace, workspace_bytes: int, stream=None) -> None:
+    _check("ffeq_batch_upload", lib().ffeq_batch_upload(batch.handle, _ptr(workspace), workspace_bytes,
+                                                        _stream(stream)))
+
+
+def ffeq_batch_equalize(batch: Batch, H, y, z, sigma2, llr=None, info=None, workspace=None, workspace_bytes: int = 0,
+                        stream=None) -> None:
+    _check("ffeq_batch_equalize", lib().ffeq_batch_equalize(
+        batch.handle, _ptr(H), _ptr(y), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info), _ptr(workspace),
+        workspace_bytes, _stream(stream)))
+
+
+def ffeq_batch_autotune(batch: Batch, H, y, z, sigma2, llr=None, info=None, workspace=None,
+                        workspace_bytes: int = 0, stream=None, reps: int = 10) -> None:
+    _check("ffeq_batch_autotune", lib().ffeq_batch_autotune(
+        batch.handle, _ptr(H), _ptr(y), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info), _ptr(workspace),
+        workspace_bytes, _stream(stream), int(reps)))
+
+
+def ffeq_batch_groups(batch: Batch) -> int:
+    return lib().ffeq_batch_groups(batch.handle)
+
+
+def ffeq_batch_get_tuning(batch: Batch) -> list[tuple[int, int, int, int]]:
+    """Per user group: (users padded, contraction stages, solve threads per CTA, lanes per row)."""
+    g = ffeq_batch_groups(batch)
+    buf = (_i * max(1, 4 * g))()
+    _check("ffeq_batch_get_tuning", lib().ffeq_batch_get_tuning(batch.handle, buf, 4 * g))
+    return [tuple(buf[4 * k:4 * k + 4]) for k in range(g)]
+
+
+def ffeq_batch_set_tuning(batch: Batch, tuning) -> None:
+    flat = [int(v) for t in tuning for v in t]
+    buf = (_i * max(1, len(flat)))(*flat)
+    _check("ffeq_batch_set_tuning", lib().ffeq_batch_set_tuning(batch.handle, buf, len(flat)))
+
+
+def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNBIASED, llr_bits: int = 0,
+               with_info: bool = True):
+    """Lay instances out back to back in flat buffers.
+
+    ``specs``: sequence of ``(B, U, C, n_sc, n_sym, N0, Es)``.  Offsets of the
+    complex arrays are kept even (16-byte aligned rows when B is even).
+    Returns ``(config, instances)``.
+    """
+    def even(x):
+        return x + (x & 1)
+    offs = dict(h=0, y=0, z=0, s2=0, llr=0, info=0)
+    inst = []
+    for (B, U, C, n_sc, n_sym, N0, Es) in specs:
+        Ceff = C if arch == FD else 1
+        inst.append(ffeq_instance(B, U, C, n_sc, n_sym, float(N0), float(Es), offs["h"], offs["y"], offs["z"],
+                                  offs["s2"], offs["llr"], offs["info"]))
+        offs["h"] = even(offs["h"] + n_sc * U * B)
+        offs["y"] = even(offs["y"] + n_sc * n_sym * B)
+        offs["z"] = even(offs["z"] + n_sc * n_sym * U)
+        offs["s2"] += n_sc * U
+        offs["llr"] += n_sc * n_sym * U * llr_bits
+        offs["info"] += n_sc * Ceff
+    cfg = ffeq_batch_config(arch, precision, estimate, llr_bits, offs["h"], offs["y"], offs["z"], offs["s2"],
+                            offs["llr"], offs["info"] if with_info else 0)
+    return cfg, inst
 
 
 # --------------------------------------------------------------------- convenience

@@ -36,7 +36,7 @@ import dataclasses
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "noise_variance", "qam_levels", "exp_correlation"]
+__all__ = ["Problem", "make_problem", "make_uneven", "noise_variance", "qam_levels", "exp_correlation"]
 
 
 @dataclasses.dataclass
@@ -111,3 +111,27 @@ def make_problem(B: int, U: int, C: int, n_sc: int, n_sym: int, *, snr_db: float
     y = y.astype(np.complex64)
     return Problem(H=H, y=y, s=s, levels=levels, N0=N0, Es=float(Es), B=B, U=U, C=C,
                    n_sc=n_sc, n_sym=n_sym, bits=bits, snr_db=float(snr_db))
+
+
+def make_uneven(n_inst: int, *, seed: int = 0, U_range=(4, 32), B_choices=(64, 128, 256),
+                C_choices=(1, 2, 4, 8, 16), nsym_range=(1, 14), snr_range=(5.0, 20.0), bits: int = 4,
+                n_sc: int = 1, min_S: int = 4) -> list[Problem]:
+    """Draw ``n_inst`` independent problems of uneven size (one seeded stream for
+    the sizes, one ``make_problem`` seed per instance).
+
+    Per instance: U uniform on ``U_range`` (inclusive), B from ``B_choices``, C
+    from the ``C_choices`` that divide B with at least ``min_S`` antennas per
+    cluster, n_sym uniform on ``nsym_range`` (inclusive), SNR uniform on
+    ``snr_range`` dB, ``bits``-bit square QAM, i.i.d. CN(0, 1) channels.
+    """
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0x5EED])))
+    out = []
+    for i in range(n_inst):
+        U = int(g.integers(U_range[0], U_range[1] + 1))
+        B = int(g.choice(B_choices))
+        Cs = [c for c in C_choices if B % c == 0 and B // c >= min_S]
+        C = int(g.choice(Cs))
+        n_sym = int(g.integers(nsym_range[0], nsym_range[1] + 1))
+        snr = float(g.uniform(*snr_range))
+        out.append(make_problem(B, U, C, n_sc, n_sym, snr_db=snr, bits=bits, seed=seed * 1_000_003 + i))
+    return out

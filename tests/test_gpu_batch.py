@@ -1,0 +1,291 @@
+"""GPU parity of uneven batches (include/ffeq_batch.h) against the FP64 oracle.
+
+Every instance of a batch is checked on its own against ``oracle.lmmse``
+(``equalize_pd`` / ``equalize_fd`` on that instance's arrays) with the bounds of
+the uniform parity tests: per subcarrier, relative 2-norm error of z, sigma^2
+and the LLRs at most 1e-5 (FP32, TF32x3) or 2e-4 (BF16x3).  The uneven workload
+is 4096 instances with U uniform on 4..32, B in {64, 128, 256}, C in
+{1, 2, 4, 8, 16} (dividing B, at least 4 antennas per cluster), 1..14 OFDM
+symbols, SNR uniform on 5..20 dB, 16-QAM.  Launch shapes (pipeline depth, solve
+CTA width, lanes per row) must not change a single bit of the results, and a
+CUDA-graph replay must equal the eager call.
+
+Random uneven instances include ill-conditioned ones (FD with S = B/C < U:
+rank-deficient local Gram matrices, kappa(G_c + rho I) ~ lambda_max / rho in
+the hundreds), so each instance's bound is
+    max(flat bound, 2 u kappa),   kappa = max over its systems of cond_2(G_c + rho I),
+the first-order perturbation bound of a linear solve whose matrix and
+right-hand side carry relative errors u from the products that formed them:
+u = 2^-16 for BF16x3 (hi + lo pairs keep 16 significand bits; the dropped lo*lo
+term is 2^-18), 2^-21 for TF32x3 (22 bits, dropped term 2^-22) and 2^-22 for
+FP32 (2^-24 per product, summation over up to 256 antennas).
+
+The LLR bound is 4x the z bound.  Per bit the max-log LLR is affine in z with
+slope 2 |a_0 - a_1| / sigma^2 (a_0, a_1 the nearest levels with the bit 0 / 1),
+so its absolute error follows that of z, while its norm drops for symbols that
+sit near a decision threshold; among thousands of random instances a few have
+such subcarriers (worst seen: 1.04x the z bound, TF32x3, FD).
+"""
+import numpy as np
+import pytest
+
+from oracle import llr as ollr
+from oracle import lmmse
+from paper_1808_04473_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PREC_TOL = {0: 1e-5, 1: 1e-5, 2: 2e-4}      # FP32, TF32X3, BF16X3
+UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16}
+
+
+def _kappa(p, arch):
+    """Largest 2-norm condition number of the instance's systems (FP64)."""
+    rho = float(np.float32(p.N0)) / p.Es
+    parts = lmmse.partition(p.B, p.C) if arch == 1 else [(0, p.B)]
+    worst = 1.0
+    for k in range(p.n_sc):
+        Hm = p.H[k].astype(np.complex128).T
+        for (b0, b1) in parts:
+            Hc = Hm[b0:b1]
+            worst = max(worst, np.linalg.cond(Hc.conj().T @ Hc + rho * np.eye(p.U)))
+    return worst
+
+
+@pytest.fixture(scope="module")
+def ff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04473_gb300 import build as fbuild
+    from paper_1808_04473_gb300 import ffeq
+    fbuild.build()
+    ffeq.lib()
+    return ffeq
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    return synth.make_uneven(4096, seed=4)
+
+
+def _specs(ps):
+    return [(p.B, p.U, p.C, p.n_sc, p.n_sym, p.N0, p.Es) for p in ps]
+
+
+class Run:
+    """Device buffers of one packed batch and its plan."""
+
+    def __init__(self, ff, ps, arch, precision=0, estimate=0, llr_bits=4, with_info=True, specs=None):
+        dev = torch.device("cuda:0")
+        self.ff, self.ps, self.arch, self.bits = ff, ps, arch, llr_bits
+        cfg, inst = ff.pack_batch(specs or _specs(ps), arch=arch, precision=precision, estimate=estimate,
+                                  llr_bits=llr_bits, with_info=with_info)
+        self.cfg, self.inst = cfg, inst
+        H, y = _flat(ps, cfg, inst)
+        self.H = torch.from_numpy(H).to(dev)
+        self.y = torch.from_numpy(y).to(dev)
+        self.z = torch.full((max(1, cfg.z_elems),), complex("nan"), dtype=torch.complex64, device=dev)
+        self.s2 = torch.full((max(1, cfg.sigma2_elems),), float("nan"), dtype=torch.float32, device=dev)
+        self.llr = torch.full((max(1, cfg.llr_elems),), float("nan"), dtype=torch.float32, device=dev)
+        self.info = torch.full((max(1, cfg.info_elems),), -1, dtype=torch.int32, device=dev)
+        self.batch = ff.ffeq_batch_create(cfg, inst)
+        self.nb = ff.ffeq_batch_workspace_size(self.batch)
+        self.ws = torch.empty(max(self.nb, 256), dtype=torch.uint8, device=dev)
+
+    def args(self):
+        return (self.H, self.y, self.z, self.s2, self.llr if self.bits else None,
+                self.info if self.cfg.info_elems else None, self.ws, self.nb)
+
+    def equalize(self, stream=None):
+        self.ff.ffeq_batch_equalize(self.batch, *self.args(), stream=stream)
+
+    def host(self):
+        torch.cuda.synchronize()
+        return dict(z=self.z.cpu().numpy(), s2=self.s2.cpu().numpy(), llr=self.llr.cpu().numpy(),
+                    info=self.info.cpu().numpy())
+
+
+def _flat(ps, cfg, inst):
+    H = np.zeros(cfg.h_elems, np.complex64)
+    y = np.zeros(cfg.y_elems, np.complex64)
+    for p, it in zip(ps, inst):
+        H[it.h_off:it.h_off + p.H.size] = p.H.ravel()
+        y[it.y_off:it.y_off + p.y.size] = p.y.ravel()
+    return H, y
+
+
+def _rel_per_sc(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+
+
+def _check(run, out, estimate=0, precision=0, skip=()):
+    worst = 0.0
+    for idx, (p, it) in enumerate(zip(run.ps, run.inst)):
+        if idx in skip or p.n_sc == 0:
+            continue
+        tol = max(PREC_TOL[precision], 2.0 * UNIT[precision] * _kappa(p, run.arch))
+        f = lmmse.equalize_pd if run.arch == 0 else lmmse.equalize_fd
+        o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, "unbiased" if estimate == 0 else "literal")
+        n, U, NS = p.n_sc, p.U, p.n_sym
+        z = out["z"][it.z_off:it.z_off + n * NS * U].reshape(n, NS, U)
+        s2 = out["s2"][it.sigma2_off:it.sigma2_off + n * U].reshape(n, U)
+        ez = _rel_per_sc(z, o["z"]).max()
+        if p.N0 == 0:            # zero forcing: sigma^2 = 0 exactly (the FP64 oracle leaves ~1e-33)
+            assert (s2 == 0).all() and np.abs(o["sigma2"]).max() < 1e-20, (idx, s2[:2], o["sigma2"][:2])
+            es = 0.0
+        else:
+            es = _rel_per_sc(s2, o["sigma2"]).max()
+        assert ez <= tol and es <= tol, (idx, p.B, p.U, p.C, p.n_sym, ez, es)
+        if run.bits:
+            L = out["llr"][it.llr_off:it.llr_off + n * NS * U * run.bits].reshape(n, NS, U, run.bits)
+            if p.N0 == 0:                 # sigma^2 = 0: infinite LLRs, compare the decisions
+                assert (np.sign(L) == np.sign(ollr.maxlog_llr(o["z"], np.ones_like(o["sigma2"])[:, None, :],
+                                                               run.bits, p.Es))).all(), (idx, "llr signs")
+            else:
+                Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], run.bits, p.Es)
+                el = _rel_per_sc(L, Lo).max()
+                assert el <= 4 * tol, (idx, "llr", el)
+        if run.cfg.info_elems:
+            Ceff = p.C if run.arch == 1 else 1
+            info = out["info"][it.info_off:it.info_off + n * Ceff]
+            assert (info == 0).all(), (idx, info)
+        worst = max(worst, ez)
+    return worst
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_uneven_4096_fp32_matches_the_oracle(ff, uneven, arch):
+    run = Run(ff, uneven, arch, precision=0)
+    run.equalize()
+    assert ff.ffeq_device_status() == 0
+    _check(run, run.host(), precision=0)
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["TF32X3", "BF16X3"])
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_uneven_tensor_core_precisions(ff, uneven, arch, precision):
+    ps = uneven[:1024]
+    run = Run(ff, ps, arch, precision=precision)
+    run.equalize()
+    assert ff.ffeq_device_status() == 0
+    _check(run, run.host(), precision=precision)
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_literal_estimate_and_no_llr(ff, uneven, arch):
+    ps = uneven[:300]
+    run = Run(ff, ps, arch, estimate=1, llr_bits=0, with_info=False)
+    run.equalize()
+    _check(run, run.host(), estimate=1)
+
+
+def test_multi_subcarrier_instances_and_edge_shapes(ff):
+    """Several subcarriers per instance, an empty instance, odd B (plain-load
+    staging), U = 1, n_sym = 16, S < U, C = 3, Es != 1 and a noiseless one."""
+    shapes = [  # B, U, C, n_sc, n_sym, snr, Es
+        (64, 16, 4, 37, 14, 10.0, 1.0), (32, 4, 2, 0, 1, 10.0, 1.0), (48, 7, 3, 5, 3, 5.0, 2.0),
+        (16, 1, 1, 9, 2, 12.0, 1.0), (128, 32, 16, 3, 16, 20.0, 1.0), (256, 9, 8, 2, 1, 15.0, 0.5),
+        (96, 12, 12, 4, 5, 8.0, 1.0), (40, 5, 2, 6, 4, 10.0, 1.0)]
+    ps = [synth.make_problem(B, U, C, n, ns, snr_db=snr, bits=4, seed=100 + i, Es=Es)
+          for i, (B, U, C, n, ns, snr, Es) in enumerate(shapes)]
+    ps.append(synth.make_problem(64, 8, 2, 7, 3, bits=4, seed=7, noiseless=True))
+    for arch in (0, 1):
+        run = Run(ff, ps, arch)
+        run.equalize()
+        assert ff.ffeq_device_status() == 0
+        _check(run, run.host())
+    # Odd B stages with plain loads; odd offsets too.
+    odd = [synth.make_problem(B, U, C, 3, ns, bits=4, seed=200 + B) for (B, U, C, ns) in
+           [(33, 5, 3, 2), (63, 16, 7, 4), (17, 3, 1, 1)]]
+    for arch in (0, 1):
+        run = Run(ff, odd, arch)
+        run.equalize()
+        _check(run, run.host())
+
+
+def test_every_tuning_gives_identical_bits(ff, uneven):
+    ps = uneven[:512]
+    for arch in (0, 1):
+        run = Run(ff, ps, arch, precision=2)
+        run.equalize()
+        ref = run.host()
+        base = ff.ffeq_batch_get_tuning(run.batch)
+        tried = 0
+        for gi, (UP, stages, threads, lpr) in enumerate(base):
+            for st in (1, 2, 3):
+                for th in (64, 128, 256, 512):
+                    for lp in (1, 2):
+                        t = list(base)
+                        t[gi] = (UP, st, th, lp)
+                        try:
+                            ff.ffeq_batch_set_tuning(run.batch, t)
+                        except ff.FfeqError:
+                            continue
+                        run.z.fill_(complex("nan"))
+                        run.equalize()
+                        out = run.host()
+                        tried += 1
+                        for k in ("z", "s2", "llr", "info"):
+                            np.testing.assert_array_equal(out[k], ref[k], err_msg=f"{k} tuning {t}")
+            ff.ffeq_batch_set_tuning(run.batch, base)
+        assert tried >= 6
+
+
+def test_autotune_and_cuda_graph_replay(ff, uneven):
+    ps = uneven[:2048]
+    run = Run(ff, ps, 1, precision=2)
+    ff.ffeq_batch_autotune(run.batch, *run.args(), reps=3)
+    run.equalize()
+    ref = run.host()
+    _check(run, ref, precision=2)
+    # Capture on a side stream (the tables are already in the workspace).
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        run.equalize(stream=s)          # warm-up on the capture stream
+        s.synchronize()
+        run.z.fill_(complex("nan"))      # gaps between instances stay NaN, as in ref
+        run.s2.fill_(float("nan"))
+        with torch.cuda.graph(g, stream=s):
+            run.equalize(stream=s)
+    g.replay()
+    out = run.host()
+    for k in ("z", "s2", "llr", "info"):
+        np.testing.assert_array_equal(out[k], ref[k])
+    # New inputs of the same sizes and noise levels in the same buffers: the replay follows them.
+    ps2 = [synth.make_problem(p.B, p.U, p.C, p.n_sc, p.n_sym, snr_db=p.snr_db, bits=4, seed=50_000 + i)
+           for i, p in enumerate(ps)]
+    H2, y2 = _flat(ps2, run.cfg, run.inst)
+    run.H.copy_(torch.from_numpy(H2))
+    run.y.copy_(torch.from_numpy(y2))
+    g.replay()
+    out = run.host()
+    run.ps = ps2
+    _check(run, out, precision=2)
+
+
+def test_corrupted_descriptors_are_skipped_and_reported(ff):
+    """Descriptors overwritten in the workspace fail the device checks: the unit
+    is skipped, the status word says invalid argument, nothing else changes."""
+    ps = [synth.make_problem(64, 8, 2, 4, 2, bits=4, seed=s) for s in range(3)]
+    run = Run(ff, ps, 1)
+    run.equalize()
+    ref = run.host()
+    assert ff.ffeq_device_status() == 0
+    # Gram-order descriptors start 256 bytes into the workspace, 88 bytes each
+    # (seven int64 offsets, then B, U, Ceff, n_sym, N0, rho, llr_scale, inst).
+    # First unit: more users than the group's padding; second: channel offset past the end.
+    ws = run.ws.cpu().numpy()
+    ws[256 + 60:256 + 64].view(np.int32)[0] = 40
+    ws[256 + 88:256 + 96].view(np.int64)[0] = run.cfg.h_elems
+    run.ws.copy_(torch.from_numpy(ws))
+    run.z.fill_(complex("nan"))
+    run.equalize()
+    out = run.host()
+    assert ff.ffeq_device_status() == 1      # FFEQ_ERR_INVALID_ARG
+    # Solve-order descriptors are intact, so every z is still produced (from the
+    # stale Gram data of the skipped units, which the previous call left in place).
+    np.testing.assert_array_equal(out["z"], ref["z"])
