@@ -227,47 +227,60 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     aug[j] = v;
   }
 
-  // ---- Gauss-Jordan sweep
+  // ---- Gauss-Jordan sweep (deferred row scaling: every lane runs the same update)
   int fail = 0;
   if constexpr (LPR == 1) {
-    // Column-rotating form (ffeq_gj.cuh): afterwards aug[0..kNsymMax) = z (RHS
-    // block) and aug[kNsymMax + j] = A[i][j].
-    fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, g < nmat);
-  } else {
-  static_for<UP>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    const float piv = __shfl_sync(kFullMask, aug[k].x, k, GS);
-    const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
-    const bool ok = piv > 0.f;
-    if (!ok && fail == 0) fail = k + 1;
-    const float r = 1.f / (ok ? piv : 1.f);
-    if (i == k) {
+    // Paired form (ffeq_gj.cuh): afterwards columns [0, kNsymMax) = z (RHS block)
+    // and column kNsymMax + j = A[i][j].
+    float re[W], im[W];
 #pragma unroll
-      for (int j = 0; j < WH; ++j) aug[j] = (h == 0 && j == k) ? make_float2(r, 0.f) : cscale(aug[j], r);
-      if (g < nmat) {
+    for (int j = 0; j < W; ++j) {
+      re[j] = aug[j].x;
+      im[j] = aug[j].y;
+    }
+    fail = gj_sweep_pairs<UP, W>(re, im, reinterpret_cast<float*>(rowbuf), i, g < nmat);
+#pragma unroll
+    for (int j = 0; j < W; ++j) aug[j] = make_float2(re[j], im[j]);
+  } else {
+    // Two lanes per row, columns in place: the same element update as the paired
+    // form (gj_update), so both layouts give identical bits.
+    float my_r = 1.f;
+    static_for<UP>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const float piv = __shfl_sync(kFullMask, aug[k].x, k, GS);
+      const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
+      const bool ok = piv > 0.f;
+      if (!ok && fail == 0) fail = k + 1;
+      const float r = 1.f / (ok ? piv : 1.f);
+      const bool me = i == k;
+      if (me) my_r = r;
+      const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(f.x * r, f.y * r);
+      if (me && g < nmat) {
 #pragma unroll
         for (int j = 0; j < WH; j += 2)
           if (h * WH + j < UP + NS)
             *reinterpret_cast<float4*>(rowbuf + h * WH + j) =
-                make_float4(aug[j].x, aug[j].y, aug[j + 1].x, aug[j + 1].y);
+                make_float4((h == 0 && j == k) ? 1.f : aug[j].x, (h == 0 && j == k) ? 0.f : aug[j].y,
+                            (h == 0 && j + 1 == k) ? 1.f : aug[j + 1].x, (h == 0 && j + 1 == k) ? 0.f : aug[j + 1].y);
       }
-    }
-    __syncwarp();
-    if (i != k) {
+      __syncwarp();
+      const float dlt = me ? 1.f : 0.f;
       const float2* rb = rowbuf + h * WH;
 #pragma unroll
       for (int j = 0; j < WH; j += 2) {
         if (h * WH + j < UP + NS) {
           const float4 q = *reinterpret_cast<const float4*>(rb + j);
-          aug[j] = (h == 0 && j == k) ? make_float2(-f.x * r, -f.y * r) : cfms(f, make_float2(q.x, q.y), aug[j]);
-          aug[j + 1] = (h == 0 && j + 1 == k) ? make_float2(-f.x * r, -f.y * r)
-                                              : cfms(f, make_float2(q.z, q.w), aug[j + 1]);
+          const float2 b0 = (h == 0 && j == k) ? make_float2(dlt, 0.f) : aug[j];
+          const float2 b1 = (h == 0 && j + 1 == k) ? make_float2(dlt, 0.f) : aug[j + 1];
+          aug[j] = gj_update(gg, make_float2(q.x, q.y), b0);
+          aug[j + 1] = gj_update(gg, make_float2(q.z, q.w), b1);
         }
       }
-    }
-    __syncwarp();
-  });
-
+      __syncwarp();
+    });
+    // Deferred scaling: row i times 1/p_i (both halves of row i recorded it at step i).
+#pragma unroll
+    for (int j = 0; j < WH; ++j) aug[j] = cscale(aug[j], my_r);
   }
 
   // ---- fusion terms of this matrix: A_ii on the first-half lane of row i

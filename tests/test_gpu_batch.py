@@ -289,3 +289,17 @@ def test_corrupted_descriptors_are_skipped_and_reported(ff):
     # Solve-order descriptors are intact, so every z is still produced (from the
     # stale Gram data of the skipped units, which the previous call left in place).
     np.testing.assert_array_equal(out["z"], ref["z"])
+
+
+def test_tuning_cache_roundtrip(ff, uneven, tmp_path):
+    from paper_1808_04473_gb300 import tuning
+    ps = uneven[:256]
+    path = str(tmp_path / "tuning.json")
+    a = Run(ff, ps, 0, precision=2)
+    t1, cached1 = tuning.autotune_cached(a.batch, *a.args(), reps=2, path=path)
+    assert not cached1
+    b = Run(ff, ps, 0, precision=2)
+    t2, cached2 = tuning.autotune_cached(b.batch, *b.args(), reps=2, path=path)
+    assert cached2 and t2 == t1
+    b.equalize()
+    _check(b, b.host(), precision=2)
