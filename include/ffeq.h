@@ -170,6 +170,26 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
                                    const float* nu, const void* gz, void* gH, void* gy, float* grho,
                                    float* gnu, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Launch shape of a plan's contraction kernel (the arithmetic is that of the
+ * plan's precision in every shape; with split-K (PD) the shapes differ in how
+ * the antennas are split among warps, hence in summation order only):
+ *   values[0]  0 = default (1), 1 = 16 warps, one CTA per SM,
+ *              2 = 8 warps, two CTAs per SM (half the shared memory each),
+ *              3 = BF16X3 only: each staged subcarrier converted once into BF16
+ *                  hi/lo planes read with ldmatrix (needs B and B/C multiples of 4);
+ *   values[1]  subcarriers staged ahead per CTA, 1..3, or 0 = as many as fit.
+ * ffeq_plan_set_tuning takes exactly 2 values and returns FFEQ_ERR_UNSUPPORTED
+ * when the shape does not apply to or fit the problem (plan unchanged);
+ * ffeq_plan_get_tuning writes min(n, 2) values.  ffeq_plan_autotune times every
+ * shape and depth that fits with `reps` calls of ffeq_equalize on the given
+ * buffers (CUDA events on `stream`; arguments as for ffeq_equalize), keeps the
+ * fastest, synchronizes the stream and must not run during stream capture. */
+ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n);
+ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n);
+ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
+                               float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
+                               void* stream, int reps);
+
 /* Device staging bytes ffeq_equalize_host needs (inputs, outputs and workspace). */
 ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes);
 

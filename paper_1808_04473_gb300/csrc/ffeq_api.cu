@@ -12,6 +12,8 @@ struct ffeq_plan {
   ffeq_problem p;
   int Ceff;              // clusters kept apart: C (FD) or 1 (PD: summed on chip)
   size_t workspace;      // bytes of the [n_sc][Ceff][U+n_sym][U] complex workspace
+  int gram_variant = 0;  // contraction launch shape (0: default)
+  int gram_stages = 0;   // staged units per CTA (0: as many as fit)
 };
 
 namespace {
@@ -132,7 +134,7 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.n_sc = p.n_sc;
   gp.n_sym = p.n_sym;
   gp.bulk = (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
-  ffeq::gram_configure(gp, p.precision);
+  if (!ffeq::gram_configure(gp, p.precision, plan->gram_variant, plan->gram_stages)) return FFEQ_ERR_UNSUPPORTED;
   const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                                  : ffeq::launch_gram_tc(gp, p.precision, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
@@ -307,6 +309,81 @@ ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes) {
   *bytes = align_up(s.H) + align_up(s.y) + align_up(s.z) + align_up(s.s2) + align_up(s.llr) +
            align_up(s.info) + align_up(ws);
   return FFEQ_OK;
+}
+
+ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n) {
+  if (!plan || n < 0 || (n > 0 && !values)) return FFEQ_ERR_INVALID_ARG;
+  const int v[2] = {plan->gram_variant, plan->gram_stages};
+  for (int i = 0; i < n && i < 2; ++i) values[i] = v[i];
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
+  if (!plan || n != 2 || !values) return FFEQ_ERR_INVALID_ARG;
+  if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGramPresplit || values[1] < 0 || values[1] > 3)
+    return FFEQ_ERR_INVALID_ARG;
+  // The shape must fit the problem with 16-byte aligned rows (the bulk-staged case).
+  ffeq::GramParams gp{};
+  gp.B = plan->p.B;
+  gp.U = plan->p.U;
+  gp.Ceff = plan->Ceff;
+  gp.n_sc = plan->p.n_sc;
+  gp.n_sym = plan->p.n_sym;
+  gp.bulk = plan->p.B % 2 == 0;
+  if (!ffeq::gram_configure(gp, plan->p.precision, values[0], values[1])) return FFEQ_ERR_UNSUPPORTED;
+  plan->gram_variant = values[0];
+  plan->gram_stages = values[1];
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
+                               float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
+                               void* stream, int reps) {
+  if (!plan || reps < 1) return FFEQ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (cap != cudaStreamCaptureStatusNone) return FFEQ_ERR_INVALID_ARG;
+  if (plan->p.n_sc == 0) return FFEQ_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e);
+  }
+  const int old[2] = {plan->gram_variant, plan->gram_stages};
+  float best = -1.f;
+  int best_v[2] = {old[0], old[1]};
+  ffeq_status s = FFEQ_OK;
+  for (int variant = ffeq::kGram16; variant <= ffeq::kGramPresplit && s == FFEQ_OK; ++variant) {
+    for (int stages = 1; stages <= 3 && s == FFEQ_OK; ++stages) {
+      const int v[2] = {variant, stages};
+      if (ffeq_plan_set_tuning(plan, v, 2) != FFEQ_OK) continue;
+      // One untimed call, then `reps` timed calls of the whole equalization.
+      s = ffeq_equalize(plan, H, y, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream);
+      if (s != FFEQ_OK) break;
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { s = cuda_fail(e); break; }
+      for (int r = 0; r < reps && s == FFEQ_OK; ++r)
+        s = ffeq_equalize(plan, H, y, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream);
+      if (s != FFEQ_OK) break;
+      float ms = 0.f;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        s = cuda_fail(e);
+        break;
+      }
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_v[0] = variant;
+        best_v[1] = stages;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->gram_variant = s == FFEQ_OK ? best_v[0] : old[0];
+  plan->gram_stages = s == FFEQ_OK ? best_v[1] : old[1];
+  return s;
 }
 
 ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const void* y_host, float N0, float Es,

@@ -148,9 +148,11 @@ ffeq_status validate_instance(const ffeq_batch_config& cfg, const ffeq_instance&
   if (cfg.info_elems > 0 && !in_range(in.info_off, nsc * Ceff, cfg.info_elems)) return FFEQ_ERR_INVALID_ARG;
   const int UP = ffeq::padded_users(in.U);
   if (Ceff > ffeq::kTileSlots || Ceff * UP > 512) return FFEQ_ERR_UNSUPPORTED;
-  int st = 0, sl = 0, ns = 0;
-  ffeq::gram_instance_capacity(cfg.precision, in.B, in.U, in.n_sym, static_cast<int>(Ceff), st, sl, ns);
-  if (ffeq::gram_stages_fit_bytes(st, static_cast<size_t>(ns) * sl * 8, false) < 1) return FFEQ_ERR_UNSUPPORTED;
+  const ffeq::GramCaps gc =
+      ffeq::gram_instance_caps(cfg.precision, in.B, in.U, in.n_sym, static_cast<int>(Ceff), ffeq::kGram16);
+  if (ffeq::gram_stages_fit_bytes(gc.stage_elems, static_cast<size_t>(gc.slots) * gc.slot_elems * 8, false,
+                                  ffeq::gram_smem_budget(ffeq::kGram16)) < 1)
+    return FFEQ_ERR_UNSUPPORTED;
   return FFEQ_OK;
 }
 
@@ -223,6 +225,7 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
   b->n_units = static_cast<long long>(b->units.size());
   b->d_elems = d_off;
 
+  const size_t kBudget = ffeq::gram_smem_budget(ffeq::kGram16);
   // Groups: users padded to 8/16/32; within one, instances by decreasing
   // staged size, split where the combined shared-memory capacities stop fitting.
   for (int UP : {8, 16, 32}) {
@@ -232,7 +235,11 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
     std::vector<int> st(n_inst), sl(n_inst), ns(n_inst);
     for (int i : ids) {
       const int Ceff = cfg->arch == FFEQ_FD ? inst[i].C : 1;
-      ffeq::gram_instance_capacity(cfg->precision, inst[i].B, inst[i].U, inst[i].n_sym, Ceff, st[i], sl[i], ns[i]);
+      const ffeq::GramCaps gc = ffeq::gram_instance_caps(cfg->precision, inst[i].B, inst[i].U, inst[i].n_sym, Ceff,
+                                                         ffeq::kGram16);
+      st[i] = gc.stage_elems;
+      sl[i] = gc.slot_elems;
+      ns[i] = gc.slots;
       // Slots are sized for the group's padded users (the kernel's slot stride).
       sl[i] = ((inst[i].U + inst[i].n_sym) * (UP + 1) + 1) & ~1;
     }
@@ -254,7 +261,7 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
         const int cst = std::max(g.stage_elems, st[i]);
         const int csl = ns[i] > 0 ? std::max(g.slot_elems, sl[i]) : g.slot_elems;
         const int cns = std::max(g.n_slots, ns[i]);
-        const int fit = ffeq::gram_stages_fit_bytes(cst, static_cast<size_t>(cns) * csl * 8, true);
+        const int fit = ffeq::gram_stages_fit_bytes(cst, static_cast<size_t>(cns) * csl * 8, true, kBudget);
         if (members.empty()) target = std::min(2, fit);
         else if (fit < target) break;
         g.stage_elems = cst;
@@ -266,7 +273,7 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
         if ((inst[i].B & 1) || (inst[i].h_off & 1) || (inst[i].y_off & 1)) g.bulk_ok = false;
       }
       g.max_stages = ffeq::gram_stages_fit_bytes(g.stage_elems, static_cast<size_t>(g.n_slots) * g.slot_elems * 8,
-                                                 true);
+                                                 true, kBudget);
       g.first = static_cast<long long>(b->gram_order.size());
       std::vector<long long> us;
       for (int i : members)
@@ -447,6 +454,7 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
     gp.queue = reinterpret_cast<int*>(ws) + gi;
     gp.UP = g.UP;
     gp.lim = lim;
+    gp.variant = ffeq::kGram16;
     e = b->cfg.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                       : ffeq::launch_gram_tc(gp, b->cfg.precision, st);
     if (e != cudaSuccess) return cuda_status(e);

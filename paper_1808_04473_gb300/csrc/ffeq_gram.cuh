@@ -44,6 +44,13 @@ __host__ __device__ inline GramSplit gram_split(int Ceff, int Mrows, int warps, 
   return g;
 }
 
+// Pre-split planes: each cluster's S antennas padded to SP = 16 * ceil(S / 16)
+// (whole 16-antenna k-steps, zero-filled), a row holds the Ceff segments plus 8
+// elements, so that rows are 16-byte aligned and ldmatrix reads of 8 rows fall
+// in distinct bank groups (the row stride is an odd multiple of 16 bytes).
+__host__ __device__ inline int presplit_seg(int B, int Ceff) { return ((B / Ceff + 15) / 16) * 16; }
+__host__ __device__ inline int presplit_row(int B, int Ceff) { return Ceff * presplit_seg(B, Ceff) + 8; }
+
 // One unit of work: a subcarrier of a uniform problem, or one descriptor of an
 // uneven batch (sizes and pointers from the descriptor, checked against the
 // group's shared-memory capacities and the buffers' extents).
@@ -72,7 +79,10 @@ __device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int wa
            span_ok(d.h_off, static_cast<long long>(u.U) * u.B, p.lim.h) &&
            span_ok(d.y_off, static_cast<long long>(u.NS) * u.B, p.lim.y) &&
            span_ok(d.d_off, static_cast<long long>(u.Ceff) * Mrows * u.U, p.lim.d) &&
-           (!p.bulk || ((u.B & 1) == 0 && (d.h_off & 1) == 0 && (d.y_off & 1) == 0));
+           (!p.bulk || ((u.B & 1) == 0 && (d.h_off & 1) == 0 && (d.y_off & 1) == 0)) &&
+           (p.plane_bytes == 0 ||
+            ((u.B & 3) == 0 && ((u.B / u.Ceff) & 3) == 0 &&
+             4ll * Mrows * presplit_row(u.B, u.Ceff) * 2 <= static_cast<long long>(p.plane_bytes)));
     }
     u.ok = ok;
     u.H = p.H + d.h_off; u.y = p.y + d.y_off; u.D = p.D + d.d_off;
@@ -116,7 +126,7 @@ __device__ __forceinline__ int gram_next(const GramParams& p, int t, int nst) {
 // one warp's share of D over antennas [k0, k1) and hands each (m, u) entry to
 // the output functor.
 template <int UP, class Contract, bool BATCH>
-__global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const GramParams p) {
+__global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) gram_kernel(const GramParams p) {
   constexpr int kWarps = Contract::kWarps;
   constexpr int kThreads = kWarps * 32;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -128,6 +138,8 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const Gr
   const int stageSize = p.stage_elems;         // capacity of one stage (float2)
   float2* slots = stage0 + nst * stageSize;    // split-K partials (only when P > 1)
   const int slotSize = p.slot_elems;           // capacity of one partial slot (float2)
+  // Pre-split planes (Contract::kPrep): [4][Mrows][PS] bf16 after the slots.
+  uint16_t* planes = reinterpret_cast<uint16_t*>(slots + static_cast<size_t>(p.n_slots) * slotSize);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_units = p.n_units;
   constexpr bool kSM = Contract::kSplitM;
@@ -184,54 +196,82 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, 1) gram_kernel(const Gr
       }
       __syncthreads();
     }
+    // Issue the unit that follows into stage s (its data are no longer read).
+    auto issue_next = [&]() {
+      if constexpr (BATCH) {
+        if (warp == 0) {
+          const int tn = lane == 0 ? gram_next(p, t, nst) : 0;
+          const int tnb = __shfl_sync(kFullMask, tn, 0);
+          if (lane == 0) ring[s] = tnb;
+          if (p.bulk) {
+            if (tnb < n_units) {
+              const GramUnit wn = gram_unit<BATCH>(p, tnb, kWarps, kSM);
+              if (!wn.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+              issue_rows(wn, Ws, &full[s], lane);
+            } else if (lane == 0) {
+              mbar_arrive(&full[s]);
+            }
+          }
+        }
+      } else {
+        // Uniform: a unit past the end is never waited on, so no arrival is needed.
+        const int tn = t + nst * gridDim.x;
+        if (p.bulk && warp == 0 && tn < n_units)
+          issue_rows(gram_unit<BATCH>(p, tn, kWarps, kSM), Ws, &full[s], lane);
+      }
+    };
+    int SP = 0, PS = 0;
+    if constexpr (Contract::kPrep) {
+      // Convert the staged rows once into hi/lo BF16 planes; the stage is then free.
+      SP = presplit_seg(B, Ceff);
+      PS = presplit_row(B, Ceff);
+      if (w.ok) Contract::prep(Ws, RS, Mrows, B, Ceff, planes, PS, SP, tid, kThreads);
+      __syncthreads();
+      issue_next();
+    }
     float2* Dk = w.D;
     for (int item = warp; item < nItems; item += kWarps) {
       const int mt = kSM ? item % nM : -1;
       const int rest = item / nM;
       const int part = rest % P, c = rest / P;
-      const int k0 = c * S + (part * S) / P, k1 = c * S + ((part + 1) * S) / P;
+      int k0, k1;
+      if constexpr (Contract::kPrep) {
+        // Plane columns of cluster c, split at whole 16-antenna steps.
+        const int nK = SP / 16;
+        k0 = c * SP + ((part * nK) / P) * 16;
+        k1 = c * SP + (((part + 1) * nK) / P) * 16;
+      } else {
+        k0 = c * S + (part * S) / P;
+        k1 = c * S + ((part + 1) * S) / P;
+      }
+      auto contract = [&](auto&& out) {
+        if constexpr (Contract::kPrep) {
+          Contract::template run<UP>(planes, PS, Mrows, U, k0, k1, lane, mt, out);
+        } else {
+          Contract::template run<UP>(Ws, RS, Mrows, U, k0, k1, vec, lane, mt, out);
+        }
+      };
       if (P == 1) {
         float2* Dc = Dk + c * matSize;
-        Contract::template run<UP>(Ws, RS, Mrows, U, k0, k1, vec, lane, mt,
-                                   [&](int m, int u, float2 v0, float2 v1, bool has1) {
-                                     float2* d = Dc + m * U + u;
-                                     if (has1 && (U & 1) == 0) {
-                                       *reinterpret_cast<float4*>(d) = make_float4(v0.x, v0.y, v1.x, v1.y);
-                                     } else {
-                                       d[0] = v0;
-                                       if (has1) d[1] = v1;
-                                     }
-                                   });
+        contract([&](int m, int u, float2 v0, float2 v1, bool has1) {
+          float2* d = Dc + m * U + u;
+          if (has1 && (U & 1) == 0) {
+            *reinterpret_cast<float4*>(d) = make_float4(v0.x, v0.y, v1.x, v1.y);
+          } else {
+            d[0] = v0;
+            if (has1) d[1] = v1;
+          }
+        });
       } else {
         float2* slot = slots + (c * P + part) * slotSize;
-        Contract::template run<UP>(Ws, RS, Mrows, U, k0, k1, vec, lane, mt,
-                                   [&](int m, int u, float2 v0, float2 v1, bool has1) {
-                                     slot[m * SU + u] = v0;
-                                     if (has1) slot[m * SU + u + 1] = v1;
-                                   });
+        contract([&](int m, int u, float2 v0, float2 v1, bool has1) {
+          slot[m * SU + u] = v0;
+          if (has1) slot[m * SU + u + 1] = v1;
+        });
       }
     }
-    __syncthreads();   // stage s (and, with split K, the partial slots) complete; ring[s] read by all
-    if constexpr (BATCH) {
-      if (warp == 0) {
-        const int tn = lane == 0 ? gram_next(p, t, nst) : 0;
-        const int tnb = __shfl_sync(kFullMask, tn, 0);
-        if (lane == 0) ring[s] = tnb;
-        if (p.bulk) {
-          if (tnb < n_units) {
-            const GramUnit wn = gram_unit<BATCH>(p, tnb, kWarps, kSM);
-            if (!wn.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
-            issue_rows(wn, Ws, &full[s], lane);
-          } else if (lane == 0) {
-            mbar_arrive(&full[s]);
-          }
-        }
-      }
-    } else {
-      // Uniform: a unit past the end is never waited on, so no arrival is needed.
-      const int tn = t + nst * gridDim.x;
-      if (p.bulk && warp == 0 && tn < n_units) issue_rows(gram_unit<BATCH>(p, tn, kWarps, kSM), Ws, &full[s], lane);
-    }
+    __syncthreads();   // stage s / planes (and, with split K, the partial slots) complete; ring[s] read by all
+    if constexpr (!Contract::kPrep) issue_next();
     if (P > 1 && w.ok) {
       // Fixed-order reduction of the K-parts, written coalesced to the workspace.
       for (int e = tid; e < Ceff * matSize; e += kThreads) {
@@ -263,10 +303,11 @@ void gram_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slo
 }
 
 // Stages that fit for the given capacities (0 when one unit does not fit).
-inline int gram_stages_fit(size_t stage_elems, size_t slot_bytes_total, bool bulk) {
+inline int gram_stages_fit(size_t stage_elems, size_t slot_bytes_total, bool bulk,
+                           size_t smem_budget = kGramSmemBudget) {
   const size_t stage = stage_elems * 8;
-  if (slot_bytes_total + kGramHeaderBytes >= kGramSmemBudget) return 0;
-  const size_t budget = kGramSmemBudget - kGramHeaderBytes - slot_bytes_total;
+  if (slot_bytes_total + kGramHeaderBytes >= smem_budget) return 0;
+  const size_t budget = smem_budget - kGramHeaderBytes - slot_bytes_total;
   if (stage > budget) return 0;
   const size_t fit = budget / stage;
   if (!bulk) return 1;
@@ -282,7 +323,7 @@ int gram_stages_for(int B, int U, int n_sym, int Ceff, bool bulk) {
 
 inline size_t gram_smem_bytes(const GramParams& p) {
   return kGramHeaderBytes + static_cast<size_t>(p.stages) * p.stage_elems * 8 +
-         static_cast<size_t>(p.n_slots) * p.slot_elems * 8;
+         static_cast<size_t>(p.n_slots) * p.slot_elems * 8 + static_cast<size_t>(p.plane_bytes);
 }
 
 // Launch on min(n_sc, #SMs) persistent CTAs.
@@ -304,7 +345,7 @@ cudaError_t launch_gram_up(const GramParams& p, size_t smem, cudaStream_t stream
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
-  const int sms = dev < 64 ? num_sms[dev] : 152;
+  const int sms = (dev < 64 ? num_sms[dev] : 152) * Contract::kMinBlocks;
   int grid = p.n_units < sms ? p.n_units : sms;
   if (p.grid_cap > 0 && grid > p.grid_cap) grid = p.grid_cap;
   if (p.desc) {

@@ -80,10 +80,13 @@ __device__ __forceinline__ void simt_tiles(const float2* __restrict__ Ws, int RS
   }
 }
 
-// Contraction policy for gram_kernel: CUDA-core FP32.
+// Contraction policy for gram_kernel: CUDA-core FP32 (MINB CTAs per SM).
+template <int MINB>
 struct SimtFp32 {
   static constexpr int kWarps = 8;
+  static constexpr int kMinBlocks = MINB;
   static constexpr bool kSplitM = false;
+  static constexpr bool kPrep = false;
   template <int UP, typename Out>
   __device__ __forceinline__ static void run(const float2* __restrict__ Ws, int RS, int Mrows, int U, int k0,
                                              int k1, bool vec, int lane, int /*mt*/, Out out) {
@@ -95,41 +98,74 @@ struct SimtFp32 {
 
 int padded_users(int U) { return U <= 8 ? 8 : (U <= 16 ? 16 : 32); }
 
-void gram_instance_capacity(int precision, int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems,
-                            int& slots) {
-  if (precision == FFEQ_FP32) {
-    gram_capacity<SimtFp32>(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
-  } else {
-    gram_tc_capacity(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
-  }
+bool gram_presplit_eligible(int precision, int B, int Ceff) {
+  return precision == FFEQ_BF16X3 && B % 4 == 0 && Ceff > 0 && B % Ceff == 0 && (B / Ceff) % 4 == 0;
 }
 
-int gram_stages_fit_bytes(size_t stage_elems, size_t slot_bytes_total, bool bulk) {
-  return gram_stages_fit(stage_elems, slot_bytes_total, bulk);
+size_t gram_smem_budget(int variant) {
+  // Two CTAs per SM share 228 KB, less 1 KB reserved per CTA.
+  return variant == kGram8x2 ? 113 * 1024 : kGramSmemBudget;
+}
+
+GramCaps gram_instance_caps(int precision, int B, int U, int n_sym, int Ceff, int variant) {
+  if (precision == FFEQ_FP32) {
+    GramCaps c{};
+    if (variant == kGram8x2) gram_capacity<SimtFp32<2>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+    else gram_capacity<SimtFp32<1>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+    return c;
+  }
+  return gram_tc_caps(B, U, n_sym, Ceff, variant);
+}
+
+int gram_stages_fit_bytes(size_t stage_elems, size_t fixed_bytes, bool bulk, size_t budget) {
+  return gram_stages_fit(stage_elems, fixed_bytes, bulk, budget);
 }
 
 int gram_stages(int precision, int B, int U, int n_sym, int Ceff, bool bulk) {
-  int st, sl, ns;
-  gram_instance_capacity(precision, B, U, n_sym, Ceff, st, sl, ns);
-  return gram_stages_fit(st, static_cast<size_t>(ns) * sl * 8, bulk);
+  const GramCaps c = gram_instance_caps(precision, B, U, n_sym, Ceff, kGram16);
+  return gram_stages_fit(c.stage_elems, static_cast<size_t>(c.slots) * c.slot_elems * 8, bulk);
 }
 
-void gram_configure(GramParams& p, int precision) {
-  gram_instance_capacity(precision, p.B, p.U, p.n_sym, p.Ceff, p.stage_elems, p.slot_elems, p.n_slots);
-  p.stages = gram_stages_fit(p.stage_elems, static_cast<size_t>(p.n_slots) * p.slot_elems * 8, p.bulk != 0);
+bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   p.n_units = p.n_sc;
   p.desc = nullptr;
   p.queue = nullptr;
   p.UP = padded_users(p.U);
   p.lim = BatchLimits{};
+  p.grid_cap = 0;
+  if (variant == kGramAuto) variant = kGram16;
+  if (variant != kGram16 && variant != kGram8x2 && variant != kGramPresplit) return false;
+  if (variant == kGramPresplit && !gram_presplit_eligible(precision, p.B, p.Ceff)) return false;
+  if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes
+    if (variant == kGramPresplit) variant = kGram16;
+    stages = 0;
+  }
+  const GramCaps c = gram_instance_caps(precision, p.B, p.U, p.n_sym, p.Ceff, variant);
+  const int fit = gram_stages_fit(c.stage_elems, static_cast<size_t>(c.slots) * c.slot_elems * 8 + c.plane_bytes,
+                                  p.bulk != 0, gram_smem_budget(variant));
+  if (fit < 1 || stages > fit) return false;
+  p.stage_elems = c.stage_elems;
+  p.slot_elems = c.slot_elems;
+  p.n_slots = c.slots;
+  p.plane_bytes = c.plane_bytes;
+  p.stages = stages > 0 ? stages : fit;
+  p.variant = variant;
+  return true;
 }
 
 cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream) {
   const size_t smem = gram_smem_bytes(p);
+  if (p.variant == kGram8x2) {
+    switch (padded_users(p.U)) {
+      case 8: return launch_gram_up<8, SimtFp32<2>>(p, smem, stream);
+      case 16: return launch_gram_up<16, SimtFp32<2>>(p, smem, stream);
+      default: return launch_gram_up<32, SimtFp32<2>>(p, smem, stream);
+    }
+  }
   switch (padded_users(p.U)) {
-    case 8: return launch_gram_up<8, SimtFp32>(p, smem, stream);
-    case 16: return launch_gram_up<16, SimtFp32>(p, smem, stream);
-    default: return launch_gram_up<32, SimtFp32>(p, smem, stream);
+    case 8: return launch_gram_up<8, SimtFp32<1>>(p, smem, stream);
+    case 16: return launch_gram_up<16, SimtFp32<1>>(p, smem, stream);
+    default: return launch_gram_up<32, SimtFp32<1>>(p, smem, stream);
   }
 }
 

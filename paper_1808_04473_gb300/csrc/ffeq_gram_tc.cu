@@ -230,9 +230,11 @@ __device__ __forceinline__ void tc_tiles(const float2* __restrict__ Ws, int RS, 
   }
 }
 
-template <int MODE>
+template <int MODE, int WARPS = 16, int MINB = 1>
 struct TensorSplit {
-  static constexpr int kWarps = 16;
+  static constexpr bool kPrep = false;
+  static constexpr int kWarps = WARPS;
+  static constexpr int kMinBlocks = MINB;
   static constexpr bool kSplitM = true;
   template <int UP, typename Out>
   __device__ __forceinline__ static void run(const float2* __restrict__ Ws, int RS, int Mrows, int U, int k0,
@@ -241,24 +243,175 @@ struct TensorSplit {
   }
 };
 
-template <int MODE>
+// ---------------------------------------------------------------------------
+// Pre-split BF16x3.  The staged FP32 rows of a unit are converted once, by all
+// warps, into four BF16 planes [plane][row][PS]: re hi, re lo, im hi, im lo
+// (hi = x rounded to BF16, lo = the rounded remainder), cluster segments
+// padded with zeros to whole 16-antenna k-steps (presplit_seg).  Fragments then
+// come straight from the planes with ldmatrix: rows m of W = [H; Y] are the A
+// operand (16 x 16 tile: one ldmatrix.x4 per plane), rows u < U of the same
+// planes the B operand (two 8-user tiles per ldmatrix.x4).  The complex
+// product conj(h) w takes four real products,
+//   Re D = sum w_re h_re + w_im h_im,   Im D = sum w_im h_re + w_re (-h_im),
+// each split as A_lo B_hi + A_hi B_lo + A_hi B_hi (the lo*lo term is dropped),
+// with -h_im formed by flipping the BF16 sign bits (exact).  Compared with
+// splitting in registers per fragment, every staged element is converted once
+// per unit instead of once per warp that reads it, and a k-step costs 8-12
+// ldmatrix + 12 NX mma instead of ~160 load/convert instructions.
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+struct TensorSplitPre {
+  static constexpr bool kPrep = true;
+  static constexpr int kWarps = 16;
+  static constexpr int kMinBlocks = 1;
+  static constexpr bool kSplitM = true;
+
+  // Rows [0, Mrows) of the stage -> planes; four antennas per thread item.
+  __device__ __forceinline__ static void prep(const float2* __restrict__ Ws, int RS, int Mrows, int B, int Ceff,
+                                              uint16_t* __restrict__ planes, int PS, int SP, int tid, int nthr) {
+    const int S = B / Ceff;
+    const int qpc = SP / 4;              // quads per cluster segment (with padding)
+    const int quads = Ceff * qpc;
+    const int plane = Mrows * PS;
+    for (int e = tid; e < Mrows * quads; e += nthr) {
+      const int m = e / quads, qq = e - m * quads;
+      const int c = qq / qpc, a = (qq - c * qpc) * 4;
+      uint2 rh = make_uint2(0u, 0u), rl = rh, ih = rh, il = rh;
+      if (a < S) {
+        const float4* src = reinterpret_cast<const float4*>(Ws + m * RS + c * S + a);
+        const float4 v01 = src[0], v23 = src[1];
+        split_bf16(v01.x, v01.z, rh.x, rl.x);
+        split_bf16(v23.x, v23.z, rh.y, rl.y);
+        split_bf16(v01.y, v01.w, ih.x, il.x);
+        split_bf16(v23.y, v23.w, ih.y, il.y);
+      }
+      const int off = m * PS + c * SP + a;
+      *reinterpret_cast<uint2*>(planes + off) = rh;
+      *reinterpret_cast<uint2*>(planes + plane + off) = rl;
+      *reinterpret_cast<uint2*>(planes + 2 * plane + off) = ih;
+      *reinterpret_cast<uint2*>(planes + 3 * plane + off) = il;
+    }
+  }
+
+  // One warp: rows [16 mt, 16 mt + 16) of D over plane columns [k0, k1) (whole
+  // 16-steps), all UP users in NX = UP/8 tiles.
+  template <int UP, typename Out>
+  __device__ __forceinline__ static void run(const uint16_t* __restrict__ planes, int PS, int Mrows, int U, int k0,
+                                             int k1, int lane, int mt, Out out) {
+    constexpr int NX = UP / 8;
+    constexpr int NB = (NX + 1) / 2;     // ldmatrix loads per plane for the B tiles
+    const uint32_t pbytes = static_cast<uint32_t>(Mrows * PS) * 2u;
+    // A: lane -> matrix lane/8 (rows +8 for odd, k +8 for the upper two), row lane%8.
+    const int ar = 16 * mt + (lane & 7) + ((lane >> 3) & 1) * 8;
+    const uint32_t a_base = smem_u32(planes + (ar < Mrows ? ar : 0) * PS + ((lane >> 4) & 1) * 8);
+    // B: lane -> users 16 jb + (lane/16)*8 + lane%8, k +8 for odd matrices.
+    uint32_t b_base[NB];
+#pragma unroll
+    for (int jb = 0; jb < NB; ++jb) {
+      const int bn = jb * 16 + ((lane >> 4) & 1) * 8 + (lane & 7);
+      b_base[jb] = smem_u32(planes + (bn < U ? bn : 0) * PS + ((lane >> 3) & 1) * 8);
+    }
+    float are[NX][4], aim[NX][4];
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) are[j][q] = aim[j][q] = 0.f;
+
+    for (int k = k0; k < k1; k += 16) {
+      const uint32_t kb = static_cast<uint32_t>(k) * 2u;
+      uint32_t A[4][4];                  // plane: re hi, re lo, im hi, im lo
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) ldsm_x4(a_base + pl * pbytes + kb, A[pl][0], A[pl][1], A[pl][2], A[pl][3]);
+      uint32_t Bf[4][NX][2];
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) {
+#pragma unroll
+        for (int jb = 0; jb < NB; ++jb) {
+          if (2 * jb + 1 < NX) {
+            ldsm_x4(b_base[jb] + pl * pbytes + kb, Bf[pl][2 * jb][0], Bf[pl][2 * jb][1], Bf[pl][2 * jb + 1][0],
+                    Bf[pl][2 * jb + 1][1]);
+          } else {
+            ldsm_x2(b_base[jb] + pl * pbytes + kb, Bf[pl][2 * jb][0], Bf[pl][2 * jb][1]);
+          }
+        }
+      }
+      // Split products, issued one split term at a time over all accumulators.
+#pragma unroll
+      for (int prod = 0; prod < 3; ++prod) {
+        const int ah = prod == 0 ? 1 : 0;      // A_lo B_hi, A_hi B_lo, A_hi B_hi
+        const int bh = prod == 1 ? 1 : 0;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const uint32_t nb0 = Bf[2 + bh][j][0] ^ 0x80008000u, nb1 = Bf[2 + bh][j][1] ^ 0x80008000u;
+          mma_bf16(are[j], A[0 + ah], Bf[0 + bh][j][0], Bf[0 + bh][j][1]);   // w_re h_re
+          mma_bf16(aim[j], A[2 + ah], Bf[0 + bh][j][0], Bf[0 + bh][j][1]);   // w_im h_re
+          mma_bf16(are[j], A[2 + ah], Bf[2 + bh][j][0], Bf[2 + bh][j][1]);   // w_im h_im
+          mma_bf16(aim[j], A[0 + ah], nb0, nb1);                             // w_re (-h_im)
+        }
+      }
+    }
+    // c0: (g, 2t)  c1: (g, 2t+1)  c2: (g+8, 2t)  c3: (g+8, 2t+1)
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = 16 * mt + g + 8 * h;
+        const int u = j * 8 + 2 * t;
+        if (m < Mrows && u < U)
+          out(m, u, make_float2(are[j][2 * h], aim[j][2 * h]), make_float2(are[j][2 * h + 1], aim[j][2 * h + 1]),
+              u + 1 < U);
+      }
+    }
+  }
+};
+
+template <int MODE, int WARPS, int MINB>
 cudaError_t launch_mode(const GramParams& p, size_t smem, cudaStream_t stream) {
   switch (padded_users(p.U)) {
-    case 8: return launch_gram_up<8, TensorSplit<MODE>>(p, smem, stream);
-    case 16: return launch_gram_up<16, TensorSplit<MODE>>(p, smem, stream);
-    default: return launch_gram_up<32, TensorSplit<MODE>>(p, smem, stream);
+    case 8: return launch_gram_up<8, TensorSplit<MODE, WARPS, MINB>>(p, smem, stream);
+    case 16: return launch_gram_up<16, TensorSplit<MODE, WARPS, MINB>>(p, smem, stream);
+    default: return launch_gram_up<32, TensorSplit<MODE, WARPS, MINB>>(p, smem, stream);
   }
 }
 
 }  // namespace
 
-void gram_tc_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems, int& slots) {
-  gram_capacity<TensorSplit<kBf16x3>>(B, U, n_sym, Ceff, stage_elems, slot_elems, slots);
+GramCaps gram_tc_caps(int B, int U, int n_sym, int Ceff, int variant) {
+  GramCaps c{};
+  if (variant == kGram8x2) {
+    gram_capacity<TensorSplit<kBf16x3, 8, 2>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+  } else {
+    gram_capacity<TensorSplit<kBf16x3>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+  }
+  if (variant == kGramPresplit) c.plane_bytes = 4 * (U + n_sym) * presplit_row(B, Ceff) * 2;
+  return c;
 }
 
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream) {
   const size_t smem = gram_smem_bytes(p);
-  return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3>(p, smem, stream) : launch_mode<kBf16x3>(p, smem, stream);
+  if (precision == FFEQ_BF16X3 && p.variant == kGramPresplit && p.plane_bytes > 0) {
+    switch (padded_users(p.U)) {
+      case 8: return launch_gram_up<8, TensorSplitPre>(p, smem, stream);
+      case 16: return launch_gram_up<16, TensorSplitPre>(p, smem, stream);
+      default: return launch_gram_up<32, TensorSplitPre>(p, smem, stream);
+    }
+  }
+  if (p.variant == kGram8x2) {
+    return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3, 8, 2>(p, smem, stream)
+                                    : launch_mode<kBf16x3, 8, 2>(p, smem, stream);
+  }
+  return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3, 16, 1>(p, smem, stream)
+                                  : launch_mode<kBf16x3, 16, 1>(p, smem, stream);
 }
 
 }  // namespace ffeq

@@ -56,7 +56,14 @@ struct GramParams {
   int UP;             // batch: users padding of the group
   BatchLimits lim;    // batch: buffer extents
   int grid_cap;       // > 0: at most this many persistent CTAs
+  int plane_bytes;    // > 0: pre-split BF16 planes of this capacity (BF16x3 pre-split contraction)
+  int variant;        // contraction launch shape (kGram16 / kGram8x2 / kGramPresplit)
 };
+
+// Contraction launch shapes: 16 warps, one CTA per SM; 8 warps, two CTAs per SM
+// (half the shared memory each, so one CTA's MMA phase overlaps the other's
+// staging); BF16x3 pre-split planes (16 warps).
+constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3;
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
 struct SolveParams {
@@ -109,13 +116,25 @@ int padded_users(int U);
 // Subcarriers the contraction kernel of `precision` can stage ahead (0: one
 // subcarrier does not fit in shared memory).
 int gram_stages(int precision, int B, int U, int n_sym, int Ceff, bool bulk);
-void gram_tc_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems, int& slots);
-// Fill stage_elems / slot_elems / n_slots / stages of a uniform problem.
-void gram_configure(GramParams& p, int precision);
-// Capacities for an instance under `precision` (for batch sizing).
-void gram_instance_capacity(int precision, int B, int U, int n_sym, int Ceff, int& stage_elems, int& slot_elems,
-                            int& slots);
-int gram_stages_fit_bytes(size_t stage_elems, size_t slot_bytes_total, bool bulk);
+// Shared-memory capacities a contraction variant needs for one unit.
+struct GramCaps {
+  int stage_elems;   // one staged unit (float2)
+  int slot_elems;    // one split-K partial slot (float2)
+  int slots;         // partial slots
+  int plane_bytes;   // pre-split planes (0: variant without them)
+};
+// Whether the BF16x3 pre-split variant can take a unit (B and S multiples of 4).
+bool gram_presplit_eligible(int precision, int B, int Ceff);
+GramCaps gram_tc_caps(int B, int U, int n_sym, int Ceff, int variant);
+// Capacities of one unit under `precision` and launch shape `variant`.
+GramCaps gram_instance_caps(int precision, int B, int U, int n_sym, int Ceff, int variant);
+// Shared memory one CTA of `variant` may use.
+size_t gram_smem_budget(int variant);
+// Fill the capacities and stages of a uniform problem for `variant` (kGramAuto:
+// the default shape) and `stages` (0: as many as fit, at most 3).  Returns false
+// when the shape does not apply or does not fit.
+bool gram_configure(GramParams& p, int precision, int variant, int stages);
+int gram_stages_fit_bytes(size_t stage_elems, size_t fixed_bytes, bool bulk, size_t budget);
 cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream);
 // Tensor-core split-precision contraction (precision FFEQ_TF32X3 or FFEQ_BF16X3).
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream);

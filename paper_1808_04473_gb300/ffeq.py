@@ -75,6 +75,9 @@ _SIGS = {
     "ffeq_fd_train_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ffeq_equalize_noalloc": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
     "ffeq_device_status": ([ctypes.POINTER(_i), _i], _i),
+    "ffeq_plan_set_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
+    "ffeq_plan_get_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
+    "ffeq_plan_autotune": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _i], _i),
     "ffeq_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_batch_config), ctypes.POINTER(ffeq_instance),
                            _i], _i),
     "ffeq_batch_destroy": ([_vp], None),
@@ -230,6 +233,26 @@ def ffeq_equalize_noalloc(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr
     _check("ffeq_equalize_noalloc", lib().ffeq_equalize_noalloc(
         plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
         _stream(stream)))
+
+
+def ffeq_plan_set_tuning(plan: Plan, tuning) -> None:
+    """``tuning`` = (contraction shape, staged subcarriers); see include/ffeq.h."""
+    buf = (_i * 2)(*[int(v) for v in tuning])
+    _check("ffeq_plan_set_tuning", lib().ffeq_plan_set_tuning(plan.handle, buf, 2))
+
+
+def ffeq_plan_get_tuning(plan: Plan) -> tuple[int, int]:
+    buf = (_i * 2)()
+    _check("ffeq_plan_get_tuning", lib().ffeq_plan_get_tuning(plan.handle, buf, 2))
+    return (buf[0], buf[1])
+
+
+def ffeq_plan_autotune(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=None, info=None, workspace=None,
+                       workspace_bytes: int = 0, stream=None, reps: int = 10) -> tuple[int, int]:
+    _check("ffeq_plan_autotune", lib().ffeq_plan_autotune(
+        plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
+        _ptr(workspace), workspace_bytes, _stream(stream), int(reps)))
+    return ffeq_plan_get_tuning(plan)
 
 
 def ffeq_device_status(clear: bool = True) -> int:

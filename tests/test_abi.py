@@ -106,3 +106,22 @@ def test_oracle_and_cuda_sources_are_independent(repo_root):
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_plan_tuning_validation(built):
+    ff = ffeq
+    plan = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP32)
+    assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
+    for bad, status in (((4, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2)):    # pre-split needs BF16X3
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_set_tuning(plan, bad)
+        assert e.value.status == status, bad
+    assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
+    ff.ffeq_plan_set_tuning(plan, (2, 1))
+    assert ff.ffeq_plan_get_tuning(plan) == (2, 1)
+    # Too deep a pipeline for this problem: three 99 KB stages do not fit.
+    big = ff.ffeq_plan_create(256, 32, 16, 10, 16, arch=ff.FD, precision=ff.BF16X3)
+    with pytest.raises(ff.FfeqError) as e:
+        ff.ffeq_plan_set_tuning(big, (1, 3))
+    assert e.value.status == 2
+    ff.ffeq_plan_set_tuning(big, (3, 0))

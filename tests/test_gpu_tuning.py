@@ -1,0 +1,72 @@
+"""GPU parity of every launch shape of the uniform plan (include/ffeq.h tuning).
+
+Each contraction shape and pipeline depth that fits is run on the same inputs
+and checked against the FP64 oracle with the bounds of test_gpu_parity (1e-5
+FP32, 2e-4 BF16x3 per subcarrier).  (Shapes may split a cluster's antennas
+among a different number of warps, so results agree to rounding, not bit for
+bit.)  The autotuner returns a shape that fits.
+"""
+import numpy as np
+import pytest
+
+from oracle import lmmse
+from paper_1808_04473_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 2: 2e-4}
+
+
+@pytest.fixture(scope="module")
+def ff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04473_gb300 import build as fbuild
+    from paper_1808_04473_gb300 import ffeq
+    fbuild.build()
+    ffeq.lib()
+    return ffeq
+
+
+def _rel(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return (np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)).max()
+
+
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp32", "bf16x3"])
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+@pytest.mark.parametrize("shape", [(256, 16, 8, 300, 14), (128, 32, 16, 40, 16), (64, 8, 4, 77, 3)])
+def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
+    B, U, C, n_sc, n_sym = shape
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=12.0, bits=4, seed=B + U)
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(p.H).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    plan = ff.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=arch, precision=precision)
+    nb = ff.ffeq_workspace_size(plan)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    z = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev)
+    s2 = torch.empty((n_sc, U), dtype=torch.float32, device=dev)
+    f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
+    o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased")
+    results = {}
+    for variant in (1, 2, 3):
+        for stages in (0, 1, 2, 3):
+            try:
+                ff.ffeq_plan_set_tuning(plan, (variant, stages))
+            except ff.FfeqError as e:
+                assert e.status == 2
+                continue
+            z.fill_(complex("nan"))
+            ff.ffeq_equalize(plan, H, y, p.N0, p.Es, z, s2, None, None, ws, nb)
+            torch.cuda.synchronize()
+            zn = z.cpu().numpy()
+            assert _rel(zn, o["z"]) <= TOL[precision], (variant, stages)
+            assert _rel(s2.cpu().numpy(), o["sigma2"]) <= TOL[precision], (variant, stages)
+            results[(variant, stages)] = zn
+    assert any(k[0] == 1 for k in results)          # the default shape always fits
+    t = ff.ffeq_plan_autotune(plan, H, y, p.N0, p.Es, z, s2, None, None, ws, nb, reps=2)
+    assert t[0] in (1, 2, 3) and 1 <= t[1] <= 3
+    assert ff.ffeq_plan_get_tuning(plan) == t
