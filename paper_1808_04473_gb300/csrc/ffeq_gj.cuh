@@ -88,56 +88,59 @@ __device__ __forceinline__ float2 gj_update(float2 g, float2 q, float2 base) {
 // Same system and result layout as gj_sweep_rotating, held as separate real
 // and imaginary planes re[W], im[W] (lane i = row i).  At step k the pivot row
 // is broadcast UNSCALED (its pivot-column entry replaced by 1, the identity
-// column it turns into) and every other row does new = base - g q with
-// g = f / p_k (f its pivot-column entry; base its own value, or 0 in the pivot
-// column); the pivot row itself keeps its values (g = 0, pivot column 1).  A
-// row that has been the pivot row is thereby stored multiplied by its pivot
-// p_i, which later eliminations preserve (they are linear in the row); each
-// lane multiplies its row by 1/p_i once at the end.  This avoids scaling and
-// copying the pivot row inside the loop (a divergent path), and with rows in
-// planes each complex update is two paired FMAs on (column j, column j+1).
-// Two steps per loop trip (pivot columns 0 and 1) followed by a rotation by
-// two keeps the pairs aligned.  rowbuf: 2W floats (re plane, then im plane),
-// 16-byte aligned.  Returns the 1-based index of the first non-positive pivot,
-// or 0.
+// column it turns into) together with the pivot p_k, and every other row does
+// new = base - g q with g = f / p_k (f its pivot-column entry; base its own
+// value, or 0 in the pivot column); the pivot row itself keeps its values
+// (g = 0, pivot column 1).  A row that has been the pivot row is thereby stored
+// multiplied by its pivot p_i, which later eliminations preserve (they are
+// linear in the row); the caller multiplies the entries it uses by the returned
+// 1/p_i (`scale`).  This avoids scaling and copying the pivot row inside the loop
+// (a divergent path), and with rows in planes each complex update is two paired
+// FMAs on (column j, column j+1).  Two steps per loop trip (pivot columns 0 and
+// 1), each with its own broadcast buffer (one warp barrier per step), followed
+// by a rotation by two keep the pairs aligned.  rowbuf: 2 (2W + 4) floats, 16-byte
+// aligned.  Returns the 1-based index of the first non-positive pivot, or 0.
 template <int UP, int W>
-__device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], float* rowbuf, int i,
-                                              bool writer) {
+__device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], float* rowbuf, int i, bool writer,
+                                              float& scale) {
   static_assert(W % 4 == 0 && UP % 2 == 0, "paired sweep needs W % 4 == 0 and even UP");
+  constexpr int kBuf = 2 * W + 4;          // re plane, im plane, pivot (padded to 16 bytes)
   int fail = 0;
   float my_r = 1.f;
 #pragma unroll 1
   for (int k = 0; k < UP; k += 2) {
     static_for<2>([&](auto sc) {
       constexpr int s = decltype(sc)::value;   // pivot column of this step
+      float* buf = rowbuf + s * kBuf;
       const int kk = k + s;
-      const float piv = __shfl_sync(kFullMask, re[s], kk, UP);
-      const bool ok = piv > 0.f;
-      if (!ok && fail == 0) fail = kk + 1;
-      const float r = 1.f / (ok ? piv : 1.f);
       const bool me = i == kk;
-      if (me) my_r = r;
-      const float gr = me ? 0.f : re[s] * r;
-      const float gi = me ? 0.f : im[s] * r;
       if (me && writer) {
 #pragma unroll
         for (int j = 0; j < W; j += 4) {
-          *reinterpret_cast<float4*>(rowbuf + j) =
+          *reinterpret_cast<float4*>(buf + j) =
               make_float4(j + 0 == s ? 1.f : re[j + 0], j + 1 == s ? 1.f : re[j + 1], j + 2 == s ? 1.f : re[j + 2],
                           j + 3 == s ? 1.f : re[j + 3]);
-          *reinterpret_cast<float4*>(rowbuf + W + j) =
+          *reinterpret_cast<float4*>(buf + W + j) =
               make_float4(j + 0 == s ? 0.f : im[j + 0], j + 1 == s ? 0.f : im[j + 1], j + 2 == s ? 0.f : im[j + 2],
                           j + 3 == s ? 0.f : im[j + 3]);
         }
+        buf[2 * W] = re[s];
       }
       __syncwarp();
+      const float piv = buf[2 * W];
+      const bool ok = piv > 0.f;
+      if (!ok && fail == 0) fail = kk + 1;
+      const float r = __frcp_rn(ok ? piv : 1.f);
+      if (me) my_r = r;
+      const float gr = me ? 0.f : re[s] * r;
+      const float gi = me ? 0.f : im[s] * r;
       const float2 ngr = make_float2(-gr, -gr), pgi = make_float2(gi, gi), ngi = make_float2(-gi, -gi);
       const float dlt = me ? 1.f : 0.f;
       float nre[W], nim[W];
 #pragma unroll
       for (int j = 0; j < W; j += 4) {
-        const float4 qr = *reinterpret_cast<const float4*>(rowbuf + j);
-        const float4 qi = *reinterpret_cast<const float4*>(rowbuf + W + j);
+        const float4 qr = *reinterpret_cast<const float4*>(buf + j);
+        const float4 qi = *reinterpret_cast<const float4*>(buf + W + j);
 #pragma unroll
         for (int h = 0; h < 4; h += 2) {
           const int c = j + h;
@@ -162,14 +165,10 @@ __device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], fl
         re[j] = nre[j];
         im[j] = nim[j];
       }
-      __syncwarp();
     });
   }
-#pragma unroll
-  for (int j = 0; j < W; ++j) {
-    re[j] *= my_r;
-    im[j] *= my_r;
-  }
+  __syncwarp();   // the buffers may be reused after the sweep
+  scale = my_r;
   return fail;
 }
 

@@ -37,7 +37,8 @@ struct SolveLayout {
   // Per matrix: pivot-row broadcast buffer (UP + kNsymMax complex), fusion
   // numerators [kNsymMax][UP] complex and denominators [UP] floats; padded so
   // consecutive matrices start 64 bytes apart modulo 128.
-  static constexpr int kRow = UP + kNsymMax;
+  // (two broadcast buffers of 2W + 4 floats for the paired sweep, W = UP + kNsymMax)
+  static constexpr int kRow = 2 * (UP + kNsymMax) + 4;
   static constexpr int kNum = kNsymMax * UP;
   static constexpr int kMat = ((kRow + kNum + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
 };
@@ -238,9 +239,14 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
       re[j] = aug[j].x;
       im[j] = aug[j].y;
     }
-    fail = gj_sweep_pairs<UP, W>(re, im, reinterpret_cast<float*>(rowbuf), i, g < nmat);
+    float scl = 1.f;
+    fail = gj_sweep_pairs<UP, W>(re, im, reinterpret_cast<float*>(rowbuf), i, g < nmat, scl);
+    // Deferred scaling of the entries the epilogue reads: z (RHS block) and A_ii.
 #pragma unroll
-    for (int j = 0; j < W; ++j) aug[j] = make_float2(re[j], im[j]);
+    for (int j = 0; j < W; ++j) {
+      const bool used = j < kNsymMax || j == kNsymMax + i;
+      aug[j] = used ? make_float2(re[j] * scl, im[j] * scl) : make_float2(re[j], im[j]);
+    }
   } else {
     // Two lanes per row, columns in place: the same element update as the paired
     // form (gj_update), so both layouts give identical bits.
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
       const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
       const bool ok = piv > 0.f;
       if (!ok && fail == 0) fail = k + 1;
-      const float r = 1.f / (ok ? piv : 1.f);
+      const float r = __frcp_rn(ok ? piv : 1.f);
       const bool me = i == k;
       if (me) my_r = r;
       const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(f.x * r, f.y * r);
