@@ -94,6 +94,16 @@ typedef struct {
   int precision;   /* ffeq_precision */
   int estimate;    /* ffeq_estimate */
   int llr_bits;    /* 0 (no LLRs), 2, 4, 6 or 8 */
+  int refine;      /* 0, 1 or 2: steps of iterative refinement from the inputs:
+                    * r_c = H_c^H (y_c - H_c x_c) - rho x_c, x_c += A_c r_c (FP32, with
+                    * A_c the solve's inverse), and one Newton step for the diagonal
+                    * of the inverse, A_uu <- 2 A_uu - ||H_c a_u||^2 - rho ||a_u||^2
+                    * (a_u its u-th column), which the unbiasing and fusion use.
+                    * Each step shrinks the error of the mixed-precision
+                    * preprocessing by about kappa(G_c + rho I) * 2^-16 (BF16X3).
+                    * Costs a second read of H and y and a larger workspace; only
+                    * ffeq_equalize (and the entry points built on it) support it:
+                    * ffeq_fuse_equalize returns FFEQ_ERR_UNSUPPORTED. */
 } ffeq_problem;
 
 typedef struct ffeq_plan ffeq_plan;
@@ -112,7 +122,9 @@ void ffeq_plan_destroy(ffeq_plan* plan);
 
 /* Device workspace bytes ffeq_equalize needs: the per-(subcarrier, cluster)
  * local Gram matrices and MRC outputs, n_sc * Ceff * (U + n_sym) * U * 8 bytes
- * with Ceff = C (FD) or 1 (PD).  Owned by the caller, 16-byte aligned. */
+ * with Ceff = C (FD) or 1 (PD); with refinement also the local estimates, the
+ * inverses and the pivot status (n_sc * Ceff * ((n_sym + U) * U * 8 + 4) bytes
+ * more, plus alignment).  Owned by the caller, 16-byte aligned. */
 ffeq_status ffeq_workspace_size(const ffeq_plan* plan, size_t* bytes);
 
 /* Equalize on the device (Sec. II-C/D, III-A, IV-A; see the header comment).

@@ -14,6 +14,7 @@ struct ffeq_plan {
   size_t workspace;      // bytes of the [n_sc][Ceff][U+n_sym][U] complex workspace
   int gram_variant = 0;  // contraction launch shape (0: default)
   int gram_stages = 0;   // staged units per CTA (0: as many as fit)
+  size_t off_X = 0, off_A = 0, off_F = 0;   // refinement arrays in the workspace
 };
 
 namespace {
@@ -86,6 +87,7 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (p->estimate != FFEQ_UNBIASED && p->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
   if (p->llr_bits != 0 && p->llr_bits != 2 && p->llr_bits != 4 && p->llr_bits != 6 && p->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
+  if (p->refine < 0 || p->refine > 2) return FFEQ_ERR_INVALID_ARG;
   if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
   if (ffeq::gram_stages(p->precision, p->B, p->U, p->n_sym, Ceff, false) < 1) return FFEQ_ERR_UNSUPPORTED;
@@ -93,11 +95,20 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (spc * Ceff * ffeq::padded_users(p->U) * (Ceff == 1 && ffeq::padded_users(p->U) == 16 ? 2 : 1) > 512 ||
       ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
+  if (p->refine > 0 && ffeq::refine_chunk(p->B, p->U, Ceff, p->n_sym) < 1) return FFEQ_ERR_UNSUPPORTED;
   ffeq_plan* plan = new (std::nothrow) ffeq_plan;
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   plan->p = *p;
   plan->Ceff = Ceff;
   plan->workspace = static_cast<size_t>(p->n_sc) * Ceff * (p->U + p->n_sym) * p->U * 8;
+  if (p->refine > 0) {
+    // Refinement keeps the local estimates, the inverses and the pivot status.
+    const size_t sys = static_cast<size_t>(p->n_sc) * Ceff;
+    plan->off_X = align_up(plan->workspace);
+    plan->off_A = align_up(plan->off_X + sys * p->n_sym * p->U * 8);
+    plan->off_F = align_up(plan->off_A + sys * p->U * p->U * 8);
+    plan->workspace = plan->off_F + sys * 4;
+  }
   *out = plan;
   return FFEQ_OK;
 }
@@ -141,7 +152,8 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
 }
 
 ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0, float Es, void* z,
-                          float* sigma2, float* llr, int* info, cudaStream_t st) {
+                          float* sigma2, float* llr, int* info, cudaStream_t st, const void* H = nullptr,
+                          const void* y = nullptr) {
   const ffeq_problem& p = plan->p;
   if (!(N0 >= 0.f) || !std::isfinite(N0) || !(Es > 0.f) || !std::isfinite(Es)) return FFEQ_ERR_INVALID_ARG;
   if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
@@ -168,7 +180,38 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   } else {
     sp.llr_scale = 0.f;
   }
-  const cudaError_t e = ffeq::launch_solve(sp, st);
+  if (p.refine > 0) {
+    if (!H || !y) return FFEQ_ERR_UNSUPPORTED;   // the residual needs the inputs
+    unsigned char* ws = static_cast<unsigned char*>(const_cast<void*>(workspace));
+    sp.Xs = reinterpret_cast<float2*>(ws + plan->off_X);
+    sp.As = reinterpret_cast<float2*>(ws + plan->off_A);
+    sp.fails = reinterpret_cast<int*>(ws + plan->off_F);
+  }
+  cudaError_t e = ffeq::launch_solve(sp, st);
+  if (e != cudaSuccess || p.refine == 0) return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+  ffeq::RefineParams rp{};
+  rp.H = static_cast<const float2*>(H);
+  rp.y = static_cast<const float2*>(y);
+  rp.D = static_cast<const float2*>(workspace);
+  rp.As = sp.As;
+  rp.Xs = sp.Xs;
+  rp.fails = sp.fails;
+  rp.z = sp.z;
+  rp.sigma2 = sp.sigma2;
+  rp.llr = sp.llr;
+  rp.B = p.B;
+  rp.U = p.U;
+  rp.Ceff = plan->Ceff;
+  rp.n_sc = p.n_sc;
+  rp.n_sym = p.n_sym;
+  rp.steps = p.refine;
+  rp.chunk = ffeq::refine_chunk(p.B, p.U, plan->Ceff, p.n_sym);
+  rp.unbiased = sp.unbiased;
+  rp.llr_bits = p.llr_bits;
+  rp.N0 = sp.N0;
+  rp.rho = sp.rho;
+  rp.llr_scale = sp.llr_scale;
+  e = ffeq::launch_refine(rp, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
 }
 
@@ -208,7 +251,7 @@ ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, f
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   r = local_preprocess(plan, H, y, workspace, st);
   if (r != FFEQ_OK) return r;
-  return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st);
+  return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st, H, y);
 }
 
 namespace {

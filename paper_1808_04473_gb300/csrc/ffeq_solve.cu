@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "ffeq_device.cuh"
+#include "ffeq_epilogue.cuh"
 #include "ffeq_gj.cuh"
 #include "ffeq_internal.h"
 
@@ -42,45 +43,6 @@ struct SolveLayout {
   static constexpr int kNum = kNsymMax * UP;
   static constexpr int kMat = ((kRow + kNum + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
 };
-
-// Max-log LLRs of one Gray-labelled PAM axis with H bits (labels and sign as in
-// ffeq.h): for each bit, the squared distance to the nearest level carrying a 1
-// minus that to the nearest level carrying a 0, over sigma^2.
-template <int H>
-__device__ __forceinline__ void axis_llr(float x, float s2, float scale, float* out) {
-  constexpr int L = 1 << H;
-  float m0[H], m1[H];
-#pragma unroll
-  for (int t = 0; t < H; ++t) m0[t] = m1[t] = INFINITY;
-#pragma unroll
-  for (int l = 0; l < L; ++l) {
-    const float e = x - scale * static_cast<float>(2 * l - (L - 1));
-    const float d = e * e;
-    const int g = l ^ (l >> 1);
-#pragma unroll
-    for (int t = 0; t < H; ++t) {
-      if ((g >> (H - 1 - t)) & 1) m1[t] = fminf(m1[t], d);
-      else m0[t] = fminf(m0[t], d);
-    }
-  }
-  const bool s2inf = isinf(s2);
-#pragma unroll
-  for (int t = 0; t < H; ++t) {
-    const float diff = m1[t] - m0[t];
-    float v = diff / s2;
-    if (s2inf || (s2 == 0.f && diff == 0.f)) v = 0.f;
-    out[t] = v;
-  }
-}
-
-__device__ __forceinline__ void symbol_llr(float2 z, float s2, float scale, int h, float* out) {
-  switch (h) {
-    case 1: axis_llr<1>(z.x, s2, scale, out); axis_llr<1>(z.y, s2, scale, out + 1); break;
-    case 2: axis_llr<2>(z.x, s2, scale, out); axis_llr<2>(z.y, s2, scale, out + 2); break;
-    case 3: axis_llr<3>(z.x, s2, scale, out); axis_llr<3>(z.y, s2, scale, out + 3); break;
-    default: axis_llr<4>(z.x, s2, scale, out); axis_llr<4>(z.y, s2, scale, out + 4); break;
-  }
-}
 
 // Outputs of an uneven-batch tile: for each descriptor, sum its Ceff matrix
 // slots (contiguous, in tile order) and write z, sigma^2 and LLRs at its offsets.
@@ -241,10 +203,11 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     }
     float scl = 1.f;
     fail = gj_sweep_pairs<UP, W>(re, im, reinterpret_cast<float*>(rowbuf), i, g < nmat, scl);
-    // Deferred scaling of the entries the epilogue reads: z (RHS block) and A_ii.
+    // Deferred scaling of the entries read below: z (RHS block) and A_ii (all of
+    // A when the refinement follows).
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-      const bool used = j < kNsymMax || j == kNsymMax + i;
+      const bool used = j < kNsymMax || j == kNsymMax + i || (!batch && p.Xs);
       aug[j] = used ? make_float2(re[j] * scl, im[j] * scl) : make_float2(re[j], im[j]);
     }
   } else {
@@ -287,6 +250,32 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
     // Deferred scaling: row i times 1/p_i (both halves of row i recorded it at step i).
 #pragma unroll
     for (int j = 0; j < WH; ++j) aug[j] = cscale(aug[j], my_r);
+  }
+
+  if constexpr (!batch) {
+    if (p.Xs) {
+      // Refinement follows: keep this system's estimates X [n][u] and its inverse
+      // stored transposed (row j = column j of A, coalesced over the lanes i).
+      if (g < nmat && valid && i < U) {
+        const size_t sys = static_cast<size_t>(sc) * Ceff + c;
+#pragma unroll
+        for (int j = 0; j < WH; ++j) {
+          if constexpr (LPR == 1) {
+            if (j >= kNsymMax && j - kNsymMax < U) p.As[(sys * U + (j - kNsymMax)) * U + i] = aug[j];
+            if (j < NS) p.Xs[(sys * NS + j) * U + i] = aug[j];
+          } else {
+            const int col = h * WH + j;
+            if (col < U) p.As[(sys * U + col) * U + i] = aug[j];
+            if (col >= UP && col - UP < NS) p.Xs[(sys * NS + (col - UP)) * U + i] = aug[j];
+          }
+        }
+        if (gl == 0) {
+          p.fails[sys] = fail;
+          if (info_at) *info_at = fail;
+        }
+      }
+      return;   // the refinement kernel fuses and writes the outputs
+    }
   }
 
   // ---- fusion terms of this matrix: A_ii on the first-half lane of row i

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds, loads, exports every symbol
 declared in include/ffeq.h, and rejects bad arguments before touching CUDA."""
 import ctypes
+import re
 import os
 import subprocess
 
@@ -85,12 +86,12 @@ def test_staging_size_accounts_for_every_buffer(built):
 
 
 def test_plan_struct_layout_matches_header(built):
-    assert ctypes.sizeof(ffeq.ffeq_problem) == 9 * 4
+    assert ctypes.sizeof(ffeq.ffeq_problem) == 10 * 4
     text = open(ffeq.HEADER_PATH).read()
-    body = text[text.index("typedef struct {"):text.index("} ffeq_problem;")]
-    fields = [f for line in body.splitlines()[1:] for f in line.split(";")[0].replace("int", "").split(",")
-              if f.strip() and not f.strip().startswith("/*")]
-    assert [f.strip() for f in fields] == [n for n, _ in ffeq.ffeq_problem._fields_]
+    body = text[text.index("typedef struct {") + len("typedef struct {"):text.index("} ffeq_problem;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = [f.strip() for decl in body.split(";") for f in decl.replace("int", "").split(",") if f.strip()]
+    assert fields == [n for n, _ in ffeq.ffeq_problem._fields_]
 
 
 def test_oracle_and_cuda_sources_are_independent(repo_root):
@@ -125,3 +126,15 @@ def test_plan_tuning_validation(built):
         ff.ffeq_plan_set_tuning(big, (1, 3))
     assert e.value.status == 2
     ff.ffeq_plan_set_tuning(big, (3, 0))
+
+
+def test_refinement_needs_the_inputs(built):
+    plan = ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, precision=ffeq.BF16X3, refine=1)
+    plain = ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, precision=ffeq.BF16X3)
+    assert ffeq.ffeq_workspace_size(plan) >= ffeq.ffeq_workspace_size(plain) + 10 * 4 * ((2 + 8) * 8 * 8 + 4)
+    with pytest.raises(ffeq.FfeqError) as e:
+        ffeq.ffeq_fuse_equalize(plan, 256, ffeq.ffeq_workspace_size(plan), 0.1, 1.0, 256, 256, None, None, stream=0)
+    assert e.value.status == 2
+    with pytest.raises(ffeq.FfeqError) as e:
+        ffeq.ffeq_plan_create(64, 8, 4, 10, 2, refine=3)
+    assert e.value.status == 1
