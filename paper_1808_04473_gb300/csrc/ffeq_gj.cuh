@@ -59,18 +59,6 @@ __device__ __forceinline__ int gj_sweep_rotating(float2 (&aug)[W], float2* rowbu
   return fail;
 }
 
-// a * b + c on both halves: one paired FP32 FMA (fma.rn.f32x2, sm_100 and
-// later); each half rounds exactly like fmaf.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-
 // One element of the deferred-scaling elimination, shared by every sweep so
 // that all lane layouts round identically:
 //     new = base - g q       (complex; g = f / p_k, q the unscaled pivot row)
@@ -85,26 +73,112 @@ __device__ __forceinline__ float2 gj_update(float2 g, float2 q, float2 base) {
 
 // Gauss-Jordan sweep with deferred row scaling and paired FMAs.
 //
-// Same system and result layout as gj_sweep_rotating, held as separate real
-// and imaginary planes re[W], im[W] (lane i = row i).  At step k the pivot row
-// is broadcast UNSCALED (its pivot-column entry replaced by 1, the identity
-// column it turns into) together with the pivot p_k, and every other row does
-// new = base - g q with g = f / p_k (f its pivot-column entry; base its own
-// value, or 0 in the pivot column); the pivot row itself keeps its values
-// (g = 0, pivot column 1).  A row that has been the pivot row is thereby stored
-// multiplied by its pivot p_i, which later eliminations preserve (they are
-// linear in the row); the caller multiplies the entries it uses by the returned
-// 1/p_i (`scale`).  This avoids scaling and copying the pivot row inside the loop
-// (a divergent path), and with rows in planes each complex update is two paired
-// FMAs on (column j, column j+1).  Two steps per loop trip (pivot columns 0 and
-// 1), each with its own broadcast buffer (one warp barrier per step), followed
-// by a rotation by two keep the pairs aligned.  rowbuf: 2 (2W + 4) floats, 16-byte
-// aligned.  Returns the 1-based index of the first non-positive pivot, or 0.
+// Same system and result layout as gj_sweep_rotating, held as pairs of
+// adjacent columns: rp[m] = (re col 2m, re col 2m+1), ip[m] likewise for the
+// imaginary parts (lane i = row i).  At step k the pivot row is broadcast
+// UNSCALED (its pivot-column entry replaced by 1, the identity column it turns
+// into) together with the pivot p_k, and every other row does new = base - g q
+// with g = f / p_k (f its pivot-column entry; base its own value, or 0 in the
+// pivot column); the pivot row itself keeps its values (g = 0, pivot column 1).
+// A row that has been the pivot row is thereby stored multiplied by its pivot
+// p_i, which later eliminations preserve (they are linear in the row); the
+// caller multiplies the entries it uses by the returned 1/p_i (`scale`).  This
+// avoids scaling and copying the pivot row inside the loop (a divergent path),
+// and each complex update of a column pair is four paired FMAs (__ffma2_rn,
+// sm_100 and later), rounding exactly like gj_update.  Two steps per loop trip
+// (pivot columns 0 and 1: pair 0), each with its own broadcast buffer (one warp
+// barrier per step), followed by a rotation by one pair keep register indices
+// compile-time constants.  rowbuf: 2 (2W + 4) floats, 16-byte aligned.  Returns
+// the 1-based index of the first non-positive pivot, or 0.
 template <int UP, int W>
-__device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], float* rowbuf, int i, bool writer,
-                                              float& scale) {
+__device__ __forceinline__ int gj_sweep_pairs(float2 (&rp)[W / 2], float2 (&ip)[W / 2], float* rowbuf, int i,
+                                              bool writer, float& scale) {
   static_assert(W % 4 == 0 && UP % 2 == 0, "paired sweep needs W % 4 == 0 and even UP");
+  constexpr int NP = W / 2;                // column pairs
   constexpr int kBuf = 2 * W + 4;          // re plane, im plane, pivot (padded to 16 bytes)
+  int fail = 0;
+  float my_r = 1.f;
+#pragma unroll 1
+  for (int k = 0; k < UP; k += 2) {
+    static_for<2>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;   // pivot column of this step (half s of pair 0)
+      float* buf = rowbuf + s * kBuf;
+      const int kk = k + s;
+      const bool me = i == kk;
+      const float fr = s == 0 ? rp[0].x : rp[0].y;
+      const float fi = s == 0 ? ip[0].x : ip[0].y;
+      if (me && writer) {
+        const float2 r0 = s == 0 ? make_float2(1.f, rp[0].y) : make_float2(rp[0].x, 1.f);
+        const float2 i0 = s == 0 ? make_float2(0.f, ip[0].y) : make_float2(ip[0].x, 0.f);
+#pragma unroll
+        for (int m = 0; m < NP; m += 2) {
+          const float2 ra = m == 0 ? r0 : rp[m], ia = m == 0 ? i0 : ip[m];
+          *reinterpret_cast<float4*>(buf + 2 * m) = make_float4(ra.x, ra.y, rp[m + 1].x, rp[m + 1].y);
+          *reinterpret_cast<float4*>(buf + W + 2 * m) = make_float4(ia.x, ia.y, ip[m + 1].x, ip[m + 1].y);
+        }
+        buf[2 * W] = fr;
+      }
+      __syncwarp();
+      const float piv = buf[2 * W];
+      const bool ok = piv > 0.f;
+      if (!ok && fail == 0) fail = kk + 1;
+      const float r = __frcp_rn(ok ? piv : 1.f);
+      if (me) my_r = r;
+      const float gr = me ? 0.f : fr * r;
+      const float gi = me ? 0.f : fi * r;
+      const float2 ngr = make_float2(-gr, -gr), pgi = make_float2(gi, gi), ngi = make_float2(-gi, -gi);
+      const float dlt = me ? 1.f : 0.f;
+      float2 nr[NP], ni[NP];
+#pragma unroll
+      for (int m = 0; m < NP; m += 2) {
+        const float4 qr = *reinterpret_cast<const float4*>(buf + 2 * m);
+        const float4 qi = *reinterpret_cast<const float4*>(buf + W + 2 * m);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = m + h;   // pair index
+          const float2 qrp = h == 0 ? make_float2(qr.x, qr.y) : make_float2(qr.z, qr.w);
+          const float2 qip = h == 0 ? make_float2(qi.x, qi.y) : make_float2(qi.z, qi.w);
+          float2 br = rp[c], bi = ip[c];
+          if (c == 0) {
+            if (s == 0) {
+              br.x = dlt;
+              bi.x = 0.f;
+            } else {
+              br.y = dlt;
+              bi.y = 0.f;
+            }
+          }
+          float2 tr = __ffma2_rn(ngr, qrp, br);
+          tr = __ffma2_rn(pgi, qip, tr);
+          float2 ti = __ffma2_rn(ngr, qip, bi);
+          ti = __ffma2_rn(ngi, qrp, ti);
+          // After the second step, rotate left by one pair (inverse columns to the end).
+          const int d = s == 1 ? (c + NP - 1) % NP : c;
+          nr[d] = tr;
+          ni[d] = ti;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        rp[m] = nr[m];
+        ip[m] = ni[m];
+      }
+    });
+  }
+  __syncwarp();   // the buffers may be reused after the sweep
+  scale = my_r;
+  return fail;
+}
+
+// The same sweep (deferred scaling, two steps per trip, rotation by two, one
+// broadcast buffer per step) on interleaved complex registers with scalar FMAs
+// (gj_update), which rounds exactly like gj_sweep_pairs.  rowbuf: 2 (2W + 4)
+// floats, 16-byte aligned.
+template <int UP, int W>
+__device__ __forceinline__ int gj_sweep_deferred(float2 (&aug)[W], float* rowbuf, int i, bool writer,
+                                                 float& scale) {
+  static_assert(W % 2 == 0 && UP % 2 == 0, "sweep needs even W and UP");
+  constexpr int kBuf = 2 * W + 4;          // W complex, then the pivot (padded to 16 bytes)
   int fail = 0;
   float my_r = 1.f;
 #pragma unroll 1
@@ -116,15 +190,12 @@ __device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], fl
       const bool me = i == kk;
       if (me && writer) {
 #pragma unroll
-        for (int j = 0; j < W; j += 4) {
-          *reinterpret_cast<float4*>(buf + j) =
-              make_float4(j + 0 == s ? 1.f : re[j + 0], j + 1 == s ? 1.f : re[j + 1], j + 2 == s ? 1.f : re[j + 2],
-                          j + 3 == s ? 1.f : re[j + 3]);
-          *reinterpret_cast<float4*>(buf + W + j) =
-              make_float4(j + 0 == s ? 0.f : im[j + 0], j + 1 == s ? 0.f : im[j + 1], j + 2 == s ? 0.f : im[j + 2],
-                          j + 3 == s ? 0.f : im[j + 3]);
+        for (int j = 0; j < W; j += 2) {
+          const float2 a = j == s ? make_float2(1.f, 0.f) : aug[j];
+          const float2 b = j + 1 == s ? make_float2(1.f, 0.f) : aug[j + 1];
+          *reinterpret_cast<float4*>(buf + 2 * j) = make_float4(a.x, a.y, b.x, b.y);
         }
-        buf[2 * W] = re[s];
+        buf[2 * W] = aug[s].x;
       }
       __syncwarp();
       const float piv = buf[2 * W];
@@ -132,39 +203,20 @@ __device__ __forceinline__ int gj_sweep_pairs(float (&re)[W], float (&im)[W], fl
       if (!ok && fail == 0) fail = kk + 1;
       const float r = __frcp_rn(ok ? piv : 1.f);
       if (me) my_r = r;
-      const float gr = me ? 0.f : re[s] * r;
-      const float gi = me ? 0.f : im[s] * r;
-      const float2 ngr = make_float2(-gr, -gr), pgi = make_float2(gi, gi), ngi = make_float2(-gi, -gi);
+      const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(aug[s].x * r, aug[s].y * r);
       const float dlt = me ? 1.f : 0.f;
-      float nre[W], nim[W];
+      float2 nw[W];
 #pragma unroll
-      for (int j = 0; j < W; j += 4) {
-        const float4 qr = *reinterpret_cast<const float4*>(buf + j);
-        const float4 qi = *reinterpret_cast<const float4*>(buf + W + j);
-#pragma unroll
-        for (int h = 0; h < 4; h += 2) {
-          const int c = j + h;
-          const float2 qrp = h == 0 ? make_float2(qr.x, qr.y) : make_float2(qr.z, qr.w);
-          const float2 qip = h == 0 ? make_float2(qi.x, qi.y) : make_float2(qi.z, qi.w);
-          const float2 br = make_float2(c == s ? dlt : re[c], c + 1 == s ? dlt : re[c + 1]);
-          const float2 bi = make_float2(c == s ? 0.f : im[c], c + 1 == s ? 0.f : im[c + 1]);
-          float2 tr = ffma2(ngr, qrp, br);
-          tr = ffma2(pgi, qip, tr);
-          float2 ti = ffma2(ngr, qip, bi);
-          ti = ffma2(ngi, qrp, ti);
-          // After the second step, rotate left by two (inverse columns to the end).
-          const int d = s == 1 ? (c + W - 2) % W : c;
-          nre[d] = tr.x;
-          nre[d + 1] = tr.y;
-          nim[d] = ti.x;
-          nim[d + 1] = ti.y;
-        }
+      for (int j = 0; j < W; j += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(buf + 2 * j);
+        const float2 b0 = j == s ? make_float2(dlt, 0.f) : aug[j];
+        const float2 b1 = j + 1 == s ? make_float2(dlt, 0.f) : aug[j + 1];
+        const int d = s == 1 ? (j + W - 2) % W : j;   // after the second step, rotate left by two
+        nw[d] = gj_update(gg, make_float2(q.x, q.y), b0);
+        nw[d + 1] = gj_update(gg, make_float2(q.z, q.w), b1);
       }
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        re[j] = nre[j];
-        im[j] = nim[j];
-      }
+      for (int j = 0; j < W; ++j) aug[j] = nw[j];
     });
   }
   __syncwarp();   // the buffers may be reused after the sweep

@@ -105,11 +105,14 @@ __device__ __forceinline__ void issue_rows(const GramUnit& w, float2* dst, uint6
     return;
   }
   const int U = w.U, B = w.B, NS = w.NS, Mrows = U + NS, RS = B + 2;
+  // H and y are read once: evict them first, keeping the workspace this kernel
+  // writes in L2 for the solve kernel that reads it next.
+  const uint64_t pol = l2_evict_first_policy();
   if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Mrows) * B * 8u);
   __syncwarp();
   for (int r = lane; r < Mrows; r += 32) {
     const float2* src = r < U ? w.H + static_cast<size_t>(r) * B : w.y + static_cast<size_t>(r - U) * B;
-    bulk_g2s(dst + r * RS, src, static_cast<uint32_t>(B) * 8u, bar);
+    bulk_g2s_hint(dst + r * RS, src, static_cast<uint32_t>(B) * 8u, bar, pol);
   }
 }
 

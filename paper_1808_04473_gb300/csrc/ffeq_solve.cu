@@ -44,53 +44,98 @@ struct SolveLayout {
   static constexpr int kMat = ((kRow + kNum + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
 };
 
-// Outputs of an uneven-batch tile: for each descriptor, sum its Ceff matrix
-// slots (contiguous, in tile order) and write z, sigma^2 and LLRs at its offsets.
+// Per-descriptor fields the batch epilogue needs, cached in shared memory.
+struct EpiDesc {
+  long long z_off, s2_off, llr_off;
+  int U, NS, Ceff, out0, slot0;
+  float N0, llr_scale;
+  int pad;
+};
+constexpr int kEpiCacheBytes = kTileSlots * static_cast<int>(sizeof(EpiDesc));
+
+// Outputs of an uneven-batch tile: the tile's descriptors are read once into
+// shared memory (in parallel) with the prefix sums of their outputs and matrix
+// slots, then every output (descriptor j, symbol n, user u) is one work item:
+// sum descriptor j's Ceff slots (contiguous, in tile order) and write z, sigma^2
+// and LLRs at its offsets.
 template <int UP>
-__device__ void batch_epilogue(const SolveParams& p, const float2* base, const int* fail, int nslot) {
+__device__ void batch_epilogue(const SolveParams& p, const float2* base, const int* fail, int nslot,
+                               EpiDesc* cache, int* ndesc) {
   using Lay = SolveLayout<UP>;
   const SolveTile tile = p.tiles[blockIdx.x];
   const int bits = p.llr_bits, hb = bits / 2;
-  int slot0 = 0;
-  for (int j = 0; j < tile.count && tile.first >= 0 && tile.first + j < p.n_desc; ++j) {
-    const BatchDesc& d = p.desc[tile.first + j];
-    const int U = d.U, NS = d.n_sym, Ceff = d.Ceff;
-    const int per = U * NS;
-    const bool ok = U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kTileSlots &&
-                    slot0 + Ceff <= kTileSlots && slot0 + Ceff <= nslot && span_ok(d.z_off, per, p.lim.z) &&
-                    span_ok(d.s2_off, U, p.lim.s2) &&
-                    (!bits || span_ok(d.llr_off, static_cast<long long>(per) * bits, p.lim.llr));
-    if (!ok) {
-      if (threadIdx.x == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
-      break;
+  const int count = tile.first >= 0 && tile.count > 0 ? (tile.count < kTileSlots ? tile.count : kTileSlots) : 0;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    EpiDesc e{};
+    e.U = -1;   // invalid unless set below
+    if (tile.first + j < p.n_desc) {
+      const BatchDesc& d = p.desc[tile.first + j];
+      e.z_off = d.z_off;
+      e.s2_off = d.s2_off;
+      e.llr_off = d.llr_off;
+      e.U = d.U;
+      e.NS = d.n_sym;
+      e.Ceff = d.Ceff;
+      e.N0 = d.N0;
+      e.llr_scale = d.llr_scale;
     }
-    for (int e = threadIdx.x; e < per; e += blockDim.x) {
-      const int n = e / U, u = e - n * U;
-      float2 nm = make_float2(0.f, 0.f);
-      float dn = 0.f;
-      for (int cc = 0; cc < Ceff; ++cc) {
-        const float2* Lm = base + (slot0 + cc) * Lay::kMat + Lay::kRow;
-        nm = cadd(nm, Lm[n * UP + u]);
-        dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
+    cache[j] = e;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Prefix sums; the tile ends at the first descriptor that fails its checks.
+    int out = 0, slot0 = 0, n = 0;
+    for (; n < count; ++n) {
+      EpiDesc& e = cache[n];
+      const int U = e.U, NS = e.NS, Ceff = e.Ceff, per = U * NS;
+      const bool ok = U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kTileSlots &&
+                      slot0 + Ceff <= kTileSlots && slot0 + Ceff <= nslot && span_ok(e.z_off, per, p.lim.z) &&
+                      span_ok(e.s2_off, U, p.lim.s2) &&
+                      (!bits || span_ok(e.llr_off, static_cast<long long>(per) * bits, p.lim.llr));
+      if (!ok) {
+        if (p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+        break;
       }
-      float2 zz;
-      float s2;
-      if (fail[j]) {
-        zz = make_float2(NAN, NAN);
-        s2 = NAN;
-      } else if (dn > 0.f) {
-        const float rr = 1.f / dn;
-        zz = cscale(nm, rr);
-        s2 = d.N0 * rr;
-      } else {
-        zz = make_float2(0.f, 0.f);
-        s2 = INFINITY;
-      }
-      p.z[d.z_off + e] = zz;
-      if (n == 0) p.sigma2[d.s2_off + u] = s2;
-      if (bits) symbol_llr(zz, s2, d.llr_scale, hb, p.llr + d.llr_off + static_cast<long long>(e) * bits);
+      e.out0 = out;
+      e.slot0 = slot0;
+      out += per;
+      slot0 += Ceff;
     }
-    slot0 += Ceff;
+    ndesc[0] = n;
+    ndesc[1] = out;
+  }
+  __syncthreads();
+  const int nd = ndesc[0], total = ndesc[1];
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int j = 0;
+    while (j + 1 < nd && cache[j + 1].out0 <= e) ++j;
+    const EpiDesc& d = cache[j];
+    const int U = d.U, Ceff = d.Ceff;
+    const int r = e - d.out0;
+    const int n = r / U, u = r - n * U;
+    float2 nm = make_float2(0.f, 0.f);
+    float dn = 0.f;
+    for (int cc = 0; cc < Ceff; ++cc) {
+      const float2* Lm = base + (d.slot0 + cc) * Lay::kMat + Lay::kRow;
+      nm = cadd(nm, Lm[n * UP + u]);
+      dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
+    }
+    float2 zz;
+    float s2;
+    if (fail[j]) {
+      zz = make_float2(NAN, NAN);
+      s2 = NAN;
+    } else if (dn > 0.f) {
+      const float rr = 1.f / dn;
+      zz = cscale(nm, rr);
+      s2 = d.N0 * rr;
+    } else {
+      zz = make_float2(0.f, 0.f);
+      s2 = INFINITY;
+    }
+    p.z[d.z_off + r] = zz;
+    if (n == 0) p.sigma2[d.s2_off + u] = s2;
+    if (bits) symbol_llr(zz, s2, d.llr_scale, hb, p.llr + d.llr_off + static_cast<long long>(r) * bits);
   }
 }
 
@@ -112,7 +157,8 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   const int i = gl % UP;
   const int h = LPR == 1 ? 0 : gl / UP;        // which half of the row this lane holds
   int* fail_sc = reinterpret_cast<int*>(smem);                       // [spc] or [tile count]
-  float2* base = reinterpret_cast<float2*>(smem + 256);
+  // Batch mode: descriptor cache for the epilogue after the flags.
+  float2* base = reinterpret_cast<float2*>(smem + 256 + (BATCH ? kEpiCacheBytes + 16 : 0));
   const int sc0 = blockIdx.x * spc;
 
   if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
@@ -162,113 +208,105 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
   float2* Fz = rowbuf + Lay::kRow;
   float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
 
-  // ---- this lane's columns of row i of [G + rho I | y^MRC] (padding: identity, zero RHS)
-  // Loads are unconditional (clamped to valid addresses) so they all issue before
-  // the first use; padding values are selected afterwards.
-  float2 aug[WH];
-  const int ic = i < U ? i : 0;
-#pragma unroll
-  for (int j = 0; j < WH; ++j) {
-    const int col = h * WH + j;
-    const int row = col < UP ? (col < U ? col : 0) : (col - UP < NS ? U + col - UP : 0);
-    if constexpr (batch) {
-      aug[j] = valid ? Dg[row * U + ic] : make_float2(0.f, 0.f);
-    } else {
-      aug[j] = Dg[row * U + ic];   // invalid groups read subcarrier 0 (in bounds)
-    }
-  }
-  float gii = 1.f;
-#pragma unroll
-  for (int j = 0; j < WH; ++j) {
-    const int col = h * WH + j;
-    const bool real = valid && i < U && (col < UP ? col < U : col - UP < NS);
-    float2 v = real ? aug[j] : make_float2(col == i ? 1.f : 0.f, 0.f);
-    if (col == i && real) {
-      gii = v.x;
-      v = make_float2(v.x + rho, 0.f);
-    }
-    aug[j] = v;
-  }
-
-  // ---- Gauss-Jordan sweep (deferred row scaling: every lane runs the same update)
   int fail = 0;
   if constexpr (LPR == 1) {
-    // Paired form (ffeq_gj.cuh): afterwards columns [0, kNsymMax) = z (RHS block)
-    // and column kNsymMax + j = A[i][j].
-    float re[W], im[W];
+    // ---- row i of G + rho I in registers (padding: identity); the right-hand
+    // sides y^MRC go straight to this system's shared block ys[n][u] (the fusion
+    // terms overwrite it later).  Loads are unconditional where the address is
+    // clamped in bounds, so they all issue before the first use.
+    float2* ys = Fz;
+    const int ic = i < U ? i : 0;
+    float2 mrow[UP];
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      re[j] = aug[j].x;
-      im[j] = aug[j].y;
-    }
-    float scl = 1.f;
-    fail = gj_sweep_pairs<UP, W>(re, im, reinterpret_cast<float*>(rowbuf), i, g < nmat, scl);
-    // Deferred scaling of the entries read below: z (RHS block) and A_ii (all of
-    // A when the refinement follows).
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const bool used = j < kNsymMax || j == kNsymMax + i || (!batch && p.Xs);
-      aug[j] = used ? make_float2(re[j] * scl, im[j] * scl) : make_float2(re[j], im[j]);
-    }
-  } else {
-    // Two lanes per row, columns in place: the same element update as the paired
-    // form (gj_update), so both layouts give identical bits.
-    float my_r = 1.f;
-    static_for<UP>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      const float piv = __shfl_sync(kFullMask, aug[k].x, k, GS);
-      const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
-      const bool ok = piv > 0.f;
-      if (!ok && fail == 0) fail = k + 1;
-      const float r = __frcp_rn(ok ? piv : 1.f);
-      const bool me = i == k;
-      if (me) my_r = r;
-      const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(f.x * r, f.y * r);
-      if (me && g < nmat) {
-#pragma unroll
-        for (int j = 0; j < WH; j += 2)
-          if (h * WH + j < UP + NS)
-            *reinterpret_cast<float4*>(rowbuf + h * WH + j) =
-                make_float4((h == 0 && j == k) ? 1.f : aug[j].x, (h == 0 && j == k) ? 0.f : aug[j].y,
-                            (h == 0 && j + 1 == k) ? 1.f : aug[j + 1].x, (h == 0 && j + 1 == k) ? 0.f : aug[j + 1].y);
+    for (int j = 0; j < UP; ++j) {
+      const int row = j < U ? j : 0;
+      if constexpr (batch) {
+        mrow[j] = valid ? Dg[row * U + ic] : make_float2(0.f, 0.f);
+      } else {
+        mrow[j] = Dg[row * U + ic];   // invalid groups read subcarrier 0 (in bounds)
       }
-      __syncwarp();
-      const float dlt = me ? 1.f : 0.f;
-      const float2* rb = rowbuf + h * WH;
+    }
+    if (g < nmat) {
 #pragma unroll
-      for (int j = 0; j < WH; j += 2) {
-        if (h * WH + j < UP + NS) {
-          const float4 q = *reinterpret_cast<const float4*>(rb + j);
-          const float2 b0 = (h == 0 && j == k) ? make_float2(dlt, 0.f) : aug[j];
-          const float2 b1 = (h == 0 && j + 1 == k) ? make_float2(dlt, 0.f) : aug[j + 1];
-          aug[j] = gj_update(gg, make_float2(q.x, q.y), b0);
-          aug[j + 1] = gj_update(gg, make_float2(q.z, q.w), b1);
+      for (int n = 0; n < kNsymMax; ++n) {
+        const bool real = valid && i < U && n < NS;
+        float2 v = make_float2(0.f, 0.f);
+        if constexpr (batch) {
+          if (real) v = Dg[(U + n) * U + ic];
+        } else {
+          v = Dg[(real ? U + n : 0) * U + ic];
+          if (!real) v = make_float2(0.f, 0.f);
+        }
+        ys[n * UP + i] = v;
+      }
+    }
+    float gii = 1.f;
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      const bool real = valid && i < U && j < U;
+      float2 v = real ? mrow[j] : make_float2(j == i ? 1.f : 0.f, 0.f);
+      if (j == i && real) {
+        gii = v.x;
+        v = make_float2(v.x + rho, 0.f);
+      }
+      mrow[j] = v;
+    }
+    // ---- Gauss-Jordan sweep on the matrix (paired form, ffeq_gj.cuh): row i of
+    // A = (G + rho I)^{-1}, then z = A y^MRC per right-hand side.
+    float2 rp[UP / 2], ip[UP / 2];
+#pragma unroll
+    for (int m = 0; m < UP / 2; ++m) {
+      rp[m] = make_float2(mrow[2 * m].x, mrow[2 * m + 1].x);
+      ip[m] = make_float2(mrow[2 * m].y, mrow[2 * m + 1].y);
+    }
+    float rs = 1.f;
+    fail = gj_sweep_pairs<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+    float2 arow[UP];
+    float Ai = 1.f;
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      arow[j] = cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
+      if (j == i) Ai = arow[j].x;
+    }
+    const float invA = 1.f / Ai;
+    // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
+    // mu = 0 exactly, which the subtraction would only reach up to rounding.
+    const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
+    bool store = false;
+    size_t sys = 0;
+    if constexpr (!batch) {
+      store = p.Xs != nullptr;   // refinement follows: keep estimates and inverses
+      sys = static_cast<size_t>(sc) * Ceff + c;
+    }
+    // z_n = sum_j A[i][j] y^MRC_j(n) in j order; after every lane of the warp has
+    // read row n of ys, the fusion term z_n / A_ii replaces it ([n][u]: the
+    // epilogue reads along u).
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) {
+      float2 zn = make_float2(0.f, 0.f);
+      if (n < NS) {
+#pragma unroll
+        for (int j = 0; j < UP; j += 2) {
+          const float4 y2 = *reinterpret_cast<const float4*>(ys + n * UP + j);
+          zn = cfma(arow[j], make_float2(y2.x, y2.y), zn);
+          zn = cfma(arow[j + 1], make_float2(y2.z, y2.w), zn);
         }
       }
       __syncwarp();
-    });
-    // Deferred scaling: row i times 1/p_i (both halves of row i recorded it at step i).
-#pragma unroll
-    for (int j = 0; j < WH; ++j) aug[j] = cscale(aug[j], my_r);
-  }
-
-  if constexpr (!batch) {
-    if (p.Xs) {
-      // Refinement follows: keep this system's estimates X [n][u] and its inverse
-      // stored transposed (row j = column j of A, coalesced over the lanes i).
+      if (n < NS && g < nmat) {
+        if (store) {
+          if (valid && i < U) p.Xs[(sys * NS + n) * U + i] = zn;
+        } else {
+          ys[n * UP + i] = cscale(zn, invA);
+        }
+      }
+    }
+    if (store) {
+      // Inverse stored transposed (row j = column j of A, coalesced over the lanes i).
       if (g < nmat && valid && i < U) {
-        const size_t sys = static_cast<size_t>(sc) * Ceff + c;
 #pragma unroll
-        for (int j = 0; j < WH; ++j) {
-          if constexpr (LPR == 1) {
-            if (j >= kNsymMax && j - kNsymMax < U) p.As[(sys * U + (j - kNsymMax)) * U + i] = aug[j];
-            if (j < NS) p.Xs[(sys * NS + j) * U + i] = aug[j];
-          } else {
-            const int col = h * WH + j;
-            if (col < U) p.As[(sys * U + col) * U + i] = aug[j];
-            if (col >= UP && col - UP < NS) p.Xs[(sys * NS + (col - UP)) * U + i] = aug[j];
-          }
-        }
+        for (int j = 0; j < UP; ++j)
+          if (j < U) p.As[(sys * U + j) * U + i] = arow[j];
         if (gl == 0) {
           p.fails[sys] = fail;
           if (info_at) *info_at = fail;
@@ -276,37 +314,140 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
       }
       return;   // the refinement kernel fuses and writes the outputs
     }
-  }
-
-  // ---- fusion terms of this matrix: A_ii on the first-half lane of row i
-  // (column i before rotation; column kNsymMax + i after the rotating sweep)
-  constexpr int kA = LPR == 1 ? kNsymMax : 0;   // first column of A in this lane's registers
-  constexpr int kZ = LPR == 1 ? 0 : UP;         // first RHS column (global column index)
-  float Ai = 1.f;
-#pragma unroll
-  for (int j = 0; j < UP; ++j)
-    if (j == i) Ai = aug[kA + j].x;
-  Ai = __shfl_sync(kFullMask, Ai, i, GS);
-  const float invA = 1.f / Ai;
-  // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
-  // mu = 0 exactly, which the subtraction would only reach up to rounding.
-  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
-  if (g < nmat) {
-#pragma unroll
-    for (int j = 0; j < WH; ++j) {
-      const int n = h * WH + j - kZ;
-      if (n >= 0 && n < NS && (LPR != 1 || j < kNsymMax))
-        Fz[n * UP + i] = cscale(aug[j], invA);   // [n][u]: the epilogue reads along u
+    if (g < nmat) {
+      Dn[i] = (p.unbiased ? mu : 1.f) * invA;
+      if (gl == 0 && valid) {
+        if (info_at) *info_at = fail;
+        if (fail) atomicOr(&fail_sc[scl], 1);
+      }
     }
-    if (h == 0) Dn[i] = (p.unbiased ? mu : 1.f) * invA;
-    if (gl == 0 && valid) {
-      if (info_at) *info_at = fail;
-      if (fail) atomicOr(&fail_sc[scl], 1);
+  } else {
+    // ---- this lane's columns of row i of [G + rho I | y^MRC] (padding: identity, zero RHS)
+    // Loads are unconditional (clamped to valid addresses) so they all issue before
+    // the first use; padding values are selected afterwards.
+    float2 aug[WH];
+    const int ic = i < U ? i : 0;
+  #pragma unroll
+    for (int j = 0; j < WH; ++j) {
+      const int col = h * WH + j;
+      const int row = col < UP ? (col < U ? col : 0) : (col - UP < NS ? U + col - UP : 0);
+      if constexpr (batch) {
+        aug[j] = valid ? Dg[row * U + ic] : make_float2(0.f, 0.f);
+      } else {
+        aug[j] = Dg[row * U + ic];   // invalid groups read subcarrier 0 (in bounds)
+      }
+    }
+    float gii = 1.f;
+  #pragma unroll
+    for (int j = 0; j < WH; ++j) {
+      const int col = h * WH + j;
+      const bool real = valid && i < U && (col < UP ? col < U : col - UP < NS);
+      float2 v = real ? aug[j] : make_float2(col == i ? 1.f : 0.f, 0.f);
+      if (col == i && real) {
+        gii = v.x;
+        v = make_float2(v.x + rho, 0.f);
+      }
+      aug[j] = v;
+    }
+
+      // ---- Gauss-Jordan sweep (deferred row scaling: every lane runs the same update)
+      // Two lanes per row, columns in place: the same element update as the paired
+      // form (gj_update), so both layouts give identical bits.
+      float my_r = 1.f;
+      static_for<UP>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const float piv = __shfl_sync(kFullMask, aug[k].x, k, GS);
+        const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
+        const bool ok = piv > 0.f;
+        if (!ok && fail == 0) fail = k + 1;
+        const float r = __frcp_rn(ok ? piv : 1.f);
+        const bool me = i == k;
+        if (me) my_r = r;
+        const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(f.x * r, f.y * r);
+        if (me && g < nmat) {
+  #pragma unroll
+          for (int j = 0; j < WH; j += 2)
+            if (h * WH + j < UP + NS)
+              *reinterpret_cast<float4*>(rowbuf + h * WH + j) =
+                  make_float4((h == 0 && j == k) ? 1.f : aug[j].x, (h == 0 && j == k) ? 0.f : aug[j].y,
+                              (h == 0 && j + 1 == k) ? 1.f : aug[j + 1].x, (h == 0 && j + 1 == k) ? 0.f : aug[j + 1].y);
+        }
+        __syncwarp();
+        const float dlt = me ? 1.f : 0.f;
+        const float2* rb = rowbuf + h * WH;
+  #pragma unroll
+        for (int j = 0; j < WH; j += 2) {
+          if (h * WH + j < UP + NS) {
+            const float4 q = *reinterpret_cast<const float4*>(rb + j);
+            const float2 b0 = (h == 0 && j == k) ? make_float2(dlt, 0.f) : aug[j];
+            const float2 b1 = (h == 0 && j + 1 == k) ? make_float2(dlt, 0.f) : aug[j + 1];
+            aug[j] = gj_update(gg, make_float2(q.x, q.y), b0);
+            aug[j + 1] = gj_update(gg, make_float2(q.z, q.w), b1);
+          }
+        }
+        __syncwarp();
+      });
+      // Deferred scaling: row i times 1/p_i (both halves of row i recorded it at step i).
+  #pragma unroll
+      for (int j = 0; j < WH; ++j) aug[j] = cscale(aug[j], my_r);
+
+    if constexpr (!batch) {
+      if (p.Xs) {
+        // Refinement follows: keep this system's estimates X [n][u] and its inverse
+        // stored transposed (row j = column j of A, coalesced over the lanes i).
+        if (g < nmat && valid && i < U) {
+          const size_t sys = static_cast<size_t>(sc) * Ceff + c;
+  #pragma unroll
+          for (int j = 0; j < WH; ++j) {
+            if constexpr (LPR == 1) {
+              if (j >= kNsymMax && j - kNsymMax < U) p.As[(sys * U + (j - kNsymMax)) * U + i] = aug[j];
+              if (j < NS) p.Xs[(sys * NS + j) * U + i] = aug[j];
+            } else {
+              const int col = h * WH + j;
+              if (col < U) p.As[(sys * U + col) * U + i] = aug[j];
+              if (col >= UP && col - UP < NS) p.Xs[(sys * NS + (col - UP)) * U + i] = aug[j];
+            }
+          }
+          if (gl == 0) {
+            p.fails[sys] = fail;
+            if (info_at) *info_at = fail;
+          }
+        }
+        return;   // the refinement kernel fuses and writes the outputs
+      }
+    }
+
+    // ---- fusion terms of this matrix: A_ii on the first-half lane of row i
+    // (column i before rotation; column kNsymMax + i after the rotating sweep)
+    constexpr int kA = LPR == 1 ? kNsymMax : 0;   // first column of A in this lane's registers
+    constexpr int kZ = LPR == 1 ? 0 : UP;         // first RHS column (global column index)
+    float Ai = 1.f;
+  #pragma unroll
+    for (int j = 0; j < UP; ++j)
+      if (j == i) Ai = aug[kA + j].x;
+    Ai = __shfl_sync(kFullMask, Ai, i, GS);
+    const float invA = 1.f / Ai;
+    // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
+    // mu = 0 exactly, which the subtraction would only reach up to rounding.
+    const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
+    if (g < nmat) {
+  #pragma unroll
+      for (int j = 0; j < WH; ++j) {
+        const int n = h * WH + j - kZ;
+        if (n >= 0 && n < NS && (LPR != 1 || j < kNsymMax))
+          Fz[n * UP + i] = cscale(aug[j], invA);   // [n][u]: the epilogue reads along u
+      }
+      if (h == 0) Dn[i] = (p.unbiased ? mu : 1.f) * invA;
+      if (gl == 0 && valid) {
+        if (info_at) *info_at = fail;
+        if (fail) atomicOr(&fail_sc[scl], 1);
+      }
     }
   }
   __syncthreads();
   if constexpr (batch) {
-    batch_epilogue<UP>(p, base, fail_sc, nmat);
+    batch_epilogue<UP>(p, base, fail_sc, nmat, reinterpret_cast<EpiDesc*>(smem + 256),
+                       reinterpret_cast<int*>(smem + 256 + kEpiCacheBytes));
     return;
   }
 
@@ -351,7 +492,7 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   constexpr bool batch = BATCH;
   const int nmat = batch ? p.threads / (UP * LPR) : p.spc * p.Ceff;
   const int threads = batch ? p.threads : ((nmat * UP * LPR + 31) / 32) * 32;
-  const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
+  const size_t smem = 256 + (batch ? kEpiCacheBytes + 16 : 0) + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
   static int configured[64] = {0};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -418,7 +559,7 @@ cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t strea
 size_t solve_batch_smem_bytes(int UP, int lpr, int threads) {
   const int nmat = threads / (UP * lpr);
   size_t per = UP == 8 ? SolveLayout<8>::kMat : (UP == 16 ? SolveLayout<16>::kMat : SolveLayout<32>::kMat);
-  return 256 + static_cast<size_t>(nmat) * per * sizeof(float2);
+  return 256 + kEpiCacheBytes + 16 + static_cast<size_t>(nmat) * per * sizeof(float2);
 }
 
 }  // namespace ffeq
