@@ -9,9 +9,11 @@ namespace ffeq {
 
 // Max-log LLRs of one Gray-labelled PAM axis with H bits (labels and sign as in
 // ffeq.h): for each bit, the squared distance to the nearest level carrying a 1
-// minus that to the nearest level carrying a 0, over sigma^2.
+// minus that to the nearest level carrying a 0, over sigma^2 (times inv_s2 =
+// 1/sigma^2, taken once per symbol).  A zero difference gives 0 (also when
+// sigma^2 = 0); sigma^2 = +inf gives 0 (inv_s2 = 0); NaN propagates.
 template <int H>
-__device__ __forceinline__ void axis_llr(float x, float s2, float scale, float* out) {
+__device__ __forceinline__ void axis_llr(float x, float inv_s2, float scale, float* out) {
   constexpr int L = 1 << H;
   float m0[H], m1[H];
 #pragma unroll
@@ -27,22 +29,20 @@ __device__ __forceinline__ void axis_llr(float x, float s2, float scale, float* 
       else m0[t] = fminf(m0[t], d);
     }
   }
-  const bool s2inf = isinf(s2);
 #pragma unroll
   for (int t = 0; t < H; ++t) {
     const float diff = m1[t] - m0[t];
-    float v = diff / s2;
-    if (s2inf || (s2 == 0.f && diff == 0.f)) v = 0.f;
-    out[t] = v;
+    out[t] = diff == 0.f ? 0.f : diff * inv_s2;
   }
 }
 
 __device__ __forceinline__ void symbol_llr(float2 z, float s2, float scale, int h, float* out) {
+  const float inv = isinf(s2) ? 0.f : 1.f / s2;   // s2 = 0: +inf; NaN stays NaN
   switch (h) {
-    case 1: axis_llr<1>(z.x, s2, scale, out); axis_llr<1>(z.y, s2, scale, out + 1); break;
-    case 2: axis_llr<2>(z.x, s2, scale, out); axis_llr<2>(z.y, s2, scale, out + 2); break;
-    case 3: axis_llr<3>(z.x, s2, scale, out); axis_llr<3>(z.y, s2, scale, out + 3); break;
-    default: axis_llr<4>(z.x, s2, scale, out); axis_llr<4>(z.y, s2, scale, out + 4); break;
+    case 1: axis_llr<1>(z.x, inv, scale, out); axis_llr<1>(z.y, inv, scale, out + 1); break;
+    case 2: axis_llr<2>(z.x, inv, scale, out); axis_llr<2>(z.y, inv, scale, out + 2); break;
+    case 3: axis_llr<3>(z.x, inv, scale, out); axis_llr<3>(z.y, inv, scale, out + 3); break;
+    default: axis_llr<4>(z.x, inv, scale, out); axis_llr<4>(z.y, inv, scale, out + 4); break;
   }
 }
 
