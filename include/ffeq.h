@@ -189,6 +189,7 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
  *              2 = 8 warps, two CTAs per SM (half the shared memory each),
  *              3 = BF16X3 only: each staged subcarrier converted once into BF16
  *                  hi/lo planes read with ldmatrix (needs B and B/C multiples of 4);
+ *              4 = tensor-core precisions only: 4 warps, three CTAs per SM;
  *   values[1]  subcarriers staged ahead per CTA, 1..3, or 0 = as many as fit.
  * ffeq_plan_set_tuning takes exactly 2 values and returns FFEQ_ERR_UNSUPPORTED
  * when the shape does not apply to or fit the problem (plan unchanged);

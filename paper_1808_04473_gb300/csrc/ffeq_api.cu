@@ -363,7 +363,7 @@ ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n) {
 
 ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
   if (!plan || n != 2 || !values) return FFEQ_ERR_INVALID_ARG;
-  if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGramPresplit || values[1] < 0 || values[1] > 3)
+  if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGram4x3 || values[1] < 0 || values[1] > 3)
     return FFEQ_ERR_INVALID_ARG;
   // The shape must fit the problem with 16-byte aligned rows (the bulk-staged case).
   ffeq::GramParams gp{};
@@ -398,7 +398,7 @@ ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, fl
   float best = -1.f;
   int best_v[2] = {old[0], old[1]};
   ffeq_status s = FFEQ_OK;
-  for (int variant = ffeq::kGram16; variant <= ffeq::kGramPresplit && s == FFEQ_OK; ++variant) {
+  for (int variant = ffeq::kGram16; variant <= ffeq::kGram4x3 && s == FFEQ_OK; ++variant) {
     for (int stages = 1; stages <= 3 && s == FFEQ_OK; ++stages) {
       const int v[2] = {variant, stages};
       if (ffeq_plan_set_tuning(plan, v, 2) != FFEQ_OK) continue;

@@ -103,15 +103,19 @@ bool gram_presplit_eligible(int precision, int B, int Ceff) {
 }
 
 size_t gram_smem_budget(int variant) {
-  // Two CTAs per SM share 228 KB, less 1 KB reserved per CTA.
-  return variant == kGram8x2 ? 113 * 1024 : kGramSmemBudget;
+  // CTAs per SM share 228 KB, less 1 KB reserved per CTA.
+  if (variant == kGram8x2) return 113 * 1024;
+  if (variant == kGram4x3) return 75 * 1024;
+  return kGramSmemBudget;
 }
 
 GramCaps gram_instance_caps(int precision, int B, int U, int n_sym, int Ceff, int variant) {
   if (precision == FFEQ_FP32) {
     GramCaps c{};
-    if (variant == kGram8x2) gram_capacity<SimtFp32<2>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
-    else gram_capacity<SimtFp32<1>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+    if (variant == kGram8x2 || variant == kGram4x3)
+      gram_capacity<SimtFp32<2>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+    else
+      gram_capacity<SimtFp32<1>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
     return c;
   }
   return gram_tc_caps(B, U, n_sym, Ceff, variant);
@@ -134,7 +138,8 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   p.lim = BatchLimits{};
   p.grid_cap = 0;
   if (variant == kGramAuto) variant = kGram16;
-  if (variant != kGram16 && variant != kGram8x2 && variant != kGramPresplit) return false;
+  if (variant != kGram16 && variant != kGram8x2 && variant != kGramPresplit && variant != kGram4x3) return false;
+  if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
   if (variant == kGramPresplit && !gram_presplit_eligible(precision, p.B, p.Ceff)) return false;
   if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes
     if (variant == kGramPresplit) variant = kGram16;

@@ -390,6 +390,8 @@ GramCaps gram_tc_caps(int B, int U, int n_sym, int Ceff, int variant) {
   GramCaps c{};
   if (variant == kGram8x2) {
     gram_capacity<TensorSplit<kBf16x3, 8, 2>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
+  } else if (variant == kGram4x3) {
+    gram_capacity<TensorSplit<kBf16x3, 4, 3>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
   } else {
     gram_capacity<TensorSplit<kBf16x3>>(B, U, n_sym, Ceff, c.stage_elems, c.slot_elems, c.slots);
   }
@@ -409,6 +411,10 @@ cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stre
   if (p.variant == kGram8x2) {
     return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3, 8, 2>(p, smem, stream)
                                     : launch_mode<kBf16x3, 8, 2>(p, smem, stream);
+  }
+  if (p.variant == kGram4x3) {
+    return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3, 4, 3>(p, smem, stream)
+                                    : launch_mode<kBf16x3, 4, 3>(p, smem, stream);
   }
   return precision == FFEQ_TF32X3 ? launch_mode<kTf32x3, 16, 1>(p, smem, stream)
                                   : launch_mode<kBf16x3, 16, 1>(p, smem, stream);

@@ -62,8 +62,8 @@ struct GramParams {
 
 // Contraction launch shapes: 16 warps, one CTA per SM; 8 warps, two CTAs per SM
 // (half the shared memory each, so one CTA's MMA phase overlaps the other's
-// staging); BF16x3 pre-split planes (16 warps).
-constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3;
+// staging); BF16x3 pre-split planes (16 warps); 4 warps, three CTAs per SM.
+constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4;
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
 struct SolveParams {

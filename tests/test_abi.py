@@ -113,7 +113,8 @@ def test_plan_tuning_validation(built):
     ff = ffeq
     plan = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP32)
     assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
-    for bad, status in (((4, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2)):    # pre-split needs BF16X3
+    # out of range; pre-split and the 4-warp shape need a tensor-core precision
+    for bad, status in (((5, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2)):
         with pytest.raises(ff.FfeqError) as e:
             ff.ffeq_plan_set_tuning(plan, bad)
         assert e.value.status == status, bad

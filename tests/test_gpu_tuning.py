@@ -52,7 +52,7 @@ def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
     f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
     o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased")
     results = {}
-    for variant in (1, 2, 3):
+    for variant in (1, 2, 3, 4):
         for stages in (0, 1, 2, 3):
             try:
                 ff.ffeq_plan_set_tuning(plan, (variant, stages))
@@ -68,5 +68,5 @@ def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
             results[(variant, stages)] = zn
     assert any(k[0] == 1 for k in results)          # the default shape always fits
     t = ff.ffeq_plan_autotune(plan, H, y, p.N0, p.Es, z, s2, None, None, ws, nb, reps=2)
-    assert t[0] in (1, 2, 3) and 1 <= t[1] <= 3
+    assert t[0] in (1, 2, 3, 4) and 1 <= t[1] <= 3
     assert ff.ffeq_plan_get_tuning(plan) == t
