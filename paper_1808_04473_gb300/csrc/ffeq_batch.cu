@@ -282,7 +282,7 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       std::vector<long long> go = us, so = us;
       auto cost = [&](long long q) {
         const ffeq::BatchDesc& d = b->units[q];
-        return static_cast<long long>(d.U + d.n_sym) * (d.B + 2);
+        return static_cast<long long>(d.U + d.n_sym) * d.B;
       };
       std::stable_sort(go.begin(), go.end(), [&](long long a, long long c) { return cost(a) > cost(c); });
       std::stable_sort(so.begin(), so.end(),

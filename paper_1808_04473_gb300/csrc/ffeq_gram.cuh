@@ -11,7 +11,8 @@
 // [n_sc][Ceff][U + n_sym][U] complex, Ceff = C (FD) or 1 (PD).
 //
 // One CTA per SM walks subcarriers b, b + gridDim.x, ...; the U + n_sym rows of
-// B complex of each are staged into shared memory (row stride B + 2 complex)
+// B complex of each are staged into shared memory (dense for the tensor-core
+// contractions, row stride B + 2 for the CUDA-core one)
 // with one cp.async.bulk per row on a per-stage mbarrier, up to three
 // subcarriers ahead of the contraction.
 #pragma once
@@ -63,7 +64,7 @@ struct GramUnit {
 };
 
 template <bool BATCH>
-__device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int warps, bool splitM) {
+__device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int warps, bool splitM, bool dense) {
   GramUnit u;
   if constexpr (BATCH) {
     const BatchDesc& d = p.desc[t];
@@ -72,7 +73,7 @@ __device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int wa
     // (d_off even: the paired float4 stores below need 16-byte aligned rows.)
     bool ok = (d.d_off & 1) == 0 && u.U >= 1 && u.U <= p.UP && u.NS >= 1 && u.NS <= kNsymMax && u.B >= 1 && u.B <= (1 << 20) &&
               u.Ceff >= 1 &&
-              u.B % u.Ceff == 0 && Mrows * (u.B + 2) <= p.stage_elems;
+              u.B % u.Ceff == 0 && Mrows * (dense ? u.B : u.B + 2) <= p.stage_elems;
     if (ok) {
       const GramSplit sp = gram_split(u.Ceff, Mrows, warps, splitM);
       ok = sp.slots <= p.n_slots && (sp.slots == 0 || Mrows * (p.UP + 1) <= p.slot_elems) &&
@@ -96,24 +97,45 @@ __device__ __forceinline__ GramUnit gram_unit(const GramParams& p, int t, int wa
   return u;
 }
 
-// Stage a unit's U + n_sym rows into `dst` (row stride B + 2 complex),
-// completing on `bar` (one cp.async.bulk per row; issued by one warp).  A unit
-// that failed its checks completes the phase with a plain arrive.
+// Stage a unit's U + n_sym rows into `dst`, completing on `bar`.
+// DENSE (row stride B): the unit's H rows and y rows are each contiguous in
+// global memory, so two cp.async.bulk copies move them (issued by lane 0; each
+// bulk copy has a fixed issue cost, and one per row would serialize the refill).
+// Otherwise (row stride B + 2, so that consecutive rows shift by 16 bytes of bank
+// offset for the CUDA-core contraction): one copy per row, spread over the lanes.
+// A unit that failed its checks completes the phase with a plain arrive.
+template <bool DENSE>
 __device__ __forceinline__ void issue_rows(const GramUnit& w, float2* dst, uint64_t* bar, int lane) {
   if (!w.ok) {
     if (lane == 0) mbar_arrive(bar);
     return;
   }
-  const int U = w.U, B = w.B, NS = w.NS, Mrows = U + NS, RS = B + 2;
+  const int U = w.U, B = w.B, NS = w.NS;
   // H and y are read once: evict them first, keeping the workspace this kernel
   // writes in L2 for the solve kernel that reads it next.
   const uint64_t pol = l2_evict_first_policy();
-  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Mrows) * B * 8u);
-  __syncwarp();
-  for (int r = lane; r < Mrows; r += 32) {
-    const float2* src = r < U ? w.H + static_cast<size_t>(r) * B : w.y + static_cast<size_t>(r - U) * B;
-    bulk_g2s_hint(dst + r * RS, src, static_cast<uint32_t>(B) * 8u, bar, pol);
+  const uint32_t hb = static_cast<uint32_t>(U) * B * 8u, yb = static_cast<uint32_t>(NS) * B * 8u;
+  if constexpr (DENSE) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar, hb + yb);
+      bulk_g2s_hint(dst, w.H, hb, bar, pol);
+      bulk_g2s_hint(dst + static_cast<size_t>(U) * B, w.y, yb, bar, pol);
+    }
+  } else {
+    const int Mrows = U + NS, RS = B + 2;
+    if (lane == 0) mbar_arrive_expect_tx(bar, hb + yb);
+    __syncwarp();
+    for (int r = lane; r < Mrows; r += 32) {
+      const float2* src = r < U ? w.H + static_cast<size_t>(r) * B : w.y + static_cast<size_t>(r - U) * B;
+      bulk_g2s_hint(dst + r * RS, src, static_cast<uint32_t>(B) * 8u, bar, pol);
+    }
   }
+}
+
+// Row stride of a staged unit for contraction policy C.
+template <class C>
+__host__ __device__ constexpr int stage_row_stride(int B) {
+  return C::kDense ? B : B + 2;
 }
 
 // Unit that follows unit t in slot order: static stride for uniform problems,
@@ -158,9 +180,9 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) g
     for (int s = 0; s < nst; ++s) {
       const int t = blockIdx.x + s * gridDim.x;
       if (t < n_units) {
-        const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM);
+        const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM, Contract::kDense);
         if (!w.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
-        issue_rows(w, stage0 + s * stageSize, &full[s], lane);
+        issue_rows<Contract::kDense>(w, stage0 + s * stageSize, &full[s], lane);
       } else if (BATCH && lane == 0) {
         mbar_arrive(&full[s]);   // the batch loop reads the sentinel through this stage
       }
@@ -181,9 +203,9 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) g
     // Batch: the unit handed out with this stage; uniform: static stride.
     const int t = BATCH ? ring[s] : blockIdx.x + it * gridDim.x;
     if (t >= n_units) break;
-    const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM);
+    const GramUnit w = gram_unit<BATCH>(p, t, kWarps, kSM, Contract::kDense);
     const int U = w.U, B = w.B, NS = w.NS, Ceff = w.Ceff;
-    const int Mrows = U + NS, RS = B + 2, S = B / Ceff;
+    const int Mrows = U + NS, RS = stage_row_stride<Contract>(B), S = B / Ceff;
     const GramSplit sp = gram_split(Ceff, Mrows, kWarps, kSM);
     const int P = sp.P, nM = sp.nM;
     const int nItems = w.ok ? Ceff * P * nM : 0;
@@ -208,9 +230,9 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) g
           if (lane == 0) ring[s] = tnb;
           if (p.bulk) {
             if (tnb < n_units) {
-              const GramUnit wn = gram_unit<BATCH>(p, tnb, kWarps, kSM);
+              const GramUnit wn = gram_unit<BATCH>(p, tnb, kWarps, kSM, Contract::kDense);
               if (!wn.ok && lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
-              issue_rows(wn, Ws, &full[s], lane);
+              issue_rows<Contract::kDense>(wn, Ws, &full[s], lane);
             } else if (lane == 0) {
               mbar_arrive(&full[s]);
             }
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) g
         // Uniform: a unit past the end is never waited on, so no arrival is needed.
         const int tn = t + nst * gridDim.x;
         if (p.bulk && warp == 0 && tn < n_units)
-          issue_rows(gram_unit<BATCH>(p, tn, kWarps, kSM), Ws, &full[s], lane);
+          issue_rows<Contract::kDense>(gram_unit<BATCH>(p, tn, kWarps, kSM, Contract::kDense), Ws, &full[s], lane);
       }
     };
     int SP = 0, PS = 0;
@@ -300,7 +322,7 @@ void gram_capacity(int B, int U, int n_sym, int Ceff, int& stage_elems, int& slo
   const int Mrows = U + n_sym;
   const GramSplit sp = gram_split(Ceff, Mrows, Contract::kWarps, Contract::kSplitM);
   // Both rounded to an even count: stages and slots start 16-byte aligned.
-  stage_elems = (Mrows * (B + 2) + 1) & ~1;
+  stage_elems = (Mrows * stage_row_stride<Contract>(B) + 1) & ~1;
   slot_elems = (Mrows * (padded_users(U) + 1) + 1) & ~1;
   slots = sp.slots;
 }

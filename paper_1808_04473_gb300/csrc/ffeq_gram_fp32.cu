@@ -87,6 +87,7 @@ struct SimtFp32 {
   static constexpr int kMinBlocks = MINB;
   static constexpr bool kSplitM = false;
   static constexpr bool kPrep = false;
+  static constexpr bool kDense = false;
   template <int UP, typename Out>
   __device__ __forceinline__ static void run(const float2* __restrict__ Ws, int RS, int Mrows, int U, int k0,
                                              int k1, bool vec, int lane, int /*mt*/, Out out) {

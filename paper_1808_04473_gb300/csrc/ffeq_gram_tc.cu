@@ -233,6 +233,7 @@ __device__ __forceinline__ void tc_tiles(const float2* __restrict__ Ws, int RS, 
 template <int MODE, int WARPS = 16, int MINB = 1>
 struct TensorSplit {
   static constexpr bool kPrep = false;
+  static constexpr bool kDense = true;
   static constexpr int kWarps = WARPS;
   static constexpr int kMinBlocks = MINB;
   static constexpr bool kSplitM = true;
@@ -271,6 +272,7 @@ __device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r
 
 struct TensorSplitPre {
   static constexpr bool kPrep = true;
+  static constexpr bool kDense = true;
   static constexpr int kWarps = 16;
   static constexpr int kMinBlocks = 1;
   static constexpr bool kSplitM = true;
