@@ -170,6 +170,140 @@ __device__ __forceinline__ int gj_sweep_pairs(float2 (&rp)[W / 2], float2 (&ip)[
   return fail;
 }
 
+// complex helpers for the block step
+__device__ __forceinline__ float2 gj_cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Gauss-Jordan sweep with 2 x 2 block pivots, deferred row scaling and paired
+// FMAs.  Same system, result layout and pivot semantics as gj_sweep_pairs: the
+// pivots reported are the sequential ones (the squared Cholesky diagonal).
+//
+// Two consecutive pivot steps k, k+1 (pivot columns 0 and 1: pair 0) are fused
+// into one broadcast round: lanes k and k+1 publish their rows (pivot-column
+// pair replaced by (1, 0) and (0, 1), the identity columns they turn into)
+// together with the 2 x 2 pivot block P.  With p_a = P00, h = P10 / p_a and
+// p_b = P11 - h P01 (the two sequential pivots), every lane applies
+//     new = base - alpha q_k - beta q_k+1
+// with, for the other lanes (f0, f1 their pivot-column entries, base pair 0 = 0),
+//     g = f0 / p_a,  beta = (f1 - g P01) / p_b,  alpha = g - beta h;
+// for lane k (base pair 0 = (1, 0)):   beta = P01 / p_b, alpha = -beta h;
+// for lane k+1 (base pair 0 = (0, 1)): alpha = h, beta = 0,
+// which is algebraically the sequential deferred-scaling sweep (pivot rows stay
+// multiplied by their pivot; the caller scales by the returned 1/p_i).  One warp
+// barrier per two pivots instead of two (two broadcast areas, alternating), and
+// both pivot rows are stored by one instruction.  UP must be even.  rowbuf:
+// 2 (4 W + 16) floats, 16-byte aligned.
+template <int UP, int W>
+__device__ __forceinline__ int gj_sweep_block2(float2 (&rp)[W / 2], float2 (&ip)[W / 2], float* rowbuf, int i,
+                                               bool writer, float& scale) {
+  static_assert(W % 4 == 0 && UP % 2 == 0, "block sweep needs W % 4 == 0 and even UP");
+  constexpr int NP = W / 2;                // column pairs
+  constexpr int kArea = 4 * W + 16;        // one broadcast area
+  int fail = 0;
+  float my_r = 1.f;
+#pragma unroll 1
+  for (int k = 0; k < UP; k += 2) {
+    float* area = rowbuf + ((k >> 1) & 1) * kArea;
+    float* qk = area;                        // [re plane W][im plane W] of row k
+    float* qk1 = area + 2 * W;               // the same for row k + 1
+    float* blk = area + 4 * W;               // P00, P01, P10, P11 (complex)
+    const bool mk = i == k, mk1 = i == k + 1;
+    if ((mk || mk1) && writer) {
+      float* q = mk ? qk : qk1;
+      const float2 r0 = mk ? make_float2(1.f, 0.f) : make_float2(0.f, 1.f);
+#pragma unroll
+      for (int m = 0; m < NP; m += 2) {
+        const float2 ra = m == 0 ? r0 : rp[m], ia = m == 0 ? make_float2(0.f, 0.f) : ip[m];
+        *reinterpret_cast<float4*>(q + 2 * m) = make_float4(ra.x, ra.y, rp[m + 1].x, rp[m + 1].y);
+        *reinterpret_cast<float4*>(q + W + 2 * m) = make_float4(ia.x, ia.y, ip[m + 1].x, ip[m + 1].y);
+      }
+      // Row k: P00 = entry 0, P01 = entry 1; row k + 1: P10, P11.
+      *reinterpret_cast<float4*>(blk + (mk ? 0 : 4)) = make_float4(rp[0].x, ip[0].x, rp[0].y, ip[0].y);
+    }
+    __syncwarp();
+    const float4 b0 = *reinterpret_cast<const float4*>(blk);
+    const float4 b1 = *reinterpret_cast<const float4*>(blk + 4);
+    const float2 P01 = make_float2(b0.z, b0.w), P10 = make_float2(b1.x, b1.y), P11 = make_float2(b1.z, b1.w);
+    const float pa = b0.x;
+    const bool oka = pa > 0.f;
+    const float ra = __frcp_rn(oka ? pa : 1.f);
+    const float2 h = make_float2(P10.x * ra, P10.y * ra);
+    const float pb = P11.x - (h.x * P01.x - h.y * P01.y);
+    const bool okb = pb > 0.f;
+    const float rb = __frcp_rn(okb ? pb : 1.f);
+    if (fail == 0) {
+      if (!oka) fail = k + 1;
+      else if (!okb) fail = k + 2;
+    }
+    if (mk) my_r = ra;
+    if (mk1) my_r = rb;
+    float2 alpha, beta;
+    {
+      const float2 f0 = make_float2(rp[0].x, ip[0].x), f1 = make_float2(rp[0].y, ip[0].y);
+      const float2 g = make_float2(f0.x * ra, f0.y * ra);
+      const float2 gp = gj_cmul(P01, g);
+      const float2 bt = make_float2((f1.x - gp.x) * rb, (f1.y - gp.y) * rb);
+      const float2 bh = gj_cmul(bt, h);
+      alpha = make_float2(g.x - bh.x, g.y - bh.y);
+      beta = bt;
+      if (mk) {
+        beta = make_float2(P01.x * rb, P01.y * rb);
+        const float2 t = gj_cmul(beta, h);
+        alpha = make_float2(-t.x, -t.y);
+      }
+      if (mk1) {
+        alpha = h;
+        beta = make_float2(0.f, 0.f);
+      }
+    }
+    const float2 nar = make_float2(-alpha.x, -alpha.x), pai = make_float2(alpha.y, alpha.y);
+    const float2 nai = make_float2(-alpha.y, -alpha.y);
+    const float2 nbr = make_float2(-beta.x, -beta.x), pbi = make_float2(beta.y, beta.y);
+    const float2 nbi = make_float2(-beta.y, -beta.y);
+    const float2 base0 = mk ? make_float2(1.f, 0.f) : (mk1 ? make_float2(0.f, 1.f) : make_float2(0.f, 0.f));
+    float2 nr[NP], ni[NP];
+#pragma unroll
+    for (int m = 0; m < NP; m += 2) {
+      const float4 ar = *reinterpret_cast<const float4*>(qk + 2 * m);
+      const float4 ai = *reinterpret_cast<const float4*>(qk + W + 2 * m);
+      const float4 br = *reinterpret_cast<const float4*>(qk1 + 2 * m);
+      const float4 bi = *reinterpret_cast<const float4*>(qk1 + W + 2 * m);
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int c = m + hh;
+        const float2 akr = hh == 0 ? make_float2(ar.x, ar.y) : make_float2(ar.z, ar.w);
+        const float2 aki = hh == 0 ? make_float2(ai.x, ai.y) : make_float2(ai.z, ai.w);
+        const float2 bkr = hh == 0 ? make_float2(br.x, br.y) : make_float2(br.z, br.w);
+        const float2 bki = hh == 0 ? make_float2(bi.x, bi.y) : make_float2(bi.z, bi.w);
+        const float2 baser = c == 0 ? base0 : rp[c];
+        const float2 basei = c == 0 ? make_float2(0.f, 0.f) : ip[c];
+        // re: base - a.re qk.re + a.im qk.im - b.re qk1.re + b.im qk1.im
+        float2 tr = __ffma2_rn(nar, akr, baser);
+        tr = __ffma2_rn(pai, aki, tr);
+        tr = __ffma2_rn(nbr, bkr, tr);
+        tr = __ffma2_rn(pbi, bki, tr);
+        // im: base - a.re qk.im - a.im qk.re - b.re qk1.im - b.im qk1.re
+        float2 ti = __ffma2_rn(nar, aki, basei);
+        ti = __ffma2_rn(nai, akr, ti);
+        ti = __ffma2_rn(nbr, bki, ti);
+        ti = __ffma2_rn(nbi, bkr, ti);
+        const int d = (c + NP - 1) % NP;   // rotate left by one pair (inverse columns to the end)
+        nr[d] = tr;
+        ni[d] = ti;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      rp[m] = nr[m];
+      ip[m] = ni[m];
+    }
+  }
+  __syncwarp();   // the areas may be reused after the sweep
+  scale = my_r;
+  return fail;
+}
+
 // The same sweep (deferred scaling, two steps per trip, rotation by two, one
 // broadcast buffer per step) on interleaved complex registers with scalar FMAs
 // (gj_update), which rounds exactly like gj_sweep_pairs.  rowbuf: 2 (2W + 4)

@@ -38,8 +38,11 @@ struct SolveLayout {
   // Per matrix: pivot-row broadcast buffer (UP + kNsymMax complex), fusion
   // numerators [kNsymMax][UP] complex and denominators [UP] floats; padded so
   // consecutive matrices start 64 bytes apart modulo 128.
-  // (two broadcast buffers of 2W + 4 floats for the paired sweep, W = UP + kNsymMax)
-  static constexpr int kRow = 2 * (UP + kNsymMax) + 4;
+  // (two broadcast buffers of 2W + 4 floats for the paired sweep, W = UP + kNsymMax;
+  // two areas of 4 UP + 16 floats for the block sweep on the matrix)
+  static constexpr int kRowPairs = 2 * (UP + kNsymMax) + 4;
+  static constexpr int kRowBlock = 4 * UP + 16;
+  static constexpr int kRow = kRowPairs > kRowBlock ? kRowPairs : kRowBlock;
   static constexpr int kNum = kNsymMax * UP;
   static constexpr int kMat = ((kRow + kNum + UP / 2 + 15) / 16) * 16 + 8;   // float2 units
 };
@@ -260,7 +263,13 @@ __global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
       ip[m] = make_float2(mrow[2 * m].y, mrow[2 * m + 1].y);
     }
     float rs = 1.f;
-    fail = gj_sweep_pairs<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+    // 32 pivots: fuse pivot pairs (half the broadcast rounds); up to 16: the
+    // sequential paired sweep is faster (measured).
+    if constexpr (UP >= 32) {
+      fail = gj_sweep_block2<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+    } else {
+      fail = gj_sweep_pairs<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+    }
     float2 arow[UP];
     float Ai = 1.f;
 #pragma unroll
