@@ -206,11 +206,14 @@ ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, fl
 /* Device staging bytes ffeq_equalize_host needs (inputs, outputs and workspace). */
 ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes);
 
-/* Same computation on HOST buffers: copies H and y to the caller's device
- * staging buffer, runs ffeq_equalize, copies z, sigma2 (and llr, info when not
- * NULL) back, and synchronizes the stream before returning.  Host buffers should
- * be page-locked for full copy bandwidth.  staging is a device pointer of at
- * least ffeq_host_staging_size bytes, 256-byte aligned. */
+/* Same computation on HOST buffers, synchronizing the stream before returning.
+ * When every buffer passed is page-locked (cudaHostAlloc / cudaHostRegister, so
+ * the GPU can address it in place), the kernels read H and y and write the
+ * outputs directly in host memory over the host link (NVLink-C2C on Grace
+ * systems) and only the workspace lives in the staging buffer.  Otherwise H and
+ * y are copied to the staging buffer, ffeq_equalize runs, and z, sigma2 (and llr,
+ * info when not NULL) are copied back.  Same results either way.  staging is a
+ * device pointer of at least ffeq_host_staging_size bytes, 256-byte aligned. */
 ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const void* y_host,
                                float N0, float Es, void* z_host, float* sigma2_host,
                                float* llr_host, int* info_host,

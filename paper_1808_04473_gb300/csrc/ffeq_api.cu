@@ -131,7 +131,7 @@ ffeq_status check_common(const ffeq_plan* plan, const void* workspace, size_t wo
 }
 
 ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y, void* workspace,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool host_inputs = false) {
   const ffeq_problem& p = plan->p;
   if (!H || !y || !aligned(H, 8) || !aligned(y, 8)) return FFEQ_ERR_INVALID_ARG;
   ffeq::GramParams gp{};
@@ -144,7 +144,8 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.Ceff = plan->Ceff;
   gp.n_sc = p.n_sc;
   gp.n_sym = p.n_sym;
-  gp.bulk = (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
+  // Inputs in host memory (read in place over the host link) take plain loads.
+  gp.bulk = !host_inputs && (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
   if (!ffeq::gram_configure(gp, p.precision, plan->gram_variant, plan->gram_stages)) return FFEQ_ERR_UNSUPPORTED;
   const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                                  : ffeq::launch_gram_tc(gp, p.precision, st);
@@ -236,9 +237,29 @@ ffeq_status ffeq_fuse_equalize(const ffeq_plan* plan, const void* workspace, siz
   return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, static_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+namespace {
+ffeq_status equalize_impl(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
+                          float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
+                          void* stream, bool host_inputs);
+}  // namespace
+
+extern "C" {
+
 ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
                           float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
                           void* stream) {
+  return equalize_impl(plan, H, y, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream, false);
+}
+
+}  // extern "C"
+
+namespace {
+
+ffeq_status equalize_impl(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
+                          float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
+                          void* stream, bool host_inputs) {
   if (plan && bad_scalars(N0, Es)) return FFEQ_ERR_INVALID_ARG;
   ffeq_status r = check_common(plan, workspace, workspace_bytes);
   if (r != FFEQ_OK || plan->p.n_sc == 0) return r;
@@ -249,10 +270,25 @@ ffeq_status ffeq_equalize(const ffeq_plan* plan, const void* H, const void* y, f
   if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
   if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  r = local_preprocess(plan, H, y, workspace, st);
+  r = local_preprocess(plan, H, y, workspace, st, host_inputs);
   if (r != FFEQ_OK) return r;
   return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st, H, y);
 }
+
+// Device view of a host buffer the GPU can address in place (page-locked or
+// registered memory), else nullptr.
+void* device_view(const void* host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
 
 namespace {
 
@@ -440,6 +476,26 @@ ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const 
   if (!H_host || !y_host || !z_host || !sigma2_host || !staging) return FFEQ_ERR_INVALID_ARG;
   if (staging_bytes < need || !aligned(staging, kAlign)) return FFEQ_ERR_INVALID_ARG;
   if (p.llr_bits && !llr_host) return FFEQ_ERR_INVALID_ARG;
+  // Page-locked host buffers: the kernels read H, y and write the outputs in
+  // place over the host link (on Grace systems NVLink-C2C), so no staging copy
+  // is made; only the workspace uses the staging buffer.
+  {
+    void* vH = device_view(H_host);
+    void* vy = device_view(y_host);
+    void* vz = device_view(z_host);
+    void* vs = device_view(sigma2_host);
+    void* vl = p.llr_bits ? device_view(llr_host) : nullptr;
+    void* vi = info_host ? device_view(info_host) : nullptr;
+    if (vH && vy && vz && vs && (!p.llr_bits || vl) && (!info_host || vi)) {
+      size_t ws = 0;
+      ffeq_workspace_size(plan, &ws);
+      ffeq_status r = equalize_impl(plan, vH, vy, N0, Es, vz, static_cast<float*>(vs), static_cast<float*>(vl),
+                                    static_cast<int*>(vi), ws ? staging : nullptr, ws, stream, true);
+      if (r != FFEQ_OK) return r;
+      const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+      return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+    }
+  }
   const Sizes s = buffer_sizes(p);
   char* base = static_cast<char*>(staging);
   char* dH = base;

@@ -185,6 +185,31 @@ def test_host_buffer_entry_point_matches_device_path(ff):
     assert ff.ffeq_device_status() == 0
 
 
+@pytest.mark.parametrize("pinned", [True, False], ids=["in-place", "staged"])
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_host_entry_point_both_paths(ff, arch, pinned):
+    """Page-locked buffers are read and written in place by the kernels; pageable
+    ones go through the staging copies.  Both equal the device path bit for bit."""
+    p = synth.make_problem(128, 12, 4, 33, 5, seed=17, bits=4)
+    plan = ff.ffeq_plan_create(128, 12, 4, 33, 5, arch=arch, precision=ff.BF16X3, llr_bits=4)
+    nbytes = ff.ffeq_host_staging_size(plan)
+    staging = torch.empty(nbytes, dtype=torch.uint8, device="cuda:0")
+    Ceff = 4 if arch == 1 else 1
+
+    def buf(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return t.pin_memory() if pinned else t
+    Hh, yh = buf(p.H), buf(p.y)
+    z = buf(np.zeros((33, 5, 12), np.complex64))
+    s2 = buf(np.zeros((33, 12), np.float32))
+    L = buf(np.zeros((33, 5, 12, 4), np.float32))
+    info = buf(np.full((33, Ceff), -1, np.int32))
+    ff.ffeq_equalize_host(plan, Hh, yh, p.N0, p.Es, z, s2, L, info, staging, nbytes)
+    g = _gpu(ff, p, arch, 0, llr_bits=4, precision=2)
+    assert np.array_equal(z.numpy(), g["z"]) and np.array_equal(s2.numpy(), g["sigma2"])
+    assert np.array_equal(L.numpy(), g["llr"]) and (info.numpy() == 0).all()
+
+
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
 @pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp32", "tf32x3", "bf16x3"])
 def test_full_size_throughput_workload_sampled(ff, arch, precision):
