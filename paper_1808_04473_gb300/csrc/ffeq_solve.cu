@@ -145,8 +145,16 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
 // LPR lanes per row: with LPR = 2 the two lanes of row i hold halves of its
 // augmented row (columns [0, W/2) and [W/2, W)), halving the work per lane and
 // step; the pivot column k < UP always lies in the first half.
+// Uniform problems with one lane per row and up to 16 users: at most 64
+// registers, so that 8 CTAs of 128 threads fit one SM (the FD throughput
+// workload's 1200 subcarriers then run in one wave).
 template <int UP, int LPR, bool BATCH>
-__global__ void __launch_bounds__(512) solve_fuse_kernel(const SolveParams p) {
+constexpr int solve_min_blocks() {
+  return (!BATCH && LPR == 1 && UP <= 16) ? 2 : 1;
+}
+
+template <int UP, int LPR, bool BATCH>
+__global__ void __launch_bounds__(512, (solve_min_blocks<UP, LPR, BATCH>())) solve_fuse_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   using Lay = SolveLayout<UP>;
   constexpr int GS = UP * LPR;                // lanes per matrix
