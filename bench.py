@@ -312,6 +312,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"],
                     help="arithmetic of the local preprocessing (solve and fusion are FP32)")
+    ap.add_argument("--tuning", default=None,
+                    help="pin the contraction shapes instead of autotuning: PD_SHAPE,PD_STAGES,FD_SHAPE,FD_STAGES "
+                         "(values of ffeq_plan_set_tuning; for reproducible profiles)")
     ap.add_argument("--workload", default="ofdm", choices=["ofdm", "uneven"],
                     help="ofdm: the headline B=256 U=16 C=8 1200x14 step; uneven: 4096 instances of mixed "
                          "size per step (uneven-batch ABI, CUDA-graph replay)")
@@ -374,10 +377,14 @@ def main():
         steps brackets each kernel with events (which serializes the launches, so the
         per-kernel times are upper bounds) for the breakdown."""
         plans, ws_bytes, ws = make_plans(precision)
+        pinned = [int(v) for v in args.tuning.split(",")] if args.tuning else None
         for a in plans:                  # launch shape chosen by timing (outside the timed region)
             o = outs[a]
-            ffeq.ffeq_plan_autotune(plans[a], Hs[0], ys[0], p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
-                                    ws_bytes[a], stream, 10)
+            if pinned and precision == args.precision:
+                ffeq.ffeq_plan_set_tuning(plans[a], pinned[2 * a:2 * a + 2])
+            else:
+                ffeq.ffeq_plan_autotune(plans[a], Hs[0], ys[0], p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
+                                        ws_bytes[a], stream, 10)
 
         def step(i, evs=None):
             for a in (ffeq.PD, ffeq.FD):
