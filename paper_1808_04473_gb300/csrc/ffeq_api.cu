@@ -95,7 +95,7 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (spc * Ceff * ffeq::padded_users(p->U) * (Ceff == 1 && ffeq::padded_users(p->U) == 16 ? 2 : 1) > 512 ||
       ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
-  if (p->refine > 0 && ffeq::refine_chunk(p->B, p->U, Ceff, p->n_sym) < 1) return FFEQ_ERR_UNSUPPORTED;
+  if (p->refine > 0 && !ffeq::refine_fits(p->B, p->U, Ceff, p->n_sym)) return FFEQ_ERR_UNSUPPORTED;
   ffeq_plan* plan = new (std::nothrow) ffeq_plan;
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   plan->p = *p;
@@ -206,7 +206,6 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   rp.n_sc = p.n_sc;
   rp.n_sym = p.n_sym;
   rp.steps = p.refine;
-  rp.chunk = ffeq::refine_chunk(p.B, p.U, plan->Ceff, p.n_sym);
   rp.unbiased = sp.unbiased;
   rp.llr_bits = p.llr_bits;
   rp.N0 = sp.N0;

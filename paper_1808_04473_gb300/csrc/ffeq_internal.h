@@ -99,18 +99,17 @@ struct RefineParams {
   const float2* H;      // [n_sc][U][B]
   const float2* y;      // [n_sc][n_sym][B]
   const float2* D;      // contraction output (for G_uu)
-  const float2* As;     // [n_sc][Ceff][U][U] inverses, transposed
-  const float2* Xs;     // [n_sc][Ceff][n_sym][U]
+  float2* As;           // [n_sc][Ceff][U][U] inverses, transposed (refined in place)
+  float2* Xs;           // [n_sc][Ceff][n_sym][U] (refined in place)
   const int* fails;     // [n_sc][Ceff]
   float2* z;
   float* sigma2;
   float* llr;
   int B, U, Ceff, n_sc, n_sym, steps, unbiased, llr_bits;
-  int chunk;            // clusters refined together (refine_chunk)
   float N0, rho, llr_scale;
 };
-// Clusters the refinement kernel can hold at once (0: the problem does not fit).
-int refine_chunk(int B, int U, int Ceff, int n_sym);
+// Whether one local system fits the refinement kernel's shared memory.
+bool refine_fits(int B, int U, int Ceff, int n_sym);
 size_t refine_smem_bytes(int B, int U, int Ceff, int n_sym);
 cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream);
 

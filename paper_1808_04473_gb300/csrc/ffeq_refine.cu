@@ -4,8 +4,8 @@
 // operands rounded to hi + lo pairs, so the solved systems carry a relative
 // perturbation u (2^-16 for BF16x3) that the solve amplifies by
 // kappa(G_c + rho I).  A residual taken against the stored G_c cannot see that
-// error; this kernel forms it from H and y instead (FP32, per subcarrier, all
-// clusters of the subcarrier in one CTA):
+// error; these kernels form it from H and y instead (FP32, one CTA per local
+// system, then one per subcarrier for the fusion):
 //   M_c = H_c^H H_c + rho I,  b_c = H_c^H y_c                   (Sec. III-A, II-C)
 //   r_c = b_c - M_c x_c = H_c^H (y_c - H_c x_c) - rho x_c,   x_c <- x_c + A~_c r_c
 // with A~_c the inverse computed by the solve kernel (`steps` times).  The
@@ -26,141 +26,142 @@
 namespace ffeq {
 namespace {
 
-constexpr int kRefineThreads = 512;
+constexpr int kRefineThreadsMax = 512;   // per system: 2 S threads, 128..512
+constexpr int kFuseThreads = 256;
 
-// Shared memory: clusters are refined in chunks of CC (all of them when they
-// fit); the fused numerators and denominators of every cluster persist.
+// Shared memory of one system (cluster c of subcarrier k; S antennas).
 struct RefineLayout {
-  int B, U, NS, Ceff, S, CC, HS, W;
-  size_t hs, pm, va, rb, rr, an, fz, dn, total;   // offsets in bytes
-  __host__ __device__ RefineLayout(int B_, int U_, int NS_, int Ceff_, int CC_)
-      : B(B_), U(U_), NS(NS_), Ceff(Ceff_), S(B_ / Ceff_), CC(CC_), HS(CC_ * (B_ / Ceff_) + 1), W(U_ + NS_) {
+  int U, NS, S, SS, W;
+  size_t hs, pm, va, rb, rr, an, total;   // offsets in bytes
+  __host__ __device__ RefineLayout(int U_, int NS_, int S_)
+      : U(U_), NS(NS_), S(S_), SS(S_ + 1), W(U_ + NS_) {
     size_t o = 0;
-    hs = o;  o += static_cast<size_t>(U) * HS * 8;          // H rows of the chunk's antennas
-    pm = o;  o += static_cast<size_t>(CC) * W * U * 8;      // per cluster: columns a_j of A~, then x_n
-    va = o;  o += static_cast<size_t>(U) * HS * 8;          // V = H_c a_j per antenna
-    rb = o;  o += static_cast<size_t>(NS) * HS * 8;         // y - H x per antenna
-    rr = o;  o += static_cast<size_t>(CC) * NS * U * 8;     // residual
-    an = o;  o += static_cast<size_t>(CC) * U * U * 8;      // next inverse
-    fz = o;  o += static_cast<size_t>(Ceff) * NS * U * 8;   // fused numerators x / A_uu
-    dn = o;  o += static_cast<size_t>(Ceff) * U * 4;        // fusion denominators g / A_uu
-    o += 16;                                                // failure flag
+    hs = o;  o += static_cast<size_t>(U) * SS * 8;      // H_c rows (stride S + 1 complex)
+    pm = o;  o += static_cast<size_t>(W) * U * 8;       // columns a_j of A~, then x_n
+    va = o;  o += static_cast<size_t>(U) * SS * 8;      // V = H_c a_j per antenna
+    rb = o;  o += static_cast<size_t>(NS) * SS * 8;     // y_c - H_c x per antenna
+    rr = o;  o += static_cast<size_t>(NS) * U * 8;      // residual
+    an = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse
     total = o;
   }
 };
 
-template <int UP>
-__global__ void __launch_bounds__(kRefineThreads) refine_kernel(const RefineParams p) {
+// One CTA per local system: `steps` refinement steps, then the refined
+// estimates and inverse (diagonal included) go back to the workspace.
+__global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const RefineParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const RefineLayout L(p.B, p.U, p.n_sym, p.Ceff, p.chunk);
-  const int B = L.B, U = L.U, NS = L.NS, Ceff = L.Ceff, S = L.S, HS = L.HS, W = L.W;
+  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, B = p.B, S = B / Ceff;
+  const RefineLayout L(U, NS, S);
+  const int SS = L.SS, W = L.W;
   float2* Hs = reinterpret_cast<float2*>(smem + L.hs);
   float2* P = reinterpret_cast<float2*>(smem + L.pm);
   float2* Va = reinterpret_cast<float2*>(smem + L.va);
   float2* Rb = reinterpret_cast<float2*>(smem + L.rb);
   float2* Rr = reinterpret_cast<float2*>(smem + L.rr);
   float2* An = reinterpret_cast<float2*>(smem + L.an);
-  float2* Fz = reinterpret_cast<float2*>(smem + L.fz);
-  float* Dn = reinterpret_cast<float*>(smem + L.dn);
-  int* failed = reinterpret_cast<int*>(smem + L.total - 16);
-  const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const size_t sys = blockIdx.x;
+  const int k = static_cast<int>(sys / Ceff), c = static_cast<int>(sys % Ceff);
+  const int tid = threadIdx.x, nt = blockDim.x;
   const float rho = p.rho;
-  const float2* Hk = p.H + static_cast<size_t>(k) * U * B;
-  const float2* yk = p.y + static_cast<size_t>(k) * NS * B;
-  const size_t sys0 = static_cast<size_t>(k) * Ceff;
+  const float2* Hk = p.H + static_cast<size_t>(k) * U * B + static_cast<size_t>(c) * S;
+  const float2* yk = p.y + static_cast<size_t>(k) * NS * B + static_cast<size_t>(c) * S;
 
+  for (int e = tid; e < U * S; e += nt) {
+    const int u = e / S, b = e - u * S;
+    Hs[u * SS + b] = Hk[static_cast<size_t>(u) * B + b];
+  }
+  // Wait for the solve kernel (programmatic dependent launch), then its results.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  for (int e = tid; e < W * U; e += nt) {
+    const int j = e / U, i = e - j * U;
+    P[e] = j < U ? p.As[(sys * U + j) * U + i] : p.Xs[(sys * NS + (j - U)) * U + i];
+  }
+  __syncthreads();
+  const bool failed = p.fails[sys] != 0;
+
+  for (int step = 0; step < p.steps && !failed; ++step) {
+    // V = H_c [A~ | X] per (antenna b, column j); y_c - H_c x for the estimates.
+    for (int e = tid; e < S * W; e += nt) {
+      const int j = e / S, b = e - j * S;
+      const float2* pj = P + j * U;
+      float2 v = make_float2(0.f, 0.f);
+      for (int u = 0; u < U; ++u) v = cfma(Hs[u * SS + b], pj[u], v);
+      if (j < U) {
+        Va[j * SS + b] = v;
+      } else {
+        const int n = j - U;
+        Rb[n * SS + b] = csub(yk[static_cast<size_t>(n) * B + b], v);
+      }
+    }
+    __syncthreads();
+    // r = H_c^H (y_c - H_c x) - rho x;  next inverse 2 A - V^H V - rho A^H A.
+    for (int e = tid; e < NS * U; e += nt) {
+      const int n = e / U, u = e - n * U;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int b = 0; b < S; ++b) sum = cfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
+      const float2 x = P[(U + n) * U + u];
+      Rr[e] = make_float2(sum.x - rho * x.x, sum.y - rho * x.y);
+    }
+    for (int e = tid; e < U * U; e += nt) {
+      const int j = e / U, i = e - j * U;   // entry (i, j)
+      float2 vv = make_float2(0.f, 0.f);
+      for (int b = 0; b < S; ++b) vv = cfma_conj(Va[i * SS + b], Va[j * SS + b], vv);
+      float2 aa = make_float2(0.f, 0.f);
+      const float2* ai = P + i * U;
+      const float2* aj = P + j * U;
+      for (int v = 0; v < U; ++v) aa = cfma_conj(ai[v], aj[v], aa);
+      const float2 a = aj[i];
+      An[e] = make_float2(2.f * a.x - vv.x - rho * aa.x, 2.f * a.y - vv.y - rho * aa.y);
+    }
+    __syncthreads();
+    // x += A~ r   (A~[u][v] = column v of A~ at row u), then A~ <- next inverse.
+    for (int e = tid; e < NS * U; e += nt) {
+      const int n = e / U, u = e - n * U;
+      float2 d = make_float2(0.f, 0.f);
+      for (int v = 0; v < U; ++v) d = cfma(P[v * U + u], Rr[n * U + v], d);
+      float2* x = P + (U + n) * U + u;
+      *x = cadd(*x, d);
+    }
+    __syncthreads();
+    for (int e = tid; e < U * U; e += nt) P[e] = An[e];
+    __syncthreads();
+  }
+  // Refined estimates and inverse back to the workspace (same layouts).
+  for (int e = tid; e < W * U; e += nt) {
+    const int j = e / U, i = e - j * U;
+    if (j < U) p.As[(sys * U + j) * U + i] = P[e];
+    else p.Xs[(sys * NS + (j - U)) * U + i] = P[e];
+  }
+  // Let the fusion kernel start its launch while this grid drains.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Per subcarrier: fusion terms from the refined systems (as the solve kernel:
+// weight g / A_uu with g = mu or 1), sum over clusters, z, sigma^2 and LLRs.
+__global__ void __launch_bounds__(kFuseThreads) refine_fuse_kernel(const RefineParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, W = U + NS;
+  float2* Fz = reinterpret_cast<float2*>(smem);                        // [Ceff][NS][U]
+  float* Dn = reinterpret_cast<float*>(Fz + static_cast<size_t>(Ceff) * NS * U);   // [Ceff][U]
+  int* failed = reinterpret_cast<int*>(Dn + static_cast<size_t>(Ceff) * U);
+  const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const size_t sys0 = static_cast<size_t>(k) * Ceff;
+  const float rho = p.rho;
   if (tid == 0) *failed = 0;
-  // Wait for the solve kernel (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (tid < Ceff && p.fails[sys0 + tid] != 0) atomicOr(failed, 1);
-
-  for (int c0 = 0; c0 < Ceff; c0 += L.CC) {
-    const int cc = Ceff - c0 < L.CC ? Ceff - c0 : L.CC;   // clusters in this chunk
-    const int nb = cc * S;                                 // their antennas, from b0
-    const int b0 = c0 * S;
-    for (int e = tid; e < U * nb; e += nt) {
-      const int u = e / nb, b = e - u * nb;
-      Hs[u * HS + b] = Hk[static_cast<size_t>(u) * B + b0 + b];
-    }
-    for (int e = tid; e < cc * W * U; e += nt) {
-      const int c = e / (W * U), r = e - c * W * U, j = r / U, i = r - j * U;
-      const size_t sys = sys0 + c0 + c;
-      P[e] = j < U ? p.As[(sys * U + j) * U + i] : p.Xs[(sys * NS + (j - U)) * U + i];
-    }
-    __syncthreads();
-
-    for (int step = 0; step < p.steps; ++step) {
-      // V = H_c [A~_c | X_c] per antenna b (cluster c = b / S); y - H_c x for the estimates.
-      for (int b = tid; b < nb; b += nt) {
-        const int c = b / S;
-        float2 h[UP];
-#pragma unroll
-        for (int u = 0; u < UP; ++u) h[u] = u < U ? Hs[u * HS + b] : make_float2(0.f, 0.f);
-        for (int j = 0; j < W; ++j) {
-          const float2* pj = P + (c * W + j) * U;
-          float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int u = 0; u < UP; ++u)
-            if (u < U) v = cfma(h[u], pj[u], v);
-          if (j < U) {
-            Va[j * HS + b] = v;
-          } else {
-            const int n = j - U;
-            Rb[n * HS + b] = csub(yk[static_cast<size_t>(n) * B + b0 + b], v);
-          }
-        }
-      }
-      __syncthreads();
-      // r_c = H_c^H (y_c - H_c x_c) - rho x_c;  next inverse 2 A - V^H V - rho A^H A.
-      for (int e = tid; e < cc * NS * U; e += nt) {
-        const int c = e / (NS * U), r = e - c * NS * U, n = r / U, u = r - n * U;
-        float2 sum = make_float2(0.f, 0.f);
-        for (int b = c * S; b < (c + 1) * S; ++b) sum = cfma_conj(Hs[u * HS + b], Rb[n * HS + b], sum);
-        const float2 x = P[(c * W + U + n) * U + u];
-        Rr[e] = make_float2(sum.x - rho * x.x, sum.y - rho * x.y);
-      }
-      for (int e = tid; e < cc * U * U; e += nt) {
-        const int c = e / (U * U), r = e - c * U * U, j = r / U, i = r - j * U;   // entry (i, j)
-        float2 vv = make_float2(0.f, 0.f);
-        for (int b = c * S; b < (c + 1) * S; ++b) vv = cfma_conj(Va[i * HS + b], Va[j * HS + b], vv);
-        float2 aa = make_float2(0.f, 0.f);
-        const float2* ai = P + (c * W + i) * U;
-        const float2* aj = P + (c * W + j) * U;
-        for (int v = 0; v < U; ++v) aa = cfma_conj(ai[v], aj[v], aa);
-        const float2 a = aj[i];
-        An[e] = make_float2(2.f * a.x - vv.x - rho * aa.x, 2.f * a.y - vv.y - rho * aa.y);
-      }
-      __syncthreads();
-      // x_c += A~_c r_c   (A~[u][v] = column v of A~ at row u), then A~ <- next inverse.
-      for (int e = tid; e < cc * NS * U; e += nt) {
-        const int c = e / (NS * U), r = e - c * NS * U, n = r / U, u = r - n * U;
-        float2 d = make_float2(0.f, 0.f);
-        for (int v = 0; v < U; ++v) d = cfma(P[(c * W + v) * U + u], Rr[(c * NS + n) * U + v], d);
-        float2* x = P + (c * W + U + n) * U + u;
-        *x = cadd(*x, d);
-      }
-      __syncthreads();
-      for (int e = tid; e < cc * U * U; e += nt) {
-        const int c = e / (U * U), r = e - c * U * U;
-        P[c * W * U + r] = An[e];
-      }
-      __syncthreads();
-    }
-
-    // ---- fusion terms (as the solve kernel): weight g / A_uu with g = mu or 1
-    for (int e = tid; e < cc * U; e += nt) {
-      const int c = e / U, u = e - c * U;
-      const float gii = p.D[((sys0 + c0 + c) * W + u) * U + u].x;
-      const float A = P[(c * W + u) * U + u].x;
-      const float invA = 1.f / A;
-      const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * A, 0.f);
-      Dn[(c0 + c) * U + u] = (p.unbiased ? mu : 1.f) * invA;
-      for (int n = 0; n < NS; ++n) Fz[((c0 + c) * NS + n) * U + u] = cscale(P[(c * W + U + n) * U + u], invA);
-    }
-    __syncthreads();
+  for (int e = tid; e < Ceff * U; e += nt) {
+    const int c = e / U, u = e - c * U;
+    const size_t sys = sys0 + c;
+    const float gii = p.D[(sys * W + u) * U + u].x;
+    const float A = p.As[(sys * U + u) * U + u].x;
+    const float invA = 1.f / A;
+    const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * A, 0.f);
+    Dn[e] = (p.unbiased ? mu : 1.f) * invA;
+    for (int n = 0; n < NS; ++n) Fz[(c * NS + n) * U + u] = cscale(p.Xs[(sys * NS + n) * U + u], invA);
   }
-
+  __syncthreads();
   const int bits = p.llr_bits, hb = bits / 2;
   const bool fail = *failed != 0;
   for (int e = tid; e < NS * U; e += nt) {
@@ -191,49 +192,51 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const RefinePara
   }
 }
 
-template <int UP>
-cudaError_t launch_refine_up(const RefineParams& p, cudaStream_t stream) {
-  static int configured[64] = {0};
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return err;
-  if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(refine_kernel<UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (err != cudaSuccess) return err;
-    configured[dev] = 1;
-  }
+cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       const RefineParams& p) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(p.n_sc);
-  cfg.blockDim = dim3(kRefineThreads);
-  cfg.dynamicSmemBytes = RefineLayout(p.B, p.U, p.n_sym, p.Ceff, p.chunk).total;
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, refine_kernel<UP>, p);
+  void* args[] = {const_cast<RefineParams*>(&p)};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace
 
-int refine_chunk(int B, int U, int Ceff, int n_sym) {
-  for (int cc = Ceff; cc >= 1; --cc)
-    if (RefineLayout(B, U, n_sym, Ceff, cc).total <= 227 * 1024) return cc;
-  return 0;
+bool refine_fits(int B, int U, int Ceff, int n_sym) {
+  return RefineLayout(U, n_sym, B / Ceff).total <= 227 * 1024;
 }
 
-size_t refine_smem_bytes(int B, int U, int Ceff, int n_sym) {
-  const int cc = refine_chunk(B, U, Ceff, n_sym);
-  return cc ? RefineLayout(B, U, n_sym, Ceff, cc).total : 0;
-}
+size_t refine_smem_bytes(int B, int U, int Ceff, int n_sym) { return RefineLayout(U, n_sym, B / Ceff).total; }
 
 cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream) {
-  switch (padded_users(p.U)) {
-    case 8: return launch_refine_up<8>(p, stream);
-    case 16: return launch_refine_up<16>(p, stream);
-    default: return launch_refine_up<32>(p, stream);
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 64 && !configured[dev]) {
+    err = cudaFuncSetAttribute(refine_system_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(refine_fuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    configured[dev] = 1;
   }
+  const size_t nsys = static_cast<size_t>(p.n_sc) * p.Ceff;
+  const int S = p.B / p.Ceff;
+  const int threads = 2 * S < 128 ? 128 : (2 * S > kRefineThreadsMax ? kRefineThreadsMax : ((2 * S + 31) / 32) * 32);
+  err = launch_pdl(reinterpret_cast<const void*>(refine_system_kernel), dim3(static_cast<unsigned>(nsys)),
+                   dim3(threads), RefineLayout(p.U, p.n_sym, S).total, stream, p);
+  if (err != cudaSuccess) return err;
+  const size_t fsmem = static_cast<size_t>(p.Ceff) * p.n_sym * p.U * 8 + static_cast<size_t>(p.Ceff) * p.U * 4 + 16;
+  return launch_pdl(reinterpret_cast<const void*>(refine_fuse_kernel), dim3(p.n_sc), dim3(kFuseThreads), fsmem,
+                    stream, p);
 }
 
 }  // namespace ffeq
