@@ -81,8 +81,13 @@ typedef enum { FFEQ_PD = 0, FFEQ_FD = 1 } ffeq_arch;
  *   FFEQ_TF32X3  tensor cores, each FP32 operand split into TF32 hi + lo, three
  *                products accumulated in FP32 (about FP32 accuracy).
  *   FFEQ_BF16X3  tensor cores, BF16 hi + lo split, three products, FP32
- *                accumulation (mixed precision: ~16 significand bits per operand). */
-typedef enum { FFEQ_FP32 = 0, FFEQ_TF32X3 = 1, FFEQ_BF16X3 = 2 } ffeq_precision;
+ *                accumulation (mixed precision: ~16 significand bits per operand).
+ *   FFEQ_FP16X3  tensor cores, FP16 hi + lo split, three products, FP32
+ *                accumulation: ~22 significand bits at the BF16 rate, within
+ *                FP16's range (entries of H and y below 32768 in magnitude; the
+ *                lo part loses bits for entries below about 2^-3, so inputs
+ *                should be of order one, as with unit-variance channels). */
+typedef enum { FFEQ_FP32 = 0, FFEQ_TF32X3 = 1, FFEQ_BF16X3 = 2, FFEQ_FP16X3 = 3 } ffeq_precision;
 typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
 
 /* Problem statement (Sec. II-A, II-B, VI): B antennas, U users, C clusters,
@@ -95,15 +100,24 @@ typedef struct {
   int estimate;    /* ffeq_estimate */
   int llr_bits;    /* 0 (no LLRs), 2, 4, 6 or 8 */
   int refine;      /* 0, 1 or 2: steps of iterative refinement from the inputs:
-                    * r_c = H_c^H (y_c - H_c x_c) - rho x_c, x_c += A_c r_c (FP32, with
-                    * A_c the solve's inverse), and one Newton step for the diagonal
-                    * of the inverse, A_uu <- 2 A_uu - ||H_c a_u||^2 - rho ||a_u||^2
-                    * (a_u its u-th column), which the unbiasing and fusion use.
-                    * Each step shrinks the error of the mixed-precision
-                    * preprocessing by about kappa(G_c + rho I) * 2^-16 (BF16X3).
-                    * Costs a second read of H and y and a larger workspace; only
-                    * ffeq_equalize (and the entry points built on it) support it:
+                    * r_c = H_c^H (y_c - H_c x_c) - rho x_c, x_c += A_c r_c (with
+                    * A_c the solve's inverse), and one Newton-Schulz step for the
+                    * inverse, A_c <- 2 A_c - A_c^H (G_c + rho I) A_c, whose
+                    * diagonal the unbiasing and the fusion use.  Each step
+                    * shrinks the error of the mixed-precision preprocessing by
+                    * about kappa(G_c + rho I) * 2^-16 (BF16X3).  Costs a second
+                    * read of H and y and a larger workspace; only ffeq_equalize
+                    * (and the entry points built on it) support it:
                     * ffeq_fuse_equalize returns FFEQ_ERR_UNSUPPORTED. */
+  int refine_fp64; /* precision of the refinement residual r_c (needs refine > 0):
+                    * 0  FP32 for every local system: the estimates converge to
+                    *    the accuracy of an FP32 solve, about kappa * 2^-24;
+                    * 1  FP64 (y_c - H_c x_c and H_c^H of it accumulated in
+                    *    double) for the local systems whose condition estimate
+                    *    ||G_c + rho I||_1 ||A_c||_1 exceeds 1e4, FP32 for the
+                    *    others: the ill-conditioned ones converge to about
+                    *    2^-24 (the FP32 storage of x_c) instead;
+                    * 2  FP64 for every local system. */
 } ffeq_problem;
 
 typedef struct ffeq_plan ffeq_plan;
@@ -189,8 +203,17 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
  *              2 = 8 warps, two CTAs per SM (half the shared memory each),
  *              3 = BF16X3 only: each staged subcarrier converted once into BF16
  *                  hi/lo planes read with ldmatrix (needs B and B/C multiples of 4);
- *              4 = tensor-core precisions only: 4 warps, three CTAs per SM;
- *   values[1]  subcarriers staged ahead per CTA, 1..3, or 0 = as many as fit.
+ *              4 = TF32X3 / BF16X3 only: 4 warps, three CTAs per SM;
+ *              5 = BF16X3 / FP16X3 only, streamed: every warp owns output tiles
+ *                  over a whole cluster (no split-K), each subcarrier streams
+ *                  through a ring of 32-antenna slices moved by tensor-map
+ *                  copies and split once into 16-bit planes (needs B even and,
+ *                  for FD, B/C a multiple of 16; 16-byte aligned H and y, else
+ *                  shape 1 runs);
+ *   values[1]  shapes 1-4: subcarriers staged ahead per CTA, 1..3, or 0 = as
+ *              many as fit; shape 5: ring depth per subcarrier (32-antenna
+ *              slices), 2 or 3, 0 = 3.
+ * FP16X3 runs on shapes 1 and 5 only.
  * ffeq_plan_set_tuning takes exactly 2 values and returns FFEQ_ERR_UNSUPPORTED
  * when the shape does not apply to or fit the problem (plan unchanged);
  * ffeq_plan_get_tuning writes min(n, 2) values.  ffeq_plan_autotune times every

@@ -82,12 +82,15 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (p->B <= 0 || p->U <= 0 || p->C <= 0 || p->n_sc < 0 || p->n_sym <= 0) return FFEQ_ERR_INVALID_ARG;
   if (p->B % p->C != 0) return FFEQ_ERR_INVALID_ARG;
   if (p->arch != FFEQ_PD && p->arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
-  if (p->precision != FFEQ_FP32 && p->precision != FFEQ_TF32X3 && p->precision != FFEQ_BF16X3)
+  if (p->precision != FFEQ_FP32 && p->precision != FFEQ_TF32X3 && p->precision != FFEQ_BF16X3 &&
+      p->precision != FFEQ_FP16X3)
     return FFEQ_ERR_INVALID_ARG;
   if (p->estimate != FFEQ_UNBIASED && p->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
   if (p->llr_bits != 0 && p->llr_bits != 2 && p->llr_bits != 4 && p->llr_bits != 6 && p->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
   if (p->refine < 0 || p->refine > 2) return FFEQ_ERR_INVALID_ARG;
+  if (p->refine_fp64 < 0 || p->refine_fp64 > 2 || (p->refine_fp64 > 0 && p->refine == 0))
+    return FFEQ_ERR_INVALID_ARG;
   if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
   if (ffeq::gram_stages(p->precision, p->B, p->U, p->n_sym, Ceff, false) < 1) return FFEQ_ERR_UNSUPPORTED;
@@ -206,6 +209,7 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   rp.n_sc = p.n_sc;
   rp.n_sym = p.n_sym;
   rp.steps = p.refine;
+  rp.res64 = p.refine_fp64;
   rp.unbiased = sp.unbiased;
   rp.llr_bits = p.llr_bits;
   rp.N0 = sp.N0;
@@ -398,7 +402,8 @@ ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n) {
 
 ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
   if (!plan || n != 2 || !values) return FFEQ_ERR_INVALID_ARG;
-  if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGram4x3 || values[1] < 0 || values[1] > 3)
+  if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGramVariantMax || values[1] < 0 ||
+      values[1] > (values[0] == ffeq::kGramStream ? ffeq::kGramStreamRing : 3))
     return FFEQ_ERR_INVALID_ARG;
   // The shape must fit the problem with 16-byte aligned rows (the bulk-staged case).
   ffeq::GramParams gp{};
@@ -433,7 +438,7 @@ ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, fl
   float best = -1.f;
   int best_v[2] = {old[0], old[1]};
   ffeq_status s = FFEQ_OK;
-  for (int variant = ffeq::kGram16; variant <= ffeq::kGram4x3 && s == FFEQ_OK; ++variant) {
+  for (int variant = ffeq::kGram16; variant <= ffeq::kGramVariantMax && s == FFEQ_OK; ++variant) {
     for (int stages = 1; stages <= 3 && s == FFEQ_OK; ++stages) {
       const int v[2] = {variant, stages};
       if (ffeq_plan_set_tuning(plan, v, 2) != FFEQ_OK) continue;

@@ -169,7 +169,8 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
   if (!out || !cfg || n_inst < 0 || (n_inst > 0 && !inst)) return FFEQ_ERR_INVALID_ARG;
   *out = nullptr;
   if (cfg->arch != FFEQ_PD && cfg->arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
-  if (cfg->precision != FFEQ_FP32 && cfg->precision != FFEQ_TF32X3 && cfg->precision != FFEQ_BF16X3)
+  if (cfg->precision != FFEQ_FP32 && cfg->precision != FFEQ_TF32X3 && cfg->precision != FFEQ_BF16X3 &&
+      cfg->precision != FFEQ_FP16X3)
     return FFEQ_ERR_INVALID_ARG;
   if (cfg->estimate != FFEQ_UNBIASED && cfg->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
   if (cfg->llr_bits != 0 && cfg->llr_bits != 2 && cfg->llr_bits != 4 && cfg->llr_bits != 6 && cfg->llr_bits != 8)

@@ -138,13 +138,24 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   p.UP = padded_users(p.U);
   p.lim = BatchLimits{};
   p.grid_cap = 0;
+  const bool stream_ok = gram_stream_eligible(precision, p.B, p.U, p.n_sym, p.Ceff);
   if (variant == kGramAuto) variant = kGram16;
-  if (variant != kGram16 && variant != kGram8x2 && variant != kGramPresplit && variant != kGram4x3) return false;
+  if (variant < kGram16 || variant > kGramVariantMax) return false;
   if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
+  if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream) return false;
   if (variant == kGramPresplit && !gram_presplit_eligible(precision, p.B, p.Ceff)) return false;
-  if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes
-    if (variant == kGramPresplit) variant = kGram16;
+  if (variant == kGramStream && !stream_ok) return false;
+  if (variant != kGramStream && stages > kGramMaxStages) return false;
+  if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes, no tensor maps
+    if (variant == kGramPresplit || variant == kGramStream) variant = kGram16;
     stages = 0;
+  }
+  if (variant == kGramStream) {
+    if (stages == 1) return false;          // the streamed shape converts one slice ahead
+    p.stage_elems = p.slot_elems = p.n_slots = p.plane_bytes = 0;
+    p.stages = stages > 0 ? stages : kGramStreamRing;
+    p.variant = variant;
+    return true;
   }
   const GramCaps c = gram_instance_caps(precision, p.B, p.U, p.n_sym, p.Ceff, variant);
   const int fit = gram_stages_fit(c.stage_elems, static_cast<size_t>(c.slots) * c.slot_elems * 8 + c.plane_bytes,

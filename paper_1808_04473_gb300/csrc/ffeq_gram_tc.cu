@@ -17,58 +17,15 @@
 // accumulates A_lo B_hi + A_hi B_lo + A_hi B_hi in FP32 (the lo*lo term is
 // dropped):
 //   kTf32x3: mma.m16n8k8 TF32 (11-bit significands: hi+lo carries ~22 bits);
-//   kBf16x3: mma.m16n8k16 BF16 (8-bit significands: hi+lo carries ~16 bits).
+//   kBf16x3: mma.m16n8k16 BF16 (8-bit significands: hi+lo carries ~16 bits);
+//   kFp16x3: mma.m16n8k16 FP16 (11-bit significands, FP16's range).
 #include <cstdint>
 
 #include "ffeq_gram.cuh"
+#include "ffeq_mma.cuh"
 
 namespace ffeq {
 namespace {
-
-constexpr int kTf32x3 = 1;
-constexpr int kBf16x3 = 2;
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-
-// Two floats -> bf16x2 hi and lo (element 0 in the low half, as the MMA expects).
-__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
-  const float h0 = __uint_as_float(hi << 16);
-  const float h1 = __uint_as_float(hi & 0xffff0000u);
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
-}
-
-// Not volatile: the compiler may interleave MMAs on independent accumulators.
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int MODE>
-__device__ __forceinline__ void mma_any(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  if constexpr (MODE == kTf32x3) mma_tf32(c, a, b0, b1);
-  else mma_bf16(c, a, b0, b1);
-}
 
 // Complex value of row `row` at antenna a, zero outside [.., k1).
 __device__ __forceinline__ float2 ld(const float2* __restrict__ row, int a, int k1) {
@@ -145,12 +102,12 @@ __device__ __forceinline__ void tc_tiles(const float2* __restrict__ Ws, int RS, 
         float2 v0, v1, v2_, v3;
         ld2(brow[j], a0 + 2 * t, k1, v2, v0, v1);
         ld2(brow[j], a0 + 8 + 2 * t, k1, v2, v2_, v3);
-        split_bf16(v0.x, v1.x, bre_h[j][0], bre_l[j][0]);
-        split_bf16(v2_.x, v3.x, bre_h[j][1], bre_l[j][1]);
-        split_bf16(v0.y, v1.y, bim_h[j][0], bim_l[j][0]);
-        split_bf16(v2_.y, v3.y, bim_h[j][1], bim_l[j][1]);
-        split_bf16(v0.x - v0.y, v1.x - v1.y, bd_h[j][0], bd_l[j][0]);
-        split_bf16(v2_.x - v2_.y, v3.x - v3.y, bd_h[j][1], bd_l[j][1]);
+        split_pair<MODE>(v0.x, v1.x, bre_h[j][0], bre_l[j][0]);
+        split_pair<MODE>(v2_.x, v3.x, bre_h[j][1], bre_l[j][1]);
+        split_pair<MODE>(v0.y, v1.y, bim_h[j][0], bim_l[j][0]);
+        split_pair<MODE>(v2_.y, v3.y, bim_h[j][1], bim_l[j][1]);
+        split_pair<MODE>(v0.x - v0.y, v1.x - v1.y, bd_h[j][0], bd_l[j][0]);
+        split_pair<MODE>(v2_.x - v2_.y, v3.x - v3.y, bd_h[j][1], bd_l[j][1]);
       }
     }
 #pragma unroll
@@ -179,9 +136,9 @@ __device__ __forceinline__ void tc_tiles(const float2* __restrict__ Ws, int RS, 
           ld2(arow[i][1], a0 + 8 + 2 * t, k1, v2, w0[3], w1[3]);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            split_bf16(w0[q].x, w1[q].x, are_h[q], are_l[q]);
-            split_bf16(w0[q].y, w1[q].y, aim_h[q], aim_l[q]);
-            split_bf16(w0[q].x + w0[q].y, w1[q].x + w1[q].y, as_h[q], as_l[q]);
+            split_pair<MODE>(w0[q].x, w1[q].x, are_h[q], are_l[q]);
+            split_pair<MODE>(w0[q].y, w1[q].y, aim_h[q], aim_l[q]);
+            split_pair<MODE>(w0[q].x + w0[q].y, w1[q].x + w1[q].y, as_h[q], as_l[q]);
           }
         }
         // Issue order: one split product (A_lo B_hi, A_hi B_lo, A_hi B_hi) at a
@@ -402,7 +359,9 @@ GramCaps gram_tc_caps(int B, int U, int n_sym, int Ceff, int variant) {
 }
 
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream) {
+  if (p.variant == kGramStream) return launch_gram_stream(p, precision, stream);
   const size_t smem = gram_smem_bytes(p);
+  if (precision == FFEQ_FP16X3) return launch_mode<kFp16x3, 16, 1>(p, smem, stream);   // the 16-warp shape only
   if (precision == FFEQ_BF16X3 && p.variant == kGramPresplit && p.plane_bytes > 0) {
     switch (padded_users(p.U)) {
       case 8: return launch_gram_up<8, TensorSplitPre>(p, smem, stream);

@@ -57,13 +57,23 @@ struct GramParams {
   BatchLimits lim;    // batch: buffer extents
   int grid_cap;       // > 0: at most this many persistent CTAs
   int plane_bytes;    // > 0: pre-split BF16 planes of this capacity (BF16x3 pre-split contraction)
-  int variant;        // contraction launch shape (kGram16 / kGram8x2 / kGramPresplit)
+  int variant;        // contraction launch shape (kGram16 ... kGramStream)
 };
 
 // Contraction launch shapes: 16 warps, one CTA per SM; 8 warps, two CTAs per SM
 // (half the shared memory each, so one CTA's MMA phase overlaps the other's
-// staging); BF16x3 pre-split planes (16 warps); 4 warps, three CTAs per SM.
-constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4;
+// staging); BF16x3 pre-split planes (16 warps); 4 warps, three CTAs per SM;
+// streamed (ffeq_gram_stream.cu: 32-antenna slices of several subcarriers per
+// CTA moved by tensor-map copies, each warp owning its output tiles over the
+// whole antenna range; `stages` is then the depth of each subcarrier's ring).
+constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4, kGramStream = 5;
+constexpr int kGramVariantMax = kGramStream;
+constexpr int kGramStreamRing = 3;      // default (and largest) ring depth of the streamed shape (least 2)
+
+// Whether the streamed contraction takes this problem (BF16x3 or FP16x3,
+// U <= 32, B even, cluster sizes whole 16-antenna steps for FD).
+bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff);
+cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream);
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
 struct SolveParams {
@@ -106,6 +116,7 @@ struct RefineParams {
   float* sigma2;
   float* llr;
   int B, U, Ceff, n_sc, n_sym, steps, unbiased, llr_bits;
+  int res64;            // residual in FP64: 0 never, 1 above the condition threshold, 2 always
   float N0, rho, llr_scale;
 };
 // Whether one local system fits the refinement kernel's shared memory.

@@ -14,7 +14,12 @@
 // step from the same product V = H_c A~_c in each step:
 //   A~_c <- 2 A~_c - A~_c^H M_c A~_c = 2 A~_c - V^H V - rho A~_c^H A~_c,
 // which squares its relative error.  Each step shrinks the error of the
-// estimates by about kappa u.  The fusion and soft outputs then follow the solve
+// estimates by about kappa u, down to the accuracy of an FP32 solve (kappa
+// 2^-24, from the rounding of y_c - H_c x_c).  With the FP64 residual (always,
+// or for systems whose estimate ||M_c||_1 ||A~_c||_1 of the condition number
+// exceeds kCondFp64) y_c - H_c x_c and H_c^H of it accumulate in double, and the
+// estimates converge to the FP32 storage of x_c instead (classical mixed-precision
+// refinement).  The fusion and soft outputs then follow the solve
 // kernel's epilogue (Eq. fusionrule, Lemma 1, Thm. 3; PD is C = 1).  All sums
 // run in a fixed order (deterministic).
 #include <cmath>
@@ -28,11 +33,12 @@ namespace {
 
 constexpr int kRefineThreadsMax = 512;   // per system: 2 S threads, 128..512
 constexpr int kFuseThreads = 256;
+constexpr float kCondFp64 = 1e4f;        // condition estimate above which the residual is FP64
 
 // Shared memory of one system (cluster c of subcarrier k; S antennas).
 struct RefineLayout {
   int U, NS, S, SS, W;
-  size_t hs, pm, va, rb, rr, an, total;   // offsets in bytes
+  size_t hs, pm, va, rb, rr, an, ae, cn, total;   // offsets in bytes
   __host__ __device__ RefineLayout(int U_, int NS_, int S_)
       : U(U_), NS(NS_), S(S_), SS(S_ + 1), W(U_ + NS_) {
     size_t o = 0;
@@ -41,10 +47,30 @@ struct RefineLayout {
     va = o;  o += static_cast<size_t>(U) * SS * 8;      // V = H_c a_j per antenna
     rb = o;  o += static_cast<size_t>(NS) * SS * 8;     // y_c - H_c x per antenna
     rr = o;  o += static_cast<size_t>(NS) * U * 8;      // residual
-    an = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse
+    an = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse (FP64 residual: E)
+    ae = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse with the FP64 residual
+    cn = o;  o += static_cast<size_t>(2) * U * 4;       // column norms for the condition estimate
     total = o;
   }
 };
+
+// acc + a b and acc + conj(a) b in double (products of FP32 values are exact).
+__device__ __forceinline__ double2 dcfma(float2 a, float2 b, double2 acc) {
+  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+  acc.x = fma(ax, bx, acc.x);
+  acc.x = fma(-ay, by, acc.x);
+  acc.y = fma(ax, by, acc.y);
+  acc.y = fma(ay, bx, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 dcfma_conj(float2 a, float2 b, double2 acc) {
+  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+  acc.x = fma(ax, bx, acc.x);
+  acc.x = fma(ay, by, acc.x);
+  acc.y = fma(ax, by, acc.y);
+  acc.y = fma(-ay, bx, acc.y);
+  return acc;
+}
 
 // One CTA per local system: `steps` refinement steps, then the refined
 // estimates and inverse (diagonal included) go back to the workspace.
@@ -59,6 +85,7 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
   float2* Rb = reinterpret_cast<float2*>(smem + L.rb);
   float2* Rr = reinterpret_cast<float2*>(smem + L.rr);
   float2* An = reinterpret_cast<float2*>(smem + L.an);
+  float2* Ae = reinterpret_cast<float2*>(smem + L.ae);
   const size_t sys = blockIdx.x;
   const int k = static_cast<int>(sys / Ceff), c = static_cast<int>(sys % Ceff);
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -78,12 +105,46 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
   }
   __syncthreads();
   const bool failed = p.fails[sys] != 0;
+  // Residual precision of this system (block-uniform).  Condition estimate:
+  // ||G_c + rho I||_1 from the contraction output (row v of D is column v of the
+  // Hermitian G_c) times ||A~_c||_1.
+  bool use64 = p.res64 == 2;
+  if (p.res64 == 1) {
+    float* cs = reinterpret_cast<float*>(smem + L.cn);
+    for (int j = tid; j < 2 * U; j += nt) {
+      const float2* col = j < U ? p.D + (sys * W + j) * U : P + (j - U) * U;
+      float s = j < U ? rho : 0.f;
+      for (int i = 0; i < U; ++i) s += sqrtf(fmaf(col[i].x, col[i].x, col[i].y * col[i].y));
+      cs[j] = s;
+    }
+    __syncthreads();
+    float mg = 0.f, ma = 0.f;
+    for (int j = 0; j < U; ++j) {
+      mg = fmaxf(mg, cs[j]);
+      ma = fmaxf(ma, cs[U + j]);
+    }
+    use64 = mg * ma > kCondFp64;
+  }
 
   for (int step = 0; step < p.steps && !failed; ++step) {
-    // V = H_c [A~ | X] per (antenna b, column j); y_c - H_c x for the estimates.
+    // V = H_c [A~ | X] per (antenna b, column j): the columns a_j of A~ give V,
+    // the estimates give y_c - H_c x.  FP64 residual: accumulated in double, the
+    // result rounded once (exact differences first).
     for (int e = tid; e < S * W; e += nt) {
       const int j = e / S, b = e - j * S;
       const float2* pj = P + j * U;
+      if (use64) {
+        double2 v = make_double2(0.0, 0.0);
+        for (int u = 0; u < U; ++u) v = dcfma(Hs[u * SS + b], pj[u], v);
+        if (j < U) {
+          Va[j * SS + b] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+        } else {
+          const float2 yv = yk[static_cast<size_t>(j - U) * B + b];
+          Rb[(j - U) * SS + b] = make_float2(static_cast<float>(static_cast<double>(yv.x) - v.x),
+                                             static_cast<float>(static_cast<double>(yv.y) - v.y));
+        }
+        continue;
+      }
       float2 v = make_float2(0.f, 0.f);
       for (int u = 0; u < U; ++u) v = cfma(Hs[u * SS + b], pj[u], v);
       if (j < U) {
@@ -94,27 +155,47 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
       }
     }
     __syncthreads();
-    // r = H_c^H (y_c - H_c x) - rho x;  next inverse 2 A - V^H V - rho A^H A.
+    // r = H_c^H (y_c - H_c x) - rho x.
     for (int e = tid; e < NS * U; e += nt) {
       const int n = e / U, u = e - n * U;
+      const float2 x = P[(U + n) * U + u];
+      if (use64) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int b = 0; b < S; ++b) sum = dcfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
+        const double r = static_cast<double>(rho);
+        Rr[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(x.x), sum.x)),
+                            static_cast<float>(fma(-r, static_cast<double>(x.y), sum.y)));
+        continue;
+      }
       float2 sum = make_float2(0.f, 0.f);
       for (int b = 0; b < S; ++b) sum = cfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
-      const float2 x = P[(U + n) * U + u];
       Rr[e] = make_float2(sum.x - rho * x.x, sum.y - rho * x.y);
     }
+    // FP32: the next inverse 2 A - V^H V - rho A^H A.  FP64: the residual of the
+    // inverse, E = I - M_c A~ = I - H_c^H V - rho A~ (entry (i, j) at j U + i).
     for (int e = tid; e < U * U; e += nt) {
       const int j = e / U, i = e - j * U;   // entry (i, j)
+      const float2* aj = P + j * U;
+      if (use64) {
+        double2 hv = make_double2(0.0, 0.0);
+        for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[i * SS + b], Va[j * SS + b], hv);
+        const double r = static_cast<double>(rho);
+        const double id = i == j ? 1.0 : 0.0;
+        An[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(aj[i].x), id - hv.x)),
+                            static_cast<float>(fma(-r, static_cast<double>(aj[i].y), -hv.y)));
+        continue;
+      }
       float2 vv = make_float2(0.f, 0.f);
       for (int b = 0; b < S; ++b) vv = cfma_conj(Va[i * SS + b], Va[j * SS + b], vv);
       float2 aa = make_float2(0.f, 0.f);
       const float2* ai = P + i * U;
-      const float2* aj = P + j * U;
       for (int v = 0; v < U; ++v) aa = cfma_conj(ai[v], aj[v], aa);
       const float2 a = aj[i];
       An[e] = make_float2(2.f * a.x - vv.x - rho * aa.x, 2.f * a.y - vv.y - rho * aa.y);
     }
     __syncthreads();
-    // x += A~ r   (A~[u][v] = column v of A~ at row u), then A~ <- next inverse.
+    // x += A~ r   (A~[u][v] = column v of A~ at row u); FP64 residual: the next
+    // inverse A~ + A~ E (Newton-Schulz in residual form) into Ae.
     for (int e = tid; e < NS * U; e += nt) {
       const int n = e / U, u = e - n * U;
       float2 d = make_float2(0.f, 0.f);
@@ -122,8 +203,17 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
       float2* x = P + (U + n) * U + u;
       *x = cadd(*x, d);
     }
+    if (use64) {
+      for (int e = tid; e < U * U; e += nt) {
+        const int j = e / U, i = e - j * U;
+        float2 d = make_float2(0.f, 0.f);
+        for (int v = 0; v < U; ++v) d = cfma(P[v * U + i], An[j * U + v], d);
+        Ae[e] = cadd(P[e], d);
+      }
+    }
     __syncthreads();
-    for (int e = tid; e < U * U; e += nt) P[e] = An[e];
+    const float2* next = use64 ? Ae : An;
+    for (int e = tid; e < U * U; e += nt) P[e] = next[e];
     __syncthreads();
   }
   // Refined estimates and inverse back to the workspace (same layouts).

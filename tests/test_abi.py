@@ -37,6 +37,7 @@ def test_version_and_status_strings(built):
     (dict(B=0, U=4, C=1), 1), (dict(B=32, U=4, C=3), 1), (dict(B=32, U=0, C=2), 1),
     (dict(B=32, U=4, C=2, arch=7), 1), (dict(B=32, U=4, C=2, estimate=5), 1),
     (dict(B=32, U=4, C=2, llr_bits=3), 1), (dict(B=32, U=4, C=2, precision=9), 1),
+    (dict(B=32, U=4, C=2, precision=4), 1),
     (dict(B=32, U=33, C=2), 2), (dict(B=32, U=4, C=2, n_sym=17), 2), (dict(B=8192, U=32, C=2), 2),
 ])
 def test_plan_validation(built, kw, status):
@@ -86,7 +87,7 @@ def test_staging_size_accounts_for_every_buffer(built):
 
 
 def test_plan_struct_layout_matches_header(built):
-    assert ctypes.sizeof(ffeq.ffeq_problem) == 10 * 4
+    assert ctypes.sizeof(ffeq.ffeq_problem) == 11 * 4
     text = open(ffeq.HEADER_PATH).read()
     body = text[text.index("typedef struct {") + len("typedef struct {"):text.index("} ffeq_problem;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
@@ -113,8 +114,8 @@ def test_plan_tuning_validation(built):
     ff = ffeq
     plan = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP32)
     assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
-    # out of range; pre-split and the 4-warp shape need a tensor-core precision
-    for bad, status in (((5, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2)):
+    # out of range; pre-split, the 4-warp and the streamed shapes need a tensor-core precision
+    for bad, status in (((6, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2), ((5, 0), 2)):
         with pytest.raises(ff.FfeqError) as e:
             ff.ffeq_plan_set_tuning(plan, bad)
         assert e.value.status == status, bad
@@ -127,6 +128,32 @@ def test_plan_tuning_validation(built):
         ff.ffeq_plan_set_tuning(big, (1, 3))
     assert e.value.status == 2
     ff.ffeq_plan_set_tuning(big, (3, 0))
+    # The streamed shape: BF16x3 or FP16x3 with whole 16-antenna clusters (FD);
+    # its second value is the depth of each subcarrier's ring (0: 3).
+    for prec in (ff.BF16X3, ff.FP16X3):
+        fd = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=prec)
+        for st in (0, 2, 3):
+            ff.ffeq_plan_set_tuning(fd, (5, st))
+            assert ff.ffeq_plan_get_tuning(fd) == (5, st)
+        for st, status in ((4, 1), (1, 2)):        # depth 1 cannot convert one slice ahead
+            with pytest.raises(ff.FfeqError) as e:
+                ff.ffeq_plan_set_tuning(fd, (5, st))
+            assert e.value.status == status
+    odd = ff.ffeq_plan_create(96, 8, 8, 10, 2, arch=ff.FD, precision=ff.BF16X3)      # S = 12
+    with pytest.raises(ff.FfeqError) as e:
+        ff.ffeq_plan_set_tuning(odd, (5, 0))
+    assert e.value.status == 2
+    ff.ffeq_plan_set_tuning(ff.ffeq_plan_create(96, 8, 8, 10, 2, arch=ff.PD, precision=ff.BF16X3), (5, 0))
+    tf = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.TF32X3)
+    with pytest.raises(ff.FfeqError) as e:
+        ff.ffeq_plan_set_tuning(tf, (5, 0))
+    assert e.value.status == 2
+    # FP16x3 runs on the 16-warp and the streamed shapes only.
+    h = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP16X3)
+    for v in (2, 3, 4):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_set_tuning(h, (v, 0))
+        assert e.value.status == 2, v
 
 
 def test_refinement_needs_the_inputs(built):
@@ -139,3 +166,9 @@ def test_refinement_needs_the_inputs(built):
     with pytest.raises(ffeq.FfeqError) as e:
         ffeq.ffeq_plan_create(64, 8, 4, 10, 2, refine=3)
     assert e.value.status == 1
+    # The FP64 residual is a mode of the refinement: 0..2, and only with refine > 0.
+    for bad in (dict(refine=1, refine_fp64=3), dict(refine=1, refine_fp64=-1), dict(refine=0, refine_fp64=1)):
+        with pytest.raises(ffeq.FfeqError) as e:
+            ffeq.ffeq_plan_create(64, 8, 4, 10, 2, **bad)
+        assert e.value.status == 1, bad
+    ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, refine=2, refine_fp64=1)

@@ -48,10 +48,11 @@ def _kappa(p, arch):
     return out
 
 
-def _run(ff, p, arch, precision, refine, bits=4, estimate=0):
+def _run(ff, p, arch, precision, refine, bits=4, estimate=0, refine_fp64=0):
     dev = torch.device("cuda:0")
     g = ff.equalize(torch.from_numpy(p.H).to(dev), torch.from_numpy(p.y).to(dev), p.N0, p.Es, p.C, arch=arch,
-                    estimate=estimate, llr_bits=bits, with_info=True, precision=precision, refine=refine)
+                    estimate=estimate, llr_bits=bits, with_info=True, precision=precision, refine=refine,
+                    refine_fp64=refine_fp64)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in g.items()}
 
@@ -115,3 +116,70 @@ def test_refinement_reports_singular_systems(ff):
         assert np.array_equal(g["info"].cpu().numpy().reshape(o["info"].shape), o["info"])
         assert np.isnan(g["z"][1].cpu().numpy()).all()
         assert np.isfinite(g["z"][[0, 2]].cpu().numpy()).all()
+
+
+def _kappa1(p, arch):
+    """[n_sc][systems] condition estimates ||M_c||_1 ||M_c^-1||_1, M_c = G_c + rho I (FP64)."""
+    rho = float(np.float32(p.N0)) / p.Es
+    parts = lmmse.partition(p.B, p.C) if arch == 1 else [(0, p.B)]
+    out = np.zeros((p.n_sc, len(parts)))
+    for k in range(p.n_sc):
+        Hm = p.H[k].astype(np.complex128).T
+        for i, (b0, b1) in enumerate(parts):
+            M = Hm[b0:b1].conj().T @ Hm[b0:b1] + rho * np.eye(p.U)
+            out[k, i] = np.abs(M).sum(0).max() * np.abs(np.linalg.inv(M)).sum(0).max()
+    return out
+
+
+FP64_CASES = [  # B, U, C, n_sc, n_sym, snr_db, corr_r: FD clusters with S < U
+    (256, 32, 16, 8, 14, 30.0, 0.7),     # every FD cluster above 2e4, every PD system below 5e3
+    (128, 16, 8, 24, 6, 30.0, 0.7),      # FD clusters from 1e3 to 2e4
+]
+
+
+@pytest.mark.parametrize("case", FP64_CASES)
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "tf32x3"])
+def test_fp64_residual_reaches_fp32_storage_accuracy(ff, case, arch, precision):
+    """With the residual in FP64 the refined estimates and inverse converge to the
+    rounding of their FP32 storage, independent of kappa: two steps from an FP32 or
+    TF32x3 start (error kappa 2^-24 or kappa 2^-21, kappa <= 5e4 here) reach 4e-6,
+    below the FP32-residual floor of about kappa 2^-24 where that is above 1e-5."""
+    B, U, C, n_sc, n_sym, snr, r = case
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=snr, bits=4, seed=B + U + C, corr_r=r)
+    f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
+    o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased")
+    kap = _kappa(p, arch)
+    assert kap.max() <= 5e4
+    g32 = _run(ff, p, arch, precision, 2, refine_fp64=0)
+    g64 = _run(ff, p, arch, precision, 2, refine_fp64=2)
+    assert (g64["info"] == 0).all()
+    e32 = _rel(g32["z"], o["z"])
+    ez, es = _rel(g64["z"], o["z"]), _rel(g64["sigma2"], o["sigma2"])
+    print("kappa max %.3g  z err fp32-res %.3g fp64-res %.3g  sigma2 %.3g" % (kap.max(), e32.max(), ez.max(), es.max()))
+    assert ez.max() <= 4e-6 and es.max() <= 4e-6, (ez.max(), es.max(), kap.max())
+    big = e32 > 1e-5
+    if big.any():
+        assert (ez[big] <= e32[big] / 4).all()
+    Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es)
+    assert (_rel(g64["llr"], Lo) <= 1.6e-5).all()
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_fp64_residual_follows_the_condition_estimate(ff, arch):
+    """refine_fp64 = 1 takes the FP64 residual exactly for the systems whose
+    condition estimate exceeds 1e4: on this workload every FD cluster is above
+    2e4 and every PD system below 5e3 (margins for the estimate's own error), so
+    the outputs equal those of refine_fp64 = 2 (FD) or 0 (PD) bit for bit."""
+    p = synth.make_problem(256, 32, 16, 8, 14, snr_db=30.0, bits=4, seed=304, corr_r=0.7)
+    k1 = _kappa1(p, arch)
+    if arch == 1:
+        assert k1.min() > 2e4
+    else:
+        assert k1.max() < 5e3
+    g1 = _run(ff, p, arch, 1, 2, refine_fp64=1)
+    gx = _run(ff, p, arch, 1, 2, refine_fp64=2 if arch == 1 else 0)
+    gy = _run(ff, p, arch, 1, 2, refine_fp64=0 if arch == 1 else 2)
+    for key in ("z", "sigma2", "llr"):
+        assert np.array_equal(g1[key], gx[key]), key
+    assert not np.array_equal(g1["z"], gy["z"])
