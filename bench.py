@@ -373,9 +373,11 @@ def main():
     def timed(precision, K, warmup, sampler=None):
         """K steps; one step = for PD then FD, the local preprocessing kernel and the
         fusion / equalization kernel (the latter launched with programmatic dependent
-        launch).  CUDA events bracket the K steps only; a separate pass of up to 100
-        steps brackets each kernel with events (which serializes the launches, so the
-        per-kernel times are upper bounds) for the breakdown."""
+        launch).  Each step is captured once per rotating input set as a CUDA graph
+        (what a serving loop replays per frame) and replayed; CUDA events on the
+        replay stream bracket the K replays only.  A separate pass replays graphs of
+        one kernel each (that kernel alone, on the rotating input sets) for the
+        per-kernel device times of the breakdown."""
         plans, ws_bytes, ws = make_plans(precision)
         pinned = [int(v) for v in args.tuning.split(",")] if args.tuning else None
         for a in plans:                  # launch shape chosen by timing (outside the timed region)
@@ -385,36 +387,45 @@ def main():
             else:
                 ffeq.ffeq_plan_autotune(plans[a], Hs[0], ys[0], p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
                                         ws_bytes[a], stream, 10)
+        cap = torch.cuda.Stream(dev)
 
-        def step(i, evs=None):
-            for a in (ffeq.PD, ffeq.FD):
-                o = outs[a]
-                if evs is not None:
-                    evs[2 * a].record(stream)
-                ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], stream)
-                if evs is not None:
-                    evs[2 * a + 1].record(stream)
+        def launch(a, i, which):
+            o = outs[a]
+            if which in ("local", "step"):
+                ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], cap)
+            if which in ("fuse", "step"):
                 ffeq.ffeq_fuse_equalize(plans[a], ws[a], ws_bytes[a], p.N0, p.Es, o["z"], o["s2"], o["llr"],
-                                        None, stream)
-            if evs is not None:
-                evs[4].record(stream)
+                                        None, cap)
 
-        Kb = min(K, 100)
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(Kb)]
+        def capture(fn):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                fn()
+            return g
+
+        torch.cuda.synchronize()
+        with torch.cuda.stream(cap):
+            for i in range(2):           # eager warm-up before capture
+                for a in (ffeq.PD, ffeq.FD):
+                    launch(a, i, "step")
+        cap.synchronize()
+        steps = [capture(lambda i=i: [launch(a, i, "step") for a in (ffeq.PD, ffeq.FD)]) for i in range(n_sets)]
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if sampler is not None:          # clocks: sampled from the warm-up through the timed region
             sampler.__enter__()
-        for i in range(warmup):
-            step(i % n_sets)
+        with torch.cuda.stream(cap):
+            for i in range(warmup):
+                steps[i % n_sets].replay()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")      # profiling filter: ncu --nvtx --nvtx-include "timed/"
-        start.record(stream)
-        for k in range(K):
-            step(k % n_sets)
-        end.record(stream)
+        with torch.cuda.stream(cap):
+            start.record(cap)
+            for k in range(K):
+                steps[k % n_sets].replay()
+            end.record(cap)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if sampler is not None:
@@ -422,11 +433,28 @@ def main():
         if world > 1:
             dist.barrier()
         ms = start.elapsed_time(end)
-        for k in range(Kb):              # per-kernel breakdown (not part of the timed region)
-            step(k % n_sets, ev[k])
+        # Per-kernel breakdown (not part of the timed region): one kernel per graph.
+        kern = {}
+        Kb = max(8, min(K, 200))
+        for name, a, which in (("pd_local", ffeq.PD, "local"), ("pd_fuse", ffeq.PD, "fuse"),
+                               ("fd_local", ffeq.FD, "local"), ("fd_fuse", ffeq.FD, "fuse")):
+            gs = [capture(lambda i=i: launch(a, i, which)) for i in range(n_sets)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(cap):
+                for i in range(n_sets):
+                    gs[i].replay()
+                e0.record(cap)
+                for k in range(Kb):
+                    gs[k % n_sets].replay()
+                e1.record(cap)
+            torch.cuda.synchronize()
+            kern[name] = e0.elapsed_time(e1) / Kb
+            del gs
+        # Leave the outputs of a full step (the accuracy check reads them).
+        with torch.cuda.stream(cap):
+            steps[0].replay()
         torch.cuda.synchronize()
-        kern = {name: statistics.mean(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(Kb))
-                for j, name in enumerate(["pd_local", "pd_fuse", "fd_local", "fd_fuse"])}
+        del steps
         if world > 1:
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -199,7 +199,7 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
 /* Launch shape of a plan's contraction kernel (the arithmetic is that of the
  * plan's precision in every shape; with split-K (PD) the shapes differ in how
  * the antennas are split among warps, hence in summation order only):
- *   values[0]  0 = default (1), 1 = 16 warps, one CTA per SM,
+ *   values[0]  0 = default (5 where it applies, else 1), 1 = 16 warps, one CTA per SM,
  *              2 = 8 warps, two CTAs per SM (half the shared memory each),
  *              3 = BF16X3 only: each staged subcarrier converted once into BF16
  *                  hi/lo planes read with ldmatrix (needs B and B/C multiples of 4);

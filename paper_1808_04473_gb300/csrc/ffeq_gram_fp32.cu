@@ -139,7 +139,9 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   p.lim = BatchLimits{};
   p.grid_cap = 0;
   const bool stream_ok = gram_stream_eligible(precision, p.B, p.U, p.n_sym, p.Ceff);
-  if (variant == kGramAuto) variant = kGram16;
+  // Default: the streamed shape where it applies (16-byte aligned inputs),
+  // else 16 warps.
+  if (variant == kGramAuto) variant = stream_ok && p.bulk ? kGramStream : kGram16;
   if (variant < kGram16 || variant > kGramVariantMax) return false;
   if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
   if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream) return false;

@@ -296,14 +296,19 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
       tma_load_2d(st + kb * Sh::BLOCK + Sh::HR * 128, &p.map_y, x, c.k * NS, bar, pol);
     }
   };
-  SliceCursor pc{slot, 0, 0, 0u};       // next slice to copy
+  SliceCursor pc{slot, 0, 0, 0u};       // next slice to copy (producer lane)
+  int issued = 0;                        // slices copied so far (producer lane)
   if (producer) {
-    for (int q = 0; q < R && pc.k < p.n_sc; ++q) {
+    for (; issued < R && pc.k < p.n_sc; ++issued) {
       issue(pc);
       pc.next(NC, R, nslots);
     }
   }
   __syncwarp();
+  // The slice `issued` goes into the stage of slice issued - R once every warp
+  // of the team has released that one (phase pc.ph ^ 1 of the stage's empty
+  // barrier; the barrier cannot run a further phase ahead before this copy).
+  auto refill_ready = [&]() { return mbar_try_wait(&empty[pc.s], pc.ph ^ 1u); };
 
   const int g = lane >> 2, t = lane & 3;
   const int mt = wi % Sh::MT, half = wi / Sh::MT;
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
   // conv); the MMAs of its k-steps are interleaved with this thread's
   // conversion of slice i + 1 (one half-row per k-step), so that the split
   // arithmetic and the tensor pipe overlap within each warp.
-  while (cc.k < p.n_sc) {
+  for (int i = 0; cc.k < p.n_sc; ++i) {
     const bool converted = mbar_wait_bounded(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
     if (!__all_sync(kFullMask, converted)) {
       drain(cc);
@@ -377,6 +382,20 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
     SliceCursor nc = cc;
     nc.next(NC, R, nslots);
     const bool has_next = nc.k < p.n_sc;
+    // The next slice must have been copied before anyone waits for it: a refill
+    // the producer deferred becomes a (bounded) blocking wait here.
+    bool ok = true;
+    if (producer && has_next && issued <= i + 1) {
+      ok = mbar_wait_bounded(&empty[pc.s], pc.ph ^ 1u, p.status, FFEQ_ERR_TIMEOUT);
+      if (ok) {
+        issue(pc);
+        pc.next(NC, R, nslots);
+        ++issued;
+      } else {
+        drain(cc);
+      }
+    }
+    if (!__shfl_sync(kFullMask, ok, 0)) return;
     if (has_next) {
       const bool landed = mbar_wait_bounded(&full[nc.s], nc.ph, p.status, FFEQ_ERR_TIMEOUT);
       if (!__all_sync(kFullMask, landed)) {
@@ -423,21 +442,19 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
       mbar_arrive(&conv[nc.s]);
     }
     if (nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
-    // Release slice i; the team's producer refills its stage with the slice R
-    // ahead once every warp of the team has released it.
+    // Release slice i.  The producer refills every stage whose slice all warps
+    // have released, without waiting for the other warps (a refill that is not
+    // ready yet is tried again after the next slice).
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[cc.s]);
-    bool ok = true;
-    if (producer && pc.k < p.n_sc) {
-      ok = mbar_wait_bounded(&empty[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
-      if (ok) {
+    if (producer) {
+      while (pc.k < p.n_sc && issued <= i + R && refill_ready()) {
         issue(pc);
         pc.next(NC, R, nslots);
-      } else {
-        drain(cc);
+        ++issued;
       }
     }
-    if (!__shfl_sync(kFullMask, ok, 0)) return;   // the producer's wait ran out: the warp leaves together
+    __syncwarp();
     cc = nc;
   }
   // Let the dependent solve kernel start its launch while this grid drains.

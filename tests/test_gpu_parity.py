@@ -191,7 +191,9 @@ def test_host_buffer_entry_point_matches_device_path(ff):
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
 def test_host_entry_point_both_paths(ff, arch, pinned):
     """Page-locked buffers are read and written in place by the kernels; pageable
-    ones go through the staging copies.  Both equal the device path bit for bit."""
+    ones go through the staging copies.  Both equal the device path bit for bit
+    (inputs read over the host link take the plain-load contraction, shape 1:
+    the device path is pinned to the same shape for that comparison)."""
     p = synth.make_problem(128, 12, 4, 33, 5, seed=17, bits=4)
     plan = ff.ffeq_plan_create(128, 12, 4, 33, 5, arch=arch, precision=ff.BF16X3, llr_bits=4)
     nbytes = ff.ffeq_host_staging_size(plan)
@@ -207,7 +209,21 @@ def test_host_entry_point_both_paths(ff, arch, pinned):
     L = buf(np.zeros((33, 5, 12, 4), np.float32))
     info = buf(np.full((33, Ceff), -1, np.int32))
     ff.ffeq_equalize_host(plan, Hh, yh, p.N0, p.Es, z, s2, L, info, staging, nbytes)
-    g = _gpu(ff, p, arch, 0, llr_bits=4, precision=2)
+    if pinned:
+        dplan = ff.ffeq_plan_create(128, 12, 4, 33, 5, arch=arch, precision=ff.BF16X3, llr_bits=4)
+        ff.ffeq_plan_set_tuning(dplan, (1, 0))
+        dev = torch.device("cuda:0")
+        gz = torch.empty((33, 5, 12), dtype=torch.complex64, device=dev)
+        gs = torch.empty((33, 12), dtype=torch.float32, device=dev)
+        gl = torch.empty((33, 5, 12, 4), dtype=torch.float32, device=dev)
+        nb = ff.ffeq_workspace_size(dplan)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        ff.ffeq_equalize(dplan, torch.from_numpy(p.H).to(dev), torch.from_numpy(p.y).to(dev), p.N0, p.Es, gz, gs, gl,
+                         None, ws, nb)
+        torch.cuda.synchronize()
+        g = {"z": gz.cpu().numpy(), "sigma2": gs.cpu().numpy(), "llr": gl.cpu().numpy()}
+    else:
+        g = _gpu(ff, p, arch, 0, llr_bits=4, precision=2)
     assert np.array_equal(z.numpy(), g["z"]) and np.array_equal(s2.numpy(), g["sigma2"])
     assert np.array_equal(L.numpy(), g["llr"]) and (info.numpy() == 0).all()
 
