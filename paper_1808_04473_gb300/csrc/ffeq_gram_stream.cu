@@ -28,8 +28,8 @@
 // of antennas 8h .. 8h+7 become four 16-bit planes (re hi, re lo, im hi, im lo;
 // hi = x rounded to BF16 or FP16, lo = the rounded remainder), plane p in chunk
 // 4h + p of the same row.  Every staged value is split once per subcarrier.  A
-// third mbarrier (one arrival per thread) tells the team that a slice's planes
-// are complete.  The conversion of slice i + 1 is interleaved with the MMAs of
+// third mbarrier tells the team that a slice's planes
+// are complete (one arrival per warp, after a warp barrier).  The conversion of slice i + 1 is interleaved with the MMAs of
 // slice i in every warp (software pipelining), so the split arithmetic and the
 // tensor pipe overlap instead of taking turns.
 //
@@ -94,6 +94,27 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
   return v;
+}
+
+// Bounded wait on phase `parity` that lets the thread sleep in hardware until
+// the phase completes (suspend-time hint of 1 us per try) instead of spinning on
+// the issue slots; after kWaitTries tries (seconds) it records `code` and
+// returns false.
+constexpr int kWaitTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int* status, int code) {
+  for (int it = 0; it < kWaitTries; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    if (ok) return true;
+  }
+  if (status) atomicExch(status, code);
+  return false;
 }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
     if (tid < Sh::UPC * kStreamMaxRing) {
       mbar_init(&bars[tid], 1);                                         // full: the copies
       mbar_init(&bars[Sh::UPC * kStreamMaxRing + tid], Sh::WPU);        // empty: one arrival per warp
-      mbar_init(&bars[2 * Sh::UPC * kStreamMaxRing + tid], Sh::WPU * 32);   // converted: every thread
+      mbar_init(&bars[2 * Sh::UPC * kStreamMaxRing + tid], Sh::WPU);   // converted: one arrival per warp
     }
     fence_mbar_init();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -349,7 +370,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
   // Prologue: planes of slice 0.
   SliceCursor cc{slot, 0, 0, 0u};       // slice being consumed
   if (cc.k < p.n_sc) {
-    const bool landed = mbar_wait_bounded(&full[0], 0u, p.status, FFEQ_ERR_TIMEOUT);
+    const bool landed = mbar_wait_sleep(&full[0], 0u, p.status, FFEQ_ERR_TIMEOUT);
     if (!__all_sync(kFullMask, landed)) {
       drain(cc);
       return;
@@ -362,9 +383,11 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
         store_half_planes<MODE>(myring + coff, crow, h, q);
       }
     }
-    // Order the plane writes before the copy that later refills the slice.
+    // Order the plane writes before the copy that later refills the slice; the
+    // warp barrier makes every lane's writes part of lane 0's release.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive(&conv[0]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&conv[0]);
   }
   int cl_left = S;                       // antennas left in the current cluster
   float2* Dc = p.D + static_cast<size_t>(slot) * Ceff * mat;
@@ -374,7 +397,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
   // conversion of slice i + 1 (one half-row per k-step), so that the split
   // arithmetic and the tensor pipe overlap within each warp.
   for (int i = 0; cc.k < p.n_sc; ++i) {
-    const bool converted = mbar_wait_bounded(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
+    const bool converted = mbar_wait_sleep(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
     if (!__all_sync(kFullMask, converted)) {
       drain(cc);
       return;
@@ -386,7 +409,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
     // the producer deferred becomes a (bounded) blocking wait here.
     bool ok = true;
     if (producer && has_next && issued <= i + 1) {
-      ok = mbar_wait_bounded(&empty[pc.s], pc.ph ^ 1u, p.status, FFEQ_ERR_TIMEOUT);
+      ok = mbar_wait_sleep(&empty[pc.s], pc.ph ^ 1u, p.status, FFEQ_ERR_TIMEOUT);
       if (ok) {
         issue(pc);
         pc.next(NC, R, nslots);
@@ -397,7 +420,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
     }
     if (!__shfl_sync(kFullMask, ok, 0)) return;
     if (has_next) {
-      const bool landed = mbar_wait_bounded(&full[nc.s], nc.ph, p.status, FFEQ_ERR_TIMEOUT);
+      const bool landed = mbar_wait_sleep(&full[nc.s], nc.ph, p.status, FFEQ_ERR_TIMEOUT);
       if (!__all_sync(kFullMask, landed)) {
         drain(cc);
         return;
@@ -439,7 +462,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
     }
     if (has_next) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv[nc.s]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[nc.s]);
     }
     if (nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
     // Release slice i.  The producer refills every stage whose slice all warps
