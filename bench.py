@@ -385,8 +385,9 @@ def main():
             if pinned and precision == args.precision:
                 ffeq.ffeq_plan_set_tuning(plans[a], pinned[2 * a:2 * a + 2])
             else:
-                ffeq.ffeq_plan_autotune(plans[a], Hs[0], ys[0], p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
-                                        ws_bytes[a], stream, 10)
+                # Over the rotating input sets: every timed call reads cold inputs, as the steps do.
+                ffeq.ffeq_plan_autotune_sets(plans[a], Hs, ys, p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
+                                             ws_bytes[a], stream, 2 * n_sets)
         cap = torch.cuda.Stream(dev)
 
         def launch(a, i, which):

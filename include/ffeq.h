@@ -218,13 +218,26 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
  * when the shape does not apply to or fit the problem (plan unchanged);
  * ffeq_plan_get_tuning writes min(n, 2) values.  ffeq_plan_autotune times every
  * shape and depth that fits with `reps` calls of ffeq_equalize on the given
- * buffers (CUDA events on `stream`; arguments as for ffeq_equalize), keeps the
- * fastest, synchronizes the stream and must not run during stream capture. */
+ * buffers (arguments as for ffeq_equalize): the calls of each candidate are
+ * captured once into a CUDA graph on a private stream (ordered after the work
+ * already queued on `stream`) and the graph's replay is timed with CUDA events,
+ * so that host launch gaps do not decide the choice (eager calls where capture
+ * is refused).  It keeps the fastest, makes `stream` wait for its work,
+ * synchronizes, and must not run during stream capture. */
 ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n);
 ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n);
 ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
                                float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
                                void* stream, int reps);
+/* The same with n_sets input sets (host arrays of n_sets device pointers H[i],
+ * y[i], each laid out as for ffeq_equalize): timed call r reads set r % n_sets,
+ * so that with sets larger than L2 in total every call reads cold inputs, as in
+ * a stream of frames (with one set the inputs stay L2-resident between calls
+ * and the timing favours other shapes).  FFEQ_ERR_INVALID_ARG for n_sets < 1 or
+ * null arrays. */
+ffeq_status ffeq_plan_autotune_sets(ffeq_plan* plan, const void* const* H, const void* const* y, int n_sets,
+                                    float N0, float Es, void* z, float* sigma2, float* llr, int* info,
+                                    void* workspace, size_t workspace_bytes, void* stream, int reps);
 
 /* Device staging bytes ffeq_equalize_host needs (inputs, outputs and workspace). */
 ffeq_status ffeq_host_staging_size(const ffeq_plan* plan, size_t* bytes);

@@ -15,6 +15,8 @@ struct ffeq_plan {
   int gram_variant = 0;  // contraction launch shape (0: default)
   int gram_stages = 0;   // staged units per CTA (0: as many as fit)
   size_t off_X = 0, off_A = 0, off_F = 0;   // refinement arrays in the workspace
+  ffeq::TensorMapCache* maps = nullptr;      // streamed contraction: encoded maps of recent inputs
+  ~ffeq_plan() { ffeq::tensor_map_cache_destroy(maps); }
 };
 
 namespace {
@@ -103,6 +105,7 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   plan->p = *p;
   plan->Ceff = Ceff;
+  plan->maps = ffeq::tensor_map_cache_create();   // nullptr only on allocation failure: then encode every call
   plan->workspace = static_cast<size_t>(p->n_sc) * Ceff * (p->U + p->n_sym) * p->U * 8;
   if (p->refine > 0) {
     // Refinement keeps the local estimates, the inverses and the pivot status.
@@ -149,6 +152,7 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.n_sym = p.n_sym;
   // Inputs in host memory (read in place over the host link) take plain loads.
   gp.bulk = !host_inputs && (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
+  gp.map_cache = plan->maps;
   if (!ffeq::gram_configure(gp, p.precision, plan->gram_variant, plan->gram_stages)) return FFEQ_ERR_UNSUPPORTED;
   const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                                  : ffeq::launch_gram_tc(gp, p.precision, st);
@@ -422,16 +426,86 @@ ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
 ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, float N0, float Es, void* z,
                                float* sigma2, float* llr, int* info, void* workspace, size_t workspace_bytes,
                                void* stream, int reps) {
-  if (!plan || reps < 1) return FFEQ_ERR_INVALID_ARG;
+  return ffeq_plan_autotune_sets(plan, &H, &y, 1, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream,
+                                 reps);
+}
+
+namespace {
+
+// Device time of `reps` calls of ffeq_equalize on stream cs, reading the input
+// sets in rotation: captured once into a CUDA graph and replayed (after one
+// untimed replay), so that host launch gaps do not enter the comparison; eager
+// calls if the capture is refused.  Returns a negative time on failure.
+float time_equalize_calls(ffeq_plan* plan, const void* const* H, const void* const* y, int n_sets, float N0,
+                          float Es, void* z, float* sigma2, float* llr, int* info, void* workspace,
+                          size_t workspace_bytes, cudaStream_t cs, int reps, cudaEvent_t e0, cudaEvent_t e1,
+                          ffeq_status* st_out) {
+  ffeq_status s = FFEQ_OK;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    for (int r = 0; r < reps && s == FFEQ_OK; ++r)
+      s = ffeq_equalize(plan, H[r % n_sets], y[r % n_sets], N0, Es, z, sigma2, llr, info, workspace,
+                        workspace_bytes, cs);
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (s != FFEQ_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      graph = nullptr;
+      exec = nullptr;
+      cudaGetLastError();
+      s = FFEQ_OK;
+    }
+  } else {
+    cudaGetLastError();
+  }
+  float ms = -1.f;
+  bool ok = true;
+  if (exec) {
+    ok = cudaGraphLaunch(exec, cs) == cudaSuccess && cudaEventRecord(e0, cs) == cudaSuccess &&
+         cudaGraphLaunch(exec, cs) == cudaSuccess;
+  } else {
+    ok = cudaEventRecord(e0, cs) == cudaSuccess;
+    for (int r = 0; r < reps && ok && s == FFEQ_OK; ++r)
+      s = ffeq_equalize(plan, H[r % n_sets], y[r % n_sets], N0, Es, z, sigma2, llr, info, workspace,
+                        workspace_bytes, cs);
+  }
+  if (ok && s == FFEQ_OK && cudaEventRecord(e1, cs) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+    // ms is set
+  } else {
+    ms = -1.f;
+    if (s == FFEQ_OK) s = cuda_fail(cudaGetLastError());
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  *st_out = s;
+  return ms;
+}
+
+}  // namespace
+
+ffeq_status ffeq_plan_autotune_sets(ffeq_plan* plan, const void* const* H, const void* const* y, int n_sets,
+                                    float N0, float Es, void* z, float* sigma2, float* llr, int* info,
+                                    void* workspace, size_t workspace_bytes, void* stream, int reps) {
+  if (!plan || reps < 1 || n_sets < 1 || !H || !y) return FFEQ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(st, &cap);
   if (e != cudaSuccess) return cuda_fail(e);
   if (cap != cudaStreamCaptureStatusNone) return FFEQ_ERR_INVALID_ARG;
   if (plan->p.n_sc == 0) return FFEQ_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+  // A private stream (capturable even when the caller's is the legacy default
+  // stream), ordered after the caller's work.
+  cudaStream_t cs = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, dep = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&dep, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventRecord(dep, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, dep, 0)) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (dep) cudaEventDestroy(dep);
+    if (cs) cudaStreamDestroy(cs);
     return cuda_fail(e);
   }
   const int old[2] = {plan->gram_variant, plan->gram_stages};
@@ -442,28 +516,26 @@ ffeq_status ffeq_plan_autotune(ffeq_plan* plan, const void* H, const void* y, fl
     for (int stages = 1; stages <= 3 && s == FFEQ_OK; ++stages) {
       const int v[2] = {variant, stages};
       if (ffeq_plan_set_tuning(plan, v, 2) != FFEQ_OK) continue;
-      // One untimed call, then `reps` timed calls of the whole equalization.
-      s = ffeq_equalize(plan, H, y, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream);
+      // One eager untimed call (first-use configuration happens outside capture).
+      s = ffeq_equalize(plan, H[0], y[0], N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, cs);
       if (s != FFEQ_OK) break;
-      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { s = cuda_fail(e); break; }
-      for (int r = 0; r < reps && s == FFEQ_OK; ++r)
-        s = ffeq_equalize(plan, H, y, N0, Es, z, sigma2, llr, info, workspace, workspace_bytes, stream);
+      const float ms = time_equalize_calls(plan, H, y, n_sets, N0, Es, z, sigma2, llr, info, workspace,
+                                           workspace_bytes, cs, reps, e0, e1, &s);
       if (s != FFEQ_OK) break;
-      float ms = 0.f;
-      if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
-          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
-        s = cuda_fail(e);
-        break;
-      }
-      if (best < 0.f || ms < best) {
+      if (ms >= 0.f && (best < 0.f || ms < best)) {
         best = ms;
         best_v[0] = variant;
         best_v[1] = stages;
       }
     }
   }
+  // The caller's stream waits for everything run here.
+  if (cudaEventRecord(dep, cs) == cudaSuccess) cudaStreamWaitEvent(st, dep, 0);
+  cudaStreamSynchronize(cs);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(dep);
+  cudaStreamDestroy(cs);
   plan->gram_variant = s == FFEQ_OK ? best_v[0] : old[0];
   plan->gram_stages = s == FFEQ_OK ? best_v[1] : old[1];
   return s;

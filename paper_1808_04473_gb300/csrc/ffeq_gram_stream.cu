@@ -3,35 +3,42 @@
 // of ffeq_gram.cuh, reorganised so that no warp ever waits for another one's
 // partial sums.
 //
-// Work split.  A CTA of 16 warps holds several subcarriers at once (8 for
-// U <= 16, 4 for U = 32).  Each subcarrier is owned by a team of 2 (or 4) warps;
-// each warp owns a fixed set of output tiles (one 16-user m-tile times two or
-// three 8-row n-tiles of W) and accumulates them in registers over the whole
-// antenna range of a cluster (PD: all B antennas, the adder tree of Eq.
-// fullMRC in the accumulators; FD: S = B/C antennas, then the cluster's tile is
-// stored and the accumulators restart).  No split-K, no shared-memory
-// reduction, no CTA-wide barrier after the prologue.
+// Work split.  A CTA holds several subcarriers at once (8 for U <= 16, 4 for
+// U = 32).  Each subcarrier is owned by a team of 2 (or 4) MMA warps; each MMA
+// warp owns a fixed set of output tiles (one 16-user m-tile times two or three
+// 8-row n-tiles of W) and accumulates them in registers over the whole antenna
+// range of a cluster (PD: all B antennas, the adder tree of Eq. fullMRC in the
+// accumulators; FD: S = B/C antennas, then the cluster's tile is stored and the
+// accumulators restart).  No split-K, no shared-memory reduction, no CTA-wide
+// barrier after the prologue.  Besides the 16 MMA warps the CTA has converter
+// warps (8 for U <= 16, one per team; 4 for U = 32): a converter warp issues its
+// teams' copies (producer) and converts each landed slice (below), so the MMA
+// warps only wait, load fragments, multiply and release.
 //
 // Staging.  A subcarrier streams through a private ring of `ring` (2 or 3)
 // slices of 32 antennas; each slice is two 16-antenna blocks [H rows | y rows]
 // x 128 bytes, written by tensor-map copies (cp.async.bulk.tensor, four per
 // slice, 128-byte swizzle: 16-byte chunk j of row r lands at chunk j ^ (r mod
 // 8), so that the 8 rows read by one ldmatrix phase fall in distinct bank
-// groups) that complete on the slice's mbarrier.  Lane 0 of the team's first
-// warp refills a slice once every warp of the team has released it (a second
-// mbarrier).  Rows the copies never write (user slots >= U, symbol slots >=
-// n_sym) are zeroed once; antennas past B arrive as zeros from the copies'
-// bounds fill.
+// groups) that complete on the slice's mbarrier ("full").  The converter
+// refills a stage once the team's MMA warps have released it ("empty", one
+// arrival per MMA warp).  Rows the copies never write (user slots >= U, symbol
+// slots >= n_sym) are zeroed once; antennas past B arrive as zeros from the
+// copies' bounds fill.
 //
-// Conversion.  Each landed slice is converted in place by the team's threads,
-// one staged block row each, half a row at a time: the 8 complex FP32 values
-// of antennas 8h .. 8h+7 become four 16-bit planes (re hi, re lo, im hi, im lo;
-// hi = x rounded to BF16 or FP16, lo = the rounded remainder), plane p in chunk
-// 4h + p of the same row.  Every staged value is split once per subcarrier.  A
-// third mbarrier tells the team that a slice's planes
-// are complete (one arrival per warp, after a warp barrier).  The conversion of slice i + 1 is interleaved with the MMAs of
-// slice i in every warp (software pipelining), so the split arithmetic and the
-// tensor pipe overlap instead of taking turns.
+// Conversion.  Each landed slice is converted in place by its converter warp,
+// one staged block row per lane at a time, half a row at a time: the 8 complex
+// FP32 values of antennas 8h .. 8h+7 become four 16-bit planes (re hi, re lo,
+// im hi, im lo; hi = x rounded to BF16 or FP16, lo = the rounded remainder),
+// plane p in chunk 4h + p of the same row.  Every staged value is split once
+// per subcarrier; a third mbarrier ("converted", one arrival after a warp
+// barrier) hands the slice to the MMA warps.  The converter polls its teams
+// without blocking, so the slices of one team never wait behind another's.
+//
+// Measured on the 1200 x 14, B = 256, U = 16 workload (BF16x3): one converter
+// warp per four teams kept the MMA warps waiting (27-29 us per launch); one per
+// team brings PD / FD to about 22.5 / 24.6 us, against 14.2 us for the copies
+// alone.
 //
 // Arithmetic.  MMA operand A is H (16 users x 16 antennas), B is W (16 antennas
 // x 8 rows), both fragments loaded with ldmatrix from the planes.  conj(h) w
@@ -42,6 +49,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <new>
 
 #include "ffeq_device.cuh"
 #include "ffeq_internal.h"
@@ -261,30 +269,48 @@ struct SliceCursor {
   }
 };
 
+// Warp-specialized form.  kStreamWarps MMA warps (teams as above) and
+// kConvWarps converter warps per CTA.  A converter warp owns UPC / kConvWarps
+// teams: it issues their copies (producer), and as soon as a slice has landed
+// it converts it in place to planes and signals the team (conv barrier, one
+// arrival); the MMA warps only wait for converted slices, run ldmatrix and the
+// MMAs, and release the slice (empty barrier, one arrival per MMA warp).  The
+// converter polls its teams without blocking (a slice is converted only after
+// it has been issued, a refill only after its gate has completed), so no wait
+// depends on the order in which the teams progress; every wait is bounded.
+template <int UP>
+__host__ __device__ constexpr int conv_warps() { return UP <= 16 ? 8 : 4; }   // one team per converter warp
+template <int UP>
+__host__ __device__ constexpr int ws_threads() { return (kStreamWarps + conv_warps<UP>()) * 32; }
+constexpr long kConvPollLimit = 1L << 24;   // converter passes without progress before it gives up
+
 template <int UP, int MODE>
-__global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const __grid_constant__ StreamParams p) {
+__global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __grid_constant__ StreamParams p) {
   using Sh = StreamShape<UP>;
   constexpr int NTH = Sh::NTH;
+  constexpr int kConvWarps = conv_warps<UP>();
+  constexpr int kWsThreads = ws_threads<UP>();
+  constexpr int TPC = Sh::UPC / kConvWarps;       // teams per converter warp
+  static_assert(Sh::UPC % kConvWarps == 0, "teams split evenly over the converter warps");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t ring0 = (raw + 1023u) & ~1023u;   // swizzled copies want 1024-byte aligned blocks
+  const uint32_t ring0 = (raw + 1023u) & ~1023u;
   const int R = p.ring;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (ring0 - raw) + static_cast<size_t>(Sh::UPC) * R * Sh::SLICE);
+  uint64_t* full_all = bars;                                      // [UPC][kStreamMaxRing]
+  uint64_t* empty_all = bars + Sh::UPC * kStreamMaxRing;
+  uint64_t* conv_all = bars + 2 * Sh::UPC * kStreamMaxRing;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int team = warp / Sh::WPU, wi = warp % Sh::WPU;
-  uint64_t* full = bars + team * kStreamMaxRing;
-  uint64_t* empty = bars + (Sh::UPC + team) * kStreamMaxRing;
-  uint64_t* conv = bars + (2 * Sh::UPC + team) * kStreamMaxRing;
-  const uint32_t myring = ring0 + static_cast<uint32_t>(team * R * Sh::SLICE);
   const int U = p.U, NS = p.n_sym, B = p.B, Ceff = p.Ceff, S = B / Ceff, Mrows = U + NS;
-  const int NC = (B + 16 * kStreamKsb - 1) / (16 * kStreamKsb);   // slices per subcarrier
-  const int slot = blockIdx.x + gridDim.x * team, nslots = gridDim.x * Sh::UPC;
+  const int NC = (B + 16 * kStreamKsb - 1) / (16 * kStreamKsb);
+  const int nslots = gridDim.x * Sh::UPC;
+  const int nkb_last = (B - (NC - 1) * 16 * kStreamKsb + 15) / 16;
 
-  // Zero the rows no copy writes, in every block of the ring; init the barriers.
+  // Zero the rows no copy writes; init the barriers.
   {
     const int zrows = (Sh::HR - U) + (16 - NS);
     const int nblk = Sh::UPC * R * kStreamKsb;
-    for (int e = tid; e < nblk * zrows * 8; e += kStreamWarps * 32) {
+    for (int e = tid; e < nblk * zrows * 8; e += kWsThreads) {
       const int blk = e / (zrows * 8), rest = e - blk * zrows * 8;
       const int zr = rest >> 3, c16 = rest & 7;
       const int row = zr < Sh::HR - U ? U + zr : Sh::HR + NS + (zr - (Sh::HR - U));
@@ -292,149 +318,146 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
       asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
     }
     if (tid < Sh::UPC * kStreamMaxRing) {
-      mbar_init(&bars[tid], 1);                                         // full: the copies
-      mbar_init(&bars[Sh::UPC * kStreamMaxRing + tid], Sh::WPU);        // empty: one arrival per warp
-      mbar_init(&bars[2 * Sh::UPC * kStreamMaxRing + tid], Sh::WPU);   // converted: one arrival per warp
+      mbar_init(&full_all[tid], 1);          // the copies of a slice
+      mbar_init(&empty_all[tid], Sh::WPU);   // the team's MMA warps released it
+      mbar_init(&conv_all[tid], 1);          // its converter warp converted it
     }
     fence_mbar_init();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
   }
-  const uint64_t pol = l2_evict_first_policy();
-  const bool producer = wi == 0 && lane == 0;
-  const int nkb_last = (B - (NC - 1) * 16 * kStreamKsb + 15) / 16;   // 16-antenna blocks of the last slice
-  const uint32_t tx_full = static_cast<uint32_t>(kStreamKsb * 128 * Mrows);
-  const uint32_t tx_last = static_cast<uint32_t>(nkb_last * 128 * Mrows);
-  // Copies of the slice under cursor c into its stage (lane 0 of warp 0 only).
-  auto issue = [&](const SliceCursor& c) {
-    const int nkb = c.ks == NC - 1 ? nkb_last : kStreamKsb;
-    const uint32_t st = myring + static_cast<uint32_t>(c.s * Sh::SLICE);
-    const uint32_t bar = smem_u32(&full[c.s]);
-    mbar_arrive_expect_tx(&full[c.s], nkb == kStreamKsb ? tx_full : tx_last);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int x = 2 * 16 * (kStreamKsb * c.ks + kb);
-      tma_load_2d(st + kb * Sh::BLOCK, &p.map_h, x, c.k * U, bar, pol);
-      tma_load_2d(st + kb * Sh::BLOCK + Sh::HR * 128, &p.map_y, x, c.k * NS, bar, pol);
-    }
-  };
-  SliceCursor pc{slot, 0, 0, 0u};       // next slice to copy (producer lane)
-  int issued = 0;                        // slices copied so far (producer lane)
-  if (producer) {
-    for (; issued < R && pc.k < p.n_sc; ++issued) {
-      issue(pc);
-      pc.next(NC, R, nslots);
-    }
-  }
-  __syncwarp();
-  // The slice `issued` goes into the stage of slice issued - R once every warp
-  // of the team has released that one (phase pc.ph ^ 1 of the stage's empty
-  // barrier; the barrier cannot run a further phase ahead before this copy).
-  auto refill_ready = [&]() { return mbar_try_wait(&empty[pc.s], pc.ph ^ 1u); };
 
-  const int g = lane >> 2, t = lane & 3;
-  const int mt = wi % Sh::MT, half = wi / Sh::MT;
-  // Bounded chance for the copies already issued (at most R - 1 slices after
-  // the one under c) to land before the warp leaves.
-  auto drain = [&](SliceCursor c) {
-    if (!producer) return;
-    for (int q = 1; q < R; ++q) {
-      c.next(NC, R, nslots);
-      if (c.k >= p.n_sc) break;
-      mbar_wait_bounded(&full[c.s], c.ph, nullptr, 0);
+  if (warp >= kStreamWarps) {
+    // ---------------- converter / producer warp
+    const int cw = warp - kStreamWarps;
+    const uint64_t pol = l2_evict_first_policy();
+    const uint32_t tx_full = static_cast<uint32_t>(kStreamKsb * 128 * Mrows);
+    const uint32_t tx_last = static_cast<uint32_t>(nkb_last * 128 * Mrows);
+    SliceCursor pc[TPC], cv[TPC];
+    int issued[TPC], converted[TPC];
+    for (int q = 0; q < TPC; ++q) {
+      const int team = cw * TPC + q;
+      const int slot = blockIdx.x + gridDim.x * team;
+      pc[q] = SliceCursor{slot, 0, 0, 0u};
+      cv[q] = pc[q];
+      issued[q] = 0;
+      converted[q] = 0;
     }
-  };
-  const int NT = (Mrows + 7) / 8;
-  const int nt0 = half * NTH;
-  const int nt_end = min(NT, nt0 + NTH);
-  const int ntiles = nt_end - nt0;                 // may be <= 0: the warp only converts
-  const FragOffsets fo = frag_offsets<UP>(mt, nt0, nt_end, U, lane);
-  float acc[NTH][2][4];
-#pragma unroll
-  for (int j = 0; j < NTH; ++j)
-#pragma unroll
-    for (int o = 0; o < 2; ++o)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[j][o][q] = 0.f;
-  // This thread's conversion task, the same in every slice: one block row
-  // (rows U .. HR-1 and symbol slots >= n_sym are never loaded and stay zero).
-  // A team has at least kStreamKsb * (U + n_sym) threads, so one task at most.
-  const int ce = wi * 32 + lane;
-  const int ckb = ce / Mrows, crr = ce - ckb * Mrows;
-  const int crow = crr < U ? crr : Sh::HR + (crr - U);
-  const uint32_t coff = static_cast<uint32_t>(ckb * Sh::BLOCK + crow * 128);
-  const bool ctask_full = ce < kStreamKsb * Mrows, ctask_last = ce < nkb_last * Mrows;
-  // Output position of this warp's tiles: c0 (user g, row 2t), c1 (g, 2t+1),
-  // c2 (g+8, 2t), c3 (g+8, 2t+1) of each n-tile.
-  const size_t mat = static_cast<size_t>(Mrows) * U;
-
-  // Prologue: planes of slice 0.
-  SliceCursor cc{slot, 0, 0, 0u};       // slice being consumed
-  if (cc.k < p.n_sc) {
-    const bool landed = mbar_wait_sleep(&full[0], 0u, p.status, FFEQ_ERR_TIMEOUT);
-    if (!__all_sync(kFullMask, landed)) {
-      drain(cc);
-      return;
-    }
-    if (NC == 1 ? ctask_last : ctask_full) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float4 q[4];
-        load_half(myring + coff, crow, h, q);
-        store_half_planes<MODE>(myring + coff, crow, h, q);
+    auto issue = [&](int q) {   // lane 0
+      const int team = cw * TPC + q;
+      const SliceCursor& c = pc[q];
+      const int nkb = c.ks == NC - 1 ? nkb_last : kStreamKsb;
+      const uint32_t st = ring0 + static_cast<uint32_t>((team * R + c.s) * Sh::SLICE);
+      uint64_t* fb = &full_all[team * kStreamMaxRing + c.s];
+      mbar_arrive_expect_tx(fb, nkb == kStreamKsb ? tx_full : tx_last);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int x = 2 * 16 * (kStreamKsb * c.ks + kb);
+        tma_load_2d(st + kb * Sh::BLOCK, &p.map_h, x, c.k * U, smem_u32(fb), pol);
+        tma_load_2d(st + kb * Sh::BLOCK + Sh::HR * 128, &p.map_y, x, c.k * NS, smem_u32(fb), pol);
       }
+    };
+    if (lane == 0) {
+      for (int q = 0; q < TPC; ++q)
+        for (; issued[q] < R && pc[q].k < p.n_sc; ++issued[q]) {
+          issue(q);
+          pc[q].next(NC, R, nslots);
+        }
     }
-    // Order the plane writes before the copy that later refills the slice; the
-    // warp barrier makes every lane's writes part of lane 0's release.
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&conv[0]);
-  }
-  int cl_left = S;                       // antennas left in the current cluster
-  float2* Dc = p.D + static_cast<size_t>(slot) * Ceff * mat;
-
-  // Slice i: its planes are complete (every thread of the team arrived on
-  // conv); the MMAs of its k-steps are interleaved with this thread's
-  // conversion of slice i + 1 (one half-row per k-step), so that the split
-  // arithmetic and the tensor pipe overlap within each warp.
-  for (int i = 0; cc.k < p.n_sc; ++i) {
-    const bool converted = mbar_wait_sleep(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
-    if (!__all_sync(kFullMask, converted)) {
-      drain(cc);
-      return;
-    }
-    SliceCursor nc = cc;
-    nc.next(NC, R, nslots);
-    const bool has_next = nc.k < p.n_sc;
-    // The next slice must have been copied before anyone waits for it: a refill
-    // the producer deferred becomes a (bounded) blocking wait here.
-    bool ok = true;
-    if (producer && has_next && issued <= i + 1) {
-      ok = mbar_wait_sleep(&empty[pc.s], pc.ph ^ 1u, p.status, FFEQ_ERR_TIMEOUT);
-      if (ok) {
-        issue(pc);
-        pc.next(NC, R, nslots);
-        ++issued;
+    long idle = 0;
+    for (;;) {
+      bool pending = false, progressed = false;
+#pragma unroll
+      for (int q = 0; q < TPC; ++q) {
+        const int team = cw * TPC + q;
+        // Refill every stage whose slice the team's MMA warps have released.
+        if (lane == 0) {
+          while (pc[q].k < p.n_sc && mbar_try_wait(&empty_all[team * kStreamMaxRing + pc[q].s], pc[q].ph ^ 1u)) {
+            issue(q);
+            pc[q].next(NC, R, nslots);
+            ++issued[q];
+            progressed = true;
+          }
+        }
+        if (cv[q].k >= p.n_sc) continue;
+        pending = true;
+        // Convert the next slice once it has been issued and has landed.
+        const int iss = __shfl_sync(kFullMask, issued[q], 0);
+        if (converted[q] >= iss) continue;
+        const bool landed = mbar_try_wait(&full_all[team * kStreamMaxRing + cv[q].s], cv[q].ph);
+        if (!__all_sync(kFullMask, landed)) continue;
+        const int nkb = cv[q].ks == NC - 1 ? nkb_last : kStreamKsb;
+        const uint32_t st = ring0 + static_cast<uint32_t>((team * R + cv[q].s) * Sh::SLICE);
+        for (int e = lane; e < nkb * Mrows; e += 32) {
+          const int kbt = e / Mrows, rr = e - kbt * Mrows;
+          const int row = rr < U ? rr : Sh::HR + (rr - U);
+          const uint32_t addr = st + static_cast<uint32_t>(kbt * Sh::BLOCK + row * 128);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float4 v[4];
+            load_half(addr, row, h, v);
+            store_half_planes<MODE>(addr, row, h, v);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv_all[team * kStreamMaxRing + cv[q].s]);
+        cv[q].next(NC, R, nslots);
+        ++converted[q];
+        progressed = true;
+      }
+      progressed = __any_sync(kFullMask, progressed);
+      if (!pending) break;
+      if (progressed) {
+        idle = 0;
+      } else if (++idle > kConvPollLimit) {
+        if (lane == 0 && p.status) atomicExch(p.status, FFEQ_ERR_TIMEOUT);
+        break;
       } else {
-        drain(cc);
+        __nanosleep(64);
       }
     }
-    if (!__shfl_sync(kFullMask, ok, 0)) return;
-    if (has_next) {
-      const bool landed = mbar_wait_sleep(&full[nc.s], nc.ph, p.status, FFEQ_ERR_TIMEOUT);
-      if (!__all_sync(kFullMask, landed)) {
-        drain(cc);
-        return;
+    // Let the copies issued for slices nobody will convert any more land before
+    // leaving (only after a time-out; a normal exit has none in flight).
+    if (lane == 0) {
+      for (int q = 0; q < TPC; ++q) {
+        SliceCursor c = cv[q];
+        for (int r = converted[q]; r < issued[q]; ++r) {
+          mbar_wait_bounded(&full_all[(cw * TPC + q) * kStreamMaxRing + c.s], c.ph, nullptr, 0);
+          c.next(NC, R, nslots);
+        }
       }
     }
-    const bool conv_now = has_next && (nc.ks == NC - 1 ? ctask_last : ctask_full);
-    const uint32_t caddr = myring + static_cast<uint32_t>(nc.s * Sh::SLICE) + coff;
-    const int nkb = cc.ks == NC - 1 ? nkb_last : kStreamKsb;
-    const uint32_t st = myring + static_cast<uint32_t>(cc.s * Sh::SLICE);
+  } else {
+    // ---------------- MMA warp
+    const int team = warp / Sh::WPU, wi = warp % Sh::WPU;
+    const int slot = blockIdx.x + gridDim.x * team;
+    uint64_t* empty = empty_all + team * kStreamMaxRing;
+    uint64_t* conv = conv_all + team * kStreamMaxRing;
+    const uint32_t myring = ring0 + static_cast<uint32_t>(team * R * Sh::SLICE);
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = wi % Sh::MT, half = wi / Sh::MT;
+    const int NT = (Mrows + 7) / 8;
+    const int nt0 = half * NTH;
+    const int nt_end = min(NT, nt0 + NTH);
+    const int ntiles = nt_end - nt0;
+    const FragOffsets fo = frag_offsets<UP>(mt, nt0, nt_end, U, lane);
+    const size_t mat = static_cast<size_t>(Mrows) * U;
+    float acc[NTH][2][4];
 #pragma unroll
-    for (int kb = 0; kb < kStreamKsb; ++kb) {
-      float4 q[4];
-      if (conv_now) load_half(caddr, crow, kb, q);
-      if (kb < nkb) {
+    for (int j = 0; j < NTH; ++j)
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][o][q] = 0.f;
+    int cl_left = S;
+    float2* Dc = p.D + static_cast<size_t>(slot) * Ceff * mat;
+    SliceCursor cc{slot, 0, 0, 0u};
+    while (cc.k < p.n_sc) {
+      const bool ready = mbar_wait_sleep(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
+      if (!__all_sync(kFullMask, ready)) break;
+      const int nkb = cc.ks == NC - 1 ? nkb_last : kStreamKsb;
+      const uint32_t st = myring + static_cast<uint32_t>(cc.s * Sh::SLICE);
+      for (int kb = 0; kb < nkb; ++kb) {
         stream_kstep<UP, MODE>(st + kb * Sh::BLOCK, fo, ntiles, acc);
         cl_left -= 16;
         if (cl_left <= 0) {
@@ -458,28 +481,13 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1) gram_stream_kernel(const
           Dc += mat;
         }
       }
-      if (conv_now) store_half_planes<MODE>(caddr, crow, kb, q);
-    }
-    if (has_next) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[nc.s]);
+      if (lane == 0) mbar_arrive(&empty[cc.s]);
+      SliceCursor nc = cc;
+      nc.next(NC, R, nslots);
+      if (nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
+      cc = nc;
     }
-    if (nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
-    // Release slice i.  The producer refills every stage whose slice all warps
-    // have released, without waiting for the other warps (a refill that is not
-    // ready yet is tried again after the next slice).
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[cc.s]);
-    if (producer) {
-      while (pc.k < p.n_sc && issued <= i + R && refill_ready()) {
-        issue(pc);
-        pc.next(NC, R, nslots);
-        ++issued;
-      }
-    }
-    __syncwarp();
-    cc = nc;
   }
   // Let the dependent solve kernel start its launch while this grid drains.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -529,7 +537,7 @@ cudaError_t launch_stream_up(const StreamParams& sp, cudaStream_t stream) {
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(gram_stream_kernel<UP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(gram_ws_kernel<UP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(stream_smem_bytes<UP>(kStreamMaxRing)));
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
@@ -539,11 +547,27 @@ cudaError_t launch_stream_up(const StreamParams& sp, cudaStream_t stream) {
   const int sms = dev < 64 ? num_sms[dev] : 152;
   const int need = (sp.n_sc + StreamShape<UP>::UPC - 1) / StreamShape<UP>::UPC;
   const int grid = need < sms ? need : sms;
-  gram_stream_kernel<UP, MODE><<<grid, kStreamWarps * 32, stream_smem_bytes<UP>(sp.ring), stream>>>(sp);
+  gram_ws_kernel<UP, MODE><<<grid, ws_threads<UP>(), stream_smem_bytes<UP>(sp.ring), stream>>>(sp);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// Maps of the last kEntries input pairs of a plan (the plan fixes every size,
+// so the addresses of H and y identify the maps).
+struct TensorMapCache {
+  static constexpr int kEntries = 16;
+  struct Entry {
+    CUtensorMap mh, my;
+    const void* H = nullptr;
+    const void* y = nullptr;
+  };
+  Entry e[kEntries];
+  int next = 0;
+};
+
+TensorMapCache* tensor_map_cache_create() { return new (std::nothrow) TensorMapCache; }
+void tensor_map_cache_destroy(TensorMapCache* cache) { delete cache; }
 
 bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff) {
   if (precision != FFEQ_BF16X3 && precision != FFEQ_FP16X3) return false;
@@ -554,9 +578,27 @@ bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff) {
 cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream) {
   if (p.n_sc == 0) return cudaSuccess;
   StreamParams sp{};
-  if (!encode_rows(&sp.map_h, p.H, static_cast<long long>(p.n_sc) * p.U, p.B, p.U) ||
-      !encode_rows(&sp.map_y, p.y, static_cast<long long>(p.n_sc) * p.n_sym, p.B, p.n_sym))
-    return cudaErrorInvalidValue;
+  TensorMapCache* c = p.map_cache;
+  int hit = -1;
+  if (c)
+    for (int q = 0; q < TensorMapCache::kEntries; ++q)
+      if (c->e[q].H == p.H && c->e[q].y == p.y) hit = q;
+  if (hit >= 0) {
+    sp.map_h = c->e[hit].mh;
+    sp.map_y = c->e[hit].my;
+  } else {
+    if (!encode_rows(&sp.map_h, p.H, static_cast<long long>(p.n_sc) * p.U, p.B, p.U) ||
+        !encode_rows(&sp.map_y, p.y, static_cast<long long>(p.n_sc) * p.n_sym, p.B, p.n_sym))
+      return cudaErrorInvalidValue;
+    if (c) {
+      TensorMapCache::Entry& e = c->e[c->next];
+      e.mh = sp.map_h;
+      e.my = sp.map_y;
+      e.H = p.H;
+      e.y = p.y;
+      c->next = (c->next + 1) % TensorMapCache::kEntries;
+    }
+  }
   sp.D = p.D;
   sp.status = p.status;
   sp.B = p.B;

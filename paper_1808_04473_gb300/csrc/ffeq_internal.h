@@ -39,6 +39,8 @@ struct SolveTile {
 
 // Contraction kernel: H, y -> workspace D = [n_sc][Ceff][U + n_sym][U] complex,
 // D[m][u] = sum over the cluster's antennas of conj(H[u][b]) * [H; Y][m][b].
+struct TensorMapCache;   // encoded tensor maps of the streamed contraction (host side)
+
 struct GramParams {
   const float2* H;    // [n_sc][U][B]
   const float2* y;    // [n_sc][n_sym][B]
@@ -58,6 +60,7 @@ struct GramParams {
   int grid_cap;       // > 0: at most this many persistent CTAs
   int plane_bytes;    // > 0: pre-split BF16 planes of this capacity (BF16x3 pre-split contraction)
   int variant;        // contraction launch shape (kGram16 ... kGramStream)
+  TensorMapCache* map_cache;   // streamed shape: maps of inputs seen before (nullptr: encode every call)
 };
 
 // Contraction launch shapes: 16 warps, one CTA per SM; 8 warps, two CTAs per SM
@@ -73,6 +76,10 @@ constexpr int kGramStreamRing = 3;      // default (and largest) ring depth of t
 // Whether the streamed contraction takes this problem (BF16x3 or FP16x3,
 // U <= 32, B even, cluster sizes whole 16-antenna steps for FD).
 bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff);
+// A plan's cache of encoded tensor maps (inputs at the addresses of a recent
+// call reuse their maps instead of encoding them again on the host).
+TensorMapCache* tensor_map_cache_create();
+void tensor_map_cache_destroy(TensorMapCache* cache);
 cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream);
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.

@@ -79,6 +79,8 @@ _SIGS = {
     "ffeq_plan_set_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
     "ffeq_plan_get_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
     "ffeq_plan_autotune": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _i], _i),
+    "ffeq_plan_autotune_sets": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _f, _f, _vp, _vp, _vp, _vp, _vp,
+                                 _sz, _vp, _i], _i),
     "ffeq_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_batch_config), ctypes.POINTER(ffeq_instance),
                            _i], _i),
     "ffeq_batch_destroy": ([_vp], None),
@@ -252,6 +254,19 @@ def ffeq_plan_autotune(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=No
                        workspace_bytes: int = 0, stream=None, reps: int = 10) -> tuple[int, int]:
     _check("ffeq_plan_autotune", lib().ffeq_plan_autotune(
         plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
+        _ptr(workspace), workspace_bytes, _stream(stream), int(reps)))
+    return ffeq_plan_get_tuning(plan)
+
+
+def ffeq_plan_autotune_sets(plan: Plan, Hs, ys, N0: float, Es: float, z, sigma2, llr=None, info=None, workspace=None,
+                            workspace_bytes: int = 0, stream=None, reps: int = 10) -> tuple[int, int]:
+    """Autotune over several input sets (lists of device buffers), read in rotation."""
+    if len(Hs) != len(ys) or not Hs:
+        raise ValueError("Hs and ys must be non-empty lists of the same length")
+    harr = (_vp * len(Hs))(*[_ptr(h) for h in Hs])
+    yarr = (_vp * len(ys))(*[_ptr(v) for v in ys])
+    _check("ffeq_plan_autotune_sets", lib().ffeq_plan_autotune_sets(
+        plan.handle, harr, yarr, len(Hs), float(N0), float(Es), _ptr(z), _ptr(sigma2), _ptr(llr), _ptr(info),
         _ptr(workspace), workspace_bytes, _stream(stream), int(reps)))
     return ffeq_plan_get_tuning(plan)
 

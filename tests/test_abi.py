@@ -156,6 +156,17 @@ def test_plan_tuning_validation(built):
         assert e.value.status == 2, v
 
 
+def test_autotune_sets_checks_arguments(built):
+    plan = ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, precision=ffeq.BF16X3)
+    L = ffeq.lib()
+    arr = (ctypes.c_void_p * 1)(256)
+    for H, y, n, reps in ((None, arr, 1, 2), (arr, None, 1, 2), (arr, arr, 0, 2), (arr, arr, 1, 0)):
+        st = L.ffeq_plan_autotune_sets(plan.handle, H, y, n, 1.0, 1.0, 256, 256, None, None, 256, 1 << 20, None, reps)
+        assert st == 1
+    with pytest.raises(ValueError):
+        ffeq.ffeq_plan_autotune_sets(plan, [], [], 1.0, 1.0, None, None)
+
+
 def test_refinement_needs_the_inputs(built):
     plan = ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, precision=ffeq.BF16X3, refine=1)
     plain = ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, precision=ffeq.BF16X3)

@@ -68,6 +68,9 @@ def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
             assert _rel(s2.cpu().numpy(), o["sigma2"]) <= TOL[precision], (variant, stages)
             results[(variant, stages)] = zn
     assert any(k[0] == 1 for k in results)          # the default shape always fits
+    t = ff.ffeq_plan_autotune_sets(plan, [H, H.clone()], [y, y.clone()], p.N0, p.Es, z, s2, None, None, ws, nb,
+                                   reps=2)
+    assert t[0] in (1, 2, 3, 4, 5) and 1 <= t[1] <= 3
     t = ff.ffeq_plan_autotune(plan, H, y, p.N0, p.Es, z, s2, None, None, ws, nb, reps=2)
     assert t[0] in (1, 2, 3, 4, 5) and 1 <= t[1] <= 3
     if precision != 0 and (arch == 0 or (B // C) % 16 == 0):
