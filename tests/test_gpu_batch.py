@@ -18,8 +18,9 @@ the hundreds), so each instance's bound is
 the first-order perturbation bound of a linear solve whose matrix and
 right-hand side carry relative errors u from the products that formed them:
 u = 2^-16 for BF16x3 (hi + lo pairs keep 16 significand bits; the dropped lo*lo
-term is 2^-18), 2^-21 for TF32x3 (22 bits, dropped term 2^-22) and 2^-22 for
-FP32 (2^-24 per product, summation over up to 256 antennas).
+term is 2^-18), 2^-21 for TF32x3 and FP16x3 (22 bits, dropped term 2^-22; FP16's
+subnormal lo parts of entries below 2^-3 add at most 2^-25 absolute) and 2^-22
+for FP32 (2^-24 per product, summation over up to 256 antennas).
 
 The LLR bound is 4x the z bound.  Per bit the max-log LLR is affine in z with
 slope 2 |a_0 - a_1| / sigma^2 (a_0, a_1 the nearest levels with the bit 0 / 1),
@@ -37,8 +38,8 @@ from paper_1808_04473_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PREC_TOL = {0: 1e-5, 1: 1e-5, 2: 2e-4}      # FP32, TF32X3, BF16X3
-UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16}
+PREC_TOL = {0: 1e-5, 1: 1e-5, 2: 2e-4, 3: 2e-5}      # FP32, TF32X3, BF16X3, FP16X3
+UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16, 3: 2.0 ** -21}
 
 
 def _kappa(p, arch):
@@ -165,7 +166,7 @@ def test_uneven_4096_fp32_matches_the_oracle(ff, uneven, arch):
     _check(run, run.host(), precision=0)
 
 
-@pytest.mark.parametrize("precision", [1, 2], ids=["TF32X3", "BF16X3"])
+@pytest.mark.parametrize("precision", [1, 2, 3], ids=["TF32X3", "BF16X3", "FP16X3"])
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
 def test_uneven_tensor_core_precisions(ff, uneven, arch, precision):
     ps = uneven[:1024]
