@@ -183,3 +183,23 @@ def test_fp64_residual_follows_the_condition_estimate(ff, arch):
     for key in ("z", "sigma2", "llr"):
         assert np.array_equal(g1[key], gx[key]), key
     assert not np.array_equal(g1["z"], gy["z"])
+
+
+def test_fp64_residual_branch_at_40db(ff):
+    """The stress variant of the U = 32 correlated workload (S = 16 < U, r = 0.7,
+    64-QAM, 40 dB): every FD cluster's condition estimate is above 1e4 (about
+    2e5-5e5), so refine_fp64 = 1 takes the FP64 residual everywhere.  From an
+    FP32 start (error about kappa 2^-24) two FP64-residual steps reach the FP32
+    storage floor (4e-6 on z and sigma^2), while two FP32-residual steps stay at
+    the FP32 solve's accuracy, at least 10x worse here."""
+    p = synth.make_problem(256, 32, 16, 8, 14, snr_db=40.0, bits=6, seed=304, corr_r=0.7)
+    assert _kappa1(p, 1).min() > 1e4
+    o = lmmse.equalize_fd(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, "unbiased")
+    g64 = _run(ff, p, 1, 0, 2, bits=6, refine_fp64=1)
+    g32 = _run(ff, p, 1, 0, 2, bits=6, refine_fp64=0)
+    assert (g64["info"] == 0).all()
+    ez, es = _rel(g64["z"], o["z"]), _rel(g64["sigma2"], o["sigma2"])
+    e32 = _rel(g32["z"], o["z"])
+    print("40 dB: z err fp64-res %.3g (sigma2 %.3g), fp32-res %.3g" % (ez.max(), es.max(), e32.max()))
+    assert ez.max() <= 4e-6 and es.max() <= 4e-6, (ez.max(), es.max())
+    assert e32.max() >= 10 * ez.max()
