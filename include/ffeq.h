@@ -131,6 +131,18 @@ typedef struct ffeq_plan ffeq_plan;
  * Returns FFEQ_ERR_INVALID_ARG or FFEQ_ERR_UNSUPPORTED otherwise. */
 ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p);
 
+/* The same with clusters of given sizes (Sec. II-B: cluster c holds B_c
+ * contiguous antennas, c = 0..C-1, in order along each row of H and y):
+ * cluster_sizes holds C integers >= 0 summing to B (B % C need not be 0);
+ * NULL means B / C each, as ffeq_plan_create.  For PD the partition does not
+ * enter the result (the local results are summed, Eq. fullMRC).  FD with
+ * unequal sizes runs the contraction on shapes 1-4 (the streamed and pre-split
+ * shapes need equal clusters) and at most 64 clusters; the training entry
+ * points (ffeq_fd_train_*) need equal clusters and return
+ * FFEQ_ERR_UNSUPPORTED otherwise.  FFEQ_ERR_INVALID_ARG for a negative size or
+ * sizes that do not sum to B. */
+ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, const int* cluster_sizes);
+
 /* Destroy a plan (NULL is ignored). */
 void ffeq_plan_destroy(ffeq_plan* plan);
 

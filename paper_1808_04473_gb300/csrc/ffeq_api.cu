@@ -16,6 +16,9 @@ struct ffeq_plan {
   int gram_stages = 0;   // staged units per CTA (0: as many as fit)
   size_t off_X = 0, off_A = 0, off_F = 0;   // refinement arrays in the workspace
   ffeq::TensorMapCache* maps = nullptr;      // streamed contraction: encoded maps of recent inputs
+  bool cl_uniform = true;                    // clusters of B / C antennas
+  int cl_off[ffeq::kMaxClusters + 1] = {};   // otherwise cluster c: antennas [cl_off[c], cl_off[c+1])
+  int max_S = 0;                             // antennas of the largest cluster (FD; B for PD)
   ~ffeq_plan() { ffeq::tensor_map_cache_destroy(maps); }
 };
 
@@ -79,10 +82,33 @@ const char* ffeq_status_string(ffeq_status s) {
 const char* ffeq_last_cuda_error(void) { return g_last_cuda_error; }
 
 ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
+  return ffeq_plan_create_clusters(out, p, nullptr);
+}
+
+ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, const int* cluster_sizes) {
   if (!out || !p) return FFEQ_ERR_INVALID_ARG;
   *out = nullptr;
   if (p->B <= 0 || p->U <= 0 || p->C <= 0 || p->n_sc < 0 || p->n_sym <= 0) return FFEQ_ERR_INVALID_ARG;
-  if (p->B % p->C != 0) return FFEQ_ERR_INVALID_ARG;
+  if (!cluster_sizes && p->B % p->C != 0) return FFEQ_ERR_INVALID_ARG;
+  // Clusters of given sizes (Sec. II-B): C sizes >= 0 summing to B.
+  bool uniform = true;
+  int off[ffeq::kMaxClusters + 1] = {};
+  int max_S = p->B / p->C;
+  if (cluster_sizes) {
+    if (p->C > ffeq::kMaxClusters) return p->arch == FFEQ_FD ? FFEQ_ERR_UNSUPPORTED : FFEQ_ERR_INVALID_ARG;
+    long long sum = 0;
+    max_S = 0;
+    for (int c = 0; c < p->C; ++c) {
+      if (cluster_sizes[c] < 0) return FFEQ_ERR_INVALID_ARG;
+      off[c] = static_cast<int>(sum);
+      sum += cluster_sizes[c];
+      if (cluster_sizes[c] > max_S) max_S = cluster_sizes[c];
+      if (sum > p->B) return FFEQ_ERR_INVALID_ARG;
+      if (cluster_sizes[c] != cluster_sizes[0]) uniform = false;
+    }
+    if (sum != p->B) return FFEQ_ERR_INVALID_ARG;
+    off[p->C] = p->B;
+  }
   if (p->arch != FFEQ_PD && p->arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
   if (p->precision != FFEQ_FP32 && p->precision != FFEQ_TF32X3 && p->precision != FFEQ_BF16X3 &&
       p->precision != FFEQ_FP16X3)
@@ -100,11 +126,18 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p) {
   if (spc * Ceff * ffeq::padded_users(p->U) * (Ceff == 1 && ffeq::padded_users(p->U) == 16 ? 2 : 1) > 512 ||
       ffeq::solve_smem_bytes(p->U, Ceff) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
-  if (p->refine > 0 && !ffeq::refine_fits(p->B, p->U, Ceff, p->n_sym)) return FFEQ_ERR_UNSUPPORTED;
+  if (Ceff == 1) {
+    uniform = true;          // PD sums every cluster: the partition does not enter (Eq. fullMRC)
+    max_S = p->B;
+  }
+  if (p->refine > 0 && !ffeq::refine_fits(max_S, p->U, p->n_sym)) return FFEQ_ERR_UNSUPPORTED;
   ffeq_plan* plan = new (std::nothrow) ffeq_plan;
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   plan->p = *p;
   plan->Ceff = Ceff;
+  plan->cl_uniform = uniform;
+  plan->max_S = max_S;
+  for (int c = 0; c <= Ceff && !uniform; ++c) plan->cl_off[c] = off[c];
   plan->maps = ffeq::tensor_map_cache_create();   // nullptr only on allocation failure: then encode every call
   plan->workspace = static_cast<size_t>(p->n_sc) * Ceff * (p->U + p->n_sym) * p->U * 8;
   if (p->refine > 0) {
@@ -153,6 +186,8 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   // Inputs in host memory (read in place over the host link) take plain loads.
   gp.bulk = !host_inputs && (p.B % 2 == 0) && aligned(H, 16) && aligned(y, 16);
   gp.map_cache = plan->maps;
+  gp.cl_uniform = plan->cl_uniform ? 1 : 0;
+  for (int c = 0; c <= plan->Ceff && !plan->cl_uniform; ++c) gp.cl_off[c] = plan->cl_off[c];
   if (!ffeq::gram_configure(gp, p.precision, plan->gram_variant, plan->gram_stages)) return FFEQ_ERR_UNSUPPORTED;
   const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
                                                  : ffeq::launch_gram_tc(gp, p.precision, st);
@@ -214,6 +249,9 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   rp.n_sym = p.n_sym;
   rp.steps = p.refine;
   rp.res64 = p.refine_fp64;
+  rp.max_S = plan->max_S;
+  for (int c = 0; c <= plan->Ceff; ++c)
+    rp.cl_off[c] = plan->cl_uniform ? c * (p.B / plan->Ceff) : plan->cl_off[c];
   rp.unbiased = sp.unbiased;
   rp.llr_bits = p.llr_bits;
   rp.N0 = sp.N0;
@@ -321,6 +359,7 @@ ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, co
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   const ffeq_problem& p = plan->p;
   if (p.arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
+  if (!plan->cl_uniform) return FFEQ_ERR_UNSUPPORTED;   // the training kernels take clusters of B / C antennas
   if (ffeq::padded_users(p.U) * p.C > 512 || ffeq::train_smem_bytes(p.U, p.C) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
   const TrainLayoutBytes t = train_layout(plan);
@@ -417,6 +456,7 @@ ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
   gp.n_sc = plan->p.n_sc;
   gp.n_sym = plan->p.n_sym;
   gp.bulk = plan->p.B % 2 == 0;
+  gp.cl_uniform = plan->cl_uniform ? 1 : 0;
   if (!ffeq::gram_configure(gp, plan->p.precision, values[0], values[1])) return FFEQ_ERR_UNSUPPORTED;
   plan->gram_variant = values[0];
   plan->gram_stages = values[1];

@@ -265,9 +265,14 @@ __global__ void __launch_bounds__(Contract::kWarps * 32, Contract::kMinBlocks) g
         const int nK = SP / 16;
         k0 = c * SP + ((part * nK) / P) * 16;
         k1 = c * SP + (((part + 1) * nK) / P) * 16;
-      } else {
+      } else if (BATCH || p.cl_uniform) {
         k0 = c * S + (part * S) / P;
         k1 = c * S + ((part + 1) * S) / P;
+      } else {
+        // Clusters of their own sizes (Sec. II-B: B_c antennas for cluster c).
+        const int cs = p.cl_off[c], Sc = p.cl_off[c + 1] - cs;
+        k0 = cs + (part * Sc) / P;
+        k1 = cs + ((part + 1) * Sc) / P;
       }
       auto contract = [&](auto&& out) {
         if constexpr (Contract::kPrep) {

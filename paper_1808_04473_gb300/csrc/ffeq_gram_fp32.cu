@@ -138,14 +138,14 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   p.UP = padded_users(p.U);
   p.lim = BatchLimits{};
   p.grid_cap = 0;
-  const bool stream_ok = gram_stream_eligible(precision, p.B, p.U, p.n_sym, p.Ceff);
+  const bool stream_ok = p.cl_uniform && gram_stream_eligible(precision, p.B, p.U, p.n_sym, p.Ceff);
   // Default: the streamed shape where it applies (16-byte aligned inputs),
   // else 16 warps.
   if (variant == kGramAuto) variant = stream_ok && p.bulk ? kGramStream : kGram16;
   if (variant < kGram16 || variant > kGramVariantMax) return false;
   if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
   if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream) return false;
-  if (variant == kGramPresplit && !gram_presplit_eligible(precision, p.B, p.Ceff)) return false;
+  if (variant == kGramPresplit && (!p.cl_uniform || !gram_presplit_eligible(precision, p.B, p.Ceff))) return false;
   if (variant == kGramStream && !stream_ok) return false;
   if (variant != kGramStream && stages > kGramMaxStages) return false;
   if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes, no tensor maps

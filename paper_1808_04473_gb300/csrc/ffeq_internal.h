@@ -9,6 +9,7 @@
 namespace ffeq {
 
 constexpr int kNsymMax = 16;   // OFDM symbols per subcarrier held in registers
+constexpr int kMaxClusters = 64;   // FD clusters of a plan (the solve holds C * U padded <= 512 lanes)
 
 // One unit of an uneven batch: a single subcarrier of one instance (element
 // offsets into the batch's flat buffers: complex for H, y, z, D; float for
@@ -61,6 +62,10 @@ struct GramParams {
   int plane_bytes;    // > 0: pre-split BF16 planes of this capacity (BF16x3 pre-split contraction)
   int variant;        // contraction launch shape (kGram16 ... kGramStream)
   TensorMapCache* map_cache;   // streamed shape: maps of inputs seen before (nullptr: encode every call)
+  // Uniform problems: cluster c holds antennas [cl_off[c], cl_off[c+1]) (cl_uniform:
+  // every cluster B / Ceff antennas, and cl_off is not read).
+  int cl_uniform;
+  int cl_off[kMaxClusters + 1];
 };
 
 // Contraction launch shapes: 16 warps, one CTA per SM; 8 warps, two CTAs per SM
@@ -125,10 +130,12 @@ struct RefineParams {
   int B, U, Ceff, n_sc, n_sym, steps, unbiased, llr_bits;
   int res64;            // residual in FP64: 0 never, 1 above the condition threshold, 2 always
   float N0, rho, llr_scale;
+  int max_S;            // antennas of the largest cluster
+  int cl_off[kMaxClusters + 1];   // cluster c: antennas [cl_off[c], cl_off[c+1])
 };
 // Whether one local system fits the refinement kernel's shared memory.
-bool refine_fits(int B, int U, int Ceff, int n_sym);
-size_t refine_smem_bytes(int B, int U, int Ceff, int n_sym);
+bool refine_fits(int max_S, int U, int n_sym);
+size_t refine_smem_bytes(int max_S, int U, int n_sym);
 cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream);
 
 // Differentiable FD (per-cluster rho_c, free fusion weights nu) and its adjoint.

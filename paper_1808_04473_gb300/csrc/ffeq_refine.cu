@@ -76,7 +76,10 @@ __device__ __forceinline__ double2 dcfma_conj(float2 a, float2 b, double2 acc) {
 // estimates and inverse (diagonal included) go back to the workspace.
 __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const RefineParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, B = p.B, S = B / Ceff;
+  const size_t sys = blockIdx.x;
+  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, B = p.B;
+  const int k = static_cast<int>(sys / Ceff), c = static_cast<int>(sys % Ceff);
+  const int S = p.cl_off[c + 1] - p.cl_off[c];   // antennas of this cluster
   const RefineLayout L(U, NS, S);
   const int SS = L.SS, W = L.W;
   float2* Hs = reinterpret_cast<float2*>(smem + L.hs);
@@ -86,12 +89,10 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
   float2* Rr = reinterpret_cast<float2*>(smem + L.rr);
   float2* An = reinterpret_cast<float2*>(smem + L.an);
   float2* Ae = reinterpret_cast<float2*>(smem + L.ae);
-  const size_t sys = blockIdx.x;
-  const int k = static_cast<int>(sys / Ceff), c = static_cast<int>(sys % Ceff);
   const int tid = threadIdx.x, nt = blockDim.x;
   const float rho = p.rho;
-  const float2* Hk = p.H + static_cast<size_t>(k) * U * B + static_cast<size_t>(c) * S;
-  const float2* yk = p.y + static_cast<size_t>(k) * NS * B + static_cast<size_t>(c) * S;
+  const float2* Hk = p.H + static_cast<size_t>(k) * U * B + p.cl_off[c];
+  const float2* yk = p.y + static_cast<size_t>(k) * NS * B + p.cl_off[c];
 
   for (int e = tid; e < U * S; e += nt) {
     const int u = e / S, b = e - u * S;
@@ -300,11 +301,9 @@ cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaS
 
 }  // namespace
 
-bool refine_fits(int B, int U, int Ceff, int n_sym) {
-  return RefineLayout(U, n_sym, B / Ceff).total <= 227 * 1024;
-}
+bool refine_fits(int max_S, int U, int n_sym) { return RefineLayout(U, n_sym, max_S).total <= 227 * 1024; }
 
-size_t refine_smem_bytes(int B, int U, int Ceff, int n_sym) { return RefineLayout(U, n_sym, B / Ceff).total; }
+size_t refine_smem_bytes(int max_S, int U, int n_sym) { return RefineLayout(U, n_sym, max_S).total; }
 
 cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream) {
   static int configured[64] = {0};
@@ -319,7 +318,7 @@ cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream) {
     configured[dev] = 1;
   }
   const size_t nsys = static_cast<size_t>(p.n_sc) * p.Ceff;
-  const int S = p.B / p.Ceff;
+  const int S = p.max_S;   // shared memory and threads for the largest cluster
   const int threads = 2 * S < 128 ? 128 : (2 * S > kRefineThreadsMax ? kRefineThreadsMax : ((2 * S + 31) / 32) * 32);
   err = launch_pdl(reinterpret_cast<const void*>(refine_system_kernel), dim3(static_cast<unsigned>(nsys)),
                    dim3(threads), RefineLayout(p.U, p.n_sym, S).total, stream, p);

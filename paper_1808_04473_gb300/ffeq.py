@@ -64,6 +64,7 @@ _SIGS = {
     "ffeq_status_string": ([_i], ctypes.c_char_p),
     "ffeq_last_cuda_error": ([], ctypes.c_char_p),
     "ffeq_plan_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_problem)], _i),
+    "ffeq_plan_create_clusters": ([ctypes.POINTER(_vp), ctypes.POINTER(ffeq_problem), ctypes.POINTER(_i)], _i),
     "ffeq_plan_destroy": ([_vp], None),
     "ffeq_workspace_size": ([_vp, ctypes.POINTER(_sz)], _i),
     "ffeq_equalize": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
@@ -163,10 +164,18 @@ def ffeq_version() -> int:
 
 
 def ffeq_plan_create(B: int, U: int, C: int, n_sc: int, n_sym: int, arch: int = PD, precision: int = FP32,
-                     estimate: int = UNBIASED, llr_bits: int = 0, refine: int = 0, refine_fp64: int = 0) -> Plan:
+                     estimate: int = UNBIASED, llr_bits: int = 0, refine: int = 0, refine_fp64: int = 0,
+                     cluster_sizes=None) -> Plan:
+    """Create a plan; ``cluster_sizes`` (C antenna counts summing to B) for clusters of unequal size."""
     p = ffeq_problem(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64)
     h = _vp()
-    _check("ffeq_plan_create", lib().ffeq_plan_create(ctypes.byref(h), ctypes.byref(p)))
+    if cluster_sizes is None:
+        _check("ffeq_plan_create", lib().ffeq_plan_create(ctypes.byref(h), ctypes.byref(p)))
+    else:
+        if len(cluster_sizes) != C:
+            raise ValueError("cluster_sizes must have C entries")
+        sizes = (_i * len(cluster_sizes))(*[int(v) for v in cluster_sizes])
+        _check("ffeq_plan_create_clusters", lib().ffeq_plan_create_clusters(ctypes.byref(h), ctypes.byref(p), sizes))
     return Plan(h.value, p)
 
 
@@ -380,7 +389,7 @@ def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNB
 
 def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int = UNBIASED, llr_bits: int = 0,
              with_info: bool = False, stream=None, precision: int = FP32, refine: int = 0,
-             refine_fp64: int = 0) -> dict:
+             refine_fp64: int = 0, cluster_sizes=None) -> dict:
     """Allocate outputs on ``H.device`` and run one equalization (returns torch tensors)."""
     import torch
     if H.dtype != torch.complex64 or y.dtype != torch.complex64:
@@ -391,7 +400,8 @@ def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int =
     n_sym = y.shape[1]
     if tuple(y.shape) != (n_sc, n_sym, B):
         raise ValueError("y must be [n_sc][n_sym][B]")
-    plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64)
+    plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64,
+                            cluster_sizes)
     dev = H.device
     out = {"z": torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
            "sigma2": torch.empty((n_sc, U), dtype=torch.float32, device=dev)}

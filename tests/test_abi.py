@@ -183,3 +183,35 @@ def test_refinement_needs_the_inputs(built):
             ffeq.ffeq_plan_create(64, 8, 4, 10, 2, **bad)
         assert e.value.status == 1, bad
     ffeq.ffeq_plan_create(64, 8, 4, 10, 2, arch=ffeq.FD, refine=2, refine_fp64=1)
+
+
+def test_cluster_sizes_validation(built):
+    ff = ffeq
+    # C sizes >= 0 summing to B; B % C need not be 0 then.
+    ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.FD, cluster_sizes=[40, 35, 25])
+    ff.ffeq_plan_create(128, 8, 3, 10, 2, arch=ff.FD, cluster_sizes=[64, 0, 64])
+    ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.PD, cluster_sizes=[40, 35, 25])
+    for sizes in ([40, 35, 24], [40, 35, 26], [50, -5, 55]):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.FD, cluster_sizes=sizes)
+        assert e.value.status == 1, sizes
+    with pytest.raises(ff.FfeqError) as e:                     # B % C != 0 needs sizes
+        ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.FD)
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.FD, cluster_sizes=[50, 50])
+    # Unequal FD clusters: the streamed and pre-split shapes do not apply.
+    fd = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.BF16X3,
+                             cluster_sizes=[16, 48, 32, 32, 32, 32, 32, 32])
+    for v in (3, 5):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_set_tuning(fd, (v, 0))
+        assert e.value.status == 2, v
+    ff.ffeq_plan_set_tuning(fd, (1, 0))
+    # Equal sizes given explicitly are the uniform plan (the streamed shape applies).
+    eq = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.BF16X3, cluster_sizes=[32] * 8)
+    ff.ffeq_plan_set_tuning(eq, (5, 0))
+    # The training kernels need equal clusters (checked before any device call).
+    L = ff.lib()
+    st = L.ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 1 << 30, None)
+    assert st == 2

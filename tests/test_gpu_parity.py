@@ -251,3 +251,74 @@ def test_full_size_correlated_workload_sampled(ff):
             g = _gpu(ff, p, arch, 0, llr_bits=6, precision=precision)
             _check(g, _oracle(p, arch, 0, idx=idx), p, 6, tol=PREC_TOL[precision], idx=idx)
             assert np.isfinite(g["z"]).all()
+
+
+UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16, 3: 2.0 ** -21}
+
+
+def _kappa_clusters(p, sizes):
+    """Largest cond_2(G_c + rho I) over the clusters of each subcarrier (FD)."""
+    rho = float(np.float32(p.N0)) / p.Es
+    out = np.ones(p.n_sc)
+    for k in range(p.n_sc):
+        Hm = p.H[k].astype(np.complex128).T
+        for b0, b1 in lmmse.partition(p.B, p.C, sizes):
+            Hc = Hm[b0:b1]
+            out[k] = max(out[k], np.linalg.cond(Hc.conj().T @ Hc + rho * np.eye(p.U)))
+    return out
+
+
+CLUSTER_CASES = [  # B, U, C, n_sc, n_sym, sizes
+    (100, 8, 3, 24, 3, [40, 35, 25]),                          # B % C != 0
+    (256, 16, 8, 40, 14, [16, 48, 32, 24, 40, 32, 40, 24]),     # the throughput shape, unequal
+    (128, 8, 3, 12, 2, [64, 0, 64]),                            # an empty cluster: its users get weight 0
+    (96, 12, 5, 10, 5, [7, 33, 20, 30, 6]),                     # odd sizes and offsets, S < U
+]
+
+
+@pytest.mark.parametrize("case", CLUSTER_CASES)
+@pytest.mark.parametrize("precision", [0, 1, 2, 3], ids=["fp32", "tf32x3", "bf16x3", "fp16x3"])
+def test_unequal_clusters_match_the_oracle(ff, case, precision):
+    """Clusters of given sizes B_c (Sec. II-B) through ffeq_plan_create_clusters:
+    FD against the oracle's partition with the same sizes (bound max(tolerance,
+    2 u kappa) per subcarrier, kappa the largest local condition number), and PD,
+    which sums every cluster, equal to the uniform-plan result."""
+    B, U, C, n_sc, n_sym, sizes = case
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=15.0, bits=4, seed=B + U + C)
+    dev = torch.device("cuda:0")
+    H, y = torch.from_numpy(p.H).to(dev), torch.from_numpy(p.y).to(dev)
+    g = ff.equalize(H, y, p.N0, p.Es, C, arch=1, llr_bits=4, with_info=True, precision=precision,
+                    cluster_sizes=sizes)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    o = lmmse.equalize_fd(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased", cluster_sizes=sizes)
+    assert np.array_equal(g["info"], o["info"])
+    tol = np.maximum(PREC_TOL[precision], 2.0 * UNIT[precision] * _kappa_clusters(p, sizes))
+    ez, es = _rel_per_sc(g["z"], o["z"]), _rel_per_sc(g["sigma2"], o["sigma2"])
+    assert (ez <= tol).all(), (ez.max(), tol[np.argmax(ez - tol)])
+    assert (es <= tol).all(), (es.max(), tol[np.argmax(es - tol)])
+    Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es)
+    assert (_rel_per_sc(g["llr"], Lo) <= 4 * tol).all()
+    if B % C == 0:
+        pd_sizes = ff.equalize(H, y, p.N0, p.Es, C, arch=0, precision=precision, cluster_sizes=sizes)
+        pd_equal = ff.equalize(H, y, p.N0, p.Es, C, arch=0, precision=precision)
+        torch.cuda.synchronize()
+        assert torch.equal(pd_sizes["z"], pd_equal["z"]) and torch.equal(pd_sizes["sigma2"], pd_equal["sigma2"])
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+def test_unequal_clusters_with_refinement(ff, steps):
+    """Refinement re-reads each cluster's own antennas (offsets, not B / C)."""
+    B, U, C, n_sc, n_sym, sizes = 96, 12, 5, 10, 5, [7, 33, 20, 30, 6]
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=20.0, bits=4, seed=7, corr_r=0.5)
+    dev = torch.device("cuda:0")
+    g = ff.equalize(torch.from_numpy(p.H).to(dev), torch.from_numpy(p.y).to(dev), p.N0, p.Es, C, arch=1,
+                    with_info=True, precision=2, refine=steps, cluster_sizes=sizes)
+    torch.cuda.synchronize()
+    o = lmmse.equalize_fd(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased", cluster_sizes=sizes)
+    kap = _kappa_clusters(p, sizes)
+    tol = np.maximum(1e-5, 2.0 * 2.0 ** -22 * kap)
+    if steps == 1:
+        tol = np.maximum(tol, 4.0 * (2.0 ** -16 * kap) ** 2)
+    ez = _rel_per_sc(g["z"].cpu().numpy(), o["z"])
+    assert (ez <= tol).all(), (ez.max(), kap.max())
