@@ -11,10 +11,12 @@
 // [n_sc][Ceff][U + n_sym][U] complex, Ceff = C (FD) or 1 (PD).
 //
 // One CTA per SM walks subcarriers b, b + gridDim.x, ...; the U + n_sym rows of
-// B complex of each are staged into shared memory (dense for the tensor-core
-// contractions, row stride B + 2 for the CUDA-core one)
-// with one cp.async.bulk per row on a per-stage mbarrier, up to three
-// subcarriers ahead of the contraction.
+// B complex of each are staged into shared memory on a per-stage mbarrier, up
+// to three subcarriers ahead of the contraction: densely with two cp.async.bulk
+// copies (the H block, the y block) for the tensor-core contractions, with row
+// stride B + 2 and one copy per row for the CUDA-core one.  Clusters are B / C
+// antennas each, or of the sizes given to the plan (offsets cl_off).  The
+// default tensor-core shape is the streamed kernel of ffeq_gram_stream.cu.
 #pragma once
 
 #include "ffeq_device.cuh"
