@@ -8,6 +8,8 @@ Modules
 -------
 ``lmmse``   PD and FD L-MMSE equalization, error variances and optimal fusion
             (Sec. II-B..D, Sec. III-A, Sec. IV-A, Lemma 1, Thm. 3).
+``linear``  PD and FD with the MRC and ZF equalizers of Sec. III-A in place of
+            L-MMSE (FD fuses them with the same optimal weights).
 ``llr``     max-log soft outputs for square QAM (the paper names LLRs but gives
             no formula; the reading is stated in that module).
 ``adjoint`` the differentiable FD form (per-cluster regularizers, free fusion
@@ -20,4 +22,4 @@ given (they are upcast once), loops over subcarriers in plain Python and uses
 library primitives (``numpy.linalg.inv``, matrix products) only as steps of the
 paper's definitions, so it can be checked against the paper by eye.
 """
-from . import adjoint, llr, lmmse, theory  # noqa: F401
+from . import adjoint, linear, llr, lmmse, theory  # noqa: F401
