@@ -418,13 +418,14 @@ def main():
             for a in (ffeq.PD, ffeq.FD)}
     stream = torch.cuda.current_stream(dev)
 
-    def make_plans(precision):
-        pl = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=PREC[precision], llr_bits=bits)
+    def make_plans(precision, equalizer=0):
+        pl = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=PREC[precision], llr_bits=bits,
+                                       equalizer=equalizer)
               for a in (ffeq.PD, ffeq.FD)}
         nb = {a: ffeq.ffeq_workspace_size(x) for a, x in pl.items()}
         return pl, nb, {a: torch.empty(nb[a], dtype=torch.uint8, device=dev) for a in pl}
 
-    def timed(precision, K, warmup, sampler=None):
+    def timed(precision, K, warmup, sampler=None, equalizer=0):
         """K steps; one step = for PD then FD, the local preprocessing kernel and the
         fusion / equalization kernel (the latter launched with programmatic dependent
         launch).  Each step is captured once per rotating input set as a CUDA graph
@@ -432,11 +433,11 @@ def main():
         replay stream bracket the K replays only.  A separate pass replays graphs of
         one kernel each (that kernel alone, on the rotating input sets) for the
         per-kernel device times of the breakdown."""
-        plans, ws_bytes, ws = make_plans(precision)
+        plans, ws_bytes, ws = make_plans(precision, equalizer)
         pinned = [int(v) for v in args.tuning.split(",")] if args.tuning else None
         for a in plans:                  # launch shape chosen by timing (outside the timed region)
             o = outs[a]
-            if pinned and precision == args.precision:
+            if pinned and precision == args.precision and equalizer == 0:
                 ffeq.ffeq_plan_set_tuning(plans[a], pinned[2 * a:2 * a + 2])
             else:
                 # Over the rotating input sets: every timed call reads cold inputs, as the steps do.
@@ -546,6 +547,15 @@ def main():
             es = np.linalg.norm(sg - o["sigma2"].reshape(len(idx), -1), axis=1) / np.linalg.norm(o["sigma2"].reshape(len(idx), -1), axis=1)
             accuracy["pd" if a == ffeq.PD else "fd"] = {"z": float(ez.max()), "sigma2": float(es.max())}
 
+    # ---- the same step with the ZF and MRC equalizers of Sec. III-A (same contraction)
+    variants = {}
+    if not args.tuning:
+        Kv = max(5, K // 4)
+        for name, eq in (("zf", ffeq.ZF), ("mrc", ffeq.MRC)):
+            msv, kernv, _ = timed(args.precision, Kv, args.warmup, equalizer=eq)
+            variants[name] = {"value": world * symbols_per_step * Kv / (msv * 1e-3), "ms_per_step": msv / Kv,
+                              "steps": Kv, "kernels_ms": kernv}
+
     # ---- end to end through the host-buffer entry point (pinned host memory)
     Hh = torch.from_numpy(p.H).pin_memory()
     yh = torch.from_numpy(p.y).pin_memory()
@@ -612,6 +622,7 @@ def main():
         "roofline": roof,
         "roofline_gram_stage": {"pd": gram_roof("pd_local"), "fd": gram_roof("fd_local")},
         "fp32_same_gpu": fp32_cmp,
+        "equalizers": variants or None,
         "accuracy": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * K,

@@ -15,6 +15,8 @@
  *       z_u = sum_c nu_{c,u} z_{c,u},  nu = sigma_c^-2 / sum sigma^-2 (Eq. fusionrule,
  *       Lemma 1 Eq. opt_fusion), sigma^2 = (sum_c sigma_c^-2)^-1     (Thm. 3)
  *   error variances sigma^2 and max-log LLRs of the decoupled channel (Eq. 4).
+ * In place of L-MMSE, the same two architectures run the zero-forcing (ZF) or
+ * maximum-ratio (MRC) equalizer of Sec. III-A (ffeq_problem.equalizer).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -89,6 +91,20 @@ typedef enum { FFEQ_PD = 0, FFEQ_FD = 1 } ffeq_arch;
  *                should be of order one, as with unit-variance channels). */
 typedef enum { FFEQ_FP32 = 0, FFEQ_TF32X3 = 1, FFEQ_BF16X3 = 2, FFEQ_FP16X3 = 3 } ffeq_precision;
 typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
+/* Equalizer of the central (PD) or local (FD) solve, Sec. III-A:
+ *   FFEQ_LMMSE  z = (G + rho I)^{-1} y^MRC, rho = N0/Es (the estimate field
+ *               selects the literal or unbiased pairs);
+ *   FFEQ_ZF     z = G^{-1} y^MRC, sigma^2 = N0 diag(G^{-1}) (L-MMSE with rho = 0;
+ *               info reports the first non-positive pivot of G or G_c);
+ *   FFEQ_MRC    z = diag(G)^{-1} y^MRC, sigma^2_u = (N0 G_uu + Es sum_{v != u}
+ *               |G_uv|^2) / G_uu^2 (no inversion; info is always 0).
+ * ZF and MRC estimates are unbiased, so the estimate field does not apply; FD
+ * fuses the per-cluster pairs with the optimal weights of Lemma 1 as for
+ * L-MMSE.  A user that a cluster cannot see (G_c,uu = 0) gets MRC weight 0.
+ * With N0 == 0, ZF weights take the N0 -> 0 limit (proportional to
+ * 1/[G_c^{-1}]_uu) and so do MRC weights for U == 1 (proportional to G_c,uu);
+ * for U > 1 the MRC variance is the interference term alone. */
+typedef enum { FFEQ_LMMSE = 0, FFEQ_ZF = 1, FFEQ_MRC = 2 } ffeq_equalizer;
 
 /* Problem statement (Sec. II-A, II-B, VI): B antennas, U users, C clusters,
  * n_sc subcarriers, n_sym OFDM symbols sharing one channel per subcarrier. */
@@ -118,6 +134,8 @@ typedef struct {
                     *    others: the ill-conditioned ones converge to about
                     *    2^-24 (the FP32 storage of x_c) instead;
                     * 2  FP64 for every local system. */
+  int equalizer;   /* ffeq_equalizer: 0 = L-MMSE.  Refinement applies to
+                    * L-MMSE and ZF; MRC with refine > 0 is FFEQ_ERR_INVALID_ARG. */
 } ffeq_problem;
 
 typedef struct ffeq_plan ffeq_plan;
@@ -199,7 +217,8 @@ ffeq_status ffeq_fuse_equalize(const ffeq_plan* plan, const void* workspace, siz
  *   G_b = (G_c + rho_c I)^{-1} diag(nu_c) gz.
  * The same H, y, rho_c, nu and workspace must be passed to both calls, in order
  * on one stream.  Outputs of a subcarrier whose system is not positive definite
- * are NaN.  Limits: C * U padded <= 512. */
+ * are NaN.  Limits: C * U padded <= 512; the plan's equalizer must be
+ * FFEQ_LMMSE (FFEQ_ERR_UNSUPPORTED otherwise). */
 ffeq_status ffeq_fd_train_workspace_size(const ffeq_plan* plan, size_t* bytes);
 ffeq_status ffeq_fd_train_forward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
                                   const float* nu, void* z, void* workspace, size_t workspace_bytes,

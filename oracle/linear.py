@@ -20,7 +20,10 @@ cluster cannot see (``G_uu = 0``) gets weight 0 (infinite variance); for
 ``N0 = 0`` every ZF variance is 0 and the fusion weights are taken in the limit
 ``N0 -> 0`` (proportional to ``1 / [G_c^{-1}]_uu``); MRC variances with
 ``N0 = 0`` are zero only without interference (``U = 1``), then the weights are
-proportional to ``G_uu``.  ZF needs ``G`` (FD: every ``G_c``) positive definite;
+proportional to ``G_uu``.  Outside that limit a variance of exactly 0 (``N0 = 0``
+and a user with no interference in that cluster, a set of channels of measure
+zero) leaves the weight ``1 / sigma^2`` undefined: such a pair gets weight 0,
+in PD (one pair through the same rule) as in FD.  ZF needs ``G`` (FD: every ``G_c``) positive definite;
 ``info`` is the first non-positive leading minor as for L-MMSE (parity pinned
 for clusters of at least ``U`` antennas).
 """
@@ -42,6 +45,7 @@ def mrc_unit(G: np.ndarray, yMR: np.ndarray, N0: float, Es: float):
     Dinv = np.diag(np.where(seen, 1.0 / np.where(seen, g, 1.0), 0.0))
     z = Dinv @ yMR
     E = Dinv @ G - np.eye(U)
+    np.fill_diagonal(E, 0.0)     # [diag(G)^{-1} G]_uu = 1 exactly; (1/g) g - 1 would leave rounding
     sigma2 = np.real(np.diag(Dinv @ G @ Dinv.conj().T * N0 + E @ E.conj().T * Es))
     sigma2 = np.where(seen, sigma2, np.inf)
     weight_var = np.where(seen, 1.0 / np.where(seen, g, 1.0), np.inf)
@@ -86,7 +90,12 @@ def equalize_pd_linear(H, y, N0: float, Es: float, C: int, equalizer: str, clust
         Hm, Ym = _as_math(H, y, k)
         G, yMR = _pd_gram(Hm, Ym, bounds)
         if equalizer == "mrc":
-            zk, s2k, _ = mrc_unit(G, yMR, N0, Es)
+            # One estimate passed through the fusion rule, so that PD and FD at
+            # C = 1 agree in the degenerate cases too (a variance of exactly 0
+            # outside the N0 -> 0 limit carries no weight).
+            zk, s2k, wv = mrc_unit(G, yMR, N0, Es)
+            limit = N0 == 0.0 and U == 1
+            zk, s2k, _ = optimal_fusion(zk[None], s2k[None], weight_var=wv[None] if limit else None)
         else:
             zk, s2k, _, inf = zf_unit(G, yMR, N0, Es)
             info[k, 0] = inf

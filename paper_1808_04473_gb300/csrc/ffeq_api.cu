@@ -119,6 +119,9 @@ ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, co
   if (p->refine < 0 || p->refine > 2) return FFEQ_ERR_INVALID_ARG;
   if (p->refine_fp64 < 0 || p->refine_fp64 > 2 || (p->refine_fp64 > 0 && p->refine == 0))
     return FFEQ_ERR_INVALID_ARG;
+  if (p->equalizer != FFEQ_LMMSE && p->equalizer != FFEQ_ZF && p->equalizer != FFEQ_MRC)
+    return FFEQ_ERR_INVALID_ARG;
+  if (p->equalizer == FFEQ_MRC && p->refine > 0) return FFEQ_ERR_INVALID_ARG;   // nothing is solved
   if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
   if (ffeq::gram_stages(p->precision, p->B, p->U, p->n_sym, Ceff, false) < 1) return FFEQ_ERR_UNSUPPORTED;
@@ -213,10 +216,15 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   sp.n_sc = p.n_sc;
   sp.n_sym = p.n_sym;
   sp.spc = ffeq::solve_subcarriers_per_cta(p.U, plan->Ceff);
-  sp.unbiased = p.estimate == FFEQ_UNBIASED;
+  // Zero forcing is the L-MMSE sweep with rho = 0 and the literal pairs (whose
+  // gain is 1 there); MRC has its own kernel.
+  const bool zf = p.equalizer == FFEQ_ZF;
+  sp.unbiased = !zf && p.estimate == FFEQ_UNBIASED;
   sp.llr_bits = p.llr_bits;
   sp.N0 = N0;
-  sp.rho = static_cast<float>(static_cast<double>(N0) / static_cast<double>(Es));
+  sp.Es = Es;
+  sp.equalizer = p.equalizer;
+  sp.rho = zf ? 0.f : static_cast<float>(static_cast<double>(N0) / static_cast<double>(Es));
   if (p.llr_bits) {
     const double L = static_cast<double>(1 << (p.llr_bits / 2));
     sp.llr_scale = static_cast<float>(std::sqrt(static_cast<double>(Es) / (2.0 * (L * L - 1.0) / 3.0)));
@@ -360,6 +368,7 @@ ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, co
   const ffeq_problem& p = plan->p;
   if (p.arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
   if (!plan->cl_uniform) return FFEQ_ERR_UNSUPPORTED;   // the training kernels take clusters of B / C antennas
+  if (p.equalizer != FFEQ_LMMSE) return FFEQ_ERR_UNSUPPORTED;   // the differentiable form is L-MMSE
   if (ffeq::padded_users(p.U) * p.C > 512 || ffeq::train_smem_bytes(p.U, p.C) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
   const TrainLayoutBytes t = train_layout(plan);

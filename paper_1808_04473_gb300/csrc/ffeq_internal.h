@@ -98,8 +98,10 @@ struct SolveParams {
   int spc;            // subcarriers per CTA
   int unbiased;       // 1: FFEQ_UNBIASED
   int llr_bits;
-  float N0, rho;      // rho = N0 / Es
+  float N0, rho;      // rho = N0 / Es (0 for zero forcing)
   float llr_scale;    // sqrt(Es / e_avg): amplitude of level +1
+  int equalizer;      // ffeq_equalizer; FFEQ_MRC runs mrc_fuse_kernel (uniform problems)
+  float Es;
   // Uneven batch (desc != nullptr): one CTA per tile; per-unit sizes, offsets,
   // N0, rho and llr_scale from the descriptors.
   const BatchDesc* desc;

@@ -23,6 +23,9 @@
 // nu_c = sigma_c^-2 / sum sigma^-2 with sigma_c^2 = N0 A/g, written so that N0
 // cancels from the weights (N0 = 0, zero forcing, needs no special case).  PD
 // is the case C = 1.  The epilogue writes z, sigma^2 and max-log LLRs.
+// The ZF equalizer of Sec. III-A is this sweep with rho = 0 and g = 1; MRC
+// needs no inversion and has its own kernel (mrc_fuse_kernel) with the same
+// fusion areas and epilogue.
 #include <cmath>
 
 #include "ffeq_device.cuh"
@@ -139,6 +142,49 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
     p.z[d.z_off + r] = zz;
     if (n == 0) p.sigma2[d.s2_off + u] = s2;
     if (bits) symbol_llr(zz, s2, d.llr_scale, hb, p.llr + d.llr_off + static_cast<long long>(r) * bits);
+  }
+}
+
+// Outputs of a uniform problem, per subcarrier of this CTA: every (symbol, user)
+// sums the Ceff fusion numerators and denominators of its subcarrier and writes
+// z = num / den, sigma^2 = s2_scale / den (s2_scale = N0 for the solve, whose
+// denominators are g / A_uu; Es for MRC, whose are Es / sigma_c^2) and the LLRs.
+template <int UP>
+__device__ __forceinline__ void uniform_epilogue(const SolveParams& p, const float2* base, const int* fail_sc,
+                                                 int sc0, int U, int NS, int Ceff, float s2_scale) {
+  using Lay = SolveLayout<UP>;
+  const int spc = p.spc;
+  const int per = U * NS;   // uniform problem: every group has the problem's sizes
+  const int bits = p.llr_bits, hb = bits / 2;
+  for (int e = threadIdx.x; e < spc * per; e += blockDim.x) {
+    const int s = e / per, r = e - s * per;
+    const int n = r / U, u = r - n * U;
+    const int k = sc0 + s;
+    if (k >= p.n_sc) break;
+    float2 nm = make_float2(0.f, 0.f);
+    float dn = 0.f;
+    for (int cc = 0; cc < Ceff; ++cc) {
+      const float2* Lm = base + (s * Ceff + cc) * Lay::kMat + Lay::kRow;
+      nm = cadd(nm, Lm[n * UP + u]);
+      dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
+    }
+    float2 zz;
+    float s2;
+    if (fail_sc[s]) {
+      zz = make_float2(NAN, NAN);
+      s2 = NAN;
+    } else if (dn > 0.f) {
+      const float rr = 1.f / dn;
+      zz = cscale(nm, rr);
+      s2 = s2_scale * rr;
+    } else {
+      zz = make_float2(0.f, 0.f);
+      s2 = INFINITY;
+    }
+    const size_t zi = (static_cast<size_t>(k) * NS + n) * U + u;
+    p.z[zi] = zz;
+    if (n == 0) p.sigma2[static_cast<size_t>(k) * U + u] = s2;
+    if (bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * bits);
   }
 }
 
@@ -468,39 +514,7 @@ __global__ void __launch_bounds__(512, (solve_min_blocks<UP, LPR, BATCH>())) sol
     return;
   }
 
-  // ---- per subcarrier: sum over clusters, outputs
-  const int per = U * NS;   // uniform problem: every group has the problem's sizes
-  const int bits = p.llr_bits, hb = bits / 2;
-  for (int e = threadIdx.x; e < spc * per; e += blockDim.x) {
-    const int s = e / per, r = e - s * per;
-    const int n = r / U, u = r - n * U;
-    const int k = sc0 + s;
-    if (k >= p.n_sc) break;
-    float2 nm = make_float2(0.f, 0.f);
-    float dn = 0.f;
-    for (int cc = 0; cc < Ceff; ++cc) {
-      const float2* Lm = base + (s * Ceff + cc) * Lay::kMat + Lay::kRow;
-      nm = cadd(nm, Lm[n * UP + u]);
-      dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
-    }
-    float2 zz;
-    float s2;
-    if (fail_sc[s]) {
-      zz = make_float2(NAN, NAN);
-      s2 = NAN;
-    } else if (dn > 0.f) {
-      const float rr = 1.f / dn;
-      zz = cscale(nm, rr);
-      s2 = p.N0 * rr;
-    } else {
-      zz = make_float2(0.f, 0.f);
-      s2 = INFINITY;
-    }
-    const size_t zi = (static_cast<size_t>(k) * NS + n) * U + u;
-    p.z[zi] = zz;
-    if (n == 0) p.sigma2[static_cast<size_t>(k) * U + u] = s2;
-    if (bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * bits);
-  }
+  uniform_epilogue<UP>(p, base, fail_sc, sc0, U, NS, Ceff, p.N0);
 }
 
 template <int UP, int LPR, bool BATCH>
@@ -532,6 +546,93 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP, LPR, BATCH>, p);
 }
 
+// Maximum-ratio combining (Sec. III-A) per (subcarrier, cluster), uniform
+// problems: lane i of a group of UP lanes reads row i of G_c and forms
+//   sigma_c^2 / Es = (rho G_ii + sum_{j != i} |G_ij|^2) / G_ii^2,
+// then leaves the fusion denominator w = Es / sigma_c^2 and the numerators
+// w y^MRC_i(n) / G_ii in the areas the epilogue sums, so that z = sum_c (w z_c) /
+// sum_c w (Eq. fusionrule, opt_fusion) and sigma^2 = Es / sum_c w (Thm. 3).  A
+// user the cluster cannot see (G_ii = 0) gets w = 0.  With N0 = 0 and U = 1
+// every variance is 0; the weights are then those of the limit N0 -> 0,
+// proportional to G_ii, and sigma^2 is 0.  No system is solved: info is 0.
+template <int UP>
+__global__ void __launch_bounds__(512) mrc_fuse_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = SolveLayout<UP>;
+  int* fail_sc = reinterpret_cast<int*>(smem);
+  float2* base = reinterpret_cast<float2*>(smem + 256);
+  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff;
+  const int nmat = p.spc * Ceff;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int sc0 = blockIdx.x * p.spc;
+  const bool limit = p.N0 == 0.f && U == 1;
+  if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
+
+  // Wait for the contraction grid (programmatic dependent launch).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  if (g < nmat) {
+    const int c = g % Ceff, sc = sc0 + g / Ceff;
+    float2* Fz = base + g * Lay::kMat + Lay::kRow;
+    float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
+    float w = 0.f;
+    if (sc < p.n_sc && i < U) {
+      const float2* Dg = p.D + (static_cast<size_t>(sc) * Ceff + c) * static_cast<size_t>(U + NS) * U;
+      float gii = 0.f, intf = 0.f;
+#pragma unroll
+      for (int j = 0; j < UP; ++j) {
+        if (j < U) {
+          const float2 v = Dg[j * U + i];   // G_ij (conjugate symmetric)
+          if (j == i) {
+            gii = v.x;
+          } else {
+            intf = fmaf(v.x, v.x, fmaf(v.y, v.y, intf));
+          }
+        }
+      }
+      const float den = fmaf(p.rho, gii, intf);
+      float zs = 0.f;
+      if (gii > 0.f) {
+        w = limit ? gii : (den > 0.f ? gii * gii / den : 0.f);
+        zs = w / gii;
+      }
+      for (int n = 0; n < NS; ++n) Fz[n * UP + i] = cscale(Dg[(U + n) * U + i], zs);
+      if (i == 0 && p.info) p.info[static_cast<size_t>(sc) * Ceff + c] = 0;
+    }
+    Dn[i] = w;
+  }
+  __syncthreads();
+  uniform_epilogue<UP>(p, base, fail_sc, sc0, U, NS, Ceff, limit ? 0.f : p.Es);
+}
+
+template <int UP>
+cudaError_t launch_mrc_up(const SolveParams& p, cudaStream_t stream) {
+  using Lay = SolveLayout<UP>;
+  const int nmat = p.spc * p.Ceff;
+  const int threads = ((nmat * UP + 31) / 32) * 32;
+  const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 64 && !configured[dev]) {
+    err = cudaFuncSetAttribute(mrc_fuse_kernel<UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    configured[dev] = 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((p.n_sc + p.spc - 1) / p.spc);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mrc_fuse_kernel<UP>, p);
+}
+
 }  // namespace
 
 // PD (one system per subcarrier) with U <= 16: a full warp per system (two
@@ -557,6 +658,13 @@ size_t solve_smem_bytes(int U, int Ceff) {
 }
 
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream) {
+  if (p.equalizer == FFEQ_MRC) {
+    switch (padded_users(p.U)) {
+      case 8: return launch_mrc_up<8>(p, stream);
+      case 16: return launch_mrc_up<16>(p, stream);
+      default: return launch_mrc_up<32>(p, stream);
+    }
+  }
   switch (padded_users(p.U)) {
     case 8: return launch_up<8, 1, false>(p, stream);
     case 16: return lanes_per_row(p.U, p.Ceff) == 2 ? launch_up<16, 2, false>(p, stream)

@@ -87,7 +87,7 @@ def test_staging_size_accounts_for_every_buffer(built):
 
 
 def test_plan_struct_layout_matches_header(built):
-    assert ctypes.sizeof(ffeq.ffeq_problem) == 11 * 4
+    assert ctypes.sizeof(ffeq.ffeq_problem) == 12 * 4
     text = open(ffeq.HEADER_PATH).read()
     body = text[text.index("typedef struct {") + len("typedef struct {"):text.index("} ffeq_problem;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
@@ -215,3 +215,23 @@ def test_cluster_sizes_validation(built):
     L = ff.lib()
     st = L.ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 1 << 30, None)
     assert st == 2
+
+
+def test_equalizer_validation(built):
+    ff = ffeq
+    for eq in (ff.LMMSE, ff.ZF, ff.MRC):
+        for arch in (ff.PD, ff.FD):
+            ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=arch, precision=ff.BF16X3, equalizer=eq)
+    for bad in (-1, 3):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_create(64, 8, 4, 10, 2, equalizer=bad)
+        assert e.value.status == 1
+    # Refinement of a solve: L-MMSE and ZF; MRC solves nothing.
+    ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD, refine=1, equalizer=ff.ZF)
+    with pytest.raises(ff.FfeqError) as e:
+        ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD, refine=1, equalizer=ff.MRC)
+    assert e.value.status == 1
+    # The differentiable FD form is L-MMSE (checked before any device call).
+    for eq in (ff.ZF, ff.MRC):
+        fd = ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD, equalizer=eq)
+        assert ff.lib().ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 1 << 30, None) == 2

@@ -162,3 +162,16 @@ def test_lmmse_beats_zf_and_mrc_in_mean_squared_error():
     for eq in ("mrc", "zf"):
         o = linear.equalize_pd_linear(p.H, p.y, p.N0, p.Es, 1, eq)
         assert np.all(lm["sigma2"] <= o["sigma2"] * (1 + 1e-12))
+
+
+def test_mrc_zero_variance_outside_the_limit_is_the_same_in_pd_and_fd():
+    """N0 = 0, U = 2, users on disjoint antennas: no interference, so sigma^2 = 0 outside the
+    U = 1 limit; PD and FD at C = 1 give the same (weight 0: z = 0, sigma^2 = inf)."""
+    p = synth.make_problem(32, 2, 1, 3, 2, noiseless=True, seed=18)
+    H = p.H.copy()
+    H[:, 0, 16:] = 0.0
+    H[:, 1, :16] = 0.0
+    pd = linear.equalize_pd_linear(H, p.y, 0.0, p.Es, 1, "mrc")
+    fd = linear.equalize_fd_linear(H, p.y, 0.0, p.Es, 1, "mrc")
+    assert np.array_equal(pd["z"], fd["z"]) and np.array_equal(pd["sigma2"], fd["sigma2"])
+    assert (pd["z"] == 0).all() and np.isinf(pd["sigma2"]).all()
