@@ -10,6 +10,8 @@ Modules
             (Sec. II-B..D, Sec. III-A, Sec. IV-A, Lemma 1, Thm. 3).
 ``linear``  PD and FD with the MRC and ZF equalizers of Sec. III-A in place of
             L-MMSE (FD fuses them with the same optimal weights).
+``lama``    LAMA-PD (Algorithm 1 on the PD pair) and LAMA-FD (per cluster, then
+            the optimal fusion), with the posterior-mean denoiser of Eq. F.
 ``llr``     max-log soft outputs for square QAM (the paper names LLRs but gives
             no formula; the reading is stated in that module).
 ``adjoint`` the differentiable FD form (per-cluster regularizers, free fusion
@@ -22,4 +24,4 @@ given (they are upcast once), loops over subcarriers in plain Python and uses
 library primitives (``numpy.linalg.inv``, matrix products) only as steps of the
 paper's definitions, so it can be checked against the paper by eye.
 """
-from . import adjoint, linear, llr, lmmse, theory  # noqa: F401
+from . import adjoint, lama, linear, llr, lmmse, theory  # noqa: F401
