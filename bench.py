@@ -31,6 +31,7 @@ WORKLOAD = dict(B=256, U=16, C=8, n_sc=1200, n_sym=14, bits=4, snr_db=10.0)
 # 16*1200*14 symbols each; symbols/s of one PD + one FD pass of the batch.
 PAPER_SYMBOLS_PER_S = 2 * 16 * 1200 * 14 / (0.856e-3 + 0.751e-3)
 L2_BYTES = 129 * 1024 * 1024
+LAMA_ITERS = 8              # LAMA iterations of the equalizer-variant lines
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -419,8 +420,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def make_plans(precision, equalizer=0):
+        iters = LAMA_ITERS if equalizer == ffeq.LAMA else 0
         pl = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=PREC[precision], llr_bits=bits,
-                                       equalizer=equalizer)
+                                       equalizer=equalizer, lama_iters=iters)
               for a in (ffeq.PD, ffeq.FD)}
         nb = {a: ffeq.ffeq_workspace_size(x) for a, x in pl.items()}
         return pl, nb, {a: torch.empty(nb[a], dtype=torch.uint8, device=dev) for a in pl}
@@ -547,11 +549,12 @@ def main():
             es = np.linalg.norm(sg - o["sigma2"].reshape(len(idx), -1), axis=1) / np.linalg.norm(o["sigma2"].reshape(len(idx), -1), axis=1)
             accuracy["pd" if a == ffeq.PD else "fd"] = {"z": float(ez.max()), "sigma2": float(es.max())}
 
-    # ---- the same step with the ZF and MRC equalizers of Sec. III-A (same contraction)
+    # ---- the same step with the ZF and MRC equalizers of Sec. III-A and LAMA (Sec. III-B,
+    # LAMA_ITERS iterations) in place of L-MMSE (same contraction)
     variants = {}
     if not args.tuning:
         Kv = max(5, K // 4)
-        for name, eq in (("zf", ffeq.ZF), ("mrc", ffeq.MRC)):
+        for name, eq in (("zf", ffeq.ZF), ("mrc", ffeq.MRC), ("lama", ffeq.LAMA)):
             msv, kernv, _ = timed(args.precision, Kv, args.warmup, equalizer=eq)
             variants[name] = {"value": world * symbols_per_step * Kv / (msv * 1e-3), "ms_per_step": msv / Kv,
                               "steps": Kv, "kernels_ms": kernv}

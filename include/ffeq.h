@@ -16,7 +16,8 @@
  *       Lemma 1 Eq. opt_fusion), sigma^2 = (sum_c sigma_c^-2)^-1     (Thm. 3)
  *   error variances sigma^2 and max-log LLRs of the decoupled channel (Eq. 4).
  * In place of L-MMSE, the same two architectures run the zero-forcing (ZF) or
- * maximum-ratio (MRC) equalizer of Sec. III-A (ffeq_problem.equalizer).
+ * maximum-ratio (MRC) equalizer of Sec. III-A or the nonlinear LAMA of
+ * Sec. III-B (ffeq_problem.equalizer).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -103,8 +104,21 @@ typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
  * L-MMSE.  A user that a cluster cannot see (G_c,uu = 0) gets MRC weight 0.
  * With N0 == 0, ZF weights take the N0 -> 0 limit (proportional to
  * 1/[G_c^{-1}]_uu) and so do MRC weights for U == 1 (proportional to G_c,uu);
- * for U > 1 the MRC variance is the interference term alone. */
-typedef enum { FFEQ_LMMSE = 0, FFEQ_ZF = 1, FFEQ_MRC = 2 } ffeq_equalizer;
+ * for U > 1 the MRC variance is the interference term alone.
+ *   FFEQ_LAMA   Algorithm 1 (LAMA-PD) on (G, y^MRC), or per cluster on
+ *               (G_c, y_c^MRC) and fused with the weights of Lemma 1 (LAMA-FD),
+ *               for lama_iters iterations: z^T and sigma^2 = N0 + beta phi^T of
+ *               the last one.  The system is taken in the paper's normalization
+ *               (G / B, y^MRC / B, N0 / B, beta = U / B; a cluster of S_c
+ *               antennas: G_c / S_c, y_c^MRC / S_c, N0 / S_c, beta_c = U / S_c),
+ *               the prior is equiprobable square QAM of llr_bits bits per symbol
+ *               (the LLR constellation; llr_bits > 0 is required) and the
+ *               denoiser is its posterior mean and variance (Eq. F).  phi^T
+ *               depends on the received vector: sigma2 is f32 [n_sc][n_sym][U]
+ *               (the same value for every user of a vector), not [n_sc][U].
+ *               N0 > 0 (FFEQ_ERR_INVALID_ARG otherwise); info, if given, is 0.
+ *               An empty cluster gets weight 0. */
+typedef enum { FFEQ_LMMSE = 0, FFEQ_ZF = 1, FFEQ_MRC = 2, FFEQ_LAMA = 3 } ffeq_equalizer;
 
 /* Problem statement (Sec. II-A, II-B, VI): B antennas, U users, C clusters,
  * n_sc subcarriers, n_sym OFDM symbols sharing one channel per subcarrier. */
@@ -135,7 +149,10 @@ typedef struct {
                     *    2^-24 (the FP32 storage of x_c) instead;
                     * 2  FP64 for every local system. */
   int equalizer;   /* ffeq_equalizer: 0 = L-MMSE.  Refinement applies to
-                    * L-MMSE and ZF; MRC with refine > 0 is FFEQ_ERR_INVALID_ARG. */
+                    * L-MMSE and ZF; MRC or LAMA with refine > 0 is
+                    * FFEQ_ERR_INVALID_ARG. */
+  int lama_iters;  /* LAMA: iterations T, 1..64 (T = 1 is the normalized matched
+                    * filter); must be 0 for the other equalizers. */
 } ffeq_problem;
 
 typedef struct ffeq_plan ffeq_plan;

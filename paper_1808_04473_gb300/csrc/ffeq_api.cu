@@ -56,7 +56,7 @@ Sizes buffer_sizes(const ffeq_problem& p) {
   s.H = nsc * p.U * p.B * 8;
   s.y = nsc * p.n_sym * p.B * 8;
   s.z = nsc * p.n_sym * p.U * 8;
-  s.s2 = nsc * p.U * 4;
+  s.s2 = nsc * p.U * 4 * (p.equalizer == FFEQ_LAMA ? p.n_sym : 1);   // LAMA: per received vector
   s.llr = nsc * p.n_sym * p.U * p.llr_bits * 4;
   s.info = nsc * (p.arch == FFEQ_FD ? p.C : 1) * 4;
   return s;
@@ -119,9 +119,14 @@ ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, co
   if (p->refine < 0 || p->refine > 2) return FFEQ_ERR_INVALID_ARG;
   if (p->refine_fp64 < 0 || p->refine_fp64 > 2 || (p->refine_fp64 > 0 && p->refine == 0))
     return FFEQ_ERR_INVALID_ARG;
-  if (p->equalizer != FFEQ_LMMSE && p->equalizer != FFEQ_ZF && p->equalizer != FFEQ_MRC)
+  if (p->equalizer != FFEQ_LMMSE && p->equalizer != FFEQ_ZF && p->equalizer != FFEQ_MRC &&
+      p->equalizer != FFEQ_LAMA)
     return FFEQ_ERR_INVALID_ARG;
-  if (p->equalizer == FFEQ_MRC && p->refine > 0) return FFEQ_ERR_INVALID_ARG;   // nothing is solved
+  if ((p->equalizer == FFEQ_MRC || p->equalizer == FFEQ_LAMA) && p->refine > 0)
+    return FFEQ_ERR_INVALID_ARG;   // nothing is solved
+  if (p->equalizer == FFEQ_LAMA ? (p->lama_iters < 1 || p->lama_iters > 64 || p->llr_bits == 0)
+                                : p->lama_iters != 0)
+    return FFEQ_ERR_INVALID_ARG;   // LAMA's prior is the LLR constellation
   if (p->U > 32 || p->n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const int Ceff = p->arch == FFEQ_FD ? p->C : 1;
   if (ffeq::gram_stages(p->precision, p->B, p->U, p->n_sym, Ceff, false) < 1) return FFEQ_ERR_UNSUPPORTED;
@@ -204,6 +209,7 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   if (!(N0 >= 0.f) || !std::isfinite(N0) || !(Es > 0.f) || !std::isfinite(Es)) return FFEQ_ERR_INVALID_ARG;
   if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
   if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
+  if (p.equalizer == FFEQ_LAMA && !(N0 > 0.f)) return FFEQ_ERR_INVALID_ARG;   // the denoiser needs tau > 0
   if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
   ffeq::SolveParams sp{};
   sp.D = static_cast<const float2*>(workspace);
@@ -237,6 +243,14 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
     sp.Xs = reinterpret_cast<float2*>(ws + plan->off_X);
     sp.As = reinterpret_cast<float2*>(ws + plan->off_A);
     sp.fails = reinterpret_cast<int*>(ws + plan->off_F);
+  }
+  if (p.equalizer == FFEQ_LAMA) {
+    sp.lama_iters = p.lama_iters;
+    for (int c = 0; c < plan->Ceff; ++c)
+      sp.cl_size[c] = plan->Ceff == 1 ? p.B
+                    : (plan->cl_uniform ? p.B / plan->Ceff : plan->cl_off[c + 1] - plan->cl_off[c]);
+    const cudaError_t el = ffeq::launch_lama(sp, st);
+    return el == cudaSuccess ? FFEQ_OK : cuda_fail(el);
   }
   cudaError_t e = ffeq::launch_solve(sp, st);
   if (e != cudaSuccess || p.refine == 0) return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);

@@ -100,8 +100,10 @@ struct SolveParams {
   int llr_bits;
   float N0, rho;      // rho = N0 / Es (0 for zero forcing)
   float llr_scale;    // sqrt(Es / e_avg): amplitude of level +1
-  int equalizer;      // ffeq_equalizer; FFEQ_MRC runs mrc_fuse_kernel (uniform problems)
+  int equalizer;      // ffeq_equalizer; FFEQ_MRC runs mrc_fuse_kernel, FFEQ_LAMA lama_kernel (uniform problems)
   float Es;
+  int lama_iters;     // LAMA: iterations T
+  int cl_size[kMaxClusters];   // LAMA: antennas of each cluster (B for PD)
   // Uneven batch (desc != nullptr): one CTA per tile; per-unit sizes, offsets,
   // N0, rho and llr_scale from the descriptors.
   const BatchDesc* desc;
@@ -193,6 +195,8 @@ cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stre
 int solve_subcarriers_per_cta(int U, int Ceff);
 size_t solve_smem_bytes(int U, int Ceff);
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream);
+cudaError_t launch_lama(const SolveParams& p, cudaStream_t stream);
+int lama_symbols_per_cta(int U, int Ceff, int n_sym);
 // Uneven batch: p.U holds the group's padded users (8/16/32), lpr its lanes per row.
 cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream);
 size_t solve_batch_smem_bytes(int UP, int lpr, int threads);

@@ -1,0 +1,215 @@
+// LAMA equalization (Sec. III-B, Algorithm 1) for the PD and FD architectures.
+//
+// Input: the workspace D written by the contraction (per subcarrier and cluster
+// c: G_c[u][v] = D[v][u], y_c^MRC(n)_u = D[U+n][u]; PD is the case of one
+// cluster holding G and y^MRC).  One group of UP lanes (UP = U padded to 8/16/32)
+// runs the algorithm for one (subcarrier, cluster, received vector): lane i is
+// user i and keeps row i of the normalized Gram matrix in registers.  In the
+// paper's normalization (channel entries of variance 1/B; a cluster of S_c
+// antennas is the system H_c / sqrt(S_c)) the cluster's pair is scaled by
+// kappa = 1/S_c, with N0 kappa and beta_c = U kappa.  Each iteration
+//     z   = y^MRC + (I - G) s + v                (the matrix-vector product from
+//                                                 s broadcast by shuffles)
+//     tau = N0 + beta phi
+//     s'  = F(z, tau),  phi' = <G(z, tau)>      (posterior mean / variance of the
+//                                                 equiprobable square-QAM prior, Eq. F;
+//                                                 <.> a butterfly sum over the U lanes)
+//     v'  = beta phi' / tau (z - s)
+// and after T iterations the group leaves z^T with sigma_c^2 = tau^T.  The CTA
+// holds every cluster of NB received vectors of one subcarrier and fuses them
+// per user with the weights of Lemma 1 (Eq. fusionrule, opt_fusion): the
+// per-cluster variance is shared by the users, so z = sum_c z_c / sigma_c^2 /
+// sum_c 1/sigma_c^2 and sigma^2 = 1 / sum_c 1/sigma_c^2 (Thm. 3); PD is C = 1.
+// The epilogue writes z, sigma^2 per (subcarrier, symbol, user) and the LLRs.
+// Every lane of a warp runs the same T iterations (shuffles use the full mask);
+// groups past the last symbol or cluster work on clamped inputs and write nothing.
+#include <cmath>
+
+#include "ffeq_device.cuh"
+#include "ffeq_epilogue.cuh"
+#include "ffeq_internal.h"
+
+namespace ffeq {
+namespace {
+
+// Posterior mean and variance of one PAM axis (levels a_m = (2m - L + 1) d,
+// L = 2^HB, equiprobable) under Gaussian noise of variance tau/2:
+// p(a_m | x) ~ exp(-(x - a_m)^2 / tau).  Exponents are taken relative to the
+// nearest level a0, and the moments about a0, so that a sharp posterior on an
+// outer level keeps its small variance.
+template <int HB>
+__device__ __forceinline__ void pam_posterior(float x, float inv_tau, float d, float& mean, float& var) {
+  constexpr int L = 1 << HB;
+  // Nearest level index: round((x/d + L - 1) / 2), clamped to [0, L).
+  float q = rintf((x / d + static_cast<float>(L - 1)) * 0.5f);
+  q = fminf(fmaxf(q, 0.f), static_cast<float>(L - 1));
+  const float a0 = (2.f * q - static_cast<float>(L - 1)) * d;
+  const float e0 = (x - a0) * (x - a0);
+  float sw = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int m = 0; m < L; ++m) {
+    const float a = (2.f * static_cast<float>(m) - static_cast<float>(L - 1)) * d;
+    const float e = x - a;
+    const float w = expf((e0 - e * e) * inv_tau);   // <= 1; exactly 1 at a0
+    const float da = a - a0;
+    sw += w;
+    s1 = fmaf(w, da, s1);
+    s2 = fmaf(w * da, da, s2);
+  }
+  const float r = 1.f / sw;
+  const float m1 = s1 * r;
+  mean = a0 + m1;
+  var = fmaxf(fmaf(-m1, m1, s2 * r), 0.f);
+}
+
+template <int UP, int HB>
+__global__ void __launch_bounds__(512) lama_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, NB = p.spc;   // spc: received vectors per CTA
+  const int nblk = (NS + NB - 1) / NB;
+  const int sc = blockIdx.x / nblk;
+  const int n0 = (blockIdx.x - sc * nblk) * NB;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int ngroups = Ceff * NB;
+  const int c = g % Ceff, nb = g / Ceff;
+  const int n = n0 + nb;
+  const bool valid = g < ngroups && n < NS && sc < p.n_sc;
+  const int cc = g < ngroups ? c : 0;
+  const int nc = valid ? n : n0;
+  const int scc = sc < p.n_sc ? sc : p.n_sc - 1;
+  const bool real = i < U;
+  const int ic = real ? i : 0;
+
+  float2* Fz = reinterpret_cast<float2*>(smem);                 // [ngroups][UP]
+  float* Wt = reinterpret_cast<float*>(Fz + ngroups * UP);       // [ngroups]
+
+  // Wait for the contraction grid (programmatic dependent launch).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  const int S = p.cl_size[cc];
+  const float kap = S > 0 ? 1.f / static_cast<float>(S) : 0.f;
+  const float beta = static_cast<float>(U) * kap;
+  const float n0n = S > 0 ? p.N0 * kap : 1.f;     // an empty cluster: any tau > 0, weight 0 below
+  const float2* Dg = p.D + (static_cast<size_t>(scc) * Ceff + cc) * static_cast<size_t>(U + NS) * U;
+  float2 grow[UP];
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    const float2 v = Dg[(j < U ? j : 0) * U + ic];
+    grow[j] = (real && j < U) ? cscale(v, kap) : make_float2(0.f, 0.f);
+  }
+  const float2 yv = real ? cscale(Dg[(U + nc) * U + ic], kap) : make_float2(0.f, 0.f);
+  const float d = p.llr_scale;
+  const float invU = 1.f / static_cast<float>(U);
+
+  float2 s = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f), z;
+  float phi = p.Es, tau;
+  for (int t = 1;; ++t) {
+    // z = y + s - G s + v
+    float2 gs = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      const float2 sj = make_float2(__shfl_sync(kFullMask, s.x, j, UP), __shfl_sync(kFullMask, s.y, j, UP));
+      gs = cfma(grow[j], sj, gs);
+    }
+    z = cadd(csub(cadd(yv, s), gs), v);
+    tau = fmaf(beta, phi, n0n);
+    if (t >= p.lama_iters) break;
+    const float inv_tau = 1.f / tau;
+    float mr, vr, mi, vi;
+    pam_posterior<HB>(z.x, inv_tau, d, mr, vr);
+    pam_posterior<HB>(z.y, inv_tau, d, mi, vi);
+    float gsum = real ? vr + vi : 0.f;
+#pragma unroll
+    for (int o = UP / 2; o > 0; o >>= 1) gsum += __shfl_xor_sync(kFullMask, gsum, o, UP);
+    const float phin = gsum * invU;
+    v = cscale(csub(z, s), beta * phin * inv_tau);
+    s = make_float2(mr, mi);
+    phi = phin;
+  }
+
+  if (g < ngroups) {
+    const float w = S > 0 ? 1.f / tau : 0.f;
+    Fz[g * UP + i] = cscale(z, w);
+    if (i == 0) Wt[g] = w;
+    if (valid && i == 0 && p.info) p.info[static_cast<size_t>(sc) * Ceff + c] = 0;
+  }
+  __syncthreads();
+
+  // ---- per (symbol, user) of this CTA: fuse over the clusters, write the outputs
+  const int hb = p.llr_bits / 2;
+  for (int e = threadIdx.x; e < NB * U; e += blockDim.x) {
+    const int b = e / U, u = e - b * U;
+    const int nn = n0 + b;
+    if (nn >= NS || sc >= p.n_sc) break;
+    float2 nm = make_float2(0.f, 0.f);
+    float dn = 0.f;
+    for (int k = 0; k < Ceff; ++k) {
+      nm = cadd(nm, Fz[(b * Ceff + k) * UP + u]);
+      dn += Wt[b * Ceff + k];
+    }
+    float2 zz = make_float2(0.f, 0.f);
+    float s2 = INFINITY;
+    if (dn > 0.f) {
+      const float rr = 1.f / dn;
+      zz = cscale(nm, rr);
+      s2 = rr;
+    }
+    const size_t zi = (static_cast<size_t>(sc) * NS + nn) * U + u;
+    p.z[zi] = zz;
+    p.sigma2[zi] = s2;
+    if (p.llr_bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * p.llr_bits);
+  }
+}
+
+template <int UP, int HB>
+cudaError_t launch_lama_up(const SolveParams& p, cudaStream_t stream) {
+  const int ngroups = p.Ceff * p.spc;
+  const int threads = ((ngroups * UP + 31) / 32) * 32;
+  const size_t smem = static_cast<size_t>(ngroups) * UP * sizeof(float2) + static_cast<size_t>(ngroups) * 4;
+  const int nblk = (p.n_sym + p.spc - 1) / p.spc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(p.n_sc) * nblk);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lama_kernel<UP, HB>, p);
+}
+
+template <int UP>
+cudaError_t launch_lama_bits(const SolveParams& p, cudaStream_t stream) {
+  switch (p.llr_bits) {
+    case 2: return launch_lama_up<UP, 1>(p, stream);
+    case 4: return launch_lama_up<UP, 2>(p, stream);
+    case 6: return launch_lama_up<UP, 3>(p, stream);
+    default: return launch_lama_up<UP, 4>(p, stream);
+  }
+}
+
+}  // namespace
+
+// Received vectors per CTA: the groups of all clusters of NB vectors, at most
+// 256 lanes, with NB chosen so that the blocks of one subcarrier split n_sym evenly.
+int lama_symbols_per_cta(int U, int Ceff, int n_sym) {
+  const int lanes = Ceff * padded_users(U);
+  int nbmax = 256 / lanes;
+  if (nbmax < 1) nbmax = 1;
+  const int nblk = (n_sym + nbmax - 1) / nbmax;
+  return (n_sym + nblk - 1) / nblk;
+}
+
+cudaError_t launch_lama(const SolveParams& p_in, cudaStream_t stream) {
+  SolveParams p = p_in;
+  p.spc = lama_symbols_per_cta(p.U, p.Ceff, p.n_sym);
+  switch (padded_users(p.U)) {
+    case 8: return launch_lama_bits<8>(p, stream);
+    case 16: return launch_lama_bits<16>(p, stream);
+    default: return launch_lama_bits<32>(p, stream);
+  }
+}
+
+}  // namespace ffeq

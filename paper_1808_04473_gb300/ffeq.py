@@ -17,7 +17,7 @@ import re
 PD, FD = 0, 1
 FP32, TF32X3, BF16X3, FP16X3 = 0, 1, 2, 3
 UNBIASED, LITERAL = 0, 1
-LMMSE, ZF, MRC = 0, 1, 2
+LMMSE, ZF, MRC, LAMA = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffeq.so")
@@ -41,7 +41,7 @@ class ffeq_problem(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int), ("U", ctypes.c_int), ("C", ctypes.c_int), ("n_sc", ctypes.c_int),
                 ("n_sym", ctypes.c_int), ("arch", ctypes.c_int), ("precision", ctypes.c_int),
                 ("estimate", ctypes.c_int), ("llr_bits", ctypes.c_int), ("refine", ctypes.c_int),
-                ("refine_fp64", ctypes.c_int), ("equalizer", ctypes.c_int)]
+                ("refine_fp64", ctypes.c_int), ("equalizer", ctypes.c_int), ("lama_iters", ctypes.c_int)]
 
 
 class ffeq_instance(ctypes.Structure):
@@ -166,9 +166,10 @@ def ffeq_version() -> int:
 
 def ffeq_plan_create(B: int, U: int, C: int, n_sc: int, n_sym: int, arch: int = PD, precision: int = FP32,
                      estimate: int = UNBIASED, llr_bits: int = 0, refine: int = 0, refine_fp64: int = 0,
-                     cluster_sizes=None, equalizer: int = LMMSE) -> Plan:
+                     cluster_sizes=None, equalizer: int = LMMSE, lama_iters: int = 0) -> Plan:
     """Create a plan; ``cluster_sizes`` (C antenna counts summing to B) for clusters of unequal size."""
-    p = ffeq_problem(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64, equalizer)
+    p = ffeq_problem(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64, equalizer,
+                     lama_iters)
     h = _vp()
     if cluster_sizes is None:
         _check("ffeq_plan_create", lib().ffeq_plan_create(ctypes.byref(h), ctypes.byref(p)))
@@ -390,7 +391,7 @@ def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNB
 
 def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int = UNBIASED, llr_bits: int = 0,
              with_info: bool = False, stream=None, precision: int = FP32, refine: int = 0,
-             refine_fp64: int = 0, cluster_sizes=None, equalizer: int = LMMSE) -> dict:
+             refine_fp64: int = 0, cluster_sizes=None, equalizer: int = LMMSE, lama_iters: int = 0) -> dict:
     """Allocate outputs on ``H.device`` and run one equalization (returns torch tensors)."""
     import torch
     if H.dtype != torch.complex64 or y.dtype != torch.complex64:
@@ -402,10 +403,11 @@ def equalize(H, y, N0: float, Es: float, C: int, arch: int = PD, estimate: int =
     if tuple(y.shape) != (n_sc, n_sym, B):
         raise ValueError("y must be [n_sc][n_sym][B]")
     plan = ffeq_plan_create(B, U, C, n_sc, n_sym, arch, precision, estimate, llr_bits, refine, refine_fp64,
-                            cluster_sizes, equalizer)
+                            cluster_sizes, equalizer, lama_iters)
     dev = H.device
+    s2_shape = (n_sc, n_sym, U) if equalizer == LAMA else (n_sc, U)     # LAMA: per received vector
     out = {"z": torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
-           "sigma2": torch.empty((n_sc, U), dtype=torch.float32, device=dev)}
+           "sigma2": torch.empty(s2_shape, dtype=torch.float32, device=dev)}
     if llr_bits:
         out["llr"] = torch.empty((n_sc, n_sym, U, llr_bits), dtype=torch.float32, device=dev)
     if with_info:

@@ -87,7 +87,7 @@ def test_staging_size_accounts_for_every_buffer(built):
 
 
 def test_plan_struct_layout_matches_header(built):
-    assert ctypes.sizeof(ffeq.ffeq_problem) == 12 * 4
+    assert ctypes.sizeof(ffeq.ffeq_problem) == 13 * 4
     text = open(ffeq.HEADER_PATH).read()
     body = text[text.index("typedef struct {") + len("typedef struct {"):text.index("} ffeq_problem;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
@@ -235,3 +235,29 @@ def test_equalizer_validation(built):
     for eq in (ff.ZF, ff.MRC):
         fd = ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD, equalizer=eq)
         assert ff.lib().ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 1 << 30, None) == 2
+
+
+def test_lama_validation(built):
+    ff = ffeq
+    for arch in (ff.PD, ff.FD):
+        ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=arch, llr_bits=4, equalizer=ff.LAMA, lama_iters=8)
+    bad = [dict(llr_bits=0, lama_iters=8),                 # the prior is the LLR constellation
+           dict(llr_bits=4, lama_iters=0), dict(llr_bits=4, lama_iters=65),
+           dict(llr_bits=4, lama_iters=8, refine=1)]
+    for kw in bad:
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD, equalizer=ff.LAMA, **kw)
+        assert e.value.status == 1, kw
+    with pytest.raises(ff.FfeqError) as e:                    # iterations only for LAMA
+        ff.ffeq_plan_create(64, 8, 4, 10, 2, lama_iters=3)
+    assert e.value.status == 1
+    # N0 = 0 is rejected before any device work (the denoiser needs tau > 0).
+    plan = ff.ffeq_plan_create(32, 4, 2, 8, 1, llr_bits=2, equalizer=ff.LAMA, lama_iters=4)
+    fake = 1 << 20
+    with pytest.raises(ff.FfeqError) as e:
+        ff.ffeq_fuse_equalize(plan, fake, 1 << 30, 0.0, 1.0, fake, fake, fake, None, stream=0)
+    assert e.value.status == 1
+    # sigma2 holds one value per received vector: the host staging counts n_sc * n_sym * U floats.
+    lm = ff.ffeq_plan_create(256, 16, 8, 100, 14, arch=ff.FD, llr_bits=4, equalizer=ff.LAMA, lama_iters=8)
+    mm = ff.ffeq_plan_create(256, 16, 8, 100, 14, arch=ff.FD, llr_bits=4, equalizer=ff.MRC)
+    assert ff.ffeq_host_staging_size(lm) - ff.ffeq_host_staging_size(mm) >= 100 * 13 * 16 * 4
