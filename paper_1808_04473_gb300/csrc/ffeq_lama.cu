@@ -8,8 +8,9 @@
 // paper's normalization (channel entries of variance 1/B; a cluster of S_c
 // antennas is the system H_c / sqrt(S_c)) the cluster's pair is scaled by
 // kappa = 1/S_c, with N0 kappa and beta_c = U kappa.  Each iteration
-//     z   = y^MRC + (I - G) s + v                (the matrix-vector product from
-//                                                 s broadcast by shuffles)
+//     z   = y^MRC + (I - G) s + v                (the matrix-vector product reads s
+//                                                 from the group's shared-memory copy,
+//                                                 two entries per 128-bit broadcast load)
 //     tau = N0 + beta phi
 //     s'  = F(z, tau),  phi' = <G(z, tau)>      (posterior mean / variance of the
 //                                                 equiprobable square-QAM prior, Eq. F;
@@ -21,7 +22,8 @@
 // per-cluster variance is shared by the users, so z = sum_c z_c / sigma_c^2 /
 // sum_c 1/sigma_c^2 and sigma^2 = 1 / sum_c 1/sigma_c^2 (Thm. 3); PD is C = 1.
 // The epilogue writes z, sigma^2 per (subcarrier, symbol, user) and the LLRs.
-// Every lane of a warp runs the same T iterations (shuffles use the full mask);
+// Every lane of a warp runs the same T iterations (shuffles and __syncwarp use
+// the full mask);
 // groups past the last symbol or cluster work on clamped inputs and write nothing.
 #include <cmath>
 
@@ -63,7 +65,7 @@ __device__ __forceinline__ void pam_posterior(float x, float inv_tau, float d, f
 }
 
 template <int UP, int HB>
-__global__ void __launch_bounds__(512) lama_kernel(const SolveParams p) {
+__global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, NB = p.spc;   // spc: received vectors per CTA
   const int nblk = (NS + NB - 1) / NB;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(512) lama_kernel(const SolveParams p) {
   const int n0 = (blockIdx.x - sc * nblk) * NB;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
   const int ngroups = Ceff * NB;
+  const int ngroups_pad = static_cast<int>(blockDim.x) / UP;   // groups of the last warp's padding lanes included
   const int c = g % Ceff, nb = g / Ceff;
   const int n = n0 + nb;
   const bool valid = g < ngroups && n < NS && sc < p.n_sc;
@@ -80,8 +83,12 @@ __global__ void __launch_bounds__(512) lama_kernel(const SolveParams p) {
   const bool real = i < U;
   const int ic = real ? i : 0;
 
-  float2* Fz = reinterpret_cast<float2*>(smem);                 // [ngroups][UP]
+  // s of every group, double-buffered by iteration parity: [2][ngroups_pad][UP]
+  float2* sbuf = reinterpret_cast<float2*>(smem);
+  float2* Fz = sbuf + 2 * ngroups_pad * UP;                      // [ngroups][UP]
   float* Wt = reinterpret_cast<float*>(Fz + ngroups * UP);       // [ngroups]
+  float2* const sb0 = sbuf + g * UP;
+  float2* const sb1 = sbuf + (ngroups_pad + g) * UP;
 
   // Wait for the contraction grid (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -104,12 +111,19 @@ __global__ void __launch_bounds__(512) lama_kernel(const SolveParams p) {
   float2 s = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f), z;
   float phi = p.Es, tau;
   for (int t = 1;; ++t) {
-    // z = y + s - G s + v
+    // z = y + s - G s + v.  A group lies within one warp: __syncwarp orders this
+    // iteration's stores before the loads, and the buffer written next iteration
+    // is the other one (the one after that is only written once every lane has
+    // passed the next __syncwarp, i.e. finished these loads).
+    float2* cur = (t & 1) ? sb1 : sb0;
+    cur[i] = s;
+    __syncwarp();
     float2 gs = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < UP; ++j) {
-      const float2 sj = make_float2(__shfl_sync(kFullMask, s.x, j, UP), __shfl_sync(kFullMask, s.y, j, UP));
-      gs = cfma(grow[j], sj, gs);
+    for (int j = 0; j < UP; j += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(cur + j);
+      gs = cfma(grow[j], make_float2(q.x, q.y), gs);
+      gs = cfma(grow[j + 1], make_float2(q.z, q.w), gs);
     }
     z = cadd(csub(cadd(yv, s), gs), v);
     tau = fmaf(beta, phi, n0n);
@@ -165,7 +179,9 @@ template <int UP, int HB>
 cudaError_t launch_lama_up(const SolveParams& p, cudaStream_t stream) {
   const int ngroups = p.Ceff * p.spc;
   const int threads = ((ngroups * UP + 31) / 32) * 32;
-  const size_t smem = static_cast<size_t>(ngroups) * UP * sizeof(float2) + static_cast<size_t>(ngroups) * 4;
+  const int ngroups_pad = threads / UP;
+  const size_t smem = static_cast<size_t>(2 * ngroups_pad + ngroups) * UP * sizeof(float2) +
+                      static_cast<size_t>(ngroups) * 4;
   const int nblk = (p.n_sym + p.spc - 1) / p.spc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(p.n_sc) * nblk);
