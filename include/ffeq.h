@@ -26,7 +26,8 @@
  *                                  (column-major layout of the paper's B x U H)
  *   y      cf32 [n_sc][n_sym][B]   receive vectors, one per OFDM symbol
  *   z      cf32 [n_sc][n_sym][U]   equalized symbols
- *   sigma2 f32  [n_sc][U]          post-equalization error variance (real)
+ *   sigma2 f32  [n_sc][U]          post-equalization error variance (real);
+ *                                  [n_sc][n_sym][U] for FFEQ_LAMA
  *   llr    f32  [n_sc][n_sym][U][llr_bits]   optional max-log LLRs
  *   info   i32  [n_sc] (PD) or [n_sc][C] (FD)  optional: 0, or k (1-based) when
  *                                  the k-th Cholesky pivot of G + rho I (or of
