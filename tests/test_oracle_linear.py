@@ -175,3 +175,28 @@ def test_mrc_zero_variance_outside_the_limit_is_the_same_in_pd_and_fd():
     fd = linear.equalize_fd_linear(H, p.y, 0.0, p.Es, 1, "mrc")
     assert np.array_equal(pd["z"], fd["z"]) and np.array_equal(pd["sigma2"], fd["sigma2"])
     assert (pd["z"] == 0).all() and np.isinf(pd["sigma2"]).all()
+
+
+@pytest.mark.slow
+def test_large_system_mrc_matches_cor1_and_fd_equals_pd():
+    """Cor. 1: MRC reaches SINR = snr / (1 + beta snr) (paper normalization, snr = B Es / N0 here);
+    Lemma 8: FD-MRC fused with the optimal weights equals PD-MRC.  B = 1024, U = 64, C = 8:
+    the empirical Es / MSE of both within 0.2 dB of the closed form (the finite-size
+    interference of U - 1 users instead of U is 0.07 dB)."""
+    from oracle import theory
+    B, U, C = 1024, 64, 8
+    p = synth.make_problem(B, U, C, 30, 16, snr_db=10.0, bits=4, seed=19)
+    expect = theory.db(theory.sinr_pd("mrc", U / B, B * p.Es / p.N0))
+    for f in (linear.equalize_pd_linear, linear.equalize_fd_linear):
+        o = f(p.H, p.y, p.N0, p.Es, C, "mrc")
+        emp = theory.db(p.Es / np.mean(np.abs(o["z"] - p.s) ** 2))
+        assert abs(emp - expect) < 0.2, (f.__name__, emp, expect)
+
+
+def test_zf_variance_has_the_inverse_wishart_mean():
+    """PD-ZF: E[(G^{-1})_uu] = 1 / (B - U) for i.i.d. CN(0, 1) channels, so the mean reported
+    variance is N0 / (B - U) — Cor. 1's SINR snr (1 - beta) in the paper's normalization."""
+    B, U = 64, 8
+    p = synth.make_problem(B, U, 1, 800, 1, snr_db=10.0, seed=20)
+    o = linear.equalize_pd_linear(p.H, p.y, p.N0, p.Es, 1, "zf")
+    assert np.mean(o["sigma2"]) == pytest.approx(p.N0 / (B - U), rel=0.02)
