@@ -71,6 +71,22 @@ def _ncu_traffic():
     return d.get("kernels", {}) if d.get("source_digest") == _source_digest() else {}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The maximum of ``x`` over the ranks of the default process group: the job's
+    timed region ends with its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, world: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed in ``steps`` steps over
+    the (max-over-ranks) time of the timed region, per second."""
+    return world * units_per_rank_step * steps / (ms * 1e-3)
+
+
 def input_bytes(B, U, n_sc, n_sym):
     """HBM bytes the local preprocessing must read: H and y (complex64)."""
     return n_sc * 8 * (B * U + B * n_sym)
@@ -321,11 +337,9 @@ def run_uneven(args, rank, world, local_rank):
         clk.__exit__(None, None, None)
     ms = start.elapsed_time(end)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
     assert ffeq.ffeq_device_status() == 0
-    value = world * 2 * symbols * K / (ms * 1e-3)
+    value = job_rate(2 * symbols, world, K, ms)
     out_bytes = sum(r["z"].numel() * 8 + r["s2"].numel() * 4 + r["llr"].numel() * 4 for r in runs.values())
     alg = 2 * in_bytes + out_bytes
     hbm_peak, peak_src = _peaks()
@@ -514,9 +528,7 @@ def main():
         torch.cuda.synchronize()
         del steps
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dev)
         assert ffeq.ffeq_device_status() == 0
         for a in outs:
             assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
@@ -533,7 +545,7 @@ def main():
                     "steps": Kc, "kernels_ms": kern32}
 
     symbols_per_step = 2 * U * n_sc * n_sym
-    value = world * symbols_per_step * K / (elapsed_ms * 1e-3)
+    value = job_rate(symbols_per_step, world, K, elapsed_ms)
 
     # ---- accuracy of the timed outputs against the FP64 oracle on sampled subcarriers
     accuracy = None
