@@ -29,7 +29,7 @@ import numpy as np
 
 from .lmmse import partition
 
-__all__ = ["fd_train_forward", "fd_train_backward", "finite_difference"]
+__all__ = ["fd_train_forward", "fd_train_backward", "fd_optimal_backward", "finite_difference"]
 
 
 def _blocks(H, y, k, bounds):
@@ -81,6 +81,57 @@ def fd_train_backward(H, y, rho, nu, gz):
             grho[c] += -np.real(np.trace(Gb.conj().T @ X))
             gnu[c] += np.real(np.sum(np.conj(Gz) * X, axis=1))
     return gH, gy, grho, gnu
+
+
+def fd_optimal_backward(H, y, N0: float, Es: float, C: int, gz, cluster_sizes=None):
+    """Gradients through the optimal-weight rule: the FD estimate with the unbiased
+    per-cluster pairs fused by Lemma 1 (``lmmse.equalize_fd(..., "unbiased")``, the
+    forward the library computes), differentiated with respect to ``H`` and ``y``.
+
+    Per subcarrier and cluster, with ``M_c = G_c + rho I``, ``A_c = M_c^{-1}``,
+    ``X_c = A_c H_c^H Y_c``, ``a_c = diag(A_c)``, ``w_c = 1 / a_c``: the fused estimate is
+    ``z_u = sum_c w_{c,u} X_{c,u} / D_u`` with ``D_u = sum_c (w_{c,u} - rho)`` (weights
+    ``mu / (N0 a)`` with ``mu = 1 - rho a``; ``N0`` cancels).  Its differential
+    ``dz_u = (sum_c w_{c,u} dX_{c,u} + (X_{c,u} - z_u) dw_{c,u}) / D_u`` with
+    ``dw = -da / a^2``, ``dX = A (dB - dM X)``, ``da_u = -[A dM A]_uu`` gives, for
+    ``G_x = diag(w_c / D) G_z``, ``G_b = A_c G_x`` and
+    ``q_u = -Re(sum_n conj(g_z,u,n) (X_{c,u,n} - z_{u,n})) / (D_u a_{c,u}^2)``:
+
+        dL/dH_c = Y_c G_b^H - H_c (X_c G_b^H + G_b X_c^H + 2 A_c diag(q) A_c)
+        dL/dy_c = H_c G_b
+
+    (the free-weight adjoint above plus the term of the weights' dependence on
+    ``a_c``).  ``gz`` is ``dL/dRe z + i dL/dIm z`` ``[n_sc][n_sym][U]``; users whose
+    gain ``mu`` is not positive are outside the smooth region and not handled.
+    Returns ``(gH [n_sc][U][B], gy [n_sc][n_sym][B])``.
+    """
+    n_sc, U, B = H.shape
+    n_sym = y.shape[1]
+    bounds = partition(B, C, cluster_sizes)
+    rho = N0 / Es
+    gH = np.zeros((n_sc, U, B), np.complex128)
+    gy = np.zeros((n_sc, n_sym, B), np.complex128)
+    for k in range(n_sc):
+        Gz = np.asarray(gz[k], dtype=np.complex128).T              # U x n_sym
+        blocks = _blocks(H, y, k, bounds)
+        As, Xs, ws = [], [], []
+        for Hc, Yc in blocks:
+            A = np.linalg.inv(Hc.conj().T @ Hc + rho * np.eye(U))
+            As.append(A)
+            Xs.append(A @ (Hc.conj().T @ Yc))
+            ws.append(1.0 / np.real(np.diag(A)))
+        D = sum(w - rho for w in ws)                                # [U]
+        z = sum(w[:, None] * X for w, X in zip(ws, Xs)) / D[:, None]
+        for c, (Hc, Yc) in enumerate(blocks):
+            A, X, w = As[c], Xs[c], ws[c]
+            a = 1.0 / w
+            Gb = A @ ((w / D)[:, None] * Gz)
+            q = -np.real(np.sum(np.conj(Gz) * (X - z), axis=1)) / (D * a * a)
+            K = X @ Gb.conj().T + Gb @ X.conj().T + 2.0 * A @ np.diag(q) @ A
+            b0, b1 = bounds[c]
+            gH[k, :, b0:b1] = (Yc @ Gb.conj().T - Hc @ K).T
+            gy[k, :, b0:b1] = (Hc @ Gb).T
+    return gH, gy
 
 
 def finite_difference(f, x: np.ndarray, eps: float = 1e-6) -> np.ndarray:

@@ -68,3 +68,47 @@ def test_gradient_of_a_wrong_formula_is_caught():
             wrong[k, :, b0:b1] += (Hc @ (Gb @ X.conj().T)).T
     assert np.abs(wrong - fH).max() > 1e-3
     assert np.abs(gH - fH).max() < 1e-6 * max(1.0, np.abs(fH).max())
+
+
+@pytest.mark.parametrize("seed,C,sizes", [(0, 2, None), (1, 3, [3, 5, 4]), (2, 1, None)])
+def test_gradients_through_the_optimal_weights_match_finite_differences(seed, C, sizes):
+    """FD with the unbiased pairs and Lemma 1's weights (the library's forward): the closed-form
+    gradients with respect to H and y equal central differences of lmmse.equalize_fd."""
+    B = 12
+    p = synth.make_problem(B, 3, C, 2, 2, snr_db=5.0, bits=2, seed=seed)
+    H, y = p.H.astype(np.complex128), p.y.astype(np.complex128)
+    N0, Es = 0.6, 1.0
+
+    def loss(h, t):
+        return _loss(lmmse.equalize_fd(h, t, N0, Es, C, "unbiased", cluster_sizes=sizes)["z"], p.s)
+
+    z = lmmse.equalize_fd(H, y, N0, Es, C, "unbiased", cluster_sizes=sizes)["z"]
+    gH, gy = adjoint.fd_optimal_backward(H, y, N0, Es, C, 2.0 * (z - p.s), cluster_sizes=sizes)
+    fH = adjoint.finite_difference(lambda h: loss(h, y), H)
+    fy = adjoint.finite_difference(lambda t: loss(H, t), y)
+    for got, ref in ((gH, fH), (gy, fy)):
+        assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+def test_optimal_weight_term_is_needed():
+    """Sanity of the pin: without the weights' dependence on diag(A_c) (the free-weight adjoint
+    at the optimal weights) the H gradient misses the finite differences."""
+    C = 2
+    p = synth.make_problem(12, 3, C, 1, 2, snr_db=5.0, bits=2, seed=7)
+    H, y = p.H.astype(np.complex128), p.y.astype(np.complex128)
+    N0, Es = 0.6, 1.0
+    rho = N0 / Es
+    z = lmmse.equalize_fd(H, y, N0, Es, C, "unbiased")["z"]
+    gz = 2.0 * (z - p.s)
+    fH = adjoint.finite_difference(
+        lambda h: _loss(lmmse.equalize_fd(h, y, N0, Es, C, "unbiased")["z"], p.s), H)
+    # Frozen weights nu_c = w_c / D (the optimal ones at this point) through the free-weight adjoint.
+    Hm = H[0].T
+    ws = [1.0 / np.real(np.diag(np.linalg.inv(Hm[b0:b1].conj().T @ Hm[b0:b1] + rho * np.eye(3))))
+          for b0, b1 in lmmse.partition(12, C)]
+    D = sum(w - rho for w in ws)
+    nu = np.array([w / D for w in ws])
+    gH_frozen, *_ = adjoint.fd_train_backward(H, y, np.full(C, rho), nu, gz)
+    gH, _ = adjoint.fd_optimal_backward(H, y, N0, Es, C, gz)
+    assert np.abs(gH - fH).max() <= 1e-6 * max(1.0, np.abs(fH).max())
+    assert np.abs(gH_frozen - fH).max() > 1e-3 * np.abs(fH).max()
