@@ -261,3 +261,17 @@ def test_lama_validation(built):
     lm = ff.ffeq_plan_create(256, 16, 8, 100, 14, arch=ff.FD, llr_bits=4, equalizer=ff.LAMA, lama_iters=8)
     mm = ff.ffeq_plan_create(256, 16, 8, 100, 14, arch=ff.FD, llr_bits=4, equalizer=ff.MRC)
     assert ff.ffeq_host_staging_size(lm) - ff.ffeq_host_staging_size(mm) >= 100 * 13 * 16 * 4
+
+
+def test_plain_c_client_compiles_links_and_runs(built, tmp_path):
+    """The headers are plain C (C11, -Wall -Werror) and a C program linked against
+    libffeq.so makes host-side calls through them without a GPU."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "abi_check")
+    libdir = os.path.dirname(ffeq.LIB_PATH)
+    cc = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", ffeq.INCLUDE_DIR,
+                         os.path.join(root, "tests", "c", "abi_check.c"), "-o", exe, "-L", libdir, "-lffeq",
+                         "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", run.stderr
