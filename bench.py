@@ -6,6 +6,13 @@ i.i.d. Rayleigh, 10 dB, LLRs on): every stage of the hot path runs once per
 architecture.  The metric counts equalized symbols (subcarrier x symbol x user)
 of both architectures per second.
 
+The same JSON line carries the other workloads as extra keys (each timed the
+same way, with its own accuracy against the FP64 oracle on sampled subcarriers):
+``correlated`` (B=256, U=32, C=16, 3300 x 14, 64-QAM, r = 0.7, 15 dB: FP32
+against FP16x3 with and without refinement), ``training`` (one forward +
+adjoint step of the differentiable FD form, B=128, U=16, C=8, 8 x 1024
+subcarriers, QPSK, 10 dB) and ``uneven`` (4096 instances of mixed size).
+
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
 """
@@ -27,12 +34,16 @@ if ROOT not in sys.path:
 METRIC = "equalized symbols/s (subcarrier x symbol x user), PD + FD L-MMSE"
 UNIT = "symbols/s"
 WORKLOAD = dict(B=256, U=16, C=8, n_sc=1200, n_sym=14, bits=4, snr_db=10.0)
+CORRELATED = dict(B=256, U=32, C=16, n_sc=3300, n_sym=14, bits=6, snr_db=15.0, corr_r=0.7)
+TRAINING = dict(B=128, U=16, C=8, n_sc=8 * 1024, n_sym=1, bits=2, snr_db=10.0)
 # Paper, Table I (L-MMSE, B=256, C=8 on 8 V100): PD 0.856 ms, FD 0.751 ms for
 # 16*1200*14 symbols each; symbols/s of one PD + one FD pass of the batch.
 PAPER_SYMBOLS_PER_S = 2 * 16 * 1200 * 14 / (0.856e-3 + 0.751e-3)
 L2_BYTES = 129 * 1024 * 1024
 LAMA_ITERS = 8              # LAMA iterations of the equalizer-variant lines
 FALLBACK_HBM_GBS = 6800.0
+PRECISIONS = ("fp32", "tf32x3", "bf16x3", "fp16x3")
+DTYPE = {"fp32": "f32", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32", "fp16x3": "fp16x3+f32"}
 
 
 def _peaks():
@@ -155,50 +166,111 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _time_oracle(n_sc_total_budget_s: float, seed: int = 99):
-    """Oracle-only timing on pre-generated chunks (generation excluded)."""
+ORACLE_CHUNK = 40           # subcarriers per oracle call of the CPU legs
+
+
+def _time_oracle(budget_s: float, seed: int = 99):
+    """The FP64 oracle as it stands on chunks of the headline workload (generation
+    excluded): PD and FD with their LLRs, what the GPU step computes.  Returns
+    (symbols/s, subcarriers done, seconds spent)."""
+    from oracle import llr as ollr
     from oracle import lmmse
     from paper_1808_04473_gb300 import synth
     w = WORKLOAD
-    chunk = 40
-    p = synth.make_problem(w["B"], w["U"], w["C"], chunk, w["n_sym"], snr_db=w["snr_db"], bits=w["bits"], seed=seed)
+    p = synth.make_problem(w["B"], w["U"], w["C"], ORACLE_CHUNK, w["n_sym"], snr_db=w["snr_db"], bits=w["bits"],
+                           seed=seed)
     done, spent = 0, 0.0
-    while spent < n_sc_total_budget_s:
+    while spent < budget_s:
         t = time.perf_counter()
-        lmmse.equalize_pd(p.H, p.y, p.N0, p.Es, p.C)
-        lmmse.equalize_fd(p.H, p.y, p.N0, p.Es, p.C)
+        for f in (lmmse.equalize_pd, lmmse.equalize_fd):
+            o = f(p.H, p.y, p.N0, p.Es, p.C)
+            ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], w["bits"], p.Es)
         spent += time.perf_counter() - t
-        done += chunk
-    symbols = 2 * w["U"] * w["n_sym"] * done
-    return symbols / spent, done, spent
+        done += ORACLE_CHUNK
+    return 2 * w["U"] * w["n_sym"] * done / spent, done, spent
 
 
-def _oracle_worker(job):
-    budget_s, seed = job
-    _, done, spent = _time_oracle(budget_s, seed)
+def numpy32_equalize(H, y, N0: float, Es: float, C: int, fd: bool):
+    """CPU throughput baseline (not the oracle): the L-MMSE path in FP32 NumPy,
+    batched over subcarriers -- Gram matrices and matched filters by batched
+    products, Cholesky factors by ``np.linalg.cholesky``, the diagonal of the
+    inverse and the estimates by ``np.linalg.solve`` on the factors, unbiased
+    pairs, and for FD the optimal fusion.  Returns (z [n_sc][n_sym][U], sigma2)."""
+    import numpy as np
+    n_sc, U, B = H.shape
+    rho = np.float32(N0 / Es)
+    eye = np.eye(U, dtype=np.complex64)
+    S = B // C
+    parts = [(c * S, (c + 1) * S) for c in range(C)] if fd else [(0, B)]
+    num = np.zeros((n_sc, U, y.shape[1]), np.complex64)
+    den = np.zeros((n_sc, U), np.float32)
+    for b0, b1 in parts:
+        Hc = H[:, :, b0:b1]                                   # [n_sc][U][S]
+        G = Hc.conj() @ Hc.transpose(0, 2, 1) + rho * eye     # G + rho I
+        b = Hc.conj() @ y[:, :, b0:b1].transpose(0, 2, 1)     # [n_sc][U][n_sym]
+        L = np.linalg.cholesky(G)
+        Li = np.linalg.solve(L, np.broadcast_to(eye, G.shape))
+        A_diag = np.einsum("kij,kij->kj", Li.conj(), Li).real   # diag of L^-H L^-1
+        x = np.linalg.solve(L.conj().transpose(0, 2, 1), np.linalg.solve(L, b))
+        mu = np.maximum(1.0 - rho * A_diag, 0.0)
+        w = mu / A_diag                                       # Es / unbiased variance, N0 cancelled
+        num += x / A_diag[:, :, None]
+        den += w
+    z = num / den[:, :, None]
+    return z.transpose(0, 2, 1), N0 / den
+
+
+def _time_numpy32(budget_s: float, seed: int = 99):
+    from paper_1808_04473_gb300 import synth
+    w = WORKLOAD
+    p = synth.make_problem(w["B"], w["U"], w["C"], 4 * ORACLE_CHUNK, w["n_sym"], snr_db=w["snr_db"],
+                           bits=w["bits"], seed=seed)
+    done, spent = 0, 0.0
+    while spent < budget_s:
+        t = time.perf_counter()
+        for fd in (False, True):
+            numpy32_equalize(p.H, p.y, p.N0, p.Es, p.C, fd)
+        spent += time.perf_counter() - t
+        done += 4 * ORACLE_CHUNK
+    return 2 * w["U"] * w["n_sym"] * done / spent, done, spent
+
+
+def _cpu_worker(job):
+    kind, budget_s, seed = job
+    f = _time_oracle if kind == "oracle" else _time_numpy32
+    _, done, spent = f(budget_s, seed)
     return done, spent
 
 
-def _time_oracle_all_cores(budget_s: float):
-    """The oracle as it stands, one single-threaded process per host core
-    (a spawned pool: safe after CUDA initialization), each timing its own
-    chunks for about budget_s seconds.  Returns (symbols/s over the slowest
-    worker's oracle time, subcarriers done, workers)."""
-    import multiprocessing as mp
-    workers = os.cpu_count() or 1
+def _single_thread_env():
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ[k] = "1"
+    return saved
+
+
+def _restore_env(saved):
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+
+
+def _time_cpu_all_cores(kind: str, budget_s: float):
+    """One single-threaded process per host core (a spawned pool: safe after CUDA
+    initialization), each timing its own chunks of the headline workload for
+    about budget_s seconds.  Returns (symbols/s over the slowest worker's time,
+    subcarriers done, workers)."""
+    import multiprocessing as mp
+    workers = os.cpu_count() or 1
+    saved = _single_thread_env()
     try:
         with mp.get_context("spawn").Pool(workers) as pool:
-            res = pool.map(_oracle_worker, [(budget_s, 99 + i) for i in range(workers)])
+            res = pool.map(_cpu_worker, [(kind, budget_s, 99 + i) for i in range(workers)])
     finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+        _restore_env(saved)
     done = sum(r[0] for r in res)
     spent = max(r[1] for r in res)
     w = WORKLOAD
@@ -208,23 +280,21 @@ def _time_oracle_all_cores(budget_s: float):
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores: one single-threaded process per
     core (a spawned pool, created once); each step every worker times oracle
-    chunks of the workload for a bounded slice of time (at least one chunk), so
-    that the whole --steps K --warmup W run takes about two minutes."""
+    chunks of the workload (PD and FD with their LLRs) for a bounded slice of
+    time (at least one chunk), so that the whole --steps K --warmup W run takes
+    about two minutes."""
     if rank != 0:
         return
     import multiprocessing as mp
     workers = os.cpu_count() or 1
     budget = max(0.01, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
-    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
-    saved = {k: os.environ.get(k) for k in keys}
-    for k in keys:
-        os.environ[k] = "1"
+    saved = _single_thread_env()
     rates, samples, spent_all = [], 0, 0.0
     w = WORKLOAD
     try:
         with mp.get_context("spawn").Pool(workers) as pool:
             for step in range(args.warmup + args.steps):
-                res = pool.map(_oracle_worker, [(budget, 99 + i + 1000 * step) for i in range(workers)])
+                res = pool.map(_cpu_worker, [("oracle", budget, 99 + i + 1000 * step) for i in range(workers)])
                 if step < args.warmup:
                     continue
                 done = sum(r[0] for r in res)
@@ -233,20 +303,16 @@ def run_reference(args, rank, world):
                 samples += done
                 spent_all += spent
     finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+        _restore_env(saved)
     value = statistics.median(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * 2 * w["U"] * w["n_sym"] * w["n_sc"] / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD",
-                   "sample": f"FP64 oracle on 40-subcarrier chunks, {workers} single-threaded processes, "
-                             f"~{budget:.2f} s of oracle work per process per timed step"},
+        "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD, LLRs",
+                   "sample": f"FP64 oracle (z, sigma^2 and LLRs) on {ORACLE_CHUNK}-subcarrier chunks, {workers} "
+                             f"single-threaded processes, ~{budget:.2f} s of oracle work per process per timed step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": f"{samples} subcarriers over {args.steps} steps ({spent_all:.1f} s of oracle "
                                    f"time per process)"},
@@ -255,35 +321,212 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _errors(g, o):
+    """[max over subcarriers of ||g - o|| / ||o||, max over entries of |g - o| / max(|o|, rms of the
+    subcarrier)] -- the two measures of the parity tests."""
+    import numpy as np
+    g = np.asarray(g).reshape(g.shape[0], -1).astype(np.complex128)
+    o = np.asarray(o).reshape(o.shape[0], -1).astype(np.complex128)
+    nrm = np.linalg.norm(g - o, axis=1) / np.maximum(np.linalg.norm(o, axis=1), 1e-30)
+    rms = np.sqrt(np.mean(np.abs(o) ** 2, axis=1, keepdims=True))
+    ent = np.abs(g - o) / np.maximum(np.abs(o), np.maximum(rms, 1e-30))
+    return [float(nrm.max()), float(ent.max())]
+
+
+def _accuracy(p, outs, idx, archs):
+    """Errors of the outputs of input set 0 against the FP64 oracle on sampled subcarriers."""
+    import numpy as np
+    from oracle import lmmse
+    res = {}
+    for a in archs:
+        f = lmmse.equalize_pd if a == 0 else lmmse.equalize_fd
+        o = f(p.H[idx], p.y[idx], float(np.float32(p.N0)), p.Es, p.C, "unbiased")
+        z = outs[a]["z"][idx].cpu().numpy()
+        s2 = outs[a]["s2"][idx].cpu().numpy()
+        res["pd" if a == 0 else "fd"] = {"z": _errors(z, o["z"]), "sigma2": _errors(s2, o["sigma2"])}
+    return res
+
+
 UNEVEN = dict(n_inst=4096, seed=77)
 
 
-def run_uneven(args, rank, world, local_rank):
+class Runner:
+    """What every GPU leg shares: torch, the binding, the device, the rank layout."""
+
+    def __init__(self, args, rank, world, local_rank):
+        import torch
+
+        from paper_1808_04473_gb300 import build as fbuild
+        from paper_1808_04473_gb300 import ffeq
+        self.args, self.rank, self.world = args, rank, world
+        self.torch, self.ffeq = torch, ffeq
+        torch.cuda.set_device(local_rank)
+        self.local_rank = local_rank
+        self.dev = torch.device("cuda", local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+        fbuild.build()
+        ffeq.lib()
+        self.PREC = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3, "fp16x3": ffeq.FP16X3}
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def rotating_sets(self, *arrays):
+        """Device copies of the inputs, enough of them that the rotating working set
+        exceeds 4x L2 (at least 2): every step reads cold inputs."""
+        torch = self.torch
+        nbytes = sum(a.nbytes for a in arrays)
+        n_sets = max(2, -(-4 * L2_BYTES // nbytes))
+        first = [torch.from_numpy(a).to(self.dev) for a in arrays]
+        sets = [first] + [[t.clone() for t in first] for _ in range(n_sets - 1)]
+        return [list(col) for col in zip(*sets)], n_sets, nbytes
+
+
+def soak(replay, seconds: float, torch):
+    """Replay step graphs for about `seconds` (untimed) so that the clock samples
+    taken next to the timed region are under load."""
+    t_end = time.perf_counter() + seconds
+    i = 0
+    while time.perf_counter() < t_end:
+        for _ in range(16):
+            replay(i)
+            i += 1
+        torch.cuda.synchronize()
+
+
+def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equalizer=0, refine=0,
+                   refine_fp64=0, pinned=None, breakdown=False, sampler=None, soak_s=0.0):
+    """K steps of PD then FD equalization; each step is captured once per rotating
+    input set as a CUDA graph (what a serving loop replays per frame) and the
+    timed region replays K graphs, bracketed by CUDA events on the replay stream.
+    Without refinement a step is the local-preprocessing kernel and the
+    fusion / equalization kernel per architecture (the latter launched with
+    programmatic dependent launch); with refinement it is ffeq_equalize per
+    architecture.  breakdown: a separate pass replays graphs of one kernel each
+    (that kernel alone, on the rotating input sets) for per-kernel device times.
+    Leaves the outputs of input set 0 in `outs`."""
+    torch, ffeq, dev = R.torch, R.ffeq, R.dev
+    B, U, C, n_sc, n_sym = shape
+    iters = LAMA_ITERS if equalizer == ffeq.LAMA else 0
+    archs = (ffeq.PD, ffeq.FD)
+    plans = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=R.PREC[precision], llr_bits=bits,
+                                      refine=refine, refine_fp64=refine_fp64, equalizer=equalizer,
+                                      lama_iters=iters) for a in archs}
+    nb = {a: ffeq.ffeq_workspace_size(x) for a, x in plans.items()}
+    ws = {a: torch.empty(max(nb[a], 16), dtype=torch.uint8, device=dev) for a in plans}
+    s2_shape = (n_sc, n_sym, U) if equalizer == ffeq.LAMA else (n_sc, U)
+    outs = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
+                    s2=torch.empty(s2_shape, dtype=torch.float32, device=dev),
+                    llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32, device=dev) if bits else None)
+            for a in archs}
+    n_sets = len(Hs)
+    stream = torch.cuda.current_stream(dev)
+    for a in plans:                  # launch shape chosen by timing (outside the timed region)
+        o = outs[a]
+        if pinned:
+            ffeq.ffeq_plan_set_tuning(plans[a], pinned[2 * a:2 * a + 2])
+        else:
+            # Over the rotating input sets: every timed call reads cold inputs, as the steps do.
+            ffeq.ffeq_plan_autotune_sets(plans[a], Hs, ys, N0, Es, o["z"], o["s2"], o["llr"], None, ws[a], nb[a],
+                                         stream, 2 * n_sets)
+    cap = torch.cuda.Stream(dev)
+    split = refine == 0
+
+    def launch(a, i, which):
+        o = outs[a]
+        if not split:
+            ffeq.ffeq_equalize(plans[a], Hs[i], ys[i], N0, Es, o["z"], o["s2"], o["llr"], None, ws[a], nb[a], cap)
+            return
+        if which in ("local", "step"):
+            ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], nb[a], cap)
+        if which in ("fuse", "step"):
+            ffeq.ffeq_fuse_equalize(plans[a], ws[a], nb[a], N0, Es, o["z"], o["s2"], o["llr"], None, cap)
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            fn()
+        return g
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cap):
+        for i in range(2):           # eager warm-up before capture
+            for a in archs:
+                launch(a, i % n_sets, "step")
+    cap.synchronize()
+    steps = [capture(lambda i=i: [launch(a, i, "step") for a in archs]) for i in range(n_sets)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler is not None:          # clocks: sampled from the load phase through the timed region
+        sampler.__enter__()
+    with torch.cuda.stream(cap):
+        if soak_s > 0:
+            soak(lambda i: steps[i % n_sets].replay(), soak_s, torch)
+        for i in range(warmup):
+            steps[i % n_sets].replay()
+    torch.cuda.synchronize()
+    R.barrier()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")      # profiling filter: ncu --nvtx --nvtx-include "timed/"
+    with torch.cuda.stream(cap):
+        start.record(cap)
+        for k in range(K):
+            steps[k % n_sets].replay()
+        end.record(cap)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.__exit__(None, None, None)
+    R.barrier()
+    ms = start.elapsed_time(end)
+    kern = {}
+    if breakdown and split:
+        Kb = max(8, min(K, 200))
+        for name, a, which in (("pd_local", ffeq.PD, "local"), ("pd_fuse", ffeq.PD, "fuse"),
+                               ("fd_local", ffeq.FD, "local"), ("fd_fuse", ffeq.FD, "fuse")):
+            gs = [capture(lambda i=i: launch(a, i, which)) for i in range(n_sets)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(cap):
+                for i in range(n_sets):
+                    gs[i].replay()
+                e0.record(cap)
+                for k in range(Kb):
+                    gs[k % n_sets].replay()
+                e1.record(cap)
+            torch.cuda.synchronize()
+            kern[name] = e0.elapsed_time(e1) / Kb
+            del gs
+    # Leave the outputs of input set 0 (the accuracy checks read them).
+    with torch.cuda.stream(cap):
+        steps[0].replay()
+    torch.cuda.synchronize()
+    del steps
+    if R.world > 1:
+        ms = max_over_ranks(ms, dev)
+    assert ffeq.ffeq_device_status() == 0
+    for a in outs:
+        assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
+    return dict(ms=ms, kern=kern, plans=plans, outs=outs)
+
+
+def uneven_line(R, K, warmup, precision, sampler=None):
     """One step = PD and FD equalization of 4096 instances of uneven size (U 4..32,
     B 64/128/256, C 1..16, 1..14 symbols, 5..20 dB, 16-QAM) through the batch
     ABI, replayed from one CUDA graph per input set; inputs rotate over sets
     larger than L2 in total."""
     import numpy as np
-    import torch
-    import torch.distributed as dist
-
-    from paper_1808_04473_gb300 import build as fbuild
-    from paper_1808_04473_gb300 import ffeq, synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-    fbuild.build()
-    ffeq.lib()
-    PREC = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3}
-    ps = synth.make_uneven(UNEVEN["n_inst"], seed=UNEVEN["seed"] + rank)
+    torch, ffeq, dev = R.torch, R.ffeq, R.dev
+    from paper_1808_04473_gb300 import synth
+    ps = synth.make_uneven(UNEVEN["n_inst"], seed=UNEVEN["seed"] + R.rank)
     specs = [(p.B, p.U, p.C, p.n_sc, p.n_sym, p.N0, p.Es) for p in ps]
     symbols = sum(p.U * p.n_sym * p.n_sc for p in ps)
     stream = torch.cuda.Stream(dev)
     runs = {}
     for a in (ffeq.PD, ffeq.FD):
-        cfg, inst = ffeq.pack_batch(specs, arch=a, precision=PREC[args.precision], llr_bits=4, with_info=False)
+        cfg, inst = ffeq.pack_batch(specs, arch=a, precision=R.PREC[precision], llr_bits=4, with_info=False)
         H = np.zeros(cfg.h_elems, np.complex64)
         y = np.zeros(cfg.y_elems, np.complex64)
         for p, it in zip(ps, inst):
@@ -317,16 +560,15 @@ def run_uneven(args, rank, world, local_rank):
                     ffeq.ffeq_batch_equalize(r["b"], r["Hs"][i], r["ys"][i], r["z"], r["s2"], r["llr"], None,
                                              r["ws"], r["nb"], stream)
             graphs.append(g)
-        clk = ClockSampler(local_rank)
-        clk.__enter__()
-        for i in range(args.warmup):
+        if sampler is not None:
+            sampler.__enter__()
+            soak(lambda i: graphs[i % n_sets].replay(), 1.0, torch)
+        for i in range(warmup):
             graphs[i % n_sets].replay()
         stream.synchronize()
-        if world > 1:
-            dist.barrier()
+        R.barrier()
         torch.cuda.synchronize()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        K = args.steps
         torch.cuda.nvtx.range_push("timed")
         start.record(stream)
         for k in range(K):
@@ -334,27 +576,27 @@ def run_uneven(args, rank, world, local_rank):
         end.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        clk.__exit__(None, None, None)
+        if sampler is not None:
+            sampler.__exit__(None, None, None)
     ms = start.elapsed_time(end)
-    if world > 1:
+    if R.world > 1:
         ms = max_over_ranks(ms, dev)
     assert ffeq.ffeq_device_status() == 0
-    value = job_rate(2 * symbols, world, K, ms)
+    value = job_rate(2 * symbols, R.world, K, ms)
     out_bytes = sum(r["z"].numel() * 8 + r["s2"].numel() * 4 + r["llr"].numel() * 4 for r in runs.values())
     alg = 2 * in_bytes + out_bytes
     hbm_peak, peak_src = _peaks()
     achieved = alg / (ms / K * 1e-3) / 1e9
     launches = sum(2 * ffeq.ffeq_batch_groups(r["b"]) for r in runs.values())   # kernels (the memset is not one)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": R.world, "steps": K, "warmup": warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32"}[args.precision],
-        "data": "synthetic",
+        "dtype": DTYPE[precision], "data": "synthetic",
         "config": {"workload": f"uneven batch: {UNEVEN['n_inst']} instances, U 4..32, B 64/128/256, C 1..16, "
                                "1..14 sym, 5..20 dB, 16-QAM, PD+FD, LLRs, CUDA-graph replay",
-                   "precision": args.precision,
+                   "precision": precision,
                    "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{R.world}"},
         "tuning": {("pd" if a == ffeq.PD else "fd"): ffeq.ffeq_batch_get_tuning(r["b"]) for a, r in runs.items()},
         "roofline": {"kernel": "whole step (memset + per-group gram_kernel and solve_fuse_kernel)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm_peak, "peak_source": f"{peak_src} (STREAM-style copy)",
@@ -362,13 +604,123 @@ def run_uneven(args, rank, world, local_rank):
                      "algorithmic_bytes_per_step": alg},
         "gpu_launches": launches * K,
     }
-    clocks = clk.summary()
-    if clocks:
-        line["clocks"] = clocks
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return line
+
+
+def run_correlated(R, K, warmup):
+    """The correlated workload: B=256, U=32, C=16 (S=16 < U), 3300 x 14, 64-QAM,
+    receive correlation r = 0.7, 15 dB.  One step = PD + FD.  Arms: FP32 and FP16x3
+    preprocessing without refinement, and each with one refinement step whose
+    residual is FP64 for the systems with condition estimate > 1e4 (the
+    configuration); each arm's errors against the FP64 oracle on 8 sampled
+    subcarriers."""
+    import numpy as np
+    from paper_1808_04473_gb300 import synth
+    w = CORRELATED
+    shape = (w["B"], w["U"], w["C"], w["n_sc"], w["n_sym"])
+    p = synth.make_problem(*shape, snr_db=w["snr_db"], bits=w["bits"], seed=3300 + R.rank, corr_r=w["corr_r"])
+    (Hs, ys), n_sets, in_bytes = R.rotating_sets(p.H, p.y)
+    idx = np.linspace(0, w["n_sc"] - 1, 8).astype(int)
+    symbols = 2 * w["U"] * w["n_sc"] * w["n_sym"]
+    arms = {}
+    for name, prec, refine in (("fp32", "fp32", 0), ("fp16x3", "fp16x3", 0),
+                               ("fp32+refine1(fp64>1e4)", "fp32", 1), ("fp16x3+refine1(fp64>1e4)", "fp16x3", 1)):
+        r = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=prec, bits=w["bits"], K=K, warmup=warmup,
+                           refine=refine, refine_fp64=1 if refine else 0)
+        arms[name] = {"value": job_rate(symbols, R.world, K, r["ms"]), "ms_per_step": r["ms"] / K, "steps": K,
+                      "error_vs_oracle": _accuracy(p, r["outs"], idx, (0, 1)) if R.rank == 0 else None}
+        del r
+    return {"workload": "B=256 U=32 C=16 3300sc x 14sym 64-QAM, exponential correlation r=0.7, 15dB, PD+FD, LLRs",
+            "unit": UNIT, "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
+            "error_metric": "[max over 8 sampled subcarriers of ||x - x_oracle|| / ||x_oracle||, max entry "
+                            "|x - x_oracle| / max(|x_oracle|, rms of its subcarrier)]",
+            "arms": arms}
+
+
+def run_training(R, K, warmup):
+    """One training step of the differentiable FD form: ffeq_fd_train_forward and
+    ffeq_fd_train_backward on B=128, U=16, C=8, 8 draws x 1024 subcarriers, QPSK,
+    10 dB (one symbol per draw), with per-cluster rho_c = N0/Es and fusion weights
+    1/C; the upstream gradient dL/dz is that of the MSE against the sent symbols,
+    formed once from the first forward pass (an input of the adjoint)."""
+    import numpy as np
+    torch, ffeq, dev = R.torch, R.ffeq, R.dev
+    from paper_1808_04473_gb300 import synth
+    w = TRAINING
+    B, U, C, n_sc, n_sym = w["B"], w["U"], w["C"], w["n_sc"], w["n_sym"]
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=w["snr_db"], bits=w["bits"], seed=1024 + R.rank)
+    (Hs, ys), n_sets, in_bytes = R.rotating_sets(p.H, p.y)
+    rho = torch.full((C,), p.N0 / p.Es, dtype=torch.float32, device=dev)
+    nu = torch.full((C, U), 1.0 / C, dtype=torch.float32, device=dev)
+    plan = ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=ffeq.FD)
+    nb = ffeq.ffeq_fd_train_workspace_size(plan)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    z = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev)
+    gH, gy = torch.empty_like(Hs[0]), torch.empty_like(ys[0])
+    grho, gnu = torch.empty_like(rho), torch.empty_like(nu)
+    cap = torch.cuda.Stream(dev)
+    with torch.cuda.stream(cap):
+        ffeq.ffeq_fd_train_forward(plan, Hs[0], ys[0], rho, nu, z, ws, nb, cap)
+    cap.synchronize()
+    s = torch.from_numpy(p.s.astype(np.complex64)).to(dev)
+    gz = (2.0 / z.numel()) * (z - s)
+
+    def step(i):
+        ffeq.ffeq_fd_train_forward(plan, Hs[i], ys[i], rho, nu, z, ws, nb, cap)
+        ffeq.ffeq_fd_train_backward(plan, Hs[i], ys[i], rho, nu, gz, gH, gy, grho, gnu, ws, nb, cap)
+
+    with torch.cuda.stream(cap):
+        for i in range(2):
+            step(i % n_sets)
+    cap.synchronize()
+    graphs = []
+    for i in range(n_sets):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            step(i)
+        graphs.append(g)
+    with torch.cuda.stream(cap):
+        for i in range(warmup):
+            graphs[i % n_sets].replay()
+    torch.cuda.synchronize()
+    R.barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(cap):
+        start.record(cap)
+        for k in range(K):
+            graphs[k % n_sets].replay()
+        end.record(cap)
+        graphs[0].replay()                   # leave the outputs of input set 0
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    if R.world > 1:
+        ms = max_over_ranks(ms, dev)
+    assert ffeq.ffeq_device_status() == 0
+    out = {"workload": "differentiable FD, B=128 U=16 C=8, 8 draws x 1024 subcarriers x 1 sym, QPSK, 10dB: "
+                       "forward + adjoint (dL/dH, dL/dy, dL/drho_c, dL/dnu)",
+           "value": job_rate(U * n_sc * n_sym, R.world, K, ms), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
+           "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)"}
+    # HBM roofline of the step: forward reads H, y and writes z; the adjoint reads
+    # H, y, dL/dz and writes dL/dH, dL/dy (complex64).
+    alg = n_sc * (24 * (B * U + B * n_sym) + 24 * U * n_sym)
+    hbm_peak, peak_src = _peaks()
+    achieved = alg / (ms / K * 1e-3) / 1e9
+    out["roofline"] = {"kernel": "whole step (contraction, train_forward, adjoint kernels)", "bound": "hbm",
+                       "achieved": achieved, "peak": hbm_peak, "peak_source": f"{peak_src} (STREAM-style copy)",
+                       "unit": "GB/s", "frac": achieved / hbm_peak, "algorithmic_bytes_per_step": alg}
+    if R.rank == 0:
+        from oracle import adjoint
+        idx = np.linspace(0, n_sc - 1, 8).astype(int)
+        r64 = np.full(C, p.N0 / p.Es)
+        n64 = np.full((C, U), 1.0 / C)
+        z0, _ = adjoint.fd_train_forward(p.H[idx], p.y[idx], r64.astype(np.float32).astype(np.float64),
+                                         n64.astype(np.float32).astype(np.float64))
+        gzs = gz[idx].cpu().numpy().astype(np.complex128)
+        oH, oy, _, _ = adjoint.fd_train_backward(p.H[idx], p.y[idx], r64.astype(np.float32).astype(np.float64),
+                                                 n64.astype(np.float32).astype(np.float64), gzs)
+        out["error_vs_oracle"] = {"z": _errors(z[idx].cpu().numpy(), z0), "gH": _errors(gH[idx].cpu().numpy(), oH),
+                                  "gy": _errors(gy[idx].cpu().numpy(), oy), "subcarriers": len(idx)}
+    return out
 
 
 def main():
@@ -378,15 +730,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ffeq", choices=["ffeq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline step only (no equalizer variants, correlated, training or uneven lines)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"],
+    ap.add_argument("--precision", default="bf16x3", choices=PRECISIONS,
                     help="arithmetic of the local preprocessing (solve and fusion are FP32)")
     ap.add_argument("--tuning", default=None,
                     help="pin the contraction shapes instead of autotuning: PD_SHAPE,PD_STAGES,FD_SHAPE,FD_STAGES "
                          "(values of ffeq_plan_set_tuning; for reproducible profiles)")
-    ap.add_argument("--workload", default="ofdm", choices=["ofdm", "uneven"],
-                    help="ofdm: the headline B=256 U=16 C=8 1200x14 step; uneven: 4096 instances of mixed "
-                         "size per step (uneven-batch ABI, CUDA-graph replay)")
+    ap.add_argument("--workload", default="ofdm", choices=["ofdm", "uneven", "correlated", "training"],
+                    help="ofdm: the headline B=256 U=16 C=8 1200x14 step (other workloads as extra keys); "
+                         "uneven / correlated / training: that workload's line alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -398,180 +752,72 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "uneven":
-        run_uneven(args, rank, world, local_rank)
+    R = Runner(args, rank, world, local_rank)
+    if args.workload != "ofdm":
+        if args.workload == "uneven":
+            line = uneven_line(R, args.steps, args.warmup, args.precision, ClockSampler(local_rank))
+        elif args.workload == "correlated":
+            line = run_correlated(R, args.steps, args.warmup)
+        else:
+            line = run_training(R, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
 
     import numpy as np
-    import torch
-    import torch.distributed as dist
-
-    from paper_1808_04473_gb300 import build as fbuild
-    from paper_1808_04473_gb300 import ffeq, synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-    fbuild.build()
-    ffeq.lib()
+    torch, ffeq, dev = R.torch, R.ffeq, R.dev
+    from paper_1808_04473_gb300 import synth
 
     w = WORKLOAD
     B, U, C, n_sc, n_sym, bits = w["B"], w["U"], w["C"], w["n_sc"], w["n_sym"], w["bits"]
+    shape = (B, U, C, n_sc, n_sym)
     p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=w["snr_db"], bits=bits, seed=12345 + rank)
-    in_bytes = p.H.nbytes + p.y.nbytes
-    n_sets = max(2, -(-4 * L2_BYTES // in_bytes))          # rotate inputs: working set > 4x L2
-    H0 = torch.from_numpy(p.H).to(dev)
-    y0 = torch.from_numpy(p.y).to(dev)
-    Hs = [H0] + [H0.clone() for _ in range(n_sets - 1)]
-    ys = [y0] + [y0.clone() for _ in range(n_sets - 1)]
-
-    PREC = {"fp32": ffeq.FP32, "tf32x3": ffeq.TF32X3, "bf16x3": ffeq.BF16X3}
-    outs = {a: dict(z=torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
-                    s2=torch.empty((n_sc, U), dtype=torch.float32, device=dev),
-                    llr=torch.empty((n_sc, n_sym, U, bits), dtype=torch.float32, device=dev))
-            for a in (ffeq.PD, ffeq.FD)}
-    stream = torch.cuda.current_stream(dev)
-
-    def make_plans(precision, equalizer=0):
-        iters = LAMA_ITERS if equalizer == ffeq.LAMA else 0
-        pl = {a: ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=a, precision=PREC[precision], llr_bits=bits,
-                                       equalizer=equalizer, lama_iters=iters)
-              for a in (ffeq.PD, ffeq.FD)}
-        nb = {a: ffeq.ffeq_workspace_size(x) for a, x in pl.items()}
-        return pl, nb, {a: torch.empty(nb[a], dtype=torch.uint8, device=dev) for a in pl}
-
-    def timed(precision, K, warmup, sampler=None, equalizer=0):
-        """K steps; one step = for PD then FD, the local preprocessing kernel and the
-        fusion / equalization kernel (the latter launched with programmatic dependent
-        launch).  Each step is captured once per rotating input set as a CUDA graph
-        (what a serving loop replays per frame) and replayed; CUDA events on the
-        replay stream bracket the K replays only.  A separate pass replays graphs of
-        one kernel each (that kernel alone, on the rotating input sets) for the
-        per-kernel device times of the breakdown."""
-        plans, ws_bytes, ws = make_plans(precision, equalizer)
-        pinned = [int(v) for v in args.tuning.split(",")] if args.tuning else None
-        for a in plans:                  # launch shape chosen by timing (outside the timed region)
-            o = outs[a]
-            if pinned and precision == args.precision and equalizer == 0:
-                ffeq.ffeq_plan_set_tuning(plans[a], pinned[2 * a:2 * a + 2])
-            else:
-                # Over the rotating input sets: every timed call reads cold inputs, as the steps do.
-                ffeq.ffeq_plan_autotune_sets(plans[a], Hs, ys, p.N0, p.Es, o["z"], o["s2"], o["llr"], None, ws[a],
-                                             ws_bytes[a], stream, 2 * n_sets)
-        cap = torch.cuda.Stream(dev)
-
-        def launch(a, i, which):
-            o = outs[a]
-            if which in ("local", "step"):
-                ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], ws_bytes[a], cap)
-            if which in ("fuse", "step"):
-                ffeq.ffeq_fuse_equalize(plans[a], ws[a], ws_bytes[a], p.N0, p.Es, o["z"], o["s2"], o["llr"],
-                                        None, cap)
-
-        def capture(fn):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=cap):
-                fn()
-            return g
-
-        torch.cuda.synchronize()
-        with torch.cuda.stream(cap):
-            for i in range(2):           # eager warm-up before capture
-                for a in (ffeq.PD, ffeq.FD):
-                    launch(a, i, "step")
-        cap.synchronize()
-        steps = [capture(lambda i=i: [launch(a, i, "step") for a in (ffeq.PD, ffeq.FD)]) for i in range(n_sets)]
-        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if sampler is not None:          # clocks: sampled from the warm-up through the timed region
-            sampler.__enter__()
-        with torch.cuda.stream(cap):
-            for i in range(warmup):
-                steps[i % n_sets].replay()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")      # profiling filter: ncu --nvtx --nvtx-include "timed/"
-        with torch.cuda.stream(cap):
-            start.record(cap)
-            for k in range(K):
-                steps[k % n_sets].replay()
-            end.record(cap)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        if sampler is not None:
-            sampler.__exit__(None, None, None)
-        if world > 1:
-            dist.barrier()
-        ms = start.elapsed_time(end)
-        # Per-kernel breakdown (not part of the timed region): one kernel per graph.
-        kern = {}
-        Kb = max(8, min(K, 200))
-        for name, a, which in (("pd_local", ffeq.PD, "local"), ("pd_fuse", ffeq.PD, "fuse"),
-                               ("fd_local", ffeq.FD, "local"), ("fd_fuse", ffeq.FD, "fuse")):
-            gs = [capture(lambda i=i: launch(a, i, which)) for i in range(n_sets)]
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(cap):
-                for i in range(n_sets):
-                    gs[i].replay()
-                e0.record(cap)
-                for k in range(Kb):
-                    gs[k % n_sets].replay()
-                e1.record(cap)
-            torch.cuda.synchronize()
-            kern[name] = e0.elapsed_time(e1) / Kb
-            del gs
-        # Leave the outputs of a full step (the accuracy check reads them).
-        with torch.cuda.stream(cap):
-            steps[0].replay()
-        torch.cuda.synchronize()
-        del steps
-        if world > 1:
-            ms = max_over_ranks(ms, dev)
-        assert ffeq.ffeq_device_status() == 0
-        for a in outs:
-            assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
-        return ms, kern, plans
+    (Hs, ys), n_sets, in_bytes = R.rotating_sets(p.H, p.y)
+    pinned = [int(v) for v in args.tuning.split(",")] if args.tuning else None
+    idx = np.linspace(0, n_sc - 1, 12).astype(int)
+    do_cpu = rank == 0 and not args.no_cpu_baseline
 
     K = args.steps
     clk = ClockSampler(local_rank)
-    elapsed_ms, kern, plans = timed(args.precision, K, args.warmup, clk)
+    head = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=args.precision, bits=bits, K=K,
+                          warmup=args.warmup, pinned=pinned, breakdown=True, sampler=clk, soak_s=1.0)
+    elapsed_ms, kern, plans = head["ms"], head["kern"], head["plans"]
+    accuracy = _accuracy(p, head["outs"], idx, (0, 1)) if do_cpu else None
+    if accuracy is not None:
+        accuracy["subcarriers"] = len(idx)
+        accuracy["metric"] = ("[max over sampled subcarriers of ||x - x_oracle|| / ||x_oracle||, max entry "
+                              "|x - x_oracle| / max(|x_oracle|, rms of its subcarrier)]")
+    symbols_per_step = 2 * U * n_sc * n_sym
+    value = job_rate(symbols_per_step, world, K, elapsed_ms)
+    del head
+
     fp32_cmp = None
     if args.precision != "fp32":
         Kc = max(5, K // 4)
-        ms32, kern32, _ = timed("fp32", Kc, args.warmup)
-        fp32_cmp = {"value": world * 2 * U * n_sc * n_sym * Kc / (ms32 * 1e-3), "ms_per_step": ms32 / Kc,
-                    "steps": Kc, "kernels_ms": kern32}
-
-    symbols_per_step = 2 * U * n_sc * n_sym
-    value = job_rate(symbols_per_step, world, K, elapsed_ms)
-
-    # ---- accuracy of the timed outputs against the FP64 oracle on sampled subcarriers
-    accuracy = None
-    if rank == 0 and not args.no_cpu_baseline:
-        from oracle import lmmse
-        idx = np.linspace(0, n_sc - 1, 12).astype(int)
-        accuracy = {"subcarriers": len(idx), "metric": "max over sampled subcarriers of ||x - x_oracle|| / ||x_oracle||"}
-        for a, f in ((ffeq.PD, lmmse.equalize_pd), (ffeq.FD, lmmse.equalize_fd)):
-            o = f(p.H[idx], p.y[idx], float(np.float32(p.N0)), p.Es, C, "unbiased")
-            zg = outs[a]["z"][idx].cpu().numpy().reshape(len(idx), -1)
-            sg = outs[a]["s2"][idx].cpu().numpy().reshape(len(idx), -1)
-            ez = np.linalg.norm(zg - o["z"].reshape(len(idx), -1), axis=1) / np.linalg.norm(o["z"].reshape(len(idx), -1), axis=1)
-            es = np.linalg.norm(sg - o["sigma2"].reshape(len(idx), -1), axis=1) / np.linalg.norm(o["sigma2"].reshape(len(idx), -1), axis=1)
-            accuracy["pd" if a == ffeq.PD else "fd"] = {"z": float(ez.max()), "sigma2": float(es.max())}
+        r32 = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision="fp32", bits=bits, K=Kc, warmup=args.warmup,
+                             breakdown=True)
+        fp32_cmp = {"value": job_rate(symbols_per_step, world, Kc, r32["ms"]), "ms_per_step": r32["ms"] / Kc,
+                    "steps": Kc, "kernels_ms": r32["kern"],
+                    "error_vs_oracle": _accuracy(p, r32["outs"], idx, (0, 1)) if do_cpu else None}
+        del r32
 
     # ---- the same step with the ZF and MRC equalizers of Sec. III-A and LAMA (Sec. III-B,
     # LAMA_ITERS iterations) in place of L-MMSE (same contraction)
     variants = {}
-    if not args.tuning:
+    if not args.tuning and not args.no_extras:
         Kv = max(5, K // 4)
         for name, eq in (("zf", ffeq.ZF), ("mrc", ffeq.MRC), ("lama", ffeq.LAMA)):
-            msv, kernv, _ = timed(args.precision, Kv, args.warmup, equalizer=eq)
-            variants[name] = {"value": world * symbols_per_step * Kv / (msv * 1e-3), "ms_per_step": msv / Kv,
-                              "steps": Kv, "kernels_ms": kernv}
+            rv = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=args.precision, bits=bits, K=Kv,
+                                warmup=args.warmup, equalizer=eq, breakdown=True)
+            variants[name] = {"value": job_rate(symbols_per_step, world, Kv, rv["ms"]), "ms_per_step": rv["ms"] / Kv,
+                              "steps": Kv, "kernels_ms": rv["kern"]}
+            del rv
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
+    stream = torch.cuda.current_stream(dev)
     Hh = torch.from_numpy(p.H).pin_memory()
     yh = torch.from_numpy(p.y).pin_memory()
     stage_bytes = max(ffeq.ffeq_host_staging_size(pl) for pl in plans.values())
@@ -597,7 +843,17 @@ def main():
     e2e_s = (time.perf_counter() - t0) / Ke
     e2e_value = world * symbols_per_step / e2e_s
     h2d = 2 * in_bytes
-    d2h = 2 * (outs[0]["z"].numel() * 8 + outs[0]["s2"].numel() * 4 + outs[0]["llr"].numel() * 4)
+    d2h = 2 * (n_sc * n_sym * U * 8 + n_sc * U * 4 + n_sc * n_sym * U * bits * 4)
+
+    # ---- the other workloads (extra keys)
+    extras = {}
+    if world == 1 and not args.no_extras and not args.tuning:
+        Kx = max(5, min(K // 10, 100))
+        extras["correlated"] = run_correlated(R, Kx, args.warmup)
+        extras["training"] = run_training(R, max(5, min(K // 10, 200)), args.warmup)
+        u = uneven_line(R, max(5, min(K // 10, 200)), args.warmup, args.precision)
+        extras["uneven"] = {k: u[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "roofline",
+                                              "tuning")}
 
     # ---- roofline of the dominant kernel (and of the Gram stage)
     hbm_peak, peak_src = _peaks()
@@ -626,9 +882,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_SYMBOLS_PER_S,
-        "dtype": {"fp32": "f32", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32"}[args.precision], "data": "synthetic",
+        "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": "B=256 U=16 C=8 1200sc x 14sym 16-QAM Rayleigh 10dB, PD+FD, LLRs",
-                   "precision": args.precision, "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
+                   "precision": args.precision,
+                   "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
                    "parallelism": f"replicas x{world}"},
         "kernels_ms": kern,
         "tuning": {("pd" if a == ffeq.PD else "fd"): list(ffeq.ffeq_plan_get_tuning(pl)) for a, pl in plans.items()},
@@ -642,17 +899,25 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * K,
     }
+    line.update(extras)
     clocks = clk.summary()
     if clocks:
+        clocks["window"] = "1 s of step replays directly before the timed region, then the timed region"
         line["clocks"] = clocks
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, n, cores = _time_oracle_all_cores(args.cpu_seconds)
+    if do_cpu and world == 1:
+        r, n, cores = _time_cpu_all_cores("oracle", args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{n} subcarriers of the same workload, PD+FD, one single-threaded "
-                                          f"process per core for ~{args.cpu_seconds:.0f} s"}
+                                "sample": f"{n} subcarriers of the same workload, PD+FD with LLRs, one "
+                                          f"single-threaded process per core for ~{args.cpu_seconds:.0f} s"}
+        r2, n2, cores2 = _time_cpu_all_cores("numpy32", max(2.0, args.cpu_seconds / 3))
+        line["cpu_baseline_numpy_fp32"] = {
+            "value": r2, "unit": UNIT, "cores": cores2, "kind": "batched FP32 NumPy (Cholesky / solve)",
+            "sample": f"{n2} subcarriers of the same workload, PD+FD z and sigma^2 (no LLRs), one single-threaded "
+                      f"process per core for ~{max(2.0, args.cpu_seconds / 3):.0f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 

@@ -102,10 +102,14 @@ typedef enum { FFEQ_UNBIASED = 0, FFEQ_LITERAL = 1 } ffeq_estimate;
  *               |G_uv|^2) / G_uu^2 (no inversion; info is always 0).
  * ZF and MRC estimates are unbiased, so the estimate field does not apply; FD
  * fuses the per-cluster pairs with the optimal weights of Lemma 1 as for
- * L-MMSE.  A user that a cluster cannot see (G_c,uu = 0) gets MRC weight 0.
- * With N0 == 0, ZF weights take the N0 -> 0 limit (proportional to
- * 1/[G_c^{-1}]_uu) and so do MRC weights for U == 1 (proportional to G_c,uu);
- * for U > 1 the MRC variance is the interference term alone.
+ * L-MMSE; PD-MRC is z = diag(G)^{-1} y^MRC with no fusion step.  A user that a
+ * cluster cannot see (G_c,uu = 0) gets MRC weight 0.  With N0 == 0 the weights
+ * are those of the N0 -> 0 limit of Lemma 1's: for ZF proportional to
+ * 1/[G_c^{-1}]_uu (every variance is 0); for MRC, per user, the clusters where
+ * the user has no interference (sum_{v != u} |G_c,uv|^2 = 0: variance exactly 0)
+ * share all the weight in proportion to G_c,uu and the fused variance is 0,
+ * while a user with interference in every cluster keeps the ordinary weights
+ * (its variance is the interference term alone).
  *   FFEQ_LAMA   Algorithm 1 (LAMA-PD) on (G, y^MRC), or per cluster on
  *               (G_c, y_c^MRC) and fused with the weights of Lemma 1 (LAMA-FD),
  *               for lama_iters iterations: z^T and sigma^2 = N0 + beta phi^T of
@@ -130,13 +134,17 @@ typedef struct {
   int precision;   /* ffeq_precision */
   int estimate;    /* ffeq_estimate */
   int llr_bits;    /* 0 (no LLRs), 2, 4, 6 or 8 */
-  int refine;      /* 0, 1 or 2: steps of iterative refinement from the inputs:
+  int refine;      /* 0..4: steps of iterative refinement from the inputs:
                     * r_c = H_c^H (y_c - H_c x_c) - rho x_c, x_c += A_c r_c (with
                     * A_c the solve's inverse), and one Newton-Schulz step for the
                     * inverse, A_c <- 2 A_c - A_c^H (G_c + rho I) A_c, whose
                     * diagonal the unbiasing and the fusion use.  Each step
-                    * shrinks the error of the mixed-precision preprocessing by
-                    * about kappa(G_c + rho I) * 2^-16 (BF16X3).  Costs a second
+                    * multiplies the error by about the current relative error
+                    * of the inverse, which the Newton-Schulz step squares:
+                    * from the kappa(G_c + rho I) * 2^-16 (BF16X3) or 2^-21
+                    * (FP16X3) of the preprocessing, one step suffices while
+                    * that is far below 1, more steps where it nears 1
+                    * (kappa ~ 1e5 for FP16X3).  Costs a second
                     * read of H and y and a larger workspace; only ffeq_equalize
                     * (and the entry points built on it) support it:
                     * ffeq_fuse_equalize returns FFEQ_ERR_UNSUPPORTED. */
@@ -312,8 +320,10 @@ ffeq_status ffeq_equalize_host(const ffeq_plan* plan, const void* H_host, const 
  * uses a 64 MiB array compiled into the library, one per device, which every
  * GPU that loads the library holds until the process exits.  Problems whose
  * ffeq_workspace_size exceeds 64 MiB return FFEQ_ERR_UNSUPPORTED.  The first
- * call on a device looks up that device's array address (cudaGetSymbolAddress)
- * and so must come before any stream capture on that device.  All calls share
+ * call in each CUDA context (a device's primary context, or any other context
+ * made current) looks up the array's address there (cudaGetSymbolAddress) and
+ * caches it under the context's unique ID, so that first call must come before
+ * any stream capture in that context.  All calls share
  * the array: calls that overlap on the GPU (other streams, other threads) race
  * and must be serialized by the caller; nothing in it needs clearing between
  * calls.  It calls no cudaMalloc, cudaFree or allocating library routine. */

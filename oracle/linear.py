@@ -15,15 +15,20 @@ Both estimates are unbiased (the coefficient of ``s_u`` in ``z_u`` is 1), so the
 fusion uses them as they are.  The fused variance is Thm. 3's
 ``(sum_c sigma_c^-2)^-1``; for ZF it is the exact MSE given ``H`` (the cluster
 errors are noise on disjoint antennas), for MRC it is the paper's model value
-(the clusters' interference terms share ``s``).  Readings (shared with the kernels): a user a
-cluster cannot see (``G_uu = 0``) gets weight 0 (infinite variance); for
-``N0 = 0`` every ZF variance is 0 and the fusion weights are taken in the limit
-``N0 -> 0`` (proportional to ``1 / [G_c^{-1}]_uu``); MRC variances with
-``N0 = 0`` are zero only without interference (``U = 1``), then the weights are
-proportional to ``G_uu``.  Outside that limit a variance of exactly 0 (``N0 = 0``
-and a user with no interference in that cluster, a set of channels of measure
-zero) leaves the weight ``1 / sigma^2`` undefined: such a pair gets weight 0,
-in PD (one pair through the same rule) as in FD.  ZF needs ``G`` (FD: every ``G_c``) positive definite;
+(the clusters' interference terms share ``s``).  Readings (shared with the
+kernels): a user a cluster cannot see (``G_uu = 0``) gets weight 0 (infinite
+variance).  PD-MRC is ``z = diag(G)^{-1} y^MRC`` with its variance and no
+fusion step.  A variance of exactly 0 happens only with ``N0 = 0``: for ZF
+always, for MRC when the user has no interference in that cluster
+(``G_uv = 0`` for every ``v != u``: a single user, or channels of disjoint
+support).  The weights are then those of the limit ``N0 -> 0`` of Lemma 1's
+weights ``sigma_c^-2 / sum sigma^-2``: ZF ``sigma_c^2 = N0 [G_c^{-1}]_uu``
+gives weights proportional to ``1 / [G_c^{-1}]_uu``; MRC
+``sigma_c^2 = (N0 G_uu + Es I_c) / G_uu^2`` (``I_c`` the interference sum) is
+``~ N0 / G_uu`` where ``I_c = 0`` and stays positive elsewhere, so per user the
+zero-interference clusters share all the weight in proportion to ``G_c,uu`` and
+the fused variance is 0; a user with interference in every cluster keeps the
+ordinary weights.  ZF needs ``G`` (FD: every ``G_c``) positive definite;
 ``info`` is the first non-positive leading minor as for L-MMSE (parity pinned
 for clusters of at least ``U`` antennas).
 """
@@ -33,12 +38,12 @@ import numpy as np
 
 from .lmmse import _as_math, first_nonpositive_minor, local_preprocess, optimal_fusion, partition
 
-__all__ = ["mrc_unit", "zf_unit", "equalize_pd_linear", "equalize_fd_linear"]
+__all__ = ["mrc_unit", "mrc_fusion", "zf_unit", "equalize_pd_linear", "equalize_fd_linear"]
 
 
 def mrc_unit(G: np.ndarray, yMR: np.ndarray, N0: float, Es: float):
-    """MRC on ``(G, y^MRC)``: ``(z, sigma2, weight_var)``; ``weight_var`` is what
-    the fusion weights use when ``sigma2`` vanishes (``N0 = 0``, no interference)."""
+    """MRC on ``(G, y^MRC)`` (Sec. III-A): ``(z, sigma2, g)`` with ``g = diag(G)``
+    (what the ``N0 -> 0`` limit weights use)."""
     U = G.shape[0]
     g = np.real(np.diag(G))
     seen = g > 0
@@ -48,8 +53,23 @@ def mrc_unit(G: np.ndarray, yMR: np.ndarray, N0: float, Es: float):
     np.fill_diagonal(E, 0.0)     # [diag(G)^{-1} G]_uu = 1 exactly; (1/g) g - 1 would leave rounding
     sigma2 = np.real(np.diag(Dinv @ G @ Dinv.conj().T * N0 + E @ E.conj().T * Es))
     sigma2 = np.where(seen, sigma2, np.inf)
-    weight_var = np.where(seen, 1.0 / np.where(seen, g, 1.0), np.inf)
-    return z, sigma2, weight_var
+    return z, sigma2, g
+
+
+def mrc_fusion(z_c: np.ndarray, sigma2_c: np.ndarray, g_c: np.ndarray):
+    """Lemma 1 fusion of MRC pairs ``z_c [C][U][n_sym]``, ``sigma2_c [C][U]``,
+    ``g_c = G_c,uu [C][U]``, user by user: where some seen cluster has variance
+    exactly 0 (``N0 = 0``, no interference there) the weights are the limit ones,
+    ``g_c / sum g`` over those clusters, and the fused variance is 0; otherwise
+    the ordinary optimal fusion (Eq. opt_fusion, Thm. 3)."""
+    z, s2, nu = optimal_fusion(z_c, sigma2_c)
+    zero = (g_c > 0) & (sigma2_c == 0.0)
+    for u in np.nonzero(zero.any(axis=0))[0]:
+        w = np.where(zero[:, u], g_c[:, u], 0.0)
+        nu[:, u] = w / w.sum()
+        z[u] = np.einsum("c,cn->n", nu[:, u], z_c[:, u])
+        s2[u] = 0.0
+    return z, s2, nu
 
 
 def zf_unit(G: np.ndarray, yMR: np.ndarray, N0: float, Es: float):
@@ -90,12 +110,7 @@ def equalize_pd_linear(H, y, N0: float, Es: float, C: int, equalizer: str, clust
         Hm, Ym = _as_math(H, y, k)
         G, yMR = _pd_gram(Hm, Ym, bounds)
         if equalizer == "mrc":
-            # One estimate passed through the fusion rule, so that PD and FD at
-            # C = 1 agree in the degenerate cases too (a variance of exactly 0
-            # outside the N0 -> 0 limit carries no weight).
-            zk, s2k, wv = mrc_unit(G, yMR, N0, Es)
-            limit = N0 == 0.0 and U == 1
-            zk, s2k, _ = optimal_fusion(zk[None], s2k[None], weight_var=wv[None] if limit else None)
+            zk, s2k, _ = mrc_unit(G, yMR, N0, Es)   # the paper's z = diag(G)^{-1} y^MRC, no fusion
         else:
             zk, s2k, _, inf = zf_unit(G, yMR, N0, Es)
             info[k, 0] = inf
@@ -117,11 +132,12 @@ def equalize_fd_linear(H, y, N0: float, Es: float, C: int, equalizer: str, clust
         Hm, Ym = _as_math(H, y, k)
         zc = np.zeros((C, U, n_sym), np.complex128)
         s2c = np.zeros((C, U))
+        gc = np.zeros((C, U))
         wvar = np.zeros((C, U))
         for c, (b0, b1) in enumerate(bounds):
             Gc, yc = local_preprocess(Hm[b0:b1], Ym[b0:b1])
             if equalizer == "mrc":
-                zc[c], s2c[c], wvar[c] = mrc_unit(Gc, yc, N0, Es)
+                zc[c], s2c[c], gc[c] = mrc_unit(Gc, yc, N0, Es)
             else:
                 zc[c], s2c[c], A, info[k, c] = zf_unit(Gc, yc, N0, Es)
                 if not info[k, c]:
@@ -129,9 +145,10 @@ def equalize_fd_linear(H, y, N0: float, Es: float, C: int, equalizer: str, clust
         if info[k].any():
             z[k], s2[k] = np.nan, np.nan
             continue
-        # Vanishing variances (N0 = 0: ZF always, MRC without interference): the
-        # weights of the limit N0 -> 0.
-        limit = N0 == 0.0 and (equalizer == "zf" or U == 1)
-        zf_, s2f, _ = optimal_fusion(zc, s2c, weight_var=wvar if limit else None)
+        if equalizer == "mrc":
+            zf_, s2f, _ = mrc_fusion(zc, s2c, gc)
+        else:
+            # N0 = 0: every ZF variance vanishes; the weights of the limit N0 -> 0.
+            zf_, s2f, _ = optimal_fusion(zc, s2c, weight_var=wvar if N0 == 0.0 else None)
         z[k], s2[k] = zf_.T, s2f
     return {"z": z, "sigma2": s2, "info": info}

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <cuda.h>
 #include <new>
 
 #include "ffeq.h"
@@ -35,6 +36,54 @@ ffeq_status cuda_fail(cudaError_t e) {
 
 namespace ffeq {
 int record_cuda_error(cudaError_t e) { return static_cast<int>(cuda_fail(e)); }
+
+unsigned long long current_context_id() {
+  // cuCtxGetCurrent / cuCtxGetId from the driver, looked up once through the
+  // runtime (no link-time dependency on the driver library).
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+  static const GetCurrentFn get_current = []() -> GetCurrentFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<GetCurrentFn>(f);
+    return nullptr;
+  }();
+  static const GetIdFn get_id = []() -> GetIdFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<GetIdFn>(f);
+    return nullptr;
+  }();
+  CUcontext ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  unsigned long long id = 0;
+  return get_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
+
+void* cached_symbol_address(SymbolAddressCache& cache, cudaError_t (*fetch)(void**), cudaError_t* err) {
+  *err = cudaSuccess;
+  unsigned long long id = current_context_id();
+  std::lock_guard<std::mutex> lock(cache.m);
+  for (int i = 0; i < cache.n && id != 0; ++i)
+    if (cache.id[i] == id) return cache.ptr[i];
+  void* p = nullptr;
+  const cudaError_t e = fetch(&p);
+  if (e != cudaSuccess || !p) {
+    *err = e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    return nullptr;
+  }
+  if (id == 0) id = current_context_id();   // the lookup made the primary context current
+  if (id != 0) {
+    const int slot = cache.n < SymbolAddressCache::kEntries ? cache.n++ : (cache.next++ % SymbolAddressCache::kEntries);
+    cache.id[slot] = id;
+    cache.ptr[slot] = p;
+  }
+  return p;
+}
 }  // namespace ffeq
 
 namespace {
@@ -116,7 +165,7 @@ ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, co
   if (p->estimate != FFEQ_UNBIASED && p->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
   if (p->llr_bits != 0 && p->llr_bits != 2 && p->llr_bits != 4 && p->llr_bits != 6 && p->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
-  if (p->refine < 0 || p->refine > 2) return FFEQ_ERR_INVALID_ARG;
+  if (p->refine < 0 || p->refine > 4) return FFEQ_ERR_INVALID_ARG;
   if (p->refine_fp64 < 0 || p->refine_fp64 > 2 || (p->refine_fp64 > 0 && p->refine == 0))
     return FFEQ_ERR_INVALID_ARG;
   if (p->equalizer != FFEQ_LMMSE && p->equalizer != FFEQ_ZF && p->equalizer != FFEQ_MRC &&

@@ -189,15 +189,11 @@ cudaError_t launch_gram_fp32(const GramParams& p, cudaStream_t stream) {
 }
 
 int* device_status_ptr() {
-  static int* cached[64] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return nullptr;
-  if (!cached[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_device_status) != cudaSuccess) return nullptr;
-    cached[dev] = static_cast<int*>(ptr);
-  }
-  return cached[dev];
+  static SymbolAddressCache cache;
+  cudaError_t e = cudaSuccess;
+  void* p = cached_symbol_address(
+      cache, [](void** out) { return cudaGetSymbolAddress(out, g_device_status); }, &e);
+  return static_cast<int*>(p);
 }
 
 }  // namespace ffeq

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cuda_runtime.h>
+#include <mutex>
 
 #include "ffeq.h"
 
@@ -201,7 +202,26 @@ int lama_symbols_per_cta(int U, int Ceff, int n_sym);
 cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream);
 size_t solve_batch_smem_bytes(int UP, int lpr, int threads);
 
-// Address of the device status word on the current device (nullptr on error).
+// Device addresses of a __device__ symbol, one per CUDA context (a context's
+// module holds its own copy; a context destroyed by cudaDeviceReset and the one
+// created after it are different contexts).  Keyed by the driver's context ID,
+// which is unique for the life of the process, so a stale entry can never match.
+struct SymbolAddressCache {
+  static constexpr int kEntries = 16;
+  std::mutex m;
+  unsigned long long id[kEntries] = {};
+  void* ptr[kEntries] = {};
+  int n = 0, next = 0;
+};
+// ID of the calling thread's current context, 0 when none is current.
+unsigned long long current_context_id();
+// The symbol's address in the current context: the cached one when this context
+// looked it up before, else fetch(&ptr) (a cudaGetSymbolAddress of the symbol,
+// which also makes the device's primary context current when none is), cached
+// under the context's ID.  nullptr with *err set on failure.
+void* cached_symbol_address(SymbolAddressCache& cache, cudaError_t (*fetch)(void**), cudaError_t* err);
+
+// Address of the device status word in the current context (nullptr on error).
 int* device_status_ptr();
 // Remember the CUDA error string for ffeq_last_cuda_error(); returns FFEQ_ERR_CUDA.
 int record_cuda_error(cudaError_t e);

@@ -13,11 +13,12 @@
 // The array is a file-scope static __device__ object of kScratchBytes: every
 // GPU that loads this library holds it until the process exits.  Host code
 // cannot use the name `g_scratch` as a device pointer (on the host it names a
-// stand-in object); its device address is fetched with cudaGetSymbolAddress
-// once per device, with that device current, on the first call made on it.
-#include <atomic>
+// stand-in object); its device address is fetched with cudaGetSymbolAddress,
+// with the device current, on the first call made in each CUDA context (the
+// primary context of a device, a context created after cudaDeviceReset, or a
+// context the caller made current through the driver API), and cached under
+// that context's unique ID.
 #include <cstdint>
-#include <mutex>
 
 #include "ffeq.h"
 #include "ffeq_internal.h"
@@ -25,25 +26,10 @@
 namespace {
 
 constexpr size_t kScratchBytes = size_t(64) << 20;   // 64 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::atomic<void*> g_scratch_ptr[kMaxDevices];
-std::mutex g_setup_mutex;
-
-// Device address of g_scratch on the current device; nullptr on failure.
-void* scratch_address(int dev) {
-  void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
-  if (p) return p;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  p = g_scratch_ptr[dev].load(std::memory_order_relaxed);
-  if (p) return p;
-  void* addr = nullptr;
-  if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || addr == nullptr) return nullptr;
-  g_scratch_ptr[dev].store(addr, std::memory_order_release);
-  return addr;
-}
+ffeq::SymbolAddressCache g_scratch_cache;
 
 }  // namespace
 
@@ -55,10 +41,10 @@ extern "C" ffeq_status ffeq_equalize_noalloc(const ffeq_plan* plan, const void* 
   ffeq_status r = ffeq_workspace_size(plan, &need);
   if (r != FFEQ_OK) return r;
   if (need > kScratchBytes) return FFEQ_ERR_UNSUPPORTED;   // problem too large for the fixed array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FFEQ_ERR_CUDA;
-  void* ws = scratch_address(dev);
-  if (!ws) return FFEQ_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  void* ws = ffeq::cached_symbol_address(
+      g_scratch_cache, [](void** out) { return cudaGetSymbolAddress(out, g_scratch); }, &e);
+  if (!ws) return static_cast<ffeq_status>(ffeq::record_cuda_error(e));
   // Nothing in the array needs clearing: every workspace element the solve
   // kernel reads is written by the contraction kernel earlier in this call.
   return ffeq_equalize(plan, H, y, N0, Es, z, sigma2, llr, info, ws, kScratchBytes, stream);

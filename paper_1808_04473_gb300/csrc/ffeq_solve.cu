@@ -149,9 +149,12 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
 // sums the Ceff fusion numerators and denominators of its subcarrier and writes
 // z = num / den, sigma^2 = s2_scale / den (s2_scale = N0 for the solve, whose
 // denominators are g / A_uu; Es for MRC, whose are Es / sigma_c^2) and the LLRs.
+// zflag [spc][UP] (MRC, or nullptr): users fused with the N0 -> 0 limit weights,
+// whose variance is 0.
 template <int UP>
 __device__ __forceinline__ void uniform_epilogue(const SolveParams& p, const float2* base, const int* fail_sc,
-                                                 int sc0, int U, int NS, int Ceff, float s2_scale) {
+                                                 int sc0, int U, int NS, int Ceff, float s2_scale,
+                                                 const int* zflag = nullptr) {
   using Lay = SolveLayout<UP>;
   const int spc = p.spc;
   const int per = U * NS;   // uniform problem: every group has the problem's sizes
@@ -176,7 +179,7 @@ __device__ __forceinline__ void uniform_epilogue(const SolveParams& p, const flo
     } else if (dn > 0.f) {
       const float rr = 1.f / dn;
       zz = cscale(nm, rr);
-      s2 = s2_scale * rr;
+      s2 = (zflag && zflag[s * UP + u]) ? 0.f : s2_scale * rr;
     } else {
       zz = make_float2(0.f, 0.f);
       s2 = INFINITY;
@@ -548,13 +551,17 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
 
 // Maximum-ratio combining (Sec. III-A) per (subcarrier, cluster), uniform
 // problems: lane i of a group of UP lanes reads row i of G_c and forms
-//   sigma_c^2 / Es = (rho G_ii + sum_{j != i} |G_ij|^2) / G_ii^2,
+//   sigma_c^2 / Es = (rho G_ii + I_i) / G_ii^2,   I_i = sum_{j != i} |G_ij|^2,
 // then leaves the fusion denominator w = Es / sigma_c^2 and the numerators
 // w y^MRC_i(n) / G_ii in the areas the epilogue sums, so that z = sum_c (w z_c) /
-// sum_c w (Eq. fusionrule, opt_fusion) and sigma^2 = Es / sum_c w (Thm. 3).  A
-// user the cluster cannot see (G_ii = 0) gets w = 0.  With N0 = 0 and U = 1
-// every variance is 0; the weights are then those of the limit N0 -> 0,
-// proportional to G_ii, and sigma^2 is 0.  No system is solved: info is 0.
+// sum_c w (Eq. fusionrule, opt_fusion) and sigma^2 = Es / sum_c w (Thm. 3); PD
+// (one cluster) is z = y^MRC_i / G_ii.  A user the cluster cannot see (G_ii = 0)
+// gets w = 0.  With N0 = 0 a variance is exactly 0 where the user has no
+// interference (I_i = 0: a single user, or channels of disjoint support); the
+// weights are then those of the limit N0 -> 0, where such a cluster's
+// Es / sigma_c^2 ~ G_ii Es / N0 outgrows every other: per user, the
+// zero-interference clusters share the weight in proportion to G_ii, the others
+// get 0, and the fused variance is 0.  No system is solved: info is 0.
 template <int UP>
 __global__ void __launch_bounds__(512) mrc_fuse_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -563,37 +570,48 @@ __global__ void __launch_bounds__(512) mrc_fuse_kernel(const SolveParams p) {
   float2* base = reinterpret_cast<float2*>(smem + 256);
   const int U = p.U, NS = p.n_sym, Ceff = p.Ceff;
   const int nmat = p.spc * Ceff;
+  int* zflag = reinterpret_cast<int*>(base + nmat * Lay::kMat);   // [spc][UP]: some cluster has variance 0
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
   const int sc0 = blockIdx.x * p.spc;
-  const bool limit = p.N0 == 0.f && U == 1;
+  const bool noiseless = p.N0 == 0.f;
   if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
+  for (int t = threadIdx.x; t < p.spc * UP; t += blockDim.x) zflag[t] = 0;
 
   // Wait for the contraction grid (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
+  const int c = g % Ceff, s = g / Ceff, sc = sc0 + s;
+  const bool live = g < nmat && sc < p.n_sc && i < U;
+  const float2* Dg = p.D + (static_cast<size_t>(live ? sc : 0) * Ceff + c) * static_cast<size_t>(U + NS) * U;
+  float gii = 0.f, intf = 0.f;
+  if (live) {
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      if (j < U) {
+        const float2 v = Dg[j * U + i];   // G_ij (conjugate symmetric)
+        if (j == i) {
+          gii = v.x;
+        } else {
+          intf = fmaf(v.x, v.x, fmaf(v.y, v.y, intf));
+        }
+      }
+    }
+    if (noiseless && gii > 0.f && intf == 0.f) atomicOr(&zflag[s * UP + i], 1);
+  }
+  __syncthreads();
   if (g < nmat) {
-    const int c = g % Ceff, sc = sc0 + g / Ceff;
     float2* Fz = base + g * Lay::kMat + Lay::kRow;
     float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
     float w = 0.f;
-    if (sc < p.n_sc && i < U) {
-      const float2* Dg = p.D + (static_cast<size_t>(sc) * Ceff + c) * static_cast<size_t>(U + NS) * U;
-      float gii = 0.f, intf = 0.f;
-#pragma unroll
-      for (int j = 0; j < UP; ++j) {
-        if (j < U) {
-          const float2 v = Dg[j * U + i];   // G_ij (conjugate symmetric)
-          if (j == i) {
-            gii = v.x;
-          } else {
-            intf = fmaf(v.x, v.x, fmaf(v.y, v.y, intf));
-          }
-        }
-      }
-      const float den = fmaf(p.rho, gii, intf);
+    if (live) {
       float zs = 0.f;
       if (gii > 0.f) {
-        w = limit ? gii : (den > 0.f ? gii * gii / den : 0.f);
+        if (noiseless && zflag[s * UP + i]) {
+          w = intf == 0.f ? gii : 0.f;          // the N0 -> 0 limit weights
+        } else {
+          const float den = fmaf(p.rho, gii, intf);
+          w = den > 0.f ? gii * gii / den : 0.f;
+        }
         zs = w / gii;
       }
       for (int n = 0; n < NS; ++n) Fz[n * UP + i] = cscale(Dg[(U + n) * U + i], zs);
@@ -602,7 +620,7 @@ __global__ void __launch_bounds__(512) mrc_fuse_kernel(const SolveParams p) {
     Dn[i] = w;
   }
   __syncthreads();
-  uniform_epilogue<UP>(p, base, fail_sc, sc0, U, NS, Ceff, limit ? 0.f : p.Es);
+  uniform_epilogue<UP>(p, base, fail_sc, sc0, U, NS, Ceff, p.Es, zflag);
 }
 
 template <int UP>
@@ -610,7 +628,8 @@ cudaError_t launch_mrc_up(const SolveParams& p, cudaStream_t stream) {
   using Lay = SolveLayout<UP>;
   const int nmat = p.spc * p.Ceff;
   const int threads = ((nmat * UP + 31) / 32) * 32;
-  const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
+  const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2) +
+                      static_cast<size_t>(p.spc) * UP * sizeof(int);
   static int configured[64] = {0};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);

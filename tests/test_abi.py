@@ -175,7 +175,7 @@ def test_refinement_needs_the_inputs(built):
         ffeq.ffeq_fuse_equalize(plan, 256, ffeq.ffeq_workspace_size(plan), 0.1, 1.0, 256, 256, None, None, stream=0)
     assert e.value.status == 2
     with pytest.raises(ffeq.FfeqError) as e:
-        ffeq.ffeq_plan_create(64, 8, 4, 10, 2, refine=3)
+        ffeq.ffeq_plan_create(64, 8, 4, 10, 2, refine=5)
     assert e.value.status == 1
     # The FP64 residual is a mode of the refinement: 0..2, and only with refine > 0.
     for bad in (dict(refine=1, refine_fp64=3), dict(refine=1, refine_fp64=-1), dict(refine=0, refine_fp64=1)):

@@ -31,6 +31,7 @@ such subcarriers (worst seen: 1.04x the z bound, TF32x3, FD).
 import numpy as np
 import pytest
 
+import parity
 from oracle import llr as ollr
 from oracle import lmmse
 from paper_1808_04473_gb300 import synth
@@ -117,12 +118,6 @@ def _flat(ps, cfg, inst):
     return H, y
 
 
-def _rel_per_sc(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
-
-
 def _check(run, out, estimate=0, precision=0, skip=()):
     worst = 0.0
     for idx, (p, it) in enumerate(zip(run.ps, run.inst)):
@@ -134,12 +129,12 @@ def _check(run, out, estimate=0, precision=0, skip=()):
         n, U, NS = p.n_sc, p.U, p.n_sym
         z = out["z"][it.z_off:it.z_off + n * NS * U].reshape(n, NS, U)
         s2 = out["s2"][it.sigma2_off:it.sigma2_off + n * U].reshape(n, U)
-        ez = _rel_per_sc(z, o["z"]).max()
+        ez, _ = parity.check(f"z[{idx}]", z, o["z"], tol)
         if p.N0 == 0:            # zero forcing: sigma^2 = 0 exactly (the FP64 oracle leaves ~1e-33)
             assert (s2 == 0).all() and np.abs(o["sigma2"]).max() < 1e-20, (idx, s2[:2], o["sigma2"][:2])
             es = 0.0
         else:
-            es = _rel_per_sc(s2, o["sigma2"]).max()
+            es, _ = parity.check(f"sigma2[{idx}]", s2, o["sigma2"], tol)
         assert ez <= tol and es <= tol, (idx, p.B, p.U, p.C, p.n_sym, ez, es)
         if run.bits:
             L = out["llr"][it.llr_off:it.llr_off + n * NS * U * run.bits].reshape(n, NS, U, run.bits)
@@ -148,8 +143,7 @@ def _check(run, out, estimate=0, precision=0, skip=()):
                                                                run.bits, p.Es))).all(), (idx, "llr signs")
             else:
                 Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], run.bits, p.Es)
-                el = _rel_per_sc(L, Lo).max()
-                assert el <= 4 * tol, (idx, "llr", el)
+                parity.check(f"llr[{idx}]", L, Lo, 4 * tol)
         if run.cfg.info_elems:
             Ceff = p.C if run.arch == 1 else 1
             info = out["info"][it.info_off:it.info_off + n * Ceff]

@@ -1,7 +1,14 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerance: per subcarrier, ||z_gpu - z_oracle||_2 / ||z_oracle||_2, and the same
-for sigma^2 and the LLRs of that subcarrier, must not exceed
+Tolerance: per subcarrier, ||z_gpu - z_oracle||_2 / ||z_oracle||_2, and every
+entry |z_gpu - z_oracle| / max(|z_oracle|, rms of the subcarrier's z_oracle)
+(``tests/parity.py``), and the same for sigma^2 (and 4x for the LLRs, which are
+affine in z with slope 2|a_0 - a_1| / sigma^2 and so carry the errors of both)
+of that subcarrier, must not exceed max(t, 2 u kappa), kappa the largest
+cond_2(G_c + rho I) of the matrices inverted on that subcarrier (G + rho I for
+PD) and u the unit roundoff of the preprocessing (2^-22 FP32, 2^-21 TF32x3 and
+FP16x3, 2^-16 BF16x3: the first-order bound of a solve whose matrix and
+right-hand side carry relative errors u), with t
   * 1e-5 for the FP32 and TF32x3 local preprocessing (FP32-level arithmetic);
   * 2e-4 for BF16x3: a BF16 hi/lo pair carries 16 significand bits (relative
     error 2^-17 = 7.6e-6 per operand), and the solve amplifies the Gram error by
@@ -13,6 +20,7 @@ Inputs are the same seeded complex64 arrays for both sides.
 import numpy as np
 import pytest
 
+import parity
 from oracle import llr as ollr
 from oracle import lmmse
 from paper_1808_04473_gb300 import synth
@@ -54,25 +62,36 @@ def _oracle(p, arch, estimate, H=None, y=None, N0=None, idx=None):
     return f(H, y, p.N0 if N0 is None else N0, p.Es, p.C, "unbiased" if estimate == 0 else "literal")
 
 
-def _rel_per_sc(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16, 3: 2.0 ** -21}
+
+
+def _kappa(p, arch, idx=None, sizes=None):
+    """Largest cond_2 of the regularized matrices inverted on each subcarrier:
+    G + rho I (PD) or every G_c + rho I (FD)."""
+    rho = float(np.float32(p.N0)) / p.Es
+    ks = range(p.n_sc) if idx is None else idx
+    parts = [(0, p.B)] if arch == 0 else lmmse.partition(p.B, p.C, sizes)
+    out = []
+    for k in ks:
+        Hm = p.H[k].astype(np.complex128).T
+        out.append(max(np.linalg.cond(Hm[b0:b1].conj().T @ Hm[b0:b1] + rho * np.eye(p.U)) for b0, b1 in parts))
+    return np.array(out)
+
+
+def _bound(p, arch, precision, idx=None):
+    return np.maximum(PREC_TOL[precision], 2.0 * UNIT[precision] * _kappa(p, arch, idx))
 
 
 def _check(g, o, p, bits=0, tol=TOL, idx=None):
     z = g["z"] if idx is None else g["z"][idx]
     s2 = g["sigma2"] if idx is None else g["sigma2"][idx]
-    ez = _rel_per_sc(z, o["z"])
-    es = _rel_per_sc(s2, o["sigma2"])
-    assert ez.max() <= tol, f"z rel err {ez.max():.3g}"
-    assert es.max() <= tol, f"sigma2 rel err {es.max():.3g}"
+    ez, _ = parity.check("z", z, o["z"], tol)
+    parity.check("sigma2", s2, o["sigma2"], tol)
     if bits:
         L = g["llr"] if idx is None else g["llr"][idx]
         Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], bits, p.Es)
-        el = _rel_per_sc(L, Lo)
-        assert el.max() <= tol, f"llr rel err {el.max():.3g}"
-    return ez.max()
+        parity.check("llr", L, Lo, 4 * tol)
+    return ez
 
 
 CASES = [
@@ -98,7 +117,7 @@ def test_parity_small(ff, B, U, C, n_sc, n_sym, bits, snr, Es, arch, estimate, p
     p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=snr, bits=bits, seed=B * 131 + U * 7 + C, Es=Es)
     g = _gpu(ff, p, arch, estimate, llr_bits=bits, precision=precision)
     o = _oracle(p, arch, estimate)
-    _check(g, o, p, bits, tol=PREC_TOL[precision])
+    _check(g, o, p, bits, tol=_bound(p, arch, precision))
     assert (g["info"] == 0).all()
 
 
@@ -109,7 +128,7 @@ def test_parity_correlated_channel(ff, arch, precision):
     p = synth.make_problem(256, 32, 16, 8, 14, snr_db=15.0, bits=6, seed=77, corr_r=0.7)
     g = _gpu(ff, p, arch, 0, llr_bits=6, precision=precision)
     o = _oracle(p, arch, 0)
-    _check(g, o, p, 6, tol=PREC_TOL[precision])
+    _check(g, o, p, 6, tol=_bound(p, arch, precision))
 
 
 def test_pd_ignores_partition_and_equals_fd_at_c1(ff):
@@ -238,7 +257,7 @@ def test_full_size_throughput_workload_sampled(ff, arch, precision):
     g = _gpu(ff, p, arch, 0, llr_bits=4, precision=precision)
     idx = np.random.default_rng(5).choice(1200, 48, replace=False)
     o = _oracle(p, arch, 0, idx=idx)
-    _check(g, o, p, 4, tol=PREC_TOL[precision], idx=idx)
+    _check(g, o, p, 4, tol=_bound(p, arch, precision, idx), idx=idx)
     assert np.isfinite(g["z"]).all() and np.isfinite(g["llr"]).all() and (g["info"] == 0).all()
 
 
@@ -249,11 +268,8 @@ def test_full_size_correlated_workload_sampled(ff):
     for arch in (0, 1):
         for precision in (0, 2):
             g = _gpu(ff, p, arch, 0, llr_bits=6, precision=precision)
-            _check(g, _oracle(p, arch, 0, idx=idx), p, 6, tol=PREC_TOL[precision], idx=idx)
+            _check(g, _oracle(p, arch, 0, idx=idx), p, 6, tol=_bound(p, arch, precision, idx), idx=idx)
             assert np.isfinite(g["z"]).all()
-
-
-UNIT = {0: 2.0 ** -22, 1: 2.0 ** -21, 2: 2.0 ** -16, 3: 2.0 ** -21}
 
 
 def _kappa_clusters(p, sizes):
@@ -294,11 +310,10 @@ def test_unequal_clusters_match_the_oracle(ff, case, precision):
     o = lmmse.equalize_fd(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased", cluster_sizes=sizes)
     assert np.array_equal(g["info"], o["info"])
     tol = np.maximum(PREC_TOL[precision], 2.0 * UNIT[precision] * _kappa_clusters(p, sizes))
-    ez, es = _rel_per_sc(g["z"], o["z"]), _rel_per_sc(g["sigma2"], o["sigma2"])
-    assert (ez <= tol).all(), (ez.max(), tol[np.argmax(ez - tol)])
-    assert (es <= tol).all(), (es.max(), tol[np.argmax(es - tol)])
+    parity.check("z", g["z"], o["z"], tol)
+    parity.check("sigma2", g["sigma2"], o["sigma2"], tol)
     Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es)
-    assert (_rel_per_sc(g["llr"], Lo) <= 4 * tol).all()
+    parity.check("llr", g["llr"], Lo, 4 * tol)
     if B % C == 0:
         pd_sizes = ff.equalize(H, y, p.N0, p.Es, C, arch=0, precision=precision, cluster_sizes=sizes)
         pd_equal = ff.equalize(H, y, p.N0, p.Es, C, arch=0, precision=precision)
@@ -320,5 +335,4 @@ def test_unequal_clusters_with_refinement(ff, steps):
     tol = np.maximum(1e-5, 2.0 * 2.0 ** -22 * kap)
     if steps == 1:
         tol = np.maximum(tol, 4.0 * (2.0 ** -16 * kap) ** 2)
-    ez = _rel_per_sc(g["z"].cpu().numpy(), o["z"])
-    assert (ez <= tol).all(), (ez.max(), kap.max())
+    parity.check("z", g["z"].cpu().numpy(), o["z"], tol)

@@ -4,13 +4,14 @@ On ill-conditioned systems (receive correlation r = 0.7 across the array and
 clusters with S = B/C not above U, high SNR) the mixed-precision preprocessing
 is off by about kappa(G_c + rho I) * 2^-16; one or two refinement steps from H
 and y must bring z and sigma^2 to the FP32-level bound max(1e-5, 2 kappa 2^-22)
-per subcarrier (kappa the subcarrier's largest cond_2(G_c + rho I), as in the
+per subcarrier and per entry (``tests/parity.py``) (kappa the subcarrier's largest cond_2(G_c + rho I), as in the
 batch tests), and at least 4x below the unrefined error where that exceeds
 1e-5.  Refinement must not degrade well-conditioned problems.
 """
 import numpy as np
 import pytest
 
+import parity
 from oracle import llr as ollr
 from oracle import lmmse
 from paper_1808_04473_gb300 import synth
@@ -30,10 +31,7 @@ def ff():
     return ffeq
 
 
-def _rel(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+_rel = parity.rel_per_sc
 
 
 def _kappa(p, arch):
@@ -80,15 +78,15 @@ def test_refinement_reaches_fp32_level(ff, case, arch, precision):
     for steps in (1, 2):
         g = _run(ff, p, arch, precision, steps)
         assert (g["info"] == 0).all()
-        ez, es = _rel(g["z"], o["z"]), _rel(g["sigma2"], o["sigma2"])
         need = bound if steps == 2 else np.maximum(bound, 4.0 * 2.0 ** -16 * kap * 2.0 ** -16 * kap)
-        assert (ez <= need).all(), (steps, ez.max(), need[np.argmax(ez - need)], kap.max())
-        assert (es <= need).all(), (steps, es.max(), kap.max())
+        parity.check(f"z, {steps} steps", g["z"], o["z"], need)
+        parity.check(f"sigma2, {steps} steps", g["sigma2"], o["sigma2"], need)
+        ez = _rel(g["z"], o["z"])
         big = e0 > 1e-5
         if steps == 2 and big.any():
             assert (ez[big] <= e0[big] / 4).all(), (ez[big].max(), e0[big].max())
         Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es)
-        assert (_rel(g["llr"], Lo) <= 4 * need).all()
+        parity.check(f"llr, {steps} steps", g["llr"], Lo, 4 * need)
 
 
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
@@ -99,8 +97,8 @@ def test_refinement_keeps_well_conditioned_results(ff, arch):
         o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, est)
         for precision in (0, 2):
             g = _run(ff, p, arch, precision, 1, estimate=estimate)
-            assert _rel(g["z"], o["z"]).max() <= 1e-5, (precision, estimate)
-            assert _rel(g["sigma2"], o["sigma2"]).max() <= 1e-5, (precision, estimate)
+            parity.check(f"z {precision, estimate}", g["z"], o["z"], 1e-5)
+            parity.check(f"sigma2 {precision, estimate}", g["sigma2"], o["sigma2"], 1e-5)
 
 
 def test_refinement_reports_singular_systems(ff):
@@ -157,12 +155,13 @@ def test_fp64_residual_reaches_fp32_storage_accuracy(ff, case, arch, precision):
     e32 = _rel(g32["z"], o["z"])
     ez, es = _rel(g64["z"], o["z"]), _rel(g64["sigma2"], o["sigma2"])
     print("kappa max %.3g  z err fp32-res %.3g fp64-res %.3g  sigma2 %.3g" % (kap.max(), e32.max(), ez.max(), es.max()))
-    assert ez.max() <= 4e-6 and es.max() <= 4e-6, (ez.max(), es.max(), kap.max())
+    parity.check("z", g64["z"], o["z"], 4e-6)
+    parity.check("sigma2", g64["sigma2"], o["sigma2"], 4e-6)
     big = e32 > 1e-5
     if big.any():
         assert (ez[big] <= e32[big] / 4).all()
     Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es)
-    assert (_rel(g64["llr"], Lo) <= 1.6e-5).all()
+    parity.check("llr", g64["llr"], Lo, 1.6e-5)
 
 
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
@@ -201,5 +200,57 @@ def test_fp64_residual_branch_at_40db(ff):
     ez, es = _rel(g64["z"], o["z"]), _rel(g64["sigma2"], o["sigma2"])
     e32 = _rel(g32["z"], o["z"])
     print("40 dB: z err fp64-res %.3g (sigma2 %.3g), fp32-res %.3g" % (ez.max(), es.max(), e32.max()))
-    assert ez.max() <= 4e-6 and es.max() <= 4e-6, (ez.max(), es.max())
+    parity.check("z", g64["z"], o["z"], 4e-6)
+    parity.check("sigma2", g64["sigma2"], o["sigma2"], 4e-6)
     assert e32.max() >= 10 * ez.max()
+
+
+def _cfg3(snr_db):
+    """B = 256, U = 32, C = 16 (S = 16 < U), 3300 subcarriers x 14 symbols, 64-QAM,
+    receive-side exponential correlation r = 0.7 over the array."""
+    return synth.make_problem(256, 32, 16, 3300, 14, snr_db=snr_db, bits=6, seed=3300, corr_r=0.7)
+
+
+CFG3_RUNS = [  # snr_db, refinement steps: one at 15 dB (kappa u << 1), four at 40 dB (kappa u ~ 0.2)
+    (15.0, 1),
+    (40.0, 4),
+]
+
+
+@pytest.mark.parametrize("snr,steps", CFG3_RUNS, ids=["15dB", "40dB-stress"])
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_correlated_workload_in_its_configuration(ff, snr, steps, arch):
+    """The correlated workload as configured: FP16x3 contraction, refinement from the
+    inputs with the FP64 residual for the systems whose condition estimate exceeds
+    1e4 (refine_fp64 = 1), on 24 sampled subcarriers of the full 3300.  The refined
+    mixed-precision result must meet the mixed path's target, 1e-4 relative to the
+    FP64 oracle, per subcarrier and per entry, for z, sigma^2 and (4x) the LLRs;
+    where a system took the FP32 residual the refinement converges to an FP32
+    solve's accuracy, about kappa 2^-24, so the bound is max(1e-4, 2 kappa_32 2^-24)
+    with kappa_32 the largest cond_2 among the subcarrier's systems below the
+    switch (an estimate >= 1e4 takes the FP64 residual, which converges to the FP32
+    storage of the result)."""
+    p = _cfg3(snr)
+    idx = np.random.default_rng(33).choice(p.n_sc, 24, replace=False)
+    g = _run(ff, p, arch, 3, steps, bits=6, refine_fp64=1)
+    assert (g["info"] == 0).all() and np.isfinite(g["z"]).all()
+    q = synth.Problem(**{**p.__dict__, "H": p.H[idx], "y": p.y[idx], "n_sc": len(idx)})
+    f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
+    o = f(q.H, q.y, float(np.float32(p.N0)), p.Es, p.C, "unbiased")
+    k1 = _kappa1(q, arch)
+    rho = float(np.float32(p.N0)) / p.Es
+    parts = lmmse.partition(p.B, p.C) if arch == 1 else [(0, p.B)]
+    k32 = np.ones(len(idx))
+    for k in range(len(idx)):
+        Hm = q.H[k].astype(np.complex128).T
+        for i, (b0, b1) in enumerate(parts):
+            if k1[k, i] < 1e4:
+                M = Hm[b0:b1].conj().T @ Hm[b0:b1] + rho * np.eye(p.U)
+                k32[k] = max(k32[k], np.linalg.cond(M))
+    bound = np.maximum(1e-4, 2.0 * 2.0 ** -24 * k32)
+    print(f"{snr} dB arch {arch}: systems above 1e4: {(k1 >= 1e4).mean():.2f}, max kappa below {k32.max():.3g}")
+    ez, _ = parity.check("z", g["z"][idx], o["z"], bound)
+    parity.check("sigma2", g["sigma2"][idx], o["sigma2"], bound)
+    Lo = ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 6, p.Es)
+    parity.check("llr", g["llr"][idx], Lo, 4 * bound)
+    print(f"  max z error {ez:.3g}")

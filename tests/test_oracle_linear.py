@@ -164,17 +164,60 @@ def test_lmmse_beats_zf_and_mrc_in_mean_squared_error():
         assert np.all(lm["sigma2"] <= o["sigma2"] * (1 + 1e-12))
 
 
-def test_mrc_zero_variance_outside_the_limit_is_the_same_in_pd_and_fd():
-    """N0 = 0, U = 2, users on disjoint antennas: no interference, so sigma^2 = 0 outside the
-    U = 1 limit; PD and FD at C = 1 give the same (weight 0: z = 0, sigma^2 = inf)."""
+def _disjoint_users(seed):
+    """U = 3 on B = 64 antennas, C = 4 clusters of 16, noise at 10 dB: clusters 0 and 1
+    see user 0 alone, cluster 2 all three users, cluster 3 users 1 and 2.  Read with
+    N0 = 0, user 0 has no interference in clusters 0 and 1 (variance exactly 0 there)
+    and users 1 and 2 have interference in every cluster that sees them."""
+    p = synth.make_problem(64, 3, 4, 4, 2, snr_db=10.0, seed=seed)
+    n = p.y.astype(np.complex128) - p.s @ p.H.astype(np.complex128)
+    H = p.H.copy()
+    H[:, 1:, :32] = 0.0
+    H[:, 0, 48:] = 0.0
+    y = (p.s @ H.astype(np.complex128) + n).astype(np.complex64)
+    return p, H, y
+
+
+def test_mrc_zero_variance_pairs_take_the_limit_weights():
+    """Lemma 1's weights sigma_c^-2 / sum sigma^-2 as N0 -> 0.  FD: the outputs for
+    N0 = 1e-6, 1e-9, 1e-12 (ordinary weights: no variance is 0 there) converge
+    linearly in N0 to the N0 = 0 output, in which user 0's two zero-variance clusters
+    share the weight in proportion to G_c,uu, i.e. z_0 = sum_{b < 32} conj(h_0b) y_b /
+    sum_{b < 32} |h_0b|^2 (written out here per antenna), with variance 0, and users
+    1 and 2 keep the ordinary weights.  PD (no fusion step, z = y^MRC_u / G_uu) does
+    not depend on N0."""
+    p, H, y = _disjoint_users(18)
+    for f in (linear.equalize_pd_linear, linear.equalize_fd_linear):
+        lim = f(H, y, 0.0, p.Es, 4, "mrc")
+        for N0 in (1e-6, 1e-9, 1e-12):
+            o = f(H, y, N0, p.Es, 4, "mrc")
+            assert (o["sigma2"] > 0).all()
+            assert np.abs(o["z"] - lim["z"]).max() <= 10 * N0, (f.__name__, N0)
+            assert np.abs(o["sigma2"] - lim["sigma2"]).max() <= 10 * N0, (f.__name__, N0)
+        assert (lim["sigma2"][:, 1:] > 0).all()
+    fd = linear.equalize_fd_linear(H, y, 0.0, p.Es, 4, "mrc")
+    for k in range(p.n_sc):
+        for n in range(p.n_sym):
+            num = sum(np.conj(complex(H[k, 0, b])) * complex(y[k, n, b]) for b in range(32))
+            den = sum(abs(complex(H[k, 0, b])) ** 2 for b in range(32))
+            assert abs(fd["z"][k, n, 0] - num / den) < 1e-12
+    assert (fd["sigma2"][:, 0] == 0).all()
+    # Reading the pair with variance 0 as weight 0 would drop clusters 0 and 1.
+    assert np.abs(fd["z"][:, :, 0]).min() > 0.1
+
+
+def test_mrc_zero_variance_pd_equals_fd_at_c1():
+    """PD and FD at C = 1 agree in the zero-variance case too (one pair, weight 1)."""
     p = synth.make_problem(32, 2, 1, 3, 2, noiseless=True, seed=18)
     H = p.H.copy()
     H[:, 0, 16:] = 0.0
     H[:, 1, :16] = 0.0
-    pd = linear.equalize_pd_linear(H, p.y, 0.0, p.Es, 1, "mrc")
-    fd = linear.equalize_fd_linear(H, p.y, 0.0, p.Es, 1, "mrc")
-    assert np.array_equal(pd["z"], fd["z"]) and np.array_equal(pd["sigma2"], fd["sigma2"])
-    assert (pd["z"] == 0).all() and np.isinf(pd["sigma2"]).all()
+    y = np.einsum("kub,knu->knb", H.astype(np.complex128), p.s).astype(np.complex64)
+    pd = linear.equalize_pd_linear(H, y, 0.0, p.Es, 1, "mrc")
+    fd = linear.equalize_fd_linear(H, y, 0.0, p.Es, 1, "mrc")
+    assert _rel(fd["z"], pd["z"]) < 1e-14 and np.array_equal(pd["sigma2"], fd["sigma2"])
+    np.testing.assert_allclose(pd["z"], p.s, atol=1e-12)
+    assert (pd["sigma2"] == 0).all()
 
 
 @pytest.mark.slow
