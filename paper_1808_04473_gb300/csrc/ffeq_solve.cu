@@ -549,6 +549,203 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
   return cudaLaunchKernelEx(&cfg, solve_fuse_kernel<UP, LPR, BATCH>, p);
 }
 
+// Solve / fusion / soft outputs for uniform problems whose users fill the lane
+// group (U == UP: 8, 16 or 32), one lane per row.  The same computation as
+// solve_fuse_kernel's one-lane path, specialized so that the sizes that shape
+// the work are compile-time constants: every lane loads its row with fixed
+// offsets from one column pointer (no padding rows, no clamped or selected
+// addresses), the right-hand sides reach shared memory by asynchronous copies
+// that overlap the sweep, and the epilogue walks (symbol, user) outputs with
+// shifts and masks instead of runtime divisions.
+template <int UP>
+__global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = SolveLayout<UP>;
+  constexpr int U = UP, NP = UP / 2;
+  const int NS = p.n_sym, Ceff = p.Ceff, spc = p.spc;
+  const int nmat = spc * Ceff;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  int* fail_sc = reinterpret_cast<int*>(smem);                     // [spc]
+  float2* base = reinterpret_cast<float2*>(smem + 256);
+  const int sc0 = blockIdx.x * spc;
+  if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
+  __syncthreads();
+  // Wait for the contraction grid (programmatic dependent launch).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  const int gm = g < nmat ? g : nmat - 1;       // spare lanes shadow the last matrix
+  const int scl = gm / Ceff, c = gm - scl * Ceff;
+  const int sc = sc0 + scl;
+  const bool live = g < nmat && sc < p.n_sc;
+  const float rho = p.rho;
+  const size_t mat = static_cast<size_t>(U + NS) * U;
+  // Column i of this system's D: D[v][i] = G[i][v] (v < U), D[U + n][i] = y^MRC_i(n).
+  const float2* Dg = p.D + (static_cast<size_t>(live ? sc : 0) * Ceff + c) * mat + i;
+  float2* rowbuf = base + gm * Lay::kMat;
+  float2* Fz = rowbuf + Lay::kRow;
+  float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
+
+  // The right-hand sides [n][u] are one contiguous block of D with the layout
+  // of the fusion area: copied global -> shared by the group's lanes in 16-byte
+  // pieces (cp.async, no registers), completed before the product.
+  if (g < nmat) {
+    const char* src = reinterpret_cast<const char*>(Dg - i + U * U);
+    const uint32_t dst = smem_u32(Fz);
+    const int pieces = NS * U / 2;
+    for (int e = i; e < pieces; e += UP)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * e), "l"(src + 16 * e) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float2 mrow[UP];
+#pragma unroll
+  for (int j = 0; j < UP; ++j) mrow[j] = Dg[j * U];
+  float gii = 0.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    if (j == i) {
+      gii = mrow[j].x;
+      mrow[j] = make_float2(mrow[j].x + rho, 0.f);
+    }
+  }
+  float2 rp[NP], ip[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    rp[m] = make_float2(mrow[2 * m].x, mrow[2 * m + 1].x);
+    ip[m] = make_float2(mrow[2 * m].y, mrow[2 * m + 1].y);
+  }
+  float rs = 1.f;
+  int fail;
+  if constexpr (UP >= 32) {
+    fail = gj_sweep_block2<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+  } else {
+    fail = gj_sweep_pairs<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
+  }
+  // Lane i holds row i of A = (G + rho I)^{-1} times p_i, columns in natural order.
+  float Ap = 1.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j)
+    if (j == i) Ap = j % 2 ? rp[j / 2].y : rp[j / 2].x;
+  const float Ai = Ap * rs;
+  const float invA = 1.f / Ai;
+  // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
+  // mu = 0 exactly, which the subtraction would only reach up to rounding.
+  const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
+  const bool store = p.Xs != nullptr;   // refinement follows: keep estimates and inverses
+  const size_t sys = static_cast<size_t>(sc) * Ceff + c;
+  float2 arow[UP];
+#pragma unroll
+  for (int j = 0; j < UP; ++j)
+    arow[j] = cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  // z_n = sum_j A[i][j] y^MRC_j(n) in j order; after every lane of the warp has
+  // read row n, the fusion term z_n / A_ii replaces it ([n][u]).
+#pragma unroll
+  for (int n = 0; n < kNsymMax; ++n) {
+    if (n < NS) {
+      float2 zn = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < UP; j += 2) {
+        const float4 y2 = *reinterpret_cast<const float4*>(Fz + n * UP + j);
+        zn = cfma(arow[j], make_float2(y2.x, y2.y), zn);
+        zn = cfma(arow[j + 1], make_float2(y2.z, y2.w), zn);
+      }
+      __syncwarp();
+      if (g < nmat) {
+        if (store) {
+          if (live) p.Xs[(sys * NS + n) * U + i] = zn;
+        } else {
+          Fz[n * UP + i] = cscale(zn, invA);
+        }
+      }
+    }
+  }
+  if (store) {
+    // Inverse stored transposed (row j = column j of A, coalesced over the lanes i).
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < UP; ++j)
+        p.As[(sys * U + j) * U + i] =
+            cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
+      if (i == 0) {
+        p.fails[sys] = fail;
+        if (p.info) p.info[sys] = fail;
+      }
+    }
+    return;   // the refinement kernel fuses and writes the outputs
+  }
+  if (g < nmat) {
+    Dn[i] = (p.unbiased ? mu : 1.f) * invA;
+    if (i == 0 && live) {
+      if (p.info) p.info[sys] = fail;
+      if (fail) atomicOr(&fail_sc[scl], 1);
+    }
+  }
+  __syncthreads();
+  // ---- outputs: per subcarrier of this CTA, (symbol n, user u) = (e / UP, e % UP).
+  const int per = UP * NS;
+  const int bits = p.llr_bits, hb = bits / 2;
+  for (int s = 0; s < spc; ++s) {
+    const int k = sc0 + s;
+    if (k >= p.n_sc) break;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int n = e / UP, u = e % UP;
+      float2 nm = make_float2(0.f, 0.f);
+      float dn = 0.f;
+      for (int cc = 0; cc < Ceff; ++cc) {
+        const float2* Lm = base + (s * Ceff + cc) * Lay::kMat + Lay::kRow;
+        nm = cadd(nm, Lm[n * UP + u]);
+        dn += reinterpret_cast<const float*>(Lm + Lay::kNum)[u];
+      }
+      float2 zz;
+      float s2;
+      if (fail_sc[s]) {
+        zz = make_float2(NAN, NAN);
+        s2 = NAN;
+      } else if (dn > 0.f) {
+        const float rr = 1.f / dn;
+        zz = cscale(nm, rr);
+        s2 = p.N0 * rr;
+      } else {
+        zz = make_float2(0.f, 0.f);
+        s2 = INFINITY;
+      }
+      const size_t zi = (static_cast<size_t>(k) * NS + n) * U + u;
+      p.z[zi] = zz;
+      if (n == 0) p.sigma2[static_cast<size_t>(k) * U + u] = s2;
+      if (bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * bits);
+    }
+  }
+}
+
+template <int UP>
+cudaError_t launch_full(const SolveParams& p, cudaStream_t stream) {
+  using Lay = SolveLayout<UP>;
+  const int nmat = p.spc * p.Ceff;
+  const int threads = ((nmat * UP + 31) / 32) * 32;
+  const size_t smem = 256 + static_cast<size_t>(nmat) * Lay::kMat * sizeof(float2);
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 64 && !configured[dev]) {
+    err = cudaFuncSetAttribute(solve_full_kernel<UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    configured[dev] = 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((p.n_sc + p.spc - 1) / p.spc);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, solve_full_kernel<UP>, p);
+}
+
 // Maximum-ratio combining (Sec. III-A) per (subcarrier, cluster), uniform
 // problems: lane i of a group of UP lanes reads row i of G_c and forms
 //   sigma_c^2 / Es = (rho G_ii + I_i) / G_ii^2,   I_i = sum_{j != i} |G_ij|^2,
@@ -654,13 +851,16 @@ cudaError_t launch_mrc_up(const SolveParams& p, cudaStream_t stream) {
 
 }  // namespace
 
-// PD (one system per subcarrier) with U <= 16: a full warp per system (two
-// lanes per row) and 4 subcarriers per CTA, for more warps in flight; FD: the C
-// systems of one subcarrier in one CTA, UP lanes each.
-static int lanes_per_row(int U, int Ceff) { return (Ceff == 1 && padded_users(U) == 16) ? 2 : 1; }
+// PD (one system per subcarrier) with 8 < U < 16: a full warp per system (two
+// lanes per row) and 4 subcarriers per CTA, for more warps in flight; PD with
+// U = 8, 16 or 32 (solve_full_kernel): 2 subcarriers per CTA, one lane per row
+// (measured faster than two lanes per row: half the instructions per system);
+// FD: the C systems of one subcarrier in one CTA, UP lanes each.
+static int lanes_per_row(int U, int Ceff) { return (Ceff == 1 && padded_users(U) == 16 && U != 16) ? 2 : 1; }
 
 int solve_subcarriers_per_cta(int U, int Ceff) {
   if (Ceff != 1) return 1;
+  if (padded_users(U) == U) return 2;
   return 128 / (padded_users(U) * lanes_per_row(U, Ceff));
 }
 
@@ -684,7 +884,15 @@ cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream) {
       default: return launch_mrc_up<32>(p, stream);
     }
   }
-  switch (padded_users(p.U)) {
+  const int UP = padded_users(p.U);
+  if (p.U == UP && lanes_per_row(p.U, p.Ceff) == 1) {   // users fill the lane group
+    switch (UP) {
+      case 8: return launch_full<8>(p, stream);
+      case 16: return launch_full<16>(p, stream);
+      default: return launch_full<32>(p, stream);
+    }
+  }
+  switch (UP) {
     case 8: return launch_up<8, 1, false>(p, stream);
     case 16: return lanes_per_row(p.U, p.Ceff) == 2 ? launch_up<16, 2, false>(p, stream)
                                                     : launch_up<16, 1, false>(p, stream);
