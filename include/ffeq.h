@@ -253,6 +253,35 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
                                    const float* nu, const void* gz, void* gH, void* gy, float* grho,
                                    float* gnu, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Adjoint of the FD equalizer with the paper's optimal weights (FD architecture
+ * of Sec. II-D / IV-A with the unbiased L-MMSE pairs of Sec. III-A fused by
+ * Lemma 1, Eq. opt_fusion: the computation ffeq_equalize performs for this plan),
+ * differentiated through the weights' dependence on diag(A_c):
+ *   per subcarrier and cluster, M_c = G_c + rho I, A_c = M_c^{-1}, X_c = A_c B_c,
+ *   a_c = diag(A_c), w_c = 1 / a_c, D_u = sum_c (w_{c,u} - rho), rho = N0 / Es,
+ *   z_u = sum_c w_{c,u} X_{c,u} / D_u;
+ *   G_b = A_c diag(w_c / D) G_z,
+ *   q_u = -Re(sum_n conj(g_z,u,n) (X_{c,u,n} - z_{u,n})) / (D_u a_{c,u}^2),
+ *   dL/dH_c = Y_c G_b^H - H_c (X_c G_b^H + G_b X_c^H + 2 A_c diag(q) A_c),
+ *   dL/dY_c = H_c G_b.
+ * gz = dL/dRe z + i dL/dIm z (cf32 [n_sc][n_sym][U]) of a real loss of the
+ * plan's z; gH (cf32 [n_sc][U][B]) and gy (cf32 [n_sc][n_sym][B]) in the same
+ * convention.  The call recomputes the contraction and the factorizations from
+ * H and y (nothing is kept from the forward call).  The plan must be FD with
+ * FFEQ_LMMSE, FFEQ_UNBIASED and refine = 0 (FFEQ_ERR_INVALID_ARG otherwise);
+ * clusters of given sizes are allowed; C * U padded <= 512 and one subcarrier's
+ * working set in shared memory (FFEQ_ERR_UNSUPPORTED otherwise).  N0 >= 0 and
+ * Es > 0 as for ffeq_equalize.  The workspace (ffeq_fd_optimal_workspace_size
+ * bytes, 256-byte aligned, owned by the caller) holds the contraction output,
+ * G_b and the matrices of the H term.  A user that no cluster sees contributes
+ * nothing; the gradients of a subcarrier whose systems are not all positive
+ * definite are NaN; users whose unbiasing gain mu is not positive lie outside
+ * the region where the weights are differentiable and are not treated apart. */
+ffeq_status ffeq_fd_optimal_workspace_size(const ffeq_plan* plan, size_t* bytes);
+ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es,
+                                     const void* gz, void* gH, void* gy, void* workspace, size_t workspace_bytes,
+                                     void* stream);
+
 /* Launch shape of a plan's contraction kernel (the arithmetic is that of the
  * plan's precision in every shape; with split-K (PD) the shapes differ in how
  * the antennas are split among warps, hence in summation order only):

@@ -455,10 +455,85 @@ ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, co
   tp.C = p.C;
   tp.n_sc = p.n_sc;
   tp.n_sym = p.n_sym;
+  tp.cl_uniform = 1;
+  return FFEQ_OK;
+}
+
+struct OptimalLayoutBytes {
+  size_t D, Gb, W, total;
+};
+
+OptimalLayoutBytes optimal_layout(const ffeq_plan* plan) {
+  const ffeq_problem& p = plan->p;
+  const size_t nsc = static_cast<size_t>(p.n_sc), C = static_cast<size_t>(p.C);
+  OptimalLayoutBytes t;
+  t.D = align_up(plan->workspace);
+  t.Gb = align_up(nsc * C * p.n_sym * p.U * 8);
+  t.W = align_up(nsc * C * p.U * p.U * 8);
+  t.total = t.D + t.Gb + t.W;
+  return t;
+}
+
+// The plan's forward must be the one differentiated: FD, L-MMSE, unbiased
+// pairs, no refinement; the CTA of one subcarrier must fit.
+ffeq_status optimal_plan_ok(const ffeq_plan* plan) {
+  if (!plan) return FFEQ_ERR_INVALID_ARG;
+  const ffeq_problem& p = plan->p;
+  if (p.arch != FFEQ_FD || p.equalizer != FFEQ_LMMSE || p.estimate != FFEQ_UNBIASED || p.refine != 0)
+    return FFEQ_ERR_INVALID_ARG;
+  if (ffeq::padded_users(p.U) * p.C > 512 || ffeq::train_optimal_smem_bytes(p.U, p.C) > kSolveSmemLimit)
+    return FFEQ_ERR_UNSUPPORTED;
   return FFEQ_OK;
 }
 
 }  // namespace
+
+ffeq_status ffeq_fd_optimal_workspace_size(const ffeq_plan* plan, size_t* bytes) {
+  if (!bytes) return FFEQ_ERR_INVALID_ARG;
+  const ffeq_status r = optimal_plan_ok(plan);
+  if (r != FFEQ_OK) return r;
+  *bytes = optimal_layout(plan).total;
+  return FFEQ_OK;
+}
+
+ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const void* y, float N0, float Es,
+                                     const void* gz, void* gH, void* gy, void* workspace, size_t workspace_bytes,
+                                     void* stream) {
+  ffeq_status r = optimal_plan_ok(plan);
+  if (r != FFEQ_OK) return r;
+  if (bad_scalars(N0, Es)) return FFEQ_ERR_INVALID_ARG;
+  const ffeq_problem& p = plan->p;
+  if (p.n_sc == 0) return FFEQ_OK;
+  const OptimalLayoutBytes t = optimal_layout(plan);
+  if (!H || !y || !gz || !gH || !gy || !workspace || workspace_bytes < t.total) return FFEQ_ERR_INVALID_ARG;
+  if (!aligned(H, 8) || !aligned(y, 8) || !aligned(gz, 8) || !aligned(gH, 8) || !aligned(gy, 8) ||
+      !aligned(workspace, 256))
+    return FFEQ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  r = local_preprocess(plan, H, y, workspace, st);
+  if (r != FFEQ_OK) return r;
+  char* base = static_cast<char*>(workspace);
+  ffeq::TrainParams tp{};
+  tp.H = static_cast<const float2*>(H);
+  tp.y = static_cast<const float2*>(y);
+  tp.D = reinterpret_cast<const float2*>(base);
+  tp.Gb = reinterpret_cast<float2*>(base + t.D);
+  tp.Wm = reinterpret_cast<float2*>(base + t.D + t.Gb);
+  tp.gz = static_cast<const float2*>(gz);
+  tp.gH = static_cast<float2*>(gH);
+  tp.gy = static_cast<float2*>(gy);
+  tp.B = p.B;
+  tp.U = p.U;
+  tp.C = p.C;
+  tp.n_sc = p.n_sc;
+  tp.n_sym = p.n_sym;
+  tp.rho = static_cast<float>(static_cast<double>(N0) / static_cast<double>(Es));
+  tp.status = ffeq::device_status_ptr();
+  tp.cl_uniform = plan->cl_uniform ? 1 : 0;
+  for (int c = 0; c <= p.C && !plan->cl_uniform; ++c) tp.cl_off[c] = plan->cl_off[c];
+  const cudaError_t e = ffeq::launch_train_optimal_backward(tp, st);
+  return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+}
 
 ffeq_status ffeq_fd_train_workspace_size(const ffeq_plan* plan, size_t* bytes) {
   if (!plan || !bytes) return FFEQ_ERR_INVALID_ARG;

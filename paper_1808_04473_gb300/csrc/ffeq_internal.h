@@ -161,10 +161,19 @@ struct TrainParams {
   float* grho;         // [C]
   float* gnu;          // [C][U]
   int B, U, C, n_sc, n_sym;
+  // Adjoint through the optimal weights (ffeq_fd_optimal_backward): rho = N0 / Es
+  // shared by every cluster; clusters of cl_off (cl_uniform: B / C antennas each).
+  float rho;
+  int* status;
+  int cl_uniform;
+  int cl_off[kMaxClusters + 1];
 };
 size_t train_smem_bytes(int U, int C);
 cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t stream);
 cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t stream);
+// Shared memory of the optimal-weight backward solve (one CTA per subcarrier).
+size_t train_optimal_smem_bytes(int U, int C);
+cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t stream);
 
 // Padded user count (8, 16 or 32) used for register tiles.
 int padded_users(int U);

@@ -170,6 +170,146 @@ __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainPa
   }
 }
 
+// Adjoint through the optimal-weight rule (the FD estimate ffeq_equalize
+// computes with unbiased pairs: Lemma 1's weights from diag(A_c) and mu),
+// per subcarrier, from the contraction output D and dL/dz.  With M_c = G_c +
+// rho I, A_c = M_c^{-1}, X_c = A_c B_c, a_c = diag(A_c), w_c = 1 / a_c,
+// D_u = sum_c (w_{c,u} - rho) and z_u = sum_c w_{c,u} X_{c,u} / D_u (Eq. fusionrule
+// with nu = mu / (N0 a) / sum, N0 cancelled):
+//   G_x = diag(w_c / D) G_z,   G_b = A_c G_x,
+//   q_u = -Re(sum_n conj(g_z,u,n) (X_{c,u,n} - z_{u,n})) / (D_u a_{c,u}^2),
+//   W_c = X_c G_b^H + G_b X_c^H + 2 A_c diag(q) A_c,
+// after which train_backward_contract_kernel forms dL/dH_c = Y_c G_b^H - H_c W_c
+// and dL/dY_c = H_c G_b.  (dz_u = sum_c (w dX + (X - z) dw) / D with dw = -da / a^2,
+// dX = A (dB - dM X), da_u = -[A dM A]_uu.)  One CTA per subcarrier, one group of
+// UP lanes per cluster; lane i = user i.  The sweep runs on [M_c | B_c] and
+// leaves row i of X_c and of A_c.  A user no cluster can see (D_u <= 0) has
+// z = 0 and contributes nothing.  A subcarrier with a system that is not
+// positive definite gets NaN gradients.
+template <int UP>
+struct OptimalLayout {
+  static constexpr int kW = UP + kNsymMax;
+  // Per group: pivot-row buffer (kW), X [kNsymMax][UP], G_x then G_b [kNsymMax][UP],
+  // and q (UP floats as UP / 2 complex).
+  static constexpr int kGroup = kW + 2 * kNsymMax * UP + UP / 2 + 8;
+};
+
+template <int UP>
+__global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = OptimalLayout<UP>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  int* fail_any = reinterpret_cast<int*>(smem);
+  float* wv = reinterpret_cast<float*>(smem + 16);                       // [C][UP]: w_{c,u}
+  float2* grp = reinterpret_cast<float2*>(smem + 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16);
+  float2* rowbuf = grp + gm * Lay::kGroup;
+  float2* Xs = rowbuf + W;                     // [kNsymMax][UP]
+  float2* Gs = Xs + kNsymMax * UP;             // [kNsymMax][UP]
+  float* qv = reinterpret_cast<float*>(Gs + kNsymMax * UP);   // [UP]
+  if (threadIdx.x == 0) *fail_any = 0;
+  __syncthreads();
+
+  const size_t matSize = static_cast<size_t>(U + NS) * U;
+  const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
+  const float rho = p.rho;
+  float2 aug[W];
+  load_row<UP>(aug, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
+  const int fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+  if (valid && i == 0 && fail) atomicOr(fail_any, 1);
+  // aug[0 .. kNsymMax) = row i of X_c, aug[kNsymMax .. W) = row i of A_c.
+  float a = 1.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j)
+    if (j == i) a = aug[kNsymMax + j].x;
+  const bool real = valid && i < U;
+  const float w = real ? 1.f / a : 0.f;
+  if (valid) {
+    wv[gm * UP + i] = real ? w : rho;         // padding users: w - rho = 0
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) Xs[n * UP + i] = (real && n < NS) ? aug[n] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const bool bad = *fail_any != 0;
+  // D_u and z_u over the clusters in a fixed order (every group for its own users).
+  float Du = 0.f;
+  for (int cc = 0; cc < C; ++cc) Du += wv[cc * UP + i] - rho;
+  const bool seen = Du > 0.f;
+  const float invD = seen ? 1.f / Du : 0.f;
+  const float2* gzk = p.gz + static_cast<size_t>(k) * NS * U;
+  float qn = 0.f;                                 // sum_n Re(conj(g_z) (X - z))
+#pragma unroll
+  for (int n = 0; n < kNsymMax; ++n) {
+    if (n < NS) {
+      float2 num = make_float2(0.f, 0.f);
+      for (int cc = 0; cc < C; ++cc) {
+        const float2 xc = (grp + cc * Lay::kGroup + W)[n * UP + i];
+        const float wc = wv[cc * UP + i];
+        num = make_float2(fmaf(wc, xc.x, num.x), fmaf(wc, xc.y, num.y));
+      }
+      const float2 zn = cscale(num, invD);
+      const float2 gzv = real ? gzk[n * U + i] : make_float2(0.f, 0.f);
+      qn = fmaf(gzv.x, aug[n].x - zn.x, fmaf(gzv.y, aug[n].y - zn.y, qn));
+      if (valid) Gs[n * UP + i] = cscale(gzv, w * invD);   // G_x
+    }
+  }
+  if (valid) qv[i] = (real && seen) ? -qn * invD * w * w : 0.f;   // 1 / a^2 = w^2
+  __syncwarp();
+  // G_b row i = sum_j A_ij G_x[j] (A row i in aug[kNsymMax ..)).
+  float2 gb[kNsymMax];
+#pragma unroll
+  for (int n = 0; n < kNsymMax; ++n) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (n < NS) {
+#pragma unroll
+      for (int j = 0; j < UP; ++j) acc = cfma(aug[kNsymMax + j], Gs[n * UP + j], acc);
+    }
+    gb[n] = bad ? make_float2(NAN, NAN) : acc;
+  }
+  __syncwarp();
+  const size_t off = (static_cast<size_t>(k) * C + gm) * NS * U;
+  if (valid) {
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) {
+      if (n < NS) {
+        Gs[n * UP + i] = gb[n];
+        if (real) p.Gb[off + n * U + i] = gb[n];
+      }
+    }
+  }
+  // W row i, column v: sum_n (G_b[i][n] conj(X[v][n]) + X[i][n] conj(G_b[v][n]))
+  // + 2 sum_j A_ij q_j A_jv, with row v of A broadcast by lane v (A_jv = conj(A_vj)).
+  float2* Wk = p.Wm + (static_cast<size_t>(k) * C + gm) * U * U + static_cast<size_t>(i) * U;
+  for (int v = 0; v < U; ++v) {
+    __syncwarp();
+    if (valid && i == v) {
+#pragma unroll
+      for (int j = 0; j < UP; ++j) rowbuf[j] = aug[kNsymMax + j];
+    }
+    __syncwarp();
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n = 0; n < kNsymMax; ++n) {
+      if (n < NS) {
+        const float2 xv = Xs[n * UP + v], gv = Gs[n * UP + v];
+        acc = cfma(gb[n], make_float2(xv.x, -xv.y), acc);
+        acc = cfma(aug[n], make_float2(gv.x, -gv.y), acc);
+      }
+    }
+    float2 ext = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      const float2 av = rowbuf[j];                                     // A_vj
+      ext = cfma(cscale(aug[kNsymMax + j], qv[j]), make_float2(av.x, -av.y), ext);
+    }
+    if (real) Wk[v] = bad ? make_float2(NAN, NAN) : make_float2(fmaf(2.f, ext.x, acc.x), fmaf(2.f, ext.y, acc.y));
+  }
+}
+
 // Backward contraction: thread per antenna b (its columns of H and Y in
 // registers, read coalesced from HBM), cluster c = b / S:
 //   dL/dH[u][b] = sum_n Y[n][b] conj(G_b[n][u]) - sum_v H[v][b] W[v][u]
@@ -180,6 +320,7 @@ __global__ void __launch_bounds__(256) train_backward_contract_kernel(const Trai
   extern __shared__ __align__(16) unsigned char smem[];
   const int U = p.U, NS = p.n_sym, C = p.C, B = p.B, S = B / C;
   const int k = blockIdx.x;
+  int c = 0;   // cluster of antenna b (clusters of given sizes: walked upwards with b)
   float2* Gs = reinterpret_cast<float2*>(smem);            // [C][NS][U]
   float2* Ws = Gs + static_cast<size_t>(C) * NS * U;       // [C][U][U]
   const float2* Gk = p.Gb + static_cast<size_t>(k) * C * NS * U;
@@ -192,7 +333,11 @@ __global__ void __launch_bounds__(256) train_backward_contract_kernel(const Trai
   float2* gHk = p.gH + static_cast<size_t>(k) * U * B;
   float2* gyk = p.gy + static_cast<size_t>(k) * NS * B;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    const int c = b / S;
+    if (p.cl_uniform) {
+      c = b / S;
+    } else {
+      while (c + 1 < C && b >= p.cl_off[c + 1]) ++c;
+    }
     const float2* Gc = Gs + static_cast<size_t>(c) * NS * U;
     const float2* Wc = Ws + static_cast<size_t>(c) * U * U;
     float2 h[UP], yv[kNsymMax];
@@ -275,6 +420,27 @@ cudaError_t launch_backward_up(const TrainParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int UP>
+size_t optimal_smem_up(int C) {
+  return 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16 +
+         static_cast<size_t>(C) * OptimalLayout<UP>::kGroup * sizeof(float2);
+}
+
+template <int UP>
+cudaError_t launch_optimal_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = optimal_smem_up<UP>(p.C);
+  cudaError_t e = set_smem(train_optimal_solve_kernel<UP>, smem);
+  if (e != cudaSuccess) return e;
+  train_optimal_solve_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem2 = (static_cast<size_t>(p.C) * p.n_sym * p.U + static_cast<size_t>(p.C) * p.U * p.U) *
+                       sizeof(float2);
+  if ((e = set_smem(train_backward_contract_kernel<UP>, smem2)) != cudaSuccess) return e;
+  train_backward_contract_kernel<UP><<<p.n_sc, 256, smem2, st>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t train_smem_bytes(int U, int C) {
@@ -298,6 +464,22 @@ cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t st) {
     case 8: return launch_backward_up<8>(p, st);
     case 16: return launch_backward_up<16>(p, st);
     default: return launch_backward_up<32>(p, st);
+  }
+}
+
+size_t train_optimal_smem_bytes(int U, int C) {
+  switch (padded_users(U)) {
+    case 8: return optimal_smem_up<8>(C);
+    case 16: return optimal_smem_up<16>(C);
+    default: return optimal_smem_up<32>(C);
+  }
+}
+
+cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t st) {
+  switch (padded_users(p.U)) {
+    case 8: return launch_optimal_up<8>(p, st);
+    case 16: return launch_optimal_up<16>(p, st);
+    default: return launch_optimal_up<32>(p, st);
   }
 }
 

@@ -76,6 +76,8 @@ _SIGS = {
     "ffeq_fd_train_workspace_size": ([_vp, ctypes.POINTER(_sz)], _i),
     "ffeq_fd_train_forward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ffeq_fd_train_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ffeq_fd_optimal_workspace_size": ([_vp, ctypes.POINTER(_sz)], _i),
+    "ffeq_fd_optimal_backward": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ffeq_equalize_noalloc": ([_vp, _vp, _vp, _f, _f, _vp, _vp, _vp, _vp, _vp], _i),
     "ffeq_device_status": ([ctypes.POINTER(_i), _i], _i),
     "ffeq_plan_set_tuning": ([_vp, ctypes.POINTER(_i), _i], _i),
@@ -236,6 +238,19 @@ def ffeq_fd_train_backward(plan: Plan, H, y, rho_c, nu, gz, gH, gy, grho, gnu, w
     _check("ffeq_fd_train_backward", lib().ffeq_fd_train_backward(
         plan.handle, _ptr(H), _ptr(y), _ptr(rho_c), _ptr(nu), _ptr(gz), _ptr(gH), _ptr(gy), _ptr(grho), _ptr(gnu),
         _ptr(workspace), workspace_bytes, _stream(stream)))
+
+
+def ffeq_fd_optimal_workspace_size(plan: Plan) -> int:
+    n = _sz()
+    _check("ffeq_fd_optimal_workspace_size", lib().ffeq_fd_optimal_workspace_size(plan.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ffeq_fd_optimal_backward(plan: Plan, H, y, N0: float, Es: float, gz, gH, gy, workspace, workspace_bytes: int,
+                             stream=None) -> None:
+    _check("ffeq_fd_optimal_backward", lib().ffeq_fd_optimal_backward(
+        plan.handle, _ptr(H), _ptr(y), float(N0), float(Es), _ptr(gz), _ptr(gH), _ptr(gy), _ptr(workspace),
+        workspace_bytes, _stream(stream)))
 
 
 def ffeq_equalize_noalloc(plan: Plan, H, y, N0: float, Es: float, z, sigma2, llr=None, info=None,

@@ -28,6 +28,8 @@ int main(void) {
   size_t ws = 0;
   CHECK(ffeq_workspace_size(plan, &ws) == FFEQ_OK);
   CHECK(ws == (size_t)1200 * 8 * (16 + 14) * 16 * 8);
+  size_t wopt = 0;
+  CHECK(ffeq_fd_optimal_workspace_size(plan, &wopt) == FFEQ_OK && wopt > ws);
   size_t staging = 0;
   CHECK(ffeq_host_staging_size(plan, &staging) == FFEQ_OK && staging > ws);
   ffeq_plan_destroy(plan);

@@ -275,3 +275,32 @@ def test_plain_c_client_compiles_links_and_runs(built, tmp_path):
     assert cc.returncode == 0, cc.stderr
     run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0 and run.stdout.strip() == "ok", run.stderr
+
+
+def test_optimal_backward_validation(built):
+    """ffeq_fd_optimal_backward differentiates the FD estimate with unbiased pairs and
+    no refinement: other plans are rejected before any launch; the workspace holds the
+    contraction output, G_b and the H-term matrices."""
+    ff = ffeq
+    ok = ff.ffeq_plan_create(64, 8, 4, 10, 2, arch=ff.FD)
+    nb = ff.ffeq_fd_optimal_workspace_size(ok)
+    plain = ff.ffeq_workspace_size(ok)
+    assert nb >= plain + 10 * 4 * (2 * 8 + 8 * 8) * 8
+    for bad in (dict(arch=ff.PD), dict(arch=ff.FD, estimate=ff.LITERAL), dict(arch=ff.FD, refine=1),
+                dict(arch=ff.FD, equalizer=ff.ZF)):
+        plan = ff.ffeq_plan_create(64, 8, 4, 10, 2, **bad)
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_fd_optimal_workspace_size(plan)
+        assert e.value.status == 1, bad
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_fd_optimal_backward(plan, 256, 256, 0.1, 1.0, 256, 256, 256, 256, nb, stream=0)
+        assert e.value.status == 1, bad
+    # Null buffers, a short workspace and bad scalars are argument errors.
+    for args in ((None, 256, 0.1, 1.0, 256, 256, 256, 256, nb), (256, 256, 0.1, 1.0, 256, 256, 256, 256, nb - 1),
+                 (256, 256, -1.0, 1.0, 256, 256, 256, 256, nb), (256, 256, 0.1, 0.0, 256, 256, 256, 256, nb)):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_fd_optimal_backward(ok, *args, stream=0)
+        assert e.value.status == 1, args
+    # Clusters of given sizes are accepted.
+    sized = ff.ffeq_plan_create(100, 8, 3, 10, 2, arch=ff.FD, cluster_sizes=[40, 35, 25])
+    assert ff.ffeq_fd_optimal_workspace_size(sized) > 0

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import parity
-from oracle import adjoint
+from oracle import adjoint, lmmse
 from paper_1808_04473_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -123,3 +123,99 @@ def test_autograd_function_matches_the_c_abi(ff):
     ref = _run(ff, p, rho, nu, 4, gz)
     for t, name in ((H, "gH"), (y, "gy"), (r, "grho"), (w, "gnu")):
         assert _relmax(t.grad.cpu().numpy(), ref[name]) <= 1e-5, name
+
+
+# ---------------------------------------------------------------- gradients through the optimal weights
+
+def _optimal(ff, p, C, gz, sizes=None, precision=0):
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(p.H).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    plan = ff.ffeq_plan_create(p.B, p.U, C, p.n_sc, p.n_sym, arch=ff.FD, precision=precision, cluster_sizes=sizes)
+    nb = ff.ffeq_fd_optimal_workspace_size(plan)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    g = torch.from_numpy(gz.astype(np.complex64)).to(dev)
+    gH, gy = torch.empty_like(H), torch.empty_like(y)
+    ff.ffeq_fd_optimal_backward(plan, H, y, p.N0, p.Es, g, gH, gy, ws, nb)
+    torch.cuda.synchronize()
+    return gH.cpu().numpy(), gy.cpu().numpy()
+
+
+OPT_CASES = [  # B, U, C, n_sc, n_sym, sizes
+    (16, 3, 2, 7, 2, None),
+    (64, 16, 4, 20, 3, None),
+    (128, 8, 8, 24, 14, None),          # n_sym = 14 right-hand sides
+    (96, 12, 3, 10, 5, [40, 24, 32]),   # clusters of given sizes (Sec. II-B)
+    (100, 8, 3, 12, 2, [40, 35, 25]),   # B % C != 0
+    (256, 32, 8, 4, 6, None),           # U = 32
+]
+
+
+@pytest.mark.parametrize("B,U,C,n_sc,n_sym,sizes", OPT_CASES)
+def test_optimal_weight_adjoint_matches_the_oracle(ff, B, U, C, n_sc, n_sym, sizes):
+    """dL/dH, dL/dy through Lemma 1's weights (ffeq_fd_optimal_backward) against the
+    oracle's closed form (pinned to finite differences of the FD forward), 1e-3 per
+    subcarrier and per entry, for an MSE loss of the FD estimate."""
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=8.0, bits=2, seed=B + 3 * U + C)
+    N0 = float(np.float32(p.N0))
+    z0 = lmmse.equalize_fd(p.H, p.y, N0, p.Es, C, "unbiased", cluster_sizes=sizes)["z"]
+    gz = 2.0 * (z0 - p.s) / z0.size
+    gH, gy = _optimal(ff, p, C, gz, sizes)
+    oH, oy = adjoint.fd_optimal_backward(p.H, p.y, N0, p.Es, C, gz.astype(np.complex64).astype(np.complex128),
+                                         cluster_sizes=sizes)
+    parity.check("gH", gH, oH, 1e-3)
+    parity.check("gy", gy, oy, 1e-3)
+    assert ff.ffeq_device_status() == 0
+
+
+def test_optimal_weight_adjoint_on_the_training_shape(ff):
+    """B=128, U=16, C=8 (S=16), 8 x 1024 subcarriers, QPSK, 10 dB; 16 sampled subcarriers
+    against the oracle (the GPU computes all of them)."""
+    p = synth.make_problem(128, 16, 8, 8 * 1024, 1, snr_db=10.0, bits=2, seed=23)
+    N0 = float(np.float32(p.N0))
+    idx = np.random.default_rng(2).choice(p.n_sc, 16, replace=False)
+    rng = np.random.default_rng(3)
+    gz = (rng.standard_normal((p.n_sc, 1, 16)) + 1j * rng.standard_normal((p.n_sc, 1, 16))) / 8192.0
+    gH, gy = _optimal(ff, p, 8, gz)
+    oH, oy = adjoint.fd_optimal_backward(p.H[idx], p.y[idx], N0, p.Es, 8,
+                                         gz[idx].astype(np.complex64).astype(np.complex128))
+    parity.check("gH", gH[idx], oH, 1e-3)
+    parity.check("gy", gy[idx], oy, 1e-3)
+    assert np.isfinite(gH).all() and np.isfinite(gy).all()
+
+
+def test_optimal_weight_adjoint_against_finite_differences(ff):
+    """Directly against central differences of the FP64 FD forward (Lemma 1 weights)
+    on a tiny case, for every entry of H and y."""
+    p = synth.make_problem(12, 3, 2, 2, 2, snr_db=5.0, bits=2, seed=4)
+    N0 = float(np.float32(p.N0))
+    H, y = p.H.astype(np.complex128), p.y.astype(np.complex128)
+
+    def loss(h, t):
+        z = lmmse.equalize_fd(h, t, N0, p.Es, 2, "unbiased")["z"]
+        return float(np.sum(np.abs(z - p.s) ** 2))
+
+    z0 = lmmse.equalize_fd(H, y, N0, p.Es, 2, "unbiased")["z"]
+    gH, gy = _optimal(ff, p, 2, 2.0 * (z0 - p.s))
+    fH = adjoint.finite_difference(lambda h: loss(h, y), H)
+    fy = adjoint.finite_difference(lambda t: loss(H, t), y)
+    assert _relmax(gH, fH) <= 1e-3 and _relmax(gy, fy) <= 1e-3
+
+
+def test_optimal_autograd_function_matches_the_c_abi(ff):
+    from paper_1808_04473_gb300.autograd import fd_equalize_optimal
+    p = synth.make_problem(64, 8, 4, 16, 2, snr_db=10.0, bits=2, seed=25)
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(p.H).to(dev).requires_grad_(True)
+    y = torch.from_numpy(p.y).to(dev).requires_grad_(True)
+    s = torch.from_numpy(p.s.astype(np.complex64)).to(dev)
+    z = fd_equalize_optimal(H, y, p.N0, p.Es, 4)
+    loss = (z - s).abs().pow(2).mean()
+    loss.backward()
+    z0 = z.detach().cpu().numpy()
+    gz = 2.0 * (z0 - p.s) / z0.size
+    gH, gy = _optimal(ff, p, 4, gz)
+    assert _relmax(H.grad.cpu().numpy(), gH) <= 1e-5 and _relmax(y.grad.cpu().numpy(), gy) <= 1e-5
+    # Its forward is the library's FD estimate.
+    ref = ff.equalize(H.detach(), y.detach(), p.N0, p.Es, 4, arch=ff.FD)
+    assert torch.equal(z.detach(), ref["z"])
