@@ -398,8 +398,12 @@ def soak(replay, seconds: float, torch):
         torch.cuda.synchronize()
 
 
+STEP_SHAPES = ((5, 0), (4, 0), (2, 0), (1, 0))   # contraction shapes tried together for a whole step
+
+
 def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equalizer=0, refine=0,
-                   refine_fp64=0, pinned=None, breakdown=False, sampler=None, soak_s=0.0):
+                   refine_fp64=0, pinned=None, breakdown=False, sampler=None, soak_s=0.0, concurrent=False,
+                   tune_step=False):
     """K steps of PD then FD equalization; each step is captured once per rotating
     input set as a CUDA graph (what a serving loop replays per frame) and the
     timed region replays K graphs, bracketed by CUDA events on the replay stream.
@@ -408,6 +412,13 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     programmatic dependent launch); with refinement it is ffeq_equalize per
     architecture.  breakdown: a separate pass replays graphs of one kernel each
     (that kernel alone, on the rotating input sets) for per-kernel device times.
+    concurrent: PD and FD as two branches of the captured step (a second stream
+    forked from and joined to the replay stream), so that one architecture's
+    kernels can run while the other's hold fewer SMs.
+    tune_step: after each plan's own autotuning, time the whole captured step for
+    every pair of contraction shapes in STEP_SHAPES, sequential and concurrent,
+    and keep the fastest (setup, outside the timed region): the best shape of a
+    plan alone is not always the best one next to the other plan's kernels.
     Leaves the outputs of input set 0 in `outs`."""
     torch, ffeq, dev = R.torch, R.ffeq, R.dev
     B, U, C, n_sc, n_sym = shape
@@ -452,13 +463,76 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
             fn()
         return g
 
+    cap2 = torch.cuda.Stream(dev)
+
+    def whole_step(i):
+        if not concurrent:
+            for a in archs:
+                launch(a, i, "step")
+            return
+        fork, join = torch.cuda.Event(), torch.cuda.Event()
+        fork.record(cap)
+        cap2.wait_event(fork)
+        launch(archs[0], i, "step")
+        o = outs[archs[1]]
+        # The second architecture on the forked stream (same calls, other stream).
+        if not split:
+            ffeq.ffeq_equalize(plans[archs[1]], Hs[i], ys[i], N0, Es, o["z"], o["s2"], o["llr"], None, ws[archs[1]],
+                               nb[archs[1]], cap2)
+        else:
+            ffeq.ffeq_local_preprocess(plans[archs[1]], Hs[i], ys[i], ws[archs[1]], nb[archs[1]], cap2)
+            ffeq.ffeq_fuse_equalize(plans[archs[1]], ws[archs[1]], nb[archs[1]], N0, Es, o["z"], o["s2"], o["llr"],
+                                    None, cap2)
+        join.record(cap2)
+        cap.wait_event(join)
+
+    def time_steps(graphs, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cap):
+            for i in range(n_sets):
+                graphs[i].replay()
+            e0.record(cap)
+            for k in range(reps):
+                graphs[k % n_sets].replay()
+            e1.record(cap)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     torch.cuda.synchronize()
     with torch.cuda.stream(cap):
         for i in range(2):           # eager warm-up before capture
             for a in archs:
                 launch(a, i % n_sets, "step")
     cap.synchronize()
-    steps = [capture(lambda i=i: [launch(a, i, "step") for a in archs]) for i in range(n_sets)]
+    schedule = {"concurrent": concurrent}
+    if tune_step and not pinned:
+        best = None
+        for tp in STEP_SHAPES:
+            for tf in STEP_SHAPES:
+                try:
+                    ffeq.ffeq_plan_set_tuning(plans[archs[0]], tp)
+                    ffeq.ffeq_plan_set_tuning(plans[archs[1]], tf)
+                except ffeq.FfeqError:
+                    continue
+                with torch.cuda.stream(cap):
+                    for a in archs:          # first use of a shape outside capture
+                        launch(a, 0, "step")
+                for conc in (False, True):
+                    concurrent = conc
+                    gs = [capture(lambda i=i: whole_step(i)) for i in range(n_sets)]
+                    t = time_steps(gs, 4 * n_sets)
+                    del gs
+                    if best is None or t < best[0]:
+                        best = (t, tp, tf, conc)
+        _, tp, tf, concurrent = best
+        ffeq.ffeq_plan_set_tuning(plans[archs[0]], tp)
+        ffeq.ffeq_plan_set_tuning(plans[archs[1]], tf)
+        schedule = {"concurrent": concurrent, "chosen_by": "whole-step timing over contraction shape pairs"}
+        with torch.cuda.stream(cap):
+            for a in archs:
+                launch(a, 0, "step")
+        cap.synchronize()
+    steps = [capture(lambda i=i: whole_step(i)) for i in range(n_sets)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if sampler is not None:          # clocks: sampled from the load phase through the timed region
         sampler.__enter__()
@@ -509,7 +583,7 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     assert ffeq.ffeq_device_status() == 0
     for a in outs:
         assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
-    return dict(ms=ms, kern=kern, plans=plans, outs=outs)
+    return dict(ms=ms, kern=kern, plans=plans, outs=outs, schedule=schedule)
 
 
 def uneven_line(R, K, warmup, precision, sampler=None):
@@ -708,6 +782,52 @@ def run_training(R, K, warmup):
     out["roofline"] = {"kernel": "whole step (contraction, train_forward, adjoint kernels)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "peak_source": f"{peak_src} (STREAM-style copy)",
                        "unit": "GB/s", "frac": achieved / hbm_peak, "algorithmic_bytes_per_step": alg}
+    # The FD estimate with the paper's optimal weights (ffeq_equalize) and its adjoint
+    # through the weight rule (ffeq_fd_optimal_backward), the same upstream gradient.
+    oplan = ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=ffeq.FD)
+    onb = ffeq.ffeq_workspace_size(oplan)
+    ows = torch.empty(onb, dtype=torch.uint8, device=dev)
+    bnb = ffeq.ffeq_fd_optimal_workspace_size(oplan)
+    bws = torch.empty(bnb, dtype=torch.uint8, device=dev)
+    zo = torch.empty_like(z)
+    s2o = torch.empty((n_sc, U), dtype=torch.float32, device=dev)
+
+    def ostep(i):
+        ffeq.ffeq_equalize(oplan, Hs[i], ys[i], p.N0, p.Es, zo, s2o, None, None, ows, onb, cap)
+        ffeq.ffeq_fd_optimal_backward(oplan, Hs[i], ys[i], p.N0, p.Es, gz, gH, gy, bws, bnb, cap)
+
+    with torch.cuda.stream(cap):
+        for i in range(2):
+            ostep(i % n_sets)
+    cap.synchronize()
+    ographs = []
+    for i in range(n_sets):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            ostep(i)
+        ographs.append(g)
+    with torch.cuda.stream(cap):
+        for i in range(warmup):
+            ographs[i % n_sets].replay()
+    torch.cuda.synchronize()
+    R.barrier()
+    with torch.cuda.stream(cap):
+        start.record(cap)
+        for k in range(K):
+            ographs[k % n_sets].replay()
+        end.record(cap)
+    torch.cuda.synchronize()
+    oms = start.elapsed_time(end)
+    if R.world > 1:
+        oms = max_over_ranks(oms, dev)
+    assert ffeq.ffeq_device_status() == 0
+    out["optimal_weights"] = {
+        "step": "ffeq_equalize (FD, Lemma 1 weights) + ffeq_fd_optimal_backward (dL/dH, dL/dy through the "
+                "weight rule)", "value": job_rate(U * n_sc * n_sym, R.world, K, oms), "unit": UNIT,
+        "ms_per_step": oms / K, "steps": K}
+    with torch.cuda.stream(cap):
+        graphs[0].replay()                   # leave the free-weight outputs of input set 0
+    torch.cuda.synchronize()
     if R.rank == 0:
         from oracle import adjoint
         idx = np.linspace(0, n_sc - 1, 8).astype(int)
@@ -733,6 +853,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline step only (no equalizer variants, correlated, training or uneven lines)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--concurrent", type=int, default=0,
+                    help="1: PD and FD as two concurrent branches of each captured step")
     ap.add_argument("--precision", default="bf16x3", choices=PRECISIONS,
                     help="arithmetic of the local preprocessing (solve and fusion are FP32)")
     ap.add_argument("--tuning", default=None,
@@ -783,8 +905,9 @@ def main():
     K = args.steps
     clk = ClockSampler(local_rank)
     head = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=args.precision, bits=bits, K=K,
-                          warmup=args.warmup, pinned=pinned, breakdown=True, sampler=clk, soak_s=1.0)
-    elapsed_ms, kern, plans = head["ms"], head["kern"], head["plans"]
+                          warmup=args.warmup, pinned=pinned, breakdown=True, sampler=clk, soak_s=1.0,
+                          concurrent=bool(args.concurrent), tune_step=not args.tuning)
+    elapsed_ms, kern, plans, schedule = head["ms"], head["kern"], head["plans"], head["schedule"]
     accuracy = _accuracy(p, head["outs"], idx, (0, 1)) if do_cpu else None
     if accuracy is not None:
         accuracy["subcarriers"] = len(idx)
@@ -798,9 +921,11 @@ def main():
     if args.precision != "fp32":
         Kc = max(5, K // 4)
         r32 = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision="fp32", bits=bits, K=Kc, warmup=args.warmup,
-                             breakdown=True)
+                             breakdown=True, tune_step=True)
         fp32_cmp = {"value": job_rate(symbols_per_step, world, Kc, r32["ms"]), "ms_per_step": r32["ms"] / Kc,
-                    "steps": Kc, "kernels_ms": r32["kern"],
+                    "steps": Kc, "kernels_ms": r32["kern"], "schedule": r32["schedule"],
+                    "tuning": {("pd" if a == ffeq.PD else "fd"): list(ffeq.ffeq_plan_get_tuning(pl))
+                               for a, pl in r32["plans"].items()},
                     "error_vs_oracle": _accuracy(p, r32["outs"], idx, (0, 1)) if do_cpu else None}
         del r32
 
@@ -811,9 +936,9 @@ def main():
         Kv = max(5, K // 4)
         for name, eq in (("zf", ffeq.ZF), ("mrc", ffeq.MRC), ("lama", ffeq.LAMA)):
             rv = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=args.precision, bits=bits, K=Kv,
-                                warmup=args.warmup, equalizer=eq, breakdown=True)
+                                warmup=args.warmup, equalizer=eq, breakdown=True, tune_step=True)
             variants[name] = {"value": job_rate(symbols_per_step, world, Kv, rv["ms"]), "ms_per_step": rv["ms"] / Kv,
-                              "steps": Kv, "kernels_ms": rv["kern"]}
+                              "steps": Kv, "kernels_ms": rv["kern"], "schedule": rv["schedule"]}
             del rv
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -889,6 +1014,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "kernels_ms": kern,
         "tuning": {("pd" if a == ffeq.PD else "fd"): list(ffeq.ffeq_plan_get_tuning(pl)) for a, pl in plans.items()},
+        "schedule": schedule,
         "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / ((kern["pd_local"] + kern["pd_fuse"]) * 1e-3),
                                    "fd": U * n_sc * n_sym / ((kern["fd_local"] + kern["fd_fuse"]) * 1e-3)},
         "roofline": roof,
