@@ -64,6 +64,15 @@ struct ffeq_batch {
   bool dirty = true;                        // tables changed since the last upload
   const void* uploaded_ws = nullptr;
   int uploaded_dev = -1;
+  // Side streams (device side_dev) on which the groups after the first run
+  // concurrently with it: forked from the caller's stream after the queue
+  // counters are reset, joined back before the call returns.
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSide] = {};
+  int n_side = 0;
+  int side_dev = -1;
   std::mutex mu;
 };
 
@@ -328,12 +337,34 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
     b->pinned = true;
   }
   build_tables(b);
+  // Side streams for the groups after the first (none when there is one group,
+  // or when no device is usable here: the groups then run in order).
+  const int want = static_cast<int>(b->groups.size()) - 1 < ffeq_batch::kSide
+                       ? static_cast<int>(b->groups.size()) - 1 : ffeq_batch::kSide;
+  if (want > 0 && cudaGetDevice(&b->side_dev) == cudaSuccess &&
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess) {
+    for (int j = 0; j < want; ++j) {
+      if (cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) != cudaSuccess) {
+        if (b->side[j]) cudaStreamDestroy(b->side[j]);
+        b->side[j] = nullptr;
+        break;
+      }
+      b->n_side = j + 1;
+    }
+  }
+  (void)cudaGetLastError();
   *out = b;
   return FFEQ_OK;
 }
 
 void ffeq_batch_destroy(ffeq_batch* b) {
   if (!b) return;
+  for (int j = 0; j < b->n_side; ++j) {
+    cudaStreamDestroy(b->side[j]);
+    cudaEventDestroy(b->join[j]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->pinned) {
     cudaFreeHost(b->host);
   } else {
@@ -436,9 +467,23 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
   const ffeq::SolveTile* tiles = reinterpret_cast<const ffeq::SolveTile*>(ws + b->off_tiles);
   const unsigned short* maps = reinterpret_cast<const unsigned short*>(ws + b->off_maps);
   float2* D = reinterpret_cast<float2*>(ws + b->off_D);
+  // Group 0 on the caller's stream, the others on the side streams (round robin)
+  // once they have waited for the counter reset; joined back at the end.
+  const int n_side = dev == b->side_dev ? b->n_side : 0;
+  if (n_side > 0 && (e = cudaEventRecord(b->fork, st)) != cudaSuccess) return cuda_status(e);
+  bool used[ffeq_batch::kSide] = {};
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     const Group& g = b->groups[gi];
     if (g.n_units == 0) continue;
+    cudaStream_t gs = st;
+    if (n_side > 0 && gi > 0) {
+      const int j = static_cast<int>((gi - 1) % n_side);
+      gs = b->side[j];
+      if (!used[j]) {
+        if ((e = cudaStreamWaitEvent(gs, b->fork, 0)) != cudaSuccess) return cuda_status(e);
+        used[j] = true;
+      }
+    }
     ffeq::GramParams gp{};
     gp.H = static_cast<const float2*>(H);
     gp.y = static_cast<const float2*>(y);
@@ -456,8 +501,8 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
     gp.UP = g.UP;
     gp.lim = lim;
     gp.variant = ffeq::kGram16;
-    e = b->cfg.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
-                                      : ffeq::launch_gram_tc(gp, b->cfg.precision, st);
+    e = b->cfg.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, gs)
+                                      : ffeq::launch_gram_tc(gp, b->cfg.precision, gs);
     if (e != cudaSuccess) return cuda_status(e);
     ffeq::SolveParams sp{};
     sp.D = D;
@@ -477,8 +522,13 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
     sp.threads = g.threads;
     sp.lim = lim;
     sp.status = status;
-    e = ffeq::launch_solve_batch(sp, g.lpr, st);
+    e = ffeq::launch_solve_batch(sp, g.lpr, gs);
     if (e != cudaSuccess) return cuda_status(e);
+  }
+  for (int j = 0; j < n_side; ++j) {
+    if (!used[j]) continue;
+    if ((e = cudaEventRecord(b->join[j], b->side[j])) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaStreamWaitEvent(st, b->join[j], 0)) != cudaSuccess) return cuda_status(e);
   }
   return FFEQ_OK;
 }
