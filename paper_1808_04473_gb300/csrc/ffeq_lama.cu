@@ -36,14 +36,15 @@ namespace {
 
 // Posterior mean and variance of one PAM axis (levels a_m = (2m - L + 1) d,
 // L = 2^HB, equiprobable) under Gaussian noise of variance tau/2:
-// p(a_m | x) ~ exp(-(x - a_m)^2 / tau).  Exponents are taken relative to the
-// nearest level a0, and the moments about a0, so that a sharp posterior on an
-// outer level keeps its small variance.
+// p(a_m | x) ~ exp(-(x - a_m)^2 / tau) = 2^(-(x - a_m)^2 log2(e) / tau).
+// Exponents are taken relative to the nearest level a0, and the moments about
+// a0, so that a sharp posterior on an outer level keeps its small variance.
+// inv_d = 1/d; l2t = log2(e) / tau (both once per call site, not per level).
 template <int HB>
-__device__ __forceinline__ void pam_posterior(float x, float inv_tau, float d, float& mean, float& var) {
+__device__ __forceinline__ void pam_posterior(float x, float l2t, float d, float inv_d, float& mean, float& var) {
   constexpr int L = 1 << HB;
   // Nearest level index: round((x/d + L - 1) / 2), clamped to [0, L).
-  float q = rintf((x / d + static_cast<float>(L - 1)) * 0.5f);
+  float q = rintf(fmaf(x, inv_d, static_cast<float>(L - 1)) * 0.5f);
   q = fminf(fmaxf(q, 0.f), static_cast<float>(L - 1));
   const float a0 = (2.f * q - static_cast<float>(L - 1)) * d;
   const float e0 = (x - a0) * (x - a0);
@@ -52,7 +53,7 @@ __device__ __forceinline__ void pam_posterior(float x, float inv_tau, float d, f
   for (int m = 0; m < L; ++m) {
     const float a = (2.f * static_cast<float>(m) - static_cast<float>(L - 1)) * d;
     const float e = x - a;
-    const float w = expf((e0 - e * e) * inv_tau);   // <= 1; exactly 1 at a0
+    const float w = exp2f(fmaf(-e, e, e0) * l2t);   // <= 1; exactly 1 at a0
     const float da = a - a0;
     sw += w;
     s1 = fmaf(w, da, s1);
@@ -106,7 +107,9 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
   }
   const float2 yv = real ? cscale(Dg[(U + nc) * U + ic], kap) : make_float2(0.f, 0.f);
   const float d = p.llr_scale;
+  const float inv_d = 1.f / d;
   const float invU = 1.f / static_cast<float>(U);
+  constexpr float kLog2e = 1.4426950408889634f;
 
   float2 s = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f), z;
   float phi = p.Es, tau;
@@ -129,9 +132,10 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
     tau = fmaf(beta, phi, n0n);
     if (t >= p.lama_iters) break;
     const float inv_tau = 1.f / tau;
+    const float l2t = kLog2e * inv_tau;
     float mr, vr, mi, vi;
-    pam_posterior<HB>(z.x, inv_tau, d, mr, vr);
-    pam_posterior<HB>(z.y, inv_tau, d, mi, vi);
+    pam_posterior<HB>(z.x, l2t, d, inv_d, mr, vr);
+    pam_posterior<HB>(z.y, l2t, d, inv_d, mi, vi);
     float gsum = real ? vr + vi : 0.f;
 #pragma unroll
     for (int o = UP / 2; o > 0; o >>= 1) gsum += __shfl_xor_sync(kFullMask, gsum, o, UP);

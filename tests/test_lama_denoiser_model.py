@@ -22,8 +22,9 @@ def _axis_model(x, tau, d, L):
     """Float32 posterior mean and variance of one axis, as the kernel forms them."""
     f = np.float32
     x = x.astype(f)
-    inv_tau = f(1.0) / f(tau)
-    q = np.clip(np.rint((x / f(d) + f(L - 1)) * f(0.5)), 0, L - 1).astype(f)
+    l2t = f(np.log2(np.e)) * (f(1.0) / f(tau))             # log2(e) / tau: the weights in base 2
+    inv_d = f(1.0) / f(d)
+    q = np.clip(np.rint((x * inv_d + f(L - 1)) * f(0.5)), 0, L - 1).astype(f)
     a0 = (f(2) * q - f(L - 1)) * f(d)
     e0 = (x - a0) * (x - a0)
     sw = np.zeros_like(x)
@@ -32,7 +33,7 @@ def _axis_model(x, tau, d, L):
     for m in range(L):
         a = (f(2 * m) - f(L - 1)) * f(d)
         e = x - a
-        w = np.exp((e0 - e * e) * inv_tau).astype(f)
+        w = np.exp2((e0 - e * e) * l2t).astype(f)
         da = a - a0
         sw += w
         s1 += w * da
