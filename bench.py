@@ -730,6 +730,10 @@ def run_training(R, K, warmup):
     nb = ffeq.ffeq_fd_train_workspace_size(plan)
     ws = torch.empty(nb, dtype=torch.uint8, device=dev)
     z = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev)
+    # The contraction shape of the plan, chosen by timing (setup, untimed).
+    s2t = torch.empty((n_sc, U), dtype=torch.float32, device=dev)
+    ffeq.ffeq_plan_autotune_sets(plan, Hs, ys, p.N0, p.Es, z, s2t, None, None, ws, nb,
+                                 torch.cuda.current_stream(dev), 2 * n_sets)
     gH, gy = torch.empty_like(Hs[0]), torch.empty_like(ys[0])
     grho, gnu = torch.empty_like(rho), torch.empty_like(nu)
     cap = torch.cuda.Stream(dev)
@@ -772,6 +776,7 @@ def run_training(R, K, warmup):
     assert ffeq.ffeq_device_status() == 0
     out = {"workload": "differentiable FD, B=128 U=16 C=8, 8 draws x 1024 subcarriers x 1 sym, QPSK, 10dB: "
                        "forward + adjoint (dL/dH, dL/dy, dL/drho_c, dL/dnu)",
+           "tuning": list(ffeq.ffeq_plan_get_tuning(plan)),
            "value": job_rate(U * n_sc * n_sym, R.world, K, ms), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
            "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)"}
     # HBM roofline of the step: forward reads H, y and writes z; the adjoint reads
@@ -791,6 +796,7 @@ def run_training(R, K, warmup):
     bws = torch.empty(bnb, dtype=torch.uint8, device=dev)
     zo = torch.empty_like(z)
     s2o = torch.empty((n_sc, U), dtype=torch.float32, device=dev)
+    ffeq.ffeq_plan_set_tuning(oplan, ffeq.ffeq_plan_get_tuning(plan))
 
     def ostep(i):
         ffeq.ffeq_equalize(oplan, Hs[i], ys[i], p.N0, p.Es, zo, s2o, None, None, ows, onb, cap)

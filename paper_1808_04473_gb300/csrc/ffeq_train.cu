@@ -14,6 +14,11 @@
 // [G_c + rho_c I | G_x,c]); the forward keeps the local Gram matrices and the
 // local estimates X_c in the workspace.
 //
+// Every sweep is the paired-FMA Gauss-Jordan sweep with deferred scaling of
+// ffeq_gj.cuh on the augmented row [G_c + rho I | R] of UP + NR columns, NR the
+// right-hand-side columns rounded up from n_sym (4 when n_sym <= 4, else 16),
+// so a one-symbol problem does not sweep 16 columns of padding.
+//
 // Workspace: D [n_sc][C][U+n_sym][U] (contraction output, as ffeq_equalize),
 // X [n_sc][C][n_sym][U], Gb [n_sc][C][n_sym][U], W [n_sc][C][U][U] (complex) and
 // per-subcarrier partial sums P [n_sc][C][1+U] (float).
@@ -26,19 +31,26 @@
 namespace ffeq {
 namespace {
 
-template <int UP>
+// Right-hand-side columns of the augmented sweep for n_sym symbols.
+inline int rhs_columns(int n_sym) { return n_sym <= 4 ? 4 : kNsymMax; }
+
+template <int UP, int NR>
 struct TrainLayout {
-  static constexpr int kW = UP + kNsymMax;   // augmented row width
-  // Per group: pivot-row buffer (kW) + two [kNsymMax][UP] blocks.
-  static constexpr int kGroup = kW + 2 * kNsymMax * UP + 8;
+  static constexpr int kW = UP + NR;              // augmented row width
+  static constexpr int kRow = 2 * kW + 4;         // the sweep's two pivot-row buffers (float2 units)
+  // Per group: pivot-row buffers + two [NR][UP] blocks.
+  static constexpr int kGroup = kRow + 2 * NR * UP + 8;
 };
 
-// Row i of [G_c + rho_c I | R] from the workspace D (padding: identity / zero).
-// rhs(n) supplies R[i][n] for n < NS.
-template <int UP, typename Rhs>
-__device__ __forceinline__ void load_row(float2 (&aug)[UP + kNsymMax], const float2* Dg, int U, int NS, int i,
-                                         bool valid, float rho, Rhs rhs) {
+// Row i of [G_c + rho I | R] from the workspace D (padding: identity / zero), as
+// pairs of adjacent columns (rp: re of columns 2m, 2m + 1; ip: im).  rhs(n)
+// supplies R[i][n] for n < NS.
+template <int UP, int NR, typename Rhs>
+__device__ __forceinline__ void load_row(float2 (&rp)[(UP + NR) / 2], float2 (&ip)[(UP + NR) / 2],
+                                         const float2* Dg, int U, int NS, int i, bool valid, float rho, Rhs rhs) {
+  constexpr int W = UP + NR;
   const int ic = i < U ? i : 0;
+  float2 aug[W];
 #pragma unroll
   for (int j = 0; j < UP; ++j) aug[j] = Dg[(j < U ? j : 0) * U + ic];
 #pragma unroll
@@ -49,14 +61,26 @@ __device__ __forceinline__ void load_row(float2 (&aug)[UP + kNsymMax], const flo
     aug[j] = v;
   }
 #pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) aug[UP + n] = (n < NS && valid && i < U) ? rhs(n) : make_float2(0.f, 0.f);
+  for (int n = 0; n < NR; ++n) aug[UP + n] = (n < NS && valid && i < U) ? rhs(n) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < W / 2; ++m) {
+    rp[m] = make_float2(aug[2 * m].x, aug[2 * m + 1].x);
+    ip[m] = make_float2(aug[2 * m].y, aug[2 * m + 1].y);
+  }
+}
+
+// Column t of the swept row (after the sweep: t < NR the solution for right-hand
+// side t, NR + j column j of the inverse), times the deferred scale 1 / p_i.
+template <int W>
+__device__ __forceinline__ float2 swept(const float2 (&rp)[W / 2], const float2 (&ip)[W / 2], int t, float rs) {
+  return make_float2((t % 2 ? rp[t / 2].y : rp[t / 2].x) * rs, (t % 2 ? ip[t / 2].y : ip[t / 2].x) * rs);
 }
 
 // Forward: one CTA per subcarrier, one group of UP lanes per cluster.
-template <int UP>
+template <int UP, int NR>
 __global__ void __launch_bounds__(512) train_forward_kernel(const TrainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using Lay = TrainLayout<UP>;
+  using Lay = TrainLayout<UP, NR>;
   constexpr int W = Lay::kW;
   const int U = p.U, NS = p.n_sym, C = p.C;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
@@ -64,27 +88,29 @@ __global__ void __launch_bounds__(512) train_forward_kernel(const TrainParams p)
   const int gm = g < C ? g : C - 1;
   const bool valid = g < C;
   float2* rowbuf = reinterpret_cast<float2*>(smem + 16) + gm * Lay::kGroup;
-  float2* F = rowbuf + W;                       // [kNsymMax][UP]: nu * X of this cluster
+  float2* F = rowbuf + Lay::kRow;              // [NR][UP]: nu * X of this cluster
   int* fail_any = reinterpret_cast<int*>(smem);
   if (threadIdx.x == 0) *fail_any = 0;
   __syncthreads();
 
   const size_t matSize = static_cast<size_t>(U + NS) * U;
   const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
-  float2 aug[W];
+  float2 rp[W / 2], ip[W / 2];
   const float rho = p.rho_c[gm];
-  load_row<UP>(aug, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
-  const int fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+  load_row<UP, NR>(rp, ip, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
+  float rs = 1.f;
+  const int fail = gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
   if (valid && i == 0 && fail) atomicOr(fail_any, 1);
 
   const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
   if (valid && i < U) {
     float2* Xk = p.X + (static_cast<size_t>(k) * C + gm) * NS * U;
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) {
+    for (int n = 0; n < NR; ++n) {
       if (n < NS) {
-        Xk[n * U + i] = aug[n];
-        F[n * UP + i] = cscale(aug[n], w);
+        const float2 x = swept<W>(rp, ip, n, rs);
+        Xk[n * U + i] = x;
+        F[n * UP + i] = cscale(x, w);
       }
     }
   }
@@ -93,17 +119,18 @@ __global__ void __launch_bounds__(512) train_forward_kernel(const TrainParams p)
   for (int e = threadIdx.x; e < U * NS; e += blockDim.x) {
     const int u = e % U, n = e / U;
     float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < C; ++c) acc = cadd(acc, (reinterpret_cast<float2*>(smem + 16) + c * Lay::kGroup + W)[n * UP + u]);
+    for (int c = 0; c < C; ++c)
+      acc = cadd(acc, (reinterpret_cast<float2*>(smem + 16) + c * Lay::kGroup + Lay::kRow)[n * UP + u]);
     p.z[(static_cast<size_t>(k) * NS + n) * U + u] = bad ? make_float2(NAN, NAN) : acc;
   }
 }
 
 // Backward, per cluster: G_b = (G_c + rho_c I)^{-1} diag(nu_c) G_z, the partial
 // sums of dL/drho_c and dL/dnu[c][.] for this subcarrier, and W_c.
-template <int UP>
+template <int UP, int NR>
 __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using Lay = TrainLayout<UP>;
+  using Lay = TrainLayout<UP, NR>;
   constexpr int W = Lay::kW;
   const int U = p.U, NS = p.n_sym, C = p.C;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
@@ -111,27 +138,31 @@ __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainPa
   const int gm = g < C ? g : C - 1;
   const bool valid = g < C;
   float2* rowbuf = reinterpret_cast<float2*>(smem + 16) + gm * Lay::kGroup;
-  float2* Gs = rowbuf + W;                      // [kNsymMax][UP]  G_b of this cluster
-  float2* Xs = Gs + kNsymMax * UP;              // [kNsymMax][UP]  X of this cluster
+  float2* Gs = rowbuf + Lay::kRow;              // [NR][UP]  G_b of this cluster
+  float2* Xs = Gs + NR * UP;                    // [NR][UP]  X of this cluster
 
   const size_t matSize = static_cast<size_t>(U + NS) * U;
   const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
   const float2* gz = p.gz + static_cast<size_t>(k) * NS * U;
   const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
-  float2 aug[W];
-  load_row<UP>(aug, Dg, U, NS, i, valid, p.rho_c[gm], [&](int n) { return cscale(gz[n * U + i], w); });
-  gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+  float2 rp[W / 2], ip[W / 2];
+  load_row<UP, NR>(rp, ip, Dg, U, NS, i, valid, p.rho_c[gm], [&](int n) { return cscale(gz[n * U + i], w); });
+  float rs = 1.f;
+  gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
 
-  // aug[0..NS) = row i of G_b; X row i from the forward pass.
+  // Row i of G_b; X row i from the forward pass.
   const size_t off = (static_cast<size_t>(k) * C + gm) * NS * U;
-  float2 x[kNsymMax];
+  float2 gb[NR], x[NR];
   float prho = 0.f, pnu = 0.f;
 #pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) {
+  for (int n = 0; n < NR; ++n) {
+    gb[n] = swept<W>(rp, ip, n, rs);
     x[n] = (n < NS && valid && i < U) ? p.X[off + n * U + i] : make_float2(0.f, 0.f);
     const float2 gzv = (n < NS && valid && i < U) ? gz[n * U + i] : make_float2(0.f, 0.f);
-    prho -= aug[n].x * x[n].x + aug[n].y * x[n].y;          // Re(conj(G_b) X)
-    pnu += gzv.x * x[n].x + gzv.y * x[n].y;                 // Re(conj(g_z) X)
+    if (n < NS) {
+      prho -= gb[n].x * x[n].x + gb[n].y * x[n].y;          // Re(conj(G_b) X)
+      pnu += gzv.x * x[n].x + gzv.y * x[n].y;               // Re(conj(g_z) X)
+    }
   }
 #pragma unroll
   for (int o = UP / 2; o > 0; o >>= 1) prho += __shfl_xor_sync(kFullMask, prho, o, UP);
@@ -142,10 +173,10 @@ __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainPa
   }
   if (valid && i < U) {
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) {
+    for (int n = 0; n < NR; ++n) {
       if (n < NS) {
-        p.Gb[off + n * U + i] = aug[n];
-        Gs[n * UP + i] = aug[n];
+        p.Gb[off + n * U + i] = gb[n];
+        Gs[n * UP + i] = gb[n];
         Xs[n * UP + i] = x[n];
       }
     }
@@ -157,11 +188,11 @@ __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainPa
     for (int v = 0; v < U; ++v) {
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int n = 0; n < kNsymMax; ++n) {
+      for (int n = 0; n < NR; ++n) {
         if (n < NS) {
           const float2 xv = Xs[n * UP + v], gv = Gs[n * UP + v];
           // G_b[i] conj(X[v]) + X[i] conj(G_b[v])
-          acc = cfma(aug[n], make_float2(xv.x, -xv.y), acc);
+          acc = cfma(gb[n], make_float2(xv.x, -xv.y), acc);
           acc = cfma(x[n], make_float2(gv.x, -gv.y), acc);
         }
       }
@@ -186,18 +217,19 @@ __global__ void __launch_bounds__(512) train_backward_solve_kernel(const TrainPa
 // leaves row i of X_c and of A_c.  A user no cluster can see (D_u <= 0) has
 // z = 0 and contributes nothing.  A subcarrier with a system that is not
 // positive definite gets NaN gradients.
-template <int UP>
+template <int UP, int NR>
 struct OptimalLayout {
-  static constexpr int kW = UP + kNsymMax;
-  // Per group: pivot-row buffer (kW), X [kNsymMax][UP], G_x then G_b [kNsymMax][UP],
-  // and q (UP floats as UP / 2 complex).
-  static constexpr int kGroup = kW + 2 * kNsymMax * UP + UP / 2 + 8;
+  static constexpr int kW = UP + NR;
+  static constexpr int kRow = 2 * kW + 4;   // the sweep's pivot-row buffers; then row broadcasts of A
+  // Per group: pivot-row buffers, X [NR][UP], G_x then G_b [NR][UP], and q
+  // (UP floats as UP / 2 complex).
+  static constexpr int kGroup = kRow + 2 * NR * UP + UP / 2 + 8;
 };
 
-template <int UP>
+template <int UP, int NR>
 __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using Lay = OptimalLayout<UP>;
+  using Lay = OptimalLayout<UP, NR>;
   constexpr int W = Lay::kW;
   const int U = p.U, NS = p.n_sym, C = p.C;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
@@ -208,30 +240,36 @@ __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainPar
   float* wv = reinterpret_cast<float*>(smem + 16);                       // [C][UP]: w_{c,u}
   float2* grp = reinterpret_cast<float2*>(smem + 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16);
   float2* rowbuf = grp + gm * Lay::kGroup;
-  float2* Xs = rowbuf + W;                     // [kNsymMax][UP]
-  float2* Gs = Xs + kNsymMax * UP;             // [kNsymMax][UP]
-  float* qv = reinterpret_cast<float*>(Gs + kNsymMax * UP);   // [UP]
+  float2* Xs = rowbuf + Lay::kRow;            // [NR][UP]
+  float2* Gs = Xs + NR * UP;                  // [NR][UP]
+  float* qv = reinterpret_cast<float*>(Gs + NR * UP);   // [UP]
   if (threadIdx.x == 0) *fail_any = 0;
   __syncthreads();
 
   const size_t matSize = static_cast<size_t>(U + NS) * U;
   const float2* Dg = p.D + (static_cast<size_t>(k) * C + gm) * matSize;
   const float rho = p.rho;
-  float2 aug[W];
-  load_row<UP>(aug, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
-  const int fail = gj_sweep_rotating<UP, W>(aug, rowbuf, i, valid);
+  float2 rp[W / 2], ip[W / 2];
+  load_row<UP, NR>(rp, ip, Dg, U, NS, i, valid, rho, [&](int n) { return Dg[(U + n) * U + i]; });
+  float rs = 1.f;
+  const int fail = gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
   if (valid && i == 0 && fail) atomicOr(fail_any, 1);
-  // aug[0 .. kNsymMax) = row i of X_c, aug[kNsymMax .. W) = row i of A_c.
+  // Row i of X_c and of A_c.
+  float2 xr[NR], ar[UP];
+#pragma unroll
+  for (int n = 0; n < NR; ++n) xr[n] = swept<W>(rp, ip, n, rs);
+#pragma unroll
+  for (int j = 0; j < UP; ++j) ar[j] = swept<W>(rp, ip, NR + j, rs);
   float a = 1.f;
 #pragma unroll
   for (int j = 0; j < UP; ++j)
-    if (j == i) a = aug[kNsymMax + j].x;
+    if (j == i) a = ar[j].x;
   const bool real = valid && i < U;
   const float w = real ? 1.f / a : 0.f;
   if (valid) {
     wv[gm * UP + i] = real ? w : rho;         // padding users: w - rho = 0
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) Xs[n * UP + i] = (real && n < NS) ? aug[n] : make_float2(0.f, 0.f);
+    for (int n = 0; n < NR; ++n) Xs[n * UP + i] = (real && n < NS) ? xr[n] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const bool bad = *fail_any != 0;
@@ -243,30 +281,30 @@ __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainPar
   const float2* gzk = p.gz + static_cast<size_t>(k) * NS * U;
   float qn = 0.f;                                 // sum_n Re(conj(g_z) (X - z))
 #pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) {
+  for (int n = 0; n < NR; ++n) {
     if (n < NS) {
       float2 num = make_float2(0.f, 0.f);
       for (int cc = 0; cc < C; ++cc) {
-        const float2 xc = (grp + cc * Lay::kGroup + W)[n * UP + i];
+        const float2 xc = (grp + cc * Lay::kGroup + Lay::kRow)[n * UP + i];
         const float wc = wv[cc * UP + i];
         num = make_float2(fmaf(wc, xc.x, num.x), fmaf(wc, xc.y, num.y));
       }
       const float2 zn = cscale(num, invD);
       const float2 gzv = real ? gzk[n * U + i] : make_float2(0.f, 0.f);
-      qn = fmaf(gzv.x, aug[n].x - zn.x, fmaf(gzv.y, aug[n].y - zn.y, qn));
+      qn = fmaf(gzv.x, xr[n].x - zn.x, fmaf(gzv.y, xr[n].y - zn.y, qn));
       if (valid) Gs[n * UP + i] = cscale(gzv, w * invD);   // G_x
     }
   }
   if (valid) qv[i] = (real && seen) ? -qn * invD * w * w : 0.f;   // 1 / a^2 = w^2
   __syncwarp();
-  // G_b row i = sum_j A_ij G_x[j] (A row i in aug[kNsymMax ..)).
-  float2 gb[kNsymMax];
+  // G_b row i = sum_j A_ij G_x[j].
+  float2 gb[NR];
 #pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) {
+  for (int n = 0; n < NR; ++n) {
     float2 acc = make_float2(0.f, 0.f);
     if (n < NS) {
 #pragma unroll
-      for (int j = 0; j < UP; ++j) acc = cfma(aug[kNsymMax + j], Gs[n * UP + j], acc);
+      for (int j = 0; j < UP; ++j) acc = cfma(ar[j], Gs[n * UP + j], acc);
     }
     gb[n] = bad ? make_float2(NAN, NAN) : acc;
   }
@@ -274,7 +312,7 @@ __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainPar
   const size_t off = (static_cast<size_t>(k) * C + gm) * NS * U;
   if (valid) {
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) {
+    for (int n = 0; n < NR; ++n) {
       if (n < NS) {
         Gs[n * UP + i] = gb[n];
         if (real) p.Gb[off + n * U + i] = gb[n];
@@ -288,39 +326,43 @@ __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainPar
     __syncwarp();
     if (valid && i == v) {
 #pragma unroll
-      for (int j = 0; j < UP; ++j) rowbuf[j] = aug[kNsymMax + j];
+      for (int j = 0; j < UP; ++j) rowbuf[j] = ar[j];
     }
     __syncwarp();
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) {
+    for (int n = 0; n < NR; ++n) {
       if (n < NS) {
         const float2 xv = Xs[n * UP + v], gv = Gs[n * UP + v];
         acc = cfma(gb[n], make_float2(xv.x, -xv.y), acc);
-        acc = cfma(aug[n], make_float2(gv.x, -gv.y), acc);
+        acc = cfma(xr[n], make_float2(gv.x, -gv.y), acc);
       }
     }
     float2 ext = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < UP; ++j) {
       const float2 av = rowbuf[j];                                     // A_vj
-      ext = cfma(cscale(aug[kNsymMax + j], qv[j]), make_float2(av.x, -av.y), ext);
+      ext = cfma(cscale(ar[j], qv[j]), make_float2(av.x, -av.y), ext);
     }
     if (real) Wk[v] = bad ? make_float2(NAN, NAN) : make_float2(fmaf(2.f, ext.x, acc.x), fmaf(2.f, ext.y, acc.y));
   }
 }
 
-// Backward contraction: thread per antenna b (its columns of H and Y in
-// registers, read coalesced from HBM), cluster c = b / S:
+// Backward contraction, per subcarrier (G_b and W of its clusters staged in
+// shared memory):
 //   dL/dH[u][b] = sum_n Y[n][b] conj(G_b[n][u]) - sum_v H[v][b] W[v][u]
 //   dL/dY[n][b] = sum_u H[u][b] G_b[n][u]
-// with G_b and W of the subcarrier's clusters staged in shared memory.
+// A work item of dL/dH is one antenna b and kUq users (kUq independent
+// accumulators, so the dependent chains overlap); its column of H is read from
+// HBM coalesced over b (the items of one antenna share it through L1).  Antenna
+// b belongs to cluster b / S, or to the cluster whose offsets hold it.
+constexpr int kUq = 4;
+
 template <int UP>
 __global__ void __launch_bounds__(256) train_backward_contract_kernel(const TrainParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int U = p.U, NS = p.n_sym, C = p.C, B = p.B, S = B / C;
   const int k = blockIdx.x;
-  int c = 0;   // cluster of antenna b (clusters of given sizes: walked upwards with b)
   float2* Gs = reinterpret_cast<float2*>(smem);            // [C][NS][U]
   float2* Ws = Gs + static_cast<size_t>(C) * NS * U;       // [C][U][U]
   const float2* Gk = p.Gb + static_cast<size_t>(k) * C * NS * U;
@@ -332,36 +374,50 @@ __global__ void __launch_bounds__(256) train_backward_contract_kernel(const Trai
   const float2* Yk = p.y + static_cast<size_t>(k) * NS * B;
   float2* gHk = p.gH + static_cast<size_t>(k) * U * B;
   float2* gyk = p.gy + static_cast<size_t>(k) * NS * B;
-  for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    if (p.cl_uniform) {
-      c = b / S;
-    } else {
-      while (c + 1 < C && b >= p.cl_off[c + 1]) ++c;
-    }
+  auto cluster_of = [&](int b) {
+    if (p.cl_uniform) return b / S;
+    int c = 0;
+    while (c + 1 < C && b >= p.cl_off[c + 1]) ++c;
+    return c;
+  };
+  const int nq = (U + kUq - 1) / kUq;
+  for (int e = threadIdx.x; e < B * nq; e += blockDim.x) {
+    const int b = e % B, u0 = (e / B) * kUq;
+    const int c = cluster_of(b);
     const float2* Gc = Gs + static_cast<size_t>(c) * NS * U;
     const float2* Wc = Ws + static_cast<size_t>(c) * U * U;
-    float2 h[UP], yv[kNsymMax];
+    float2 acc[kUq];
 #pragma unroll
-    for (int v = 0; v < UP; ++v) h[v] = v < U ? Hk[static_cast<size_t>(v) * B + b] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int n = 0; n < kNsymMax; ++n) yv[n] = n < NS ? Yk[static_cast<size_t>(n) * B + b] : make_float2(0.f, 0.f);
-    for (int u = 0; u < U; ++u) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int n = 0; n < kNsymMax; ++n)
-        if (n < NS) acc = cfma_conj(Gc[n * U + u], yv[n], acc);       // Y[n][b] conj(G_b[n][u])
-#pragma unroll
-      for (int v = 0; v < UP; ++v)
-        if (v < U) acc = cfms(h[v], Wc[v * U + u], acc);              // - H[v][b] W[v][u]
-      gHk[static_cast<size_t>(u) * B + b] = acc;
-    }
+    for (int q = 0; q < kUq; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int n = 0; n < NS; ++n) {
-      float2 acc = make_float2(0.f, 0.f);
+      const float2 yv = Yk[static_cast<size_t>(n) * B + b];
 #pragma unroll
-      for (int u = 0; u < UP; ++u)
-        if (u < U) acc = cfma(h[u], Gc[n * U + u], acc);
-      gyk[static_cast<size_t>(n) * B + b] = acc;
+      for (int q = 0; q < kUq; ++q)
+        if (u0 + q < U) acc[q] = cfma_conj(Gc[n * U + u0 + q], yv, acc[q]);   // Y[n][b] conj(G_b[n][u])
     }
+#pragma unroll
+    for (int v = 0; v < UP; ++v) {
+      if (v < U) {
+        const float2 hv = Hk[static_cast<size_t>(v) * B + b];
+#pragma unroll
+        for (int q = 0; q < kUq; ++q)
+          if (u0 + q < U) acc[q] = cfms(hv, Wc[v * U + u0 + q], acc[q]);          // - H[v][b] W[v][u]
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kUq; ++q)
+      if (u0 + q < U) gHk[static_cast<size_t>(u0 + q) * B + b] = acc[q];
+  }
+  for (int e = threadIdx.x; e < B * NS; e += blockDim.x) {
+    const int b = e % B, n = e / B;
+    const float2* Gc = Gs + static_cast<size_t>(cluster_of(b)) * NS * U;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < UP; u += 2) {
+      if (u < U) acc0 = cfma(Hk[static_cast<size_t>(u) * B + b], Gc[n * U + u], acc0);
+      if (u + 1 < U) acc1 = cfma(Hk[static_cast<size_t>(u + 1) * B + b], Gc[n * U + u + 1], acc1);
+    }
+    gyk[static_cast<size_t>(n) * B + b] = cadd(acc0, acc1);
   }
 }
 
@@ -393,94 +449,107 @@ cudaError_t set_smem(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-template <int UP>
-cudaError_t launch_forward_up(const TrainParams& p, cudaStream_t st) {
-  const int threads = ((p.C * UP + 31) / 32) * 32;
-  const size_t smem = 16 + static_cast<size_t>(p.C) * TrainLayout<UP>::kGroup * sizeof(float2);
-  cudaError_t e = set_smem(train_forward_kernel<UP>, smem);
-  if (e != cudaSuccess) return e;
-  train_forward_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
-  return cudaGetLastError();
+template <int UP, int NR>
+size_t train_smem_up(int C) {
+  return 16 + static_cast<size_t>(C) * TrainLayout<UP, NR>::kGroup * sizeof(float2);
 }
 
 template <int UP>
-cudaError_t launch_backward_up(const TrainParams& p, cudaStream_t st) {
-  const int threads = ((p.C * UP + 31) / 32) * 32;
-  const size_t smem = 16 + static_cast<size_t>(p.C) * TrainLayout<UP>::kGroup * sizeof(float2);
-  cudaError_t e = set_smem(train_backward_solve_kernel<UP>, smem);
-  if (e != cudaSuccess) return e;
-  train_backward_solve_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+cudaError_t launch_contract_up(const TrainParams& p, cudaStream_t st) {
   const size_t smem2 = (static_cast<size_t>(p.C) * p.n_sym * p.U + static_cast<size_t>(p.C) * p.U * p.U) *
                        sizeof(float2);
-  if ((e = set_smem(train_backward_contract_kernel<UP>, smem2)) != cudaSuccess) return e;
+  const cudaError_t e = set_smem(train_backward_contract_kernel<UP>, smem2);
+  if (e != cudaSuccess) return e;
   train_backward_contract_kernel<UP><<<p.n_sc, 256, smem2, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract(const TrainParams& p, cudaStream_t st) {
+  switch (padded_users(p.U)) {
+    case 8: return launch_contract_up<8>(p, st);
+    case 16: return launch_contract_up<16>(p, st);
+    default: return launch_contract_up<32>(p, st);
+  }
+}
+
+template <int UP, int NR>
+cudaError_t launch_forward_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = train_smem_up<UP, NR>(p.C);
+  cudaError_t e = set_smem(train_forward_kernel<UP, NR>, smem);
+  if (e != cudaSuccess) return e;
+  train_forward_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int UP, int NR>
+cudaError_t launch_backward_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = train_smem_up<UP, NR>(p.C);
+  cudaError_t e = set_smem(train_backward_solve_kernel<UP, NR>, smem);
+  if (e != cudaSuccess) return e;
+  train_backward_solve_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_contract(p, st)) != cudaSuccess) return e;
   train_reduce_kernel<<<p.C * (1 + p.U), 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <int UP>
+template <int UP, int NR>
 size_t optimal_smem_up(int C) {
   return 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16 +
-         static_cast<size_t>(C) * OptimalLayout<UP>::kGroup * sizeof(float2);
+         static_cast<size_t>(C) * OptimalLayout<UP, NR>::kGroup * sizeof(float2);
 }
 
-template <int UP>
+template <int UP, int NR>
 cudaError_t launch_optimal_up(const TrainParams& p, cudaStream_t st) {
   const int threads = ((p.C * UP + 31) / 32) * 32;
-  const size_t smem = optimal_smem_up<UP>(p.C);
-  cudaError_t e = set_smem(train_optimal_solve_kernel<UP>, smem);
+  const size_t smem = optimal_smem_up<UP, NR>(p.C);
+  cudaError_t e = set_smem(train_optimal_solve_kernel<UP, NR>, smem);
   if (e != cudaSuccess) return e;
-  train_optimal_solve_kernel<UP><<<p.n_sc, threads, smem, st>>>(p);
+  train_optimal_solve_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smem2 = (static_cast<size_t>(p.C) * p.n_sym * p.U + static_cast<size_t>(p.C) * p.U * p.U) *
-                       sizeof(float2);
-  if ((e = set_smem(train_backward_contract_kernel<UP>, smem2)) != cudaSuccess) return e;
-  train_backward_contract_kernel<UP><<<p.n_sc, 256, smem2, st>>>(p);
-  return cudaGetLastError();
+  return launch_contract(p, st);
 }
 
 }  // namespace
 
+// Dispatch on (padded users, right-hand-side columns of the sweep).
+#define FFEQ_TRAIN_DISPATCH(call)                                             \
+  switch (padded_users(p.U) * 100 + rhs_columns(p.n_sym)) {                   \
+    case 804: return call<8, 4>(p, st);                                       \
+    case 816: return call<8, kNsymMax>(p, st);                                \
+    case 1604: return call<16, 4>(p, st);                                     \
+    case 1616: return call<16, kNsymMax>(p, st);                              \
+    case 3204: return call<32, 4>(p, st);                                     \
+    default: return call<32, kNsymMax>(p, st);                                \
+  }
+
 size_t train_smem_bytes(int U, int C) {
+  // The widest form (n_sym > 4) bounds every problem with these U and C.
   switch (padded_users(U)) {
-    case 8: return 16 + static_cast<size_t>(C) * TrainLayout<8>::kGroup * sizeof(float2);
-    case 16: return 16 + static_cast<size_t>(C) * TrainLayout<16>::kGroup * sizeof(float2);
-    default: return 16 + static_cast<size_t>(C) * TrainLayout<32>::kGroup * sizeof(float2);
+    case 8: return train_smem_up<8, kNsymMax>(C);
+    case 16: return train_smem_up<16, kNsymMax>(C);
+    default: return train_smem_up<32, kNsymMax>(C);
   }
 }
 
-cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t st) {
-  switch (padded_users(p.U)) {
-    case 8: return launch_forward_up<8>(p, st);
-    case 16: return launch_forward_up<16>(p, st);
-    default: return launch_forward_up<32>(p, st);
-  }
-}
+cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t st) { FFEQ_TRAIN_DISPATCH(launch_forward_up) }
 
-cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t st) {
-  switch (padded_users(p.U)) {
-    case 8: return launch_backward_up<8>(p, st);
-    case 16: return launch_backward_up<16>(p, st);
-    default: return launch_backward_up<32>(p, st);
-  }
-}
+cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t st) { FFEQ_TRAIN_DISPATCH(launch_backward_up) }
 
 size_t train_optimal_smem_bytes(int U, int C) {
   switch (padded_users(U)) {
-    case 8: return optimal_smem_up<8>(C);
-    case 16: return optimal_smem_up<16>(C);
-    default: return optimal_smem_up<32>(C);
+    case 8: return optimal_smem_up<8, kNsymMax>(C);
+    case 16: return optimal_smem_up<16, kNsymMax>(C);
+    default: return optimal_smem_up<32, kNsymMax>(C);
   }
 }
 
 cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t st) {
-  switch (padded_users(p.U)) {
-    case 8: return launch_optimal_up<8>(p, st);
-    case 16: return launch_optimal_up<16>(p, st);
-    default: return launch_optimal_up<32>(p, st);
-  }
+  FFEQ_TRAIN_DISPATCH(launch_optimal_up)
 }
+
+#undef FFEQ_TRAIN_DISPATCH
 
 }  // namespace ffeq
