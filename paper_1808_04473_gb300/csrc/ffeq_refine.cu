@@ -72,6 +72,55 @@ __device__ __forceinline__ double2 dcfma_conj(float2 a, float2 b, double2 acc) {
   return acc;
 }
 
+// C(m, n) = sum_k opA(A(m, k)) opB(B(n, k)) over an M x N output of complex FP32
+// values in shared memory, in TM x TN register tiles (each operand loaded once
+// per k for the whole tile, so a tile does TM TN complex FMAs per TM + TN loads
+// instead of one per two); opX conjugates when CONJ_X.  A(m, k) =
+// A[m am + k ak], B(n, k) = B[n bn + k bk].  Tiles go to threads tid, tid + nt, ...;
+// out(m, n, c) receives every in-range element.  Out-of-range rows and columns
+// of a ragged tile read the last valid row / column (in bounds) and are dropped.
+template <int TM, int TN, bool CONJ_A, bool CONJ_B, typename Out>
+__device__ __forceinline__ void tiled_cgemm(int M, int N, int K, const float2* A, int am, int ak, const float2* B,
+                                            int bn, int bk, int tid, int nt, Out out) {
+  const int tm = (M + TM - 1) / TM, tn = (N + TN - 1) / TN;
+  for (int t = tid; t < tm * tn; t += nt) {
+    const int m0 = (t % tm) * TM, n0 = (t / tm) * TN;
+    const float2* ar[TM];
+    const float2* br[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) ar[i] = A + (m0 + i < M ? m0 + i : M - 1) * am;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) br[j] = B + (n0 + j < N ? n0 + j : N - 1) * bn;
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      float2 a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        a[i] = ar[i][k * ak];
+        if (CONJ_A) a[i].y = -a[i].y;
+      }
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        b[j] = br[j][k * bk];
+        if (CONJ_B) b[j].y = -b[j].y;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        if (m0 + i < M && n0 + j < N) out(m0 + i, n0 + j, acc[i][j]);
+  }
+}
+
 // One CTA per local system: `steps` refinement steps, then the refined
 // estimates and inverse (diagonal included) go back to the workspace.
 __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const RefineParams p) {
@@ -128,31 +177,57 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
   }
 
   for (int step = 0; step < p.steps && !failed; ++step) {
-    // V = H_c [A~ | X] per (antenna b, column j): the columns a_j of A~ give V,
-    // the estimates give y_c - H_c x.  FP64 residual: accumulated in double, the
-    // result rounded once (exact differences first).
+    if (!use64) {
+      // FP32 residual, register-tiled products.  V = H_c [A~ | X] per (antenna b,
+      // column j): the columns a_j of A~ give V, the estimates give y_c - H_c x.
+      tiled_cgemm<2, 2, false, false>(S, W, U, Hs, 1, SS, P, U, 1, tid, nt, [&](int b, int j, float2 v) {
+        if (j < U) {
+          Va[j * SS + b] = v;
+        } else {
+          const int n = j - U;
+          Rb[n * SS + b] = csub(yk[static_cast<size_t>(n) * B + b], v);
+        }
+      });
+      __syncthreads();
+      // r = H_c^H (y_c - H_c x) - rho x.
+      tiled_cgemm<2, 2, false, true>(NS, U, S, Rb, SS, 1, Hs, SS, 1, tid, nt, [&](int n, int u, float2 v) {
+        const float2 x = P[(U + n) * U + u];
+        Rr[n * U + u] = make_float2(v.x - rho * x.x, v.y - rho * x.y);
+      });
+      // The next inverse 2 A - V^H V - rho A^H A (entry (i, j) at j U + i); the
+      // second pass gives each thread the same tiles as the first.
+      tiled_cgemm<2, 2, true, false>(U, U, S, Va, SS, 1, Va, SS, 1, tid, nt, [&](int i2, int j2, float2 v) {
+        const float2 a = P[j2 * U + i2];
+        An[j2 * U + i2] = make_float2(2.f * a.x - v.x, 2.f * a.y - v.y);
+      });
+      tiled_cgemm<2, 2, true, false>(U, U, U, P, U, 1, P, U, 1, tid, nt, [&](int i2, int j2, float2 v) {
+        float2& o = An[j2 * U + i2];
+        o = make_float2(fmaf(-rho, v.x, o.x), fmaf(-rho, v.y, o.y));
+      });
+      __syncthreads();
+      // x += A~ r   (A~[u][v] = column v of A~ at row u).
+      tiled_cgemm<2, 2, false, false>(NS, U, U, Rr, U, 1, P, 1, U, tid, nt, [&](int n, int u, float2 v) {
+        float2* x = P + (U + n) * U + u;
+        *x = cadd(*x, v);
+      });
+      __syncthreads();
+      for (int e = tid; e < U * U; e += nt) P[e] = An[e];
+      __syncthreads();
+      continue;
+    }
+    // FP64 residual.  V = H_c [A~ | X] per (antenna b, column j), accumulated in
+    // double, the result rounded once (exact differences first).
     for (int e = tid; e < S * W; e += nt) {
       const int j = e / S, b = e - j * S;
       const float2* pj = P + j * U;
-      if (use64) {
-        double2 v = make_double2(0.0, 0.0);
-        for (int u = 0; u < U; ++u) v = dcfma(Hs[u * SS + b], pj[u], v);
-        if (j < U) {
-          Va[j * SS + b] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
-        } else {
-          const float2 yv = yk[static_cast<size_t>(j - U) * B + b];
-          Rb[(j - U) * SS + b] = make_float2(static_cast<float>(static_cast<double>(yv.x) - v.x),
-                                             static_cast<float>(static_cast<double>(yv.y) - v.y));
-        }
-        continue;
-      }
-      float2 v = make_float2(0.f, 0.f);
-      for (int u = 0; u < U; ++u) v = cfma(Hs[u * SS + b], pj[u], v);
+      double2 v = make_double2(0.0, 0.0);
+      for (int u = 0; u < U; ++u) v = dcfma(Hs[u * SS + b], pj[u], v);
       if (j < U) {
-        Va[j * SS + b] = v;
+        Va[j * SS + b] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
       } else {
-        const int n = j - U;
-        Rb[n * SS + b] = csub(yk[static_cast<size_t>(n) * B + b], v);
+        const float2 yv = yk[static_cast<size_t>(j - U) * B + b];
+        Rb[(j - U) * SS + b] = make_float2(static_cast<float>(static_cast<double>(yv.x) - v.x),
+                                           static_cast<float>(static_cast<double>(yv.y) - v.y));
       }
     }
     __syncthreads();
@@ -160,43 +235,27 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
     for (int e = tid; e < NS * U; e += nt) {
       const int n = e / U, u = e - n * U;
       const float2 x = P[(U + n) * U + u];
-      if (use64) {
-        double2 sum = make_double2(0.0, 0.0);
-        for (int b = 0; b < S; ++b) sum = dcfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
-        const double r = static_cast<double>(rho);
-        Rr[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(x.x), sum.x)),
-                            static_cast<float>(fma(-r, static_cast<double>(x.y), sum.y)));
-        continue;
-      }
-      float2 sum = make_float2(0.f, 0.f);
-      for (int b = 0; b < S; ++b) sum = cfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
-      Rr[e] = make_float2(sum.x - rho * x.x, sum.y - rho * x.y);
+      double2 sum = make_double2(0.0, 0.0);
+      for (int b = 0; b < S; ++b) sum = dcfma_conj(Hs[u * SS + b], Rb[n * SS + b], sum);
+      const double r = static_cast<double>(rho);
+      Rr[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(x.x), sum.x)),
+                          static_cast<float>(fma(-r, static_cast<double>(x.y), sum.y)));
     }
-    // FP32: the next inverse 2 A - V^H V - rho A^H A.  FP64: the residual of the
-    // inverse, E = I - M_c A~ = I - H_c^H V - rho A~ (entry (i, j) at j U + i).
+    // The residual of the inverse, E = I - M_c A~ = I - H_c^H V - rho A~ (entry
+    // (i, j) at j U + i).
     for (int e = tid; e < U * U; e += nt) {
       const int j = e / U, i = e - j * U;   // entry (i, j)
       const float2* aj = P + j * U;
-      if (use64) {
-        double2 hv = make_double2(0.0, 0.0);
-        for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[i * SS + b], Va[j * SS + b], hv);
-        const double r = static_cast<double>(rho);
-        const double id = i == j ? 1.0 : 0.0;
-        An[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(aj[i].x), id - hv.x)),
-                            static_cast<float>(fma(-r, static_cast<double>(aj[i].y), -hv.y)));
-        continue;
-      }
-      float2 vv = make_float2(0.f, 0.f);
-      for (int b = 0; b < S; ++b) vv = cfma_conj(Va[i * SS + b], Va[j * SS + b], vv);
-      float2 aa = make_float2(0.f, 0.f);
-      const float2* ai = P + i * U;
-      for (int v = 0; v < U; ++v) aa = cfma_conj(ai[v], aj[v], aa);
-      const float2 a = aj[i];
-      An[e] = make_float2(2.f * a.x - vv.x - rho * aa.x, 2.f * a.y - vv.y - rho * aa.y);
+      double2 hv = make_double2(0.0, 0.0);
+      for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[i * SS + b], Va[j * SS + b], hv);
+      const double r = static_cast<double>(rho);
+      const double id = i == j ? 1.0 : 0.0;
+      An[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(aj[i].x), id - hv.x)),
+                          static_cast<float>(fma(-r, static_cast<double>(aj[i].y), -hv.y)));
     }
     __syncthreads();
-    // x += A~ r   (A~[u][v] = column v of A~ at row u); FP64 residual: the next
-    // inverse A~ + A~ E (Newton-Schulz in residual form) into Ae.
+    // x += A~ r   (A~[u][v] = column v of A~ at row u); the next inverse
+    // A~ + A~ E (Newton-Schulz in residual form) into Ae.
     for (int e = tid; e < NS * U; e += nt) {
       const int n = e / U, u = e - n * U;
       float2 d = make_float2(0.f, 0.f);
@@ -204,17 +263,14 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
       float2* x = P + (U + n) * U + u;
       *x = cadd(*x, d);
     }
-    if (use64) {
-      for (int e = tid; e < U * U; e += nt) {
-        const int j = e / U, i = e - j * U;
-        float2 d = make_float2(0.f, 0.f);
-        for (int v = 0; v < U; ++v) d = cfma(P[v * U + i], An[j * U + v], d);
-        Ae[e] = cadd(P[e], d);
-      }
+    for (int e = tid; e < U * U; e += nt) {
+      const int j = e / U, i = e - j * U;
+      float2 d = make_float2(0.f, 0.f);
+      for (int v = 0; v < U; ++v) d = cfma(P[v * U + i], An[j * U + v], d);
+      Ae[e] = cadd(P[e], d);
     }
     __syncthreads();
-    const float2* next = use64 ? Ae : An;
-    for (int e = tid; e < U * U; e += nt) P[e] = next[e];
+    for (int e = tid; e < U * U; e += nt) P[e] = Ae[e];
     __syncthreads();
   }
   // Refined estimates and inverse back to the workspace (same layouts).
