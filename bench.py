@@ -398,7 +398,8 @@ def soak(replay, seconds: float, torch):
         torch.cuda.synchronize()
 
 
-STEP_SHAPES = ((5, 0), (4, 0), (2, 0), (1, 0))   # contraction shapes tried together for a whole step
+STEP_SHAPES = ((6, 0), (5, 0), (4, 0), (2, 0), (1, 0))   # launch shapes tried together for a whole step
+FUSED_SHAPE = 6          # the contraction and the solve in one launch (include/ffeq.h tuning)
 
 
 def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equalizer=0, refine=0,
@@ -447,15 +448,17 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     cap = torch.cuda.Stream(dev)
     split = refine == 0
 
-    def launch(a, i, which):
+    def launch(a, i, which, stream=None):
+        # "step": the whole equalization call (one fused launch, or the
+        # contraction then the solve kernel); "local" / "fuse": one stage alone.
         o = outs[a]
-        if not split:
-            ffeq.ffeq_equalize(plans[a], Hs[i], ys[i], N0, Es, o["z"], o["s2"], o["llr"], None, ws[a], nb[a], cap)
-            return
-        if which in ("local", "step"):
-            ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], nb[a], cap)
-        if which in ("fuse", "step"):
-            ffeq.ffeq_fuse_equalize(plans[a], ws[a], nb[a], N0, Es, o["z"], o["s2"], o["llr"], None, cap)
+        st = cap if stream is None else stream
+        if not split or which == "step":
+            ffeq.ffeq_equalize(plans[a], Hs[i], ys[i], N0, Es, o["z"], o["s2"], o["llr"], None, ws[a], nb[a], st)
+        elif which == "local":
+            ffeq.ffeq_local_preprocess(plans[a], Hs[i], ys[i], ws[a], nb[a], st)
+        else:
+            ffeq.ffeq_fuse_equalize(plans[a], ws[a], nb[a], N0, Es, o["z"], o["s2"], o["llr"], None, st)
 
     def capture(fn):
         g = torch.cuda.CUDAGraph()
@@ -474,15 +477,7 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
         fork.record(cap)
         cap2.wait_event(fork)
         launch(archs[0], i, "step")
-        o = outs[archs[1]]
-        # The second architecture on the forked stream (same calls, other stream).
-        if not split:
-            ffeq.ffeq_equalize(plans[archs[1]], Hs[i], ys[i], N0, Es, o["z"], o["s2"], o["llr"], None, ws[archs[1]],
-                               nb[archs[1]], cap2)
-        else:
-            ffeq.ffeq_local_preprocess(plans[archs[1]], Hs[i], ys[i], ws[archs[1]], nb[archs[1]], cap2)
-            ffeq.ffeq_fuse_equalize(plans[archs[1]], ws[archs[1]], nb[archs[1]], N0, Es, o["z"], o["s2"], o["llr"],
-                                    None, cap2)
+        launch(archs[1], i, "step", cap2)     # the second architecture on the forked stream
         join.record(cap2)
         cap.wait_event(join)
 
@@ -557,10 +552,18 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     R.barrier()
     ms = start.elapsed_time(end)
     kern = {}
+    fused = {a: ffeq.ffeq_plan_get_tuning(plans[a])[0] == FUSED_SHAPE for a in archs}
     if breakdown and split:
+        # Each stage alone (with a fused plan, "local" and "fuse" are the separate
+        # kernels the fused launch replaces, its contraction with a ring of 2),
+        # and a fused plan's one launch.
         Kb = max(8, min(K, 200))
-        for name, a, which in (("pd_local", ffeq.PD, "local"), ("pd_fuse", ffeq.PD, "fuse"),
-                               ("fd_local", ffeq.FD, "local"), ("fd_fuse", ffeq.FD, "fuse")):
+        items = []
+        for a, tag in ((ffeq.PD, "pd"), (ffeq.FD, "fd")):
+            items += [(f"{tag}_local", a, "local"), (f"{tag}_fuse", a, "fuse")]
+            if fused[a]:
+                items.append((f"{tag}_fused", a, "step"))
+        for name, a, which in items:
             gs = [capture(lambda i=i: launch(a, i, which)) for i in range(n_sets)]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(cap):
@@ -583,7 +586,8 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     assert ffeq.ffeq_device_status() == 0
     for a in outs:
         assert torch.isfinite(torch.view_as_real(outs[a]["z"])).all().item()
-    return dict(ms=ms, kern=kern, plans=plans, outs=outs, schedule=schedule)
+    launches = sum(1 if fused[a] else (2 if split else 1) for a in archs)   # per step, without refinement
+    return dict(ms=ms, kern=kern, plans=plans, outs=outs, schedule=schedule, fused=fused, launches=launches)
 
 
 def uneven_line(R, K, warmup, precision, sampler=None):
@@ -914,6 +918,7 @@ def main():
                           warmup=args.warmup, pinned=pinned, breakdown=True, sampler=clk, soak_s=1.0,
                           concurrent=bool(args.concurrent), tune_step=not args.tuning)
     elapsed_ms, kern, plans, schedule = head["ms"], head["kern"], head["plans"], head["schedule"]
+    fused, launches = head["fused"], head["launches"]
     accuracy = _accuracy(p, head["outs"], idx, (0, 1)) if do_cpu else None
     if accuracy is not None:
         accuracy["subcarriers"] = len(idx)
@@ -993,7 +998,11 @@ def main():
     def gram_roof(name):
         alg = input_bytes(B, U, n_sc, n_sym)
         achieved = alg / (kern[name] * 1e-3) / 1e9
-        kname = f"gram_kernel<{args.precision}> ({name[:2].upper()} local preprocessing)"
+        if name.endswith("fused"):
+            kname = (f"gram_ws_kernel<{args.precision}, fused> ({name[:2].upper()} contraction + solve + fusion "
+                     f"+ LLRs, one launch)")
+        else:
+            kname = f"gram_kernel<{args.precision}> ({name[:2].upper()} local preprocessing)"
         return {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "peak_source": f"{peak_src} (STREAM-style copy)", "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": traffic.get(f"{args.precision}:{name}"), "algorithmic_bytes_per_launch": alg,
@@ -1008,8 +1017,15 @@ def main():
                 "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic.get(f"{args.precision}:{name}"),
                 "algorithmic_flops_per_launch": flops, "kernel_ms": kern[name]}
 
-    dom = max(kern, key=kern.get)
-    roof = gram_roof(dom) if dom.endswith("local") else solve_roof(dom)
+    # The step's own kernels: a fused plan's one launch, else its two stages.
+    step_kernels = []
+    for tag, a in (("pd", ffeq.PD), ("fd", ffeq.FD)):
+        step_kernels += [f"{tag}_fused"] if fused[a] else [f"{tag}_local", f"{tag}_fuse"]
+    dom = max(step_kernels, key=kern.get)
+    roof = solve_roof(dom) if dom.endswith("_fuse") else gram_roof(dom)
+
+    def arch_ms(tag, a):
+        return kern[f"{tag}_fused"] if fused[a] else kern[f"{tag}_local"] + kern[f"{tag}_fuse"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -1022,8 +1038,8 @@ def main():
         "kernels_ms": kern,
         "tuning": {("pd" if a == ffeq.PD else "fd"): list(ffeq.ffeq_plan_get_tuning(pl)) for a, pl in plans.items()},
         "schedule": schedule,
-        "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / ((kern["pd_local"] + kern["pd_fuse"]) * 1e-3),
-                                   "fd": U * n_sc * n_sym / ((kern["fd_local"] + kern["fd_fuse"]) * 1e-3)},
+        "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / (arch_ms("pd", ffeq.PD) * 1e-3),
+                                   "fd": U * n_sc * n_sym / (arch_ms("fd", ffeq.FD) * 1e-3)},
         "roofline": roof,
         "roofline_gram_stage": {"pd": gram_roof("pd_local"), "fd": gram_roof("fd_local")},
         "roofline_solve_stage": {"pd": solve_roof("pd_fuse"), "fd": solve_roof("fd_fuse")},
@@ -1031,7 +1047,7 @@ def main():
         "equalizers": variants or None,
         "accuracy": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * K,
+        "gpu_launches": launches * K,
     }
     line.update(extras)
     clocks = clk.summary()

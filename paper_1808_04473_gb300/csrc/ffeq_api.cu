@@ -226,11 +226,12 @@ ffeq_status check_common(const ffeq_plan* plan, const void* workspace, size_t wo
   return FFEQ_OK;
 }
 
-ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y, void* workspace,
-                             cudaStream_t st, bool host_inputs = false) {
+// Contraction parameters of a plan for inputs H, y (workspace D).
+ffeq_status gram_params(const ffeq_plan* plan, const void* H, const void* y, void* workspace, bool host_inputs,
+                        ffeq::GramParams& gp) {
   const ffeq_problem& p = plan->p;
   if (!H || !y || !aligned(H, 8) || !aligned(y, 8)) return FFEQ_ERR_INVALID_ARG;
-  ffeq::GramParams gp{};
+  gp = ffeq::GramParams{};
   gp.H = static_cast<const float2*>(H);
   gp.y = static_cast<const float2*>(y);
   gp.D = static_cast<float2*>(workspace);
@@ -246,21 +247,29 @@ ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y
   gp.cl_uniform = plan->cl_uniform ? 1 : 0;
   for (int c = 0; c <= plan->Ceff && !plan->cl_uniform; ++c) gp.cl_off[c] = plan->cl_off[c];
   if (!ffeq::gram_configure(gp, p.precision, plan->gram_variant, plan->gram_stages)) return FFEQ_ERR_UNSUPPORTED;
-  const cudaError_t e = p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
-                                                 : ffeq::launch_gram_tc(gp, p.precision, st);
+  return FFEQ_OK;
+}
+
+ffeq_status local_preprocess(const ffeq_plan* plan, const void* H, const void* y, void* workspace,
+                             cudaStream_t st, bool host_inputs = false) {
+  ffeq::GramParams gp;
+  const ffeq_status r = gram_params(plan, H, y, workspace, host_inputs, gp);
+  if (r != FFEQ_OK) return r;
+  const cudaError_t e = plan->p.precision == FFEQ_FP32 ? ffeq::launch_gram_fp32(gp, st)
+                                                       : ffeq::launch_gram_tc(gp, plan->p.precision, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
 }
 
-ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0, float Es, void* z,
-                          float* sigma2, float* llr, int* info, cudaStream_t st, const void* H = nullptr,
-                          const void* y = nullptr) {
+// Solve / fusion / soft-output parameters of a plan (outputs checked here).
+ffeq_status solve_params(const ffeq_plan* plan, const void* workspace, float N0, float Es, void* z, float* sigma2,
+                         float* llr, int* info, ffeq::SolveParams& sp) {
   const ffeq_problem& p = plan->p;
   if (!(N0 >= 0.f) || !std::isfinite(N0) || !(Es > 0.f) || !std::isfinite(Es)) return FFEQ_ERR_INVALID_ARG;
   if (!z || !sigma2 || !aligned(z, 8) || !aligned(sigma2, 4)) return FFEQ_ERR_INVALID_ARG;
   if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
   if (p.equalizer == FFEQ_LAMA && !(N0 > 0.f)) return FFEQ_ERR_INVALID_ARG;   // the denoiser needs tau > 0
   if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
-  ffeq::SolveParams sp{};
+  sp = ffeq::SolveParams{};
   sp.D = static_cast<const float2*>(workspace);
   sp.z = static_cast<float2*>(z);
   sp.sigma2 = sigma2;
@@ -286,6 +295,16 @@ ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0
   } else {
     sp.llr_scale = 0.f;
   }
+  return FFEQ_OK;
+}
+
+ffeq_status fuse_equalize(const ffeq_plan* plan, const void* workspace, float N0, float Es, void* z,
+                          float* sigma2, float* llr, int* info, cudaStream_t st, const void* H = nullptr,
+                          const void* y = nullptr) {
+  const ffeq_problem& p = plan->p;
+  ffeq::SolveParams sp;
+  const ffeq_status r = solve_params(plan, workspace, N0, Es, z, sigma2, llr, info, sp);
+  if (r != FFEQ_OK) return r;
   if (p.refine > 0) {
     if (!H || !y) return FFEQ_ERR_UNSUPPORTED;   // the residual needs the inputs
     unsigned char* ws = static_cast<unsigned char*>(const_cast<void*>(workspace));
@@ -386,6 +405,21 @@ ffeq_status equalize_impl(const ffeq_plan* plan, const void* H, const void* y, f
   if (p.llr_bits && !llr) return FFEQ_ERR_INVALID_ARG;
   if ((llr && !aligned(llr, 4)) || (info && !aligned(info, 4))) return FFEQ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->gram_variant == ffeq::kGramFused && !host_inputs) {
+    // One launch: the streamed contraction with the solve, fusion and soft
+    // outputs in the same CTAs (16-byte aligned inputs; otherwise the separate
+    // kernels below, which give the same results).
+    ffeq::GramParams gp;
+    r = gram_params(plan, H, y, workspace, false, gp);
+    if (r != FFEQ_OK) return r;
+    if (gp.bulk) {
+      ffeq::SolveParams sp;
+      r = solve_params(plan, workspace, N0, Es, z, sigma2, llr, info, sp);
+      if (r != FFEQ_OK) return r;
+      const cudaError_t e = ffeq::launch_gram_fused(gp, sp, p.precision, st);
+      return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+    }
+  }
   r = local_preprocess(plan, H, y, workspace, st, host_inputs);
   if (r != FFEQ_OK) return r;
   return fuse_equalize(plan, workspace, N0, Es, z, sigma2, llr, info, st, H, y);
@@ -605,6 +639,10 @@ ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
   gp.bulk = plan->p.B % 2 == 0;
   gp.cl_uniform = plan->cl_uniform ? 1 : 0;
   if (!ffeq::gram_configure(gp, plan->p.precision, values[0], values[1])) return FFEQ_ERR_UNSUPPORTED;
+  // The fused shape solves in the contraction's CTAs: L-MMSE or ZF without refinement.
+  if (values[0] == ffeq::kGramFused &&
+      (plan->p.refine != 0 || (plan->p.equalizer != FFEQ_LMMSE && plan->p.equalizer != FFEQ_ZF)))
+    return FFEQ_ERR_UNSUPPORTED;
   plan->gram_variant = values[0];
   plan->gram_stages = values[1];
   return FFEQ_OK;

@@ -358,4 +358,60 @@ __device__ __forceinline__ int gj_sweep_deferred(float2 (&aug)[W], float* rowbuf
   return fail;
 }
 
+// One lane's part of an L-MMSE solve on a group of UP lanes (lane i = user i,
+// U = UP): mrow holds row i of the Hermitian G as loaded by the caller; rho is
+// added to its diagonal, the group runs the sweep (column pairs for UP <= 16,
+// 2 x 2 block pivots for UP = 32) and the lane is left with row i of
+// A = (G + rho I)^{-1} in arow (natural column order, scaled by 1/p_i), A_ii in
+// Ai and G_ii in gii.  Returns the sweep's failure index (0: all pivots
+// positive).  Every kernel that solves from a D tile goes through this, so the
+// separate and the fused launches round identically.
+template <int UP>
+__device__ __forceinline__ int gj_solve_row(float2 (&mrow)[UP], float rho, float* rowbuf, int i, bool writer,
+                                            float2 (&arow)[UP], float& Ai, float& gii) {
+  constexpr int NP = UP / 2;
+  gii = 0.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    if (j == i) {
+      gii = mrow[j].x;
+      mrow[j] = make_float2(mrow[j].x + rho, 0.f);
+    }
+  }
+  float2 rp[NP], ip[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    rp[m] = make_float2(mrow[2 * m].x, mrow[2 * m + 1].x);
+    ip[m] = make_float2(mrow[2 * m].y, mrow[2 * m + 1].y);
+  }
+  float rs = 1.f;
+  int fail;
+  if constexpr (UP >= 32) {
+    fail = gj_sweep_block2<UP, UP>(rp, ip, rowbuf, i, writer, rs);
+  } else {
+    fail = gj_sweep_pairs<UP, UP>(rp, ip, rowbuf, i, writer, rs);
+  }
+  Ai = 1.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    arow[j] = make_float2((j % 2 ? rp[j / 2].y : rp[j / 2].x) * rs, (j % 2 ? ip[j / 2].y : ip[j / 2].x) * rs);
+    if (j == i) Ai = arow[j].x;
+  }
+  return fail;
+}
+
+// z = sum_j arow[j] rhs[j] over j = 0 .. UP-1 in j order (rhs 16-byte aligned):
+// one right-hand side of the solved system.
+template <int UP>
+__device__ __forceinline__ float2 gj_row_dot(const float2 (&arow)[UP], const float2* rhs) {
+  float2 zn = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < UP; j += 2) {
+    const float4 y2 = *reinterpret_cast<const float4*>(rhs + j);
+    zn = cfma(arow[j], make_float2(y2.x, y2.y), zn);
+    zn = cfma(arow[j + 1], make_float2(y2.z, y2.w), zn);
+  }
+  return zn;
+}
+
 }  // namespace ffeq

@@ -143,6 +143,14 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
   // else 16 warps.
   if (variant == kGramAuto) variant = stream_ok && p.bulk ? kGramStream : kGram16;
   if (variant < kGram16 || variant > kGramVariantMax) return false;
+  if (variant == kGramFused) {
+    // The contraction of the fused shape is the streamed one with a ring of 2
+    // (what ffeq_local_preprocess runs; ffeq_equalize fuses the solve into it).
+    if (!stream_ok || !gram_fused_eligible(precision, p.B, p.U, p.n_sym, p.Ceff)) return false;
+    if (stages != 0 && stages != kGramFusedRing) return false;
+    variant = kGramStream;
+    stages = kGramFusedRing;
+  }
   if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
   if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream) return false;
   if (variant == kGramPresplit && (!p.cl_uniform || !gram_presplit_eligible(precision, p.B, p.Ceff))) return false;

@@ -46,12 +46,27 @@
 // h_re w_im + (-h_im) w_re (the sign flipped on the A fragments, exact), each
 // split as A_lo B_hi + A_hi B_lo + A_hi B_hi (the lo*lo term is dropped):
 // twelve MMAs per tile and k-step into two accumulators (Re, Im).
+//
+// Fused form (one launch for a whole equalization, U = 8 or 16).  The same CTA
+// also solves what its teams contract: a completed cluster tile D_c (G_c and
+// y_c^MRC, Sec. II-C) goes from the team's MMA warps to a shared-memory handoff
+// buffer (two per team, "tile full" / "tile free" mbarriers) instead of the
+// workspace, and a solve group of U lanes per team (solve warps after the
+// converter warps) runs the L-MMSE sweep on it (Sec. III-A; ZF is rho = 0),
+// accumulates the Lemma 1 fusion terms of the subcarrier's clusters in cluster
+// order (PD: the one central system), and writes z, sigma^2 (Thm. 3) and the
+// max-log LLRs when the last cluster is in.  The solve of cluster c overlaps the
+// contraction of cluster c + 1, and D never leaves the SM.  Per lane the
+// arithmetic is that of the separate solve kernel (gj_solve_row, gj_row_dot and
+// the same fusion order), so both launches give the same bits.
 #include <cuda.h>
 
 #include <cstdint>
 #include <new>
 
 #include "ffeq_device.cuh"
+#include "ffeq_epilogue.cuh"
+#include "ffeq_gj.cuh"
 #include "ffeq_internal.h"
 #include "ffeq_mma.cuh"
 
@@ -81,12 +96,36 @@ struct StreamParams {
   float2* D;
   int* status;
   int B, U, Ceff, n_sc, n_sym, ring;
+  // Fused form only: outputs and scalars of the solve (as in SolveParams).
+  float2* z;
+  float* sigma2;
+  float* llr;
+  int* info;
+  float rho, N0, llr_scale;
+  int unbiased, llr_bits;
 };
 
+// Shared-memory areas of one team in the fused form: two handoff tiles of
+// D_c [m][u] (m < U + n_sym <= UP + 16 rows of UP complex), the fusion
+// numerators [n][u] of the subcarrier in progress, and the sweep's two
+// broadcast buffers.
 template <int UP>
+struct FusedShape {
+  static constexpr int MR = UP + kNsymMax;
+  static constexpr int TILE = MR * UP;                        // float2 per handoff tile
+  static constexpr int ACC = kNsymMax * UP;                   // float2
+  static constexpr int ROWBUF = (2 * (2 * UP + 4) * 4 + 15) / 16 * 16;   // bytes
+  static constexpr size_t TEAM = 2 * TILE * 8 + ACC * 8 + ROWBUF;
+  static constexpr int WARPS = StreamShape<UP>::UPC * UP / 32;   // one lane group of UP lanes per team
+  static_assert(UP <= 16, "the fused form holds one 8- or 16-lane group per team");
+};
+
+template <int UP, bool FUSED>
 constexpr size_t stream_smem_bytes(int ring) {
   using Sh = StreamShape<UP>;
-  return 1024 + static_cast<size_t>(Sh::UPC) * ring * Sh::SLICE + 3 * Sh::UPC * kStreamMaxRing * 8;
+  size_t b = 1024 + static_cast<size_t>(Sh::UPC) * ring * Sh::SLICE + 3 * Sh::UPC * kStreamMaxRing * 8;
+  if constexpr (FUSED) b += 4 * Sh::UPC * 8 + 16 + Sh::UPC * FusedShape<UP>::TEAM;
+  return b;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
@@ -280,18 +319,117 @@ struct SliceCursor {
 // depends on the order in which the teams progress; every wait is bounded.
 template <int UP>
 __host__ __device__ constexpr int conv_warps() { return UP <= 16 ? 8 : 4; }   // one team per converter warp
-template <int UP>
-__host__ __device__ constexpr int ws_threads() { return (kStreamWarps + conv_warps<UP>()) * 32; }
+template <int UP, bool FUSED>
+__host__ __device__ constexpr int solve_warps() {
+  if constexpr (FUSED) return FusedShape<UP>::WARPS;
+  return 0;
+}
+template <int UP, bool FUSED>
+__host__ __device__ constexpr int ws_threads() {
+  return (kStreamWarps + conv_warps<UP>() + solve_warps<UP, FUSED>()) * 32;
+}
 constexpr long kConvPollLimit = 1L << 24;   // converter passes without progress before it gives up
 
-template <int UP, int MODE>
-__global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __grid_constant__ StreamParams p) {
+// Solve warps of the fused form.  Solve warp sw holds 32 / UP lane groups; group
+// `team` (lane i = user i) walks the team's subcarriers k = slot, slot + nslots,
+// ... and their Ceff clusters in order, taking each cluster's tile from handoff
+// buffer hq & 1: row i of G_c (D[j][i], j < U), the sweep (gj_solve_row), the
+// right-hand sides (D rows U + n, read in place), then the tile goes back to the
+// MMA warps.  The fusion numerators z_c,n / A_c,ii (Eq. fusionrule, Lemma 1) are
+// summed in cluster order in the group's area (each lane owns its column), the
+// denominators (g / A_c,ii, g = mu or 1) in a register; after the last cluster
+// lane i writes user i's z, sigma^2 = N0 / den (Thm. 3) and LLRs, NaN for a
+// subcarrier with a failed factorization.  A group whose team has no subcarrier
+// left runs the sweep on an identity (its warp's other group may still be
+// working) and writes nothing.  Every wait is bounded; a time-out ends the warp.
+template <int UP>
+__device__ __forceinline__ void fused_solve(const StreamParams& p, unsigned char* team_area, uint64_t* hfull,
+                                            uint64_t* hfree, int sw, int lane) {
+  using FS = FusedShape<UP>;
+  const int gl = sw * 32 + lane;
+  const int team = gl / UP, i = gl % UP;
+  const int nslots = gridDim.x * StreamShape<UP>::UPC;
+  const int NS = p.n_sym, Ceff = p.Ceff;
+  unsigned char* area = team_area + team * FS::TEAM;
+  const float2* tiles = reinterpret_cast<const float2*>(area);
+  float2* acc = reinterpret_cast<float2*>(area + 2 * FS::TILE * 8);           // [n][UP]
+  float* rowbuf = reinterpret_cast<float*>(area + 2 * FS::TILE * 8 + FS::ACC * 8);
+  const float rho = p.rho;
+  const int bits = p.llr_bits, hb = bits / 2;
+  int hq = 0;
+  for (int k = blockIdx.x + gridDim.x * team;; k += nslots) {
+    const bool live = k < p.n_sc;
+    if (!__any_sync(kFullMask, live)) return;
+    bool failed = false;
+    float dn = 0.f;
+    for (int c = 0; c < Ceff; ++c) {
+      const int b = hq & 1;
+      bool ready = true;
+      if (live) ready = mbar_wait_sleep(&hfull[team * 2 + b], (hq >> 1) & 1, p.status, FFEQ_ERR_TIMEOUT);
+      if (!__all_sync(kFullMask, ready)) return;
+      const float2* T = tiles + b * FS::TILE;
+      float2 mrow[UP];
+#pragma unroll
+      for (int j = 0; j < UP; ++j) mrow[j] = live ? T[j * UP + i] : make_float2(j == i ? 1.f : 0.f, 0.f);
+      float2 arow[UP];
+      float Ai, gii;
+      const int fail = gj_solve_row<UP>(mrow, rho, rowbuf, i, true, arow, Ai, gii);
+      const float invA = 1.f / Ai;
+      const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
+#pragma unroll
+      for (int n = 0; n < kNsymMax; ++n) {
+        if (n < NS) {
+          const float2 zn = gj_row_dot<UP>(arow, T + (UP + n) * UP);
+          if (live) {
+            // The term is rounded on its own before the sum (no contraction
+            // into an FMA), as when it is stored and summed by the separate kernel.
+            const float2 prev = c == 0 ? make_float2(0.f, 0.f) : acc[n * UP + i];
+            acc[n * UP + i] = cadd(prev, make_float2(__fmul_rn(zn.x, invA), __fmul_rn(zn.y, invA)));
+          }
+        }
+      }
+      __syncwarp();   // every lane of the group has read the tile
+      if (live && i == 0) {
+        mbar_arrive(&hfree[team * 2 + b]);
+        if (p.info) p.info[static_cast<size_t>(k) * Ceff + c] = fail;
+      }
+      ++hq;
+      dn += __fmul_rn(p.unbiased ? mu : 1.f, invA);
+      failed = failed || fail != 0;
+    }
+    if (!live) continue;
+    const float rr = 1.f / dn;
+    for (int n = 0; n < NS; ++n) {
+      float2 zz;
+      float s2;
+      if (failed) {
+        zz = make_float2(NAN, NAN);
+        s2 = NAN;
+      } else if (dn > 0.f) {
+        zz = cscale(acc[n * UP + i], rr);
+        s2 = p.N0 * rr;
+      } else {
+        zz = make_float2(0.f, 0.f);
+        s2 = INFINITY;
+      }
+      const size_t zi = (static_cast<size_t>(k) * NS + n) * UP + i;
+      p.z[zi] = zz;
+      if (n == 0) p.sigma2[static_cast<size_t>(k) * UP + i] = s2;
+      if (bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * bits);
+    }
+  }
+}
+
+template <int UP, int MODE, bool FUSED>
+__global__ void __launch_bounds__(ws_threads<UP, FUSED>(), 1) gram_ws_kernel(const __grid_constant__ StreamParams p) {
   using Sh = StreamShape<UP>;
+  using FS = FusedShape<UP <= 16 ? UP : 16>;
   constexpr int NTH = Sh::NTH;
   constexpr int kConvWarps = conv_warps<UP>();
-  constexpr int kWsThreads = ws_threads<UP>();
+  constexpr int kWsThreads = ws_threads<UP, FUSED>();
   constexpr int TPC = Sh::UPC / kConvWarps;       // teams per converter warp
   static_assert(Sh::UPC % kConvWarps == 0, "teams split evenly over the converter warps");
+  static_assert(!FUSED || UP <= 16, "fused form: 8 or 16 users");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t ring0 = (raw + 1023u) & ~1023u;
@@ -300,6 +438,12 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
   uint64_t* full_all = bars;                                      // [UPC][kStreamMaxRing]
   uint64_t* empty_all = bars + Sh::UPC * kStreamMaxRing;
   uint64_t* conv_all = bars + 2 * Sh::UPC * kStreamMaxRing;
+  // Fused form: handoff barriers [UPC][2] (tile full: one arrival per MMA warp
+  // of the team; tile free: one by the solve group), then the teams' areas.
+  uint64_t* hfull = bars + 3 * Sh::UPC * kStreamMaxRing;
+  uint64_t* hfree = hfull + 2 * Sh::UPC;
+  unsigned char* team_area = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(hfree + 2 * Sh::UPC) + 15) & ~static_cast<uintptr_t>(15));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int U = p.U, NS = p.n_sym, B = p.B, Ceff = p.Ceff, S = B / Ceff, Mrows = U + NS;
   const int NC = (B + 16 * kStreamKsb - 1) / (16 * kStreamKsb);
@@ -322,12 +466,18 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
       mbar_init(&empty_all[tid], Sh::WPU);   // the team's MMA warps released it
       mbar_init(&conv_all[tid], 1);          // its converter warp converted it
     }
+    if (FUSED && tid < 2 * Sh::UPC) {
+      mbar_init(&hfull[tid], Sh::WPU);       // the team's MMA warps wrote the tile
+      mbar_init(&hfree[tid], 1);             // the team's solve group is done with it
+    }
     fence_mbar_init();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
   }
 
-  if (warp >= kStreamWarps) {
+  if (FUSED && warp >= kStreamWarps + kConvWarps) {
+    if constexpr (FUSED) fused_solve<UP>(p, team_area, hfull, hfree, warp - kStreamWarps - kConvWarps, lane);
+  } else if (warp >= kStreamWarps) {
     // ---------------- converter / producer warp
     const int cw = warp - kStreamWarps;
     const uint64_t pol = l2_evict_first_policy();
@@ -450,9 +600,11 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][o][q] = 0.f;
     int cl_left = S;
-    float2* Dc = p.D + static_cast<size_t>(slot) * Ceff * mat;
+    float2* Dc = FUSED ? nullptr : p.D + static_cast<size_t>(slot) * Ceff * mat;
+    int hq = 0;              // fused: tiles handed to the solve group so far
+    bool aborted = false;
     SliceCursor cc{slot, 0, 0, 0u};
-    while (cc.k < p.n_sc) {
+    while (cc.k < p.n_sc && !aborted) {
       const bool ready = mbar_wait_sleep(&conv[cc.s], cc.ph, p.status, FFEQ_ERR_TIMEOUT);
       if (!__all_sync(kFullMask, ready)) break;
       const int nkb = cc.ks == NC - 1 ? nkb_last : kStreamKsb;
@@ -461,7 +613,21 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
         stream_kstep<UP, MODE>(st + kb * Sh::BLOCK, fo, ntiles, acc);
         cl_left -= 16;
         if (cl_left <= 0) {
-          // Cluster complete: D[k][c][m][u] for this warp's tiles.
+          // Cluster complete: D[k][c][m][u] for this warp's tiles, to the
+          // workspace, or (fused) to the team's handoff tile hq & 1 once the
+          // solve group has released that tile's previous cluster.
+          float2* out = Dc;
+          int ld = U;
+          if constexpr (FUSED) {
+            const int b = team * 2 + (hq & 1);
+            const bool freed = mbar_wait_sleep(&hfree[b], ((hq >> 1) & 1) ^ 1u, p.status, FFEQ_ERR_TIMEOUT);
+            if (!__all_sync(kFullMask, freed)) {
+              aborted = true;
+              break;
+            }
+            out = reinterpret_cast<float2*>(team_area + team * FS::TEAM) + (hq & 1) * FS::TILE;
+            ld = UP;
+          }
 #pragma unroll
           for (int j = 0; j < NTH; ++j) {
             if (j < ntiles) {
@@ -469,7 +635,7 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
               for (int q4 = 0; q4 < 4; ++q4) {
                 const int u = 16 * mt + g + 8 * (q4 >> 1);
                 const int m = 8 * (nt0 + j) + 2 * t + (q4 & 1);
-                if (u < U && m < Mrows) Dc[m * U + u] = make_float2(acc[j][0][q4], acc[j][1][q4]);
+                if (u < U && m < Mrows) out[m * ld + u] = make_float2(acc[j][0][q4], acc[j][1][q4]);
               }
             }
 #pragma unroll
@@ -477,15 +643,21 @@ __global__ void __launch_bounds__(ws_threads<UP>(), 1) gram_ws_kernel(const __gr
 #pragma unroll
               for (int q4 = 0; q4 < 4; ++q4) acc[j][o][q4] = 0.f;
           }
+          if constexpr (FUSED) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&hfull[team * 2 + (hq & 1)]);
+            ++hq;
+          }
           cl_left = S;
-          Dc += mat;
+          if constexpr (!FUSED) Dc += mat;
         }
       }
+      if (aborted) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[cc.s]);
       SliceCursor nc = cc;
       nc.next(NC, R, nslots);
-      if (nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
+      if (!FUSED && nc.ks == 0) Dc = p.D + static_cast<size_t>(nc.k) * Ceff * mat;   // next subcarrier
       cc = nc;
     }
   }
@@ -527,25 +699,28 @@ bool encode_rows(CUtensorMap* map, const void* base, long long rows, int B, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int UP, int MODE>
+template <int UP, int MODE, bool FUSED>
 cudaError_t launch_stream_up(const StreamParams& sp, cudaStream_t stream) {
   static int configured[64] = {0};
   static int num_sms[64] = {0};
+  constexpr int kMaxRing = FUSED ? kGramFusedRing : kStreamMaxRing;
+  static_assert(stream_smem_bytes<UP, FUSED>(kMaxRing) <= 227 * 1024, "shared memory of one CTA");
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(gram_ws_kernel<UP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(stream_smem_bytes<UP>(kStreamMaxRing)));
+    err = cudaFuncSetAttribute(gram_ws_kernel<UP, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(stream_smem_bytes<UP, FUSED>(kMaxRing)));
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
+  if (sp.ring < 2 || sp.ring > kMaxRing) return cudaErrorInvalidValue;
   const int sms = dev < 64 ? num_sms[dev] : 152;
   const int need = (sp.n_sc + StreamShape<UP>::UPC - 1) / StreamShape<UP>::UPC;
   const int grid = need < sms ? need : sms;
-  gram_ws_kernel<UP, MODE><<<grid, ws_threads<UP>(), stream_smem_bytes<UP>(sp.ring), stream>>>(sp);
+  gram_ws_kernel<UP, MODE, FUSED><<<grid, ws_threads<UP, FUSED>(), stream_smem_bytes<UP, FUSED>(sp.ring), stream>>>(sp);
   return cudaGetLastError();
 }
 
@@ -573,9 +748,9 @@ bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff) {
   return Ceff == 1 || (B / Ceff) % 16 == 0;
 }
 
-cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream) {
-  if (p.n_sc == 0) return cudaSuccess;
-  StreamParams sp{};
+// Tensor maps (from the plan's cache where the inputs were seen before) and
+// the contraction fields of the streamed launch.
+static bool stream_params(const GramParams& p, StreamParams& sp) {
   TensorMapCache* c = p.map_cache;
   int hit = -1;
   if (c)
@@ -587,7 +762,7 @@ cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t 
   } else {
     if (!encode_rows(&sp.map_h, p.H, static_cast<long long>(p.n_sc) * p.U, p.B, p.U) ||
         !encode_rows(&sp.map_y, p.y, static_cast<long long>(p.n_sc) * p.n_sym, p.B, p.n_sym))
-      return cudaErrorInvalidValue;
+      return false;
     if (c) {
       TensorMapCache::Entry& e = c->e[c->next];
       e.mh = sp.map_h;
@@ -606,12 +781,50 @@ cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t 
   sp.n_sym = p.n_sym;
   // The next slice is converted while the current one is consumed: two slices at least.
   sp.ring = p.stages < 2 ? 2 : (p.stages > kStreamMaxRing ? kStreamMaxRing : p.stages);
+  return true;
+}
+
+cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream) {
+  if (p.n_sc == 0) return cudaSuccess;
+  StreamParams sp{};
+  if (!stream_params(p, sp)) return cudaErrorInvalidValue;
   const bool f16 = precision == FFEQ_FP16X3;
   switch (padded_users(p.U)) {
-    case 8: return f16 ? launch_stream_up<8, kFp16x3>(sp, stream) : launch_stream_up<8, kBf16x3>(sp, stream);
-    case 16: return f16 ? launch_stream_up<16, kFp16x3>(sp, stream) : launch_stream_up<16, kBf16x3>(sp, stream);
-    default: return f16 ? launch_stream_up<32, kFp16x3>(sp, stream) : launch_stream_up<32, kBf16x3>(sp, stream);
+    case 8:
+      return f16 ? launch_stream_up<8, kFp16x3, false>(sp, stream) : launch_stream_up<8, kBf16x3, false>(sp, stream);
+    case 16:
+      return f16 ? launch_stream_up<16, kFp16x3, false>(sp, stream) : launch_stream_up<16, kBf16x3, false>(sp, stream);
+    default:
+      return f16 ? launch_stream_up<32, kFp16x3, false>(sp, stream) : launch_stream_up<32, kBf16x3, false>(sp, stream);
   }
+}
+
+bool gram_fused_eligible(int precision, int B, int U, int n_sym, int Ceff) {
+  return (U == 8 || U == 16) && gram_stream_eligible(precision, B, U, n_sym, Ceff);
+}
+
+cudaError_t launch_gram_fused(const GramParams& p, const SolveParams& s, int precision, cudaStream_t stream) {
+  if (p.n_sc == 0) return cudaSuccess;
+  if (!gram_fused_eligible(precision, p.B, p.U, p.n_sym, p.Ceff) || !p.cl_uniform || !s.z || !s.sigma2 ||
+      (s.llr_bits && !s.llr))
+    return cudaErrorInvalidValue;
+  StreamParams sp{};
+  if (!stream_params(p, sp)) return cudaErrorInvalidValue;
+  sp.D = nullptr;
+  sp.ring = kGramFusedRing;
+  sp.z = s.z;
+  sp.sigma2 = s.sigma2;
+  sp.llr = s.llr_bits ? s.llr : nullptr;
+  sp.info = s.info;
+  sp.rho = s.rho;
+  sp.N0 = s.N0;
+  sp.llr_scale = s.llr_scale;
+  sp.unbiased = s.unbiased;
+  sp.llr_bits = s.llr_bits;
+  const bool f16 = precision == FFEQ_FP16X3;
+  if (p.U == 8)
+    return f16 ? launch_stream_up<8, kFp16x3, true>(sp, stream) : launch_stream_up<8, kBf16x3, true>(sp, stream);
+  return f16 ? launch_stream_up<16, kFp16x3, true>(sp, stream) : launch_stream_up<16, kBf16x3, true>(sp, stream);
 }
 
 }  // namespace ffeq

@@ -74,9 +74,13 @@ struct GramParams {
 // staging); BF16x3 pre-split planes (16 warps); 4 warps, three CTAs per SM;
 // streamed (ffeq_gram_stream.cu: 32-antenna slices of several subcarriers per
 // CTA moved by tensor-map copies, each warp owning its output tiles over the
-// whole antenna range; `stages` is then the depth of each subcarrier's ring).
-constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4, kGramStream = 5;
-constexpr int kGramVariantMax = kGramStream;
+// whole antenna range; `stages` is then the depth of each subcarrier's ring);
+// fused (the streamed contraction with the solve, fusion and soft outputs in the
+// same launch when a whole equalization runs; ring depth 2).
+constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4, kGramStream = 5,
+              kGramFused = 6;
+constexpr int kGramVariantMax = kGramFused;
+constexpr int kGramFusedRing = 2;       // ring depth of the fused shape (its solve areas take the rest)
 constexpr int kGramStreamRing = 3;      // default (and largest) ring depth of the streamed shape (least 2)
 
 // Whether the streamed contraction takes this problem (BF16x3 or FP16x3,
@@ -87,6 +91,14 @@ bool gram_stream_eligible(int precision, int B, int U, int n_sym, int Ceff);
 TensorMapCache* tensor_map_cache_create();
 void tensor_map_cache_destroy(TensorMapCache* cache);
 cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream);
+// Whether the fused shape takes this problem: the streamed shape's conditions
+// with U = 8 or 16 (one lane per user, the users filling the lane group).  The
+// equalizer (L-MMSE or ZF) and refine = 0 are checked by the caller.
+bool gram_fused_eligible(int precision, int B, int U, int n_sym, int Ceff);
+struct SolveParams;
+// One launch: contraction (p, 16-byte aligned H and y, ring kGramFusedRing) and
+// the solve / fusion / soft outputs of every subcarrier (s; s.D is not read).
+cudaError_t launch_gram_fused(const GramParams& p, const SolveParams& s, int precision, cudaStream_t stream);
 
 // Solve / fusion / epilogue kernel: workspace D -> z, sigma2, llr, info.
 struct SolveParams {

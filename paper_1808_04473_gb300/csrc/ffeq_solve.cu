@@ -561,7 +561,7 @@ template <int UP>
 __global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   using Lay = SolveLayout<UP>;
-  constexpr int U = UP, NP = UP / 2;
+  constexpr int U = UP;
   const int NS = p.n_sym, Ceff = p.Ceff, spc = p.spc;
   const int nmat = spc * Ceff;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
@@ -599,43 +599,16 @@ __global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(con
   float2 mrow[UP];
 #pragma unroll
   for (int j = 0; j < UP; ++j) mrow[j] = Dg[j * U];
-  float gii = 0.f;
-#pragma unroll
-  for (int j = 0; j < UP; ++j) {
-    if (j == i) {
-      gii = mrow[j].x;
-      mrow[j] = make_float2(mrow[j].x + rho, 0.f);
-    }
-  }
-  float2 rp[NP], ip[NP];
-#pragma unroll
-  for (int m = 0; m < NP; ++m) {
-    rp[m] = make_float2(mrow[2 * m].x, mrow[2 * m + 1].x);
-    ip[m] = make_float2(mrow[2 * m].y, mrow[2 * m + 1].y);
-  }
-  float rs = 1.f;
-  int fail;
-  if constexpr (UP >= 32) {
-    fail = gj_sweep_block2<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
-  } else {
-    fail = gj_sweep_pairs<UP, UP>(rp, ip, reinterpret_cast<float*>(rowbuf), i, g < nmat, rs);
-  }
-  // Lane i holds row i of A = (G + rho I)^{-1} times p_i, columns in natural order.
-  float Ap = 1.f;
-#pragma unroll
-  for (int j = 0; j < UP; ++j)
-    if (j == i) Ap = j % 2 ? rp[j / 2].y : rp[j / 2].x;
-  const float Ai = Ap * rs;
+  // Lane i: row i of A = (G + rho I)^{-1} (natural column order) and A_ii.
+  float2 arow[UP];
+  float Ai, gii;
+  const int fail = gj_solve_row<UP>(mrow, rho, reinterpret_cast<float*>(rowbuf), i, g < nmat, arow, Ai, gii);
   const float invA = 1.f / Ai;
   // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
   // mu = 0 exactly, which the subtraction would only reach up to rounding.
   const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
   const bool store = p.Xs != nullptr;   // refinement follows: keep estimates and inverses
   const size_t sys = static_cast<size_t>(sc) * Ceff + c;
-  float2 arow[UP];
-#pragma unroll
-  for (int j = 0; j < UP; ++j)
-    arow[j] = cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncwarp();
   // z_n = sum_j A[i][j] y^MRC_j(n) in j order; after every lane of the warp has
@@ -643,13 +616,7 @@ __global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(con
 #pragma unroll
   for (int n = 0; n < kNsymMax; ++n) {
     if (n < NS) {
-      float2 zn = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < UP; j += 2) {
-        const float4 y2 = *reinterpret_cast<const float4*>(Fz + n * UP + j);
-        zn = cfma(arow[j], make_float2(y2.x, y2.y), zn);
-        zn = cfma(arow[j + 1], make_float2(y2.z, y2.w), zn);
-      }
+      const float2 zn = gj_row_dot<UP>(arow, Fz + n * UP);
       __syncwarp();
       if (g < nmat) {
         if (store) {
@@ -664,9 +631,7 @@ __global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(con
     // Inverse stored transposed (row j = column j of A, coalesced over the lanes i).
     if (live) {
 #pragma unroll
-      for (int j = 0; j < UP; ++j)
-        p.As[(sys * U + j) * U + i] =
-            cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
+      for (int j = 0; j < UP; ++j) p.As[(sys * U + j) * U + i] = arow[j];
       if (i == 0) {
         p.fails[sys] = fail;
         if (p.info) p.info[sys] = fail;

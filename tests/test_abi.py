@@ -115,7 +115,7 @@ def test_plan_tuning_validation(built):
     plan = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP32)
     assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
     # out of range; pre-split, the 4-warp and the streamed shapes need a tensor-core precision
-    for bad, status in (((6, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2), ((5, 0), 2)):
+    for bad, status in (((7, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2), ((5, 0), 2), ((6, 0), 2)):
         with pytest.raises(ff.FfeqError) as e:
             ff.ffeq_plan_set_tuning(plan, bad)
         assert e.value.status == status, bad
@@ -139,6 +139,25 @@ def test_plan_tuning_validation(built):
             with pytest.raises(ff.FfeqError) as e:
                 ff.ffeq_plan_set_tuning(fd, (5, st))
             assert e.value.status == status
+    # The fused shape: the streamed shape's conditions, U = 8 or 16, L-MMSE or ZF
+    # without refinement; ring depth 2 (0 means 2).
+    for prec in (ff.BF16X3, ff.FP16X3):
+        fd = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=prec)
+        for st in (0, 2):
+            ff.ffeq_plan_set_tuning(fd, (6, st))
+            assert ff.ffeq_plan_get_tuning(fd) == (6, st)
+        for st in (1, 3):
+            with pytest.raises(ff.FfeqError) as e:
+                ff.ffeq_plan_set_tuning(fd, (6, st))
+            assert e.value.status == 2
+    for kw in (dict(U=12), dict(U=32), dict(equalizer=ff.MRC), dict(equalizer=ff.LAMA, lama_iters=2, llr_bits=4),
+               dict(refine=1)):
+        a = dict(B=256, U=16, C=8, n_sc=10, n_sym=14, arch=ff.FD, precision=ff.BF16X3)
+        a.update(kw)
+        pl = ff.ffeq_plan_create(a.pop("B"), a.pop("U"), a.pop("C"), a.pop("n_sc"), a.pop("n_sym"), **a)
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_set_tuning(pl, (6, 2))
+        assert e.value.status == 2, kw
     odd = ff.ffeq_plan_create(96, 8, 8, 10, 2, arch=ff.FD, precision=ff.BF16X3)      # S = 12
     with pytest.raises(ff.FfeqError) as e:
         ff.ffeq_plan_set_tuning(odd, (5, 0))
