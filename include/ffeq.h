@@ -296,9 +296,17 @@ ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const
  *                  copies and split once into 16-bit planes (needs B even and,
  *                  for FD, B/C a multiple of 16; 16-byte aligned H and y, else
  *                  shape 1 runs);
+ *              6 = fused: shape 5's conditions with U = 8 or 16, FFEQ_LMMSE or
+ *                  FFEQ_ZF and refine = 0; ffeq_equalize then runs ONE kernel
+ *                  that also solves, fuses and writes the soft outputs (each
+ *                  cluster's G_c and y_c^MRC go through shared memory, not the
+ *                  workspace, which is left untouched), with exactly the bits of
+ *                  shape 5 with ring depth 2; ffeq_local_preprocess runs shape 5
+ *                  with ring depth 2 (16-byte aligned H and y, else the separate
+ *                  kernels of shape 1 run);
  *   values[1]  shapes 1-4: subcarriers staged ahead per CTA, 1..3, or 0 = as
  *              many as fit; shape 5: ring depth per subcarrier (32-antenna
- *              slices), 2 or 3, 0 = 3.
+ *              slices), 2 or 3, 0 = 3; shape 6: 2 or 0 (= 2).
  * FP16X3 runs on shapes 1 and 5 only.
  * ffeq_plan_set_tuning takes exactly 2 values and returns FFEQ_ERR_UNSUPPORTED
  * when the shape does not apply to or fit the problem (plan unchanged);

@@ -13,7 +13,8 @@
 // (mu = 1 - rho A_uu, sigma^2 = N0 A_uu, Eq. opt_fusion), gets a Newton-Schulz
 // step from the same product V = H_c A~_c in each step:
 //   A~_c <- 2 A~_c - A~_c^H M_c A~_c = 2 A~_c - V^H V - rho A~_c^H A~_c,
-// which squares its relative error.  Each step shrinks the error of the
+// which squares its relative error (in the last FP32 step only its diagonal,
+// the part read afterwards: half of a step's products).  Each step shrinks the error of the
 // estimates by about kappa u, down to the accuracy of an FP32 solve (kappa
 // 2^-24, from the rounding of y_c - H_c x_c).  With the FP64 residual (always,
 // or for systems whose estimate ||M_c||_1 ||A~_c||_1 of the condition number
@@ -195,15 +196,20 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
         Rr[n * U + u] = make_float2(v.x - rho * x.x, v.y - rho * x.y);
       });
       // The next inverse 2 A - V^H V - rho A^H A (entry (i, j) at j U + i); the
-      // second pass gives each thread the same tiles as the first.
-      tiled_cgemm<2, 2, true, false>(U, U, S, Va, SS, 1, Va, SS, 1, tid, nt, [&](int i2, int j2, float2 v) {
-        const float2 a = P[j2 * U + i2];
-        An[j2 * U + i2] = make_float2(2.f * a.x - v.x, 2.f * a.y - v.y);
-      });
-      tiled_cgemm<2, 2, true, false>(U, U, U, P, U, 1, P, U, 1, tid, nt, [&](int i2, int j2, float2 v) {
-        float2& o = An[j2 * U + i2];
-        o = make_float2(fmaf(-rho, v.x, o.x), fmaf(-rho, v.y, o.y));
-      });
+      // second pass gives each thread the same tiles as the first.  After the
+      // last step only its diagonal is read (the unbiasing and the fusion
+      // weights), which is formed below instead.
+      const bool last = step + 1 == p.steps;
+      if (!last) {
+        tiled_cgemm<2, 2, true, false>(U, U, S, Va, SS, 1, Va, SS, 1, tid, nt, [&](int i2, int j2, float2 v) {
+          const float2 a = P[j2 * U + i2];
+          An[j2 * U + i2] = make_float2(2.f * a.x - v.x, 2.f * a.y - v.y);
+        });
+        tiled_cgemm<2, 2, true, false>(U, U, U, P, U, 1, P, U, 1, tid, nt, [&](int i2, int j2, float2 v) {
+          float2& o = An[j2 * U + i2];
+          o = make_float2(fmaf(-rho, v.x, o.x), fmaf(-rho, v.y, o.y));
+        });
+      }
       __syncthreads();
       // x += A~ r   (A~[u][v] = column v of A~ at row u).
       tiled_cgemm<2, 2, false, false>(NS, U, U, Rr, U, 1, P, 1, U, tid, nt, [&](int n, int u, float2 v) {
@@ -211,7 +217,19 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
         *x = cadd(*x, v);
       });
       __syncthreads();
-      for (int e = tid; e < U * U; e += nt) P[e] = An[e];
+      if (!last) {
+        for (int e = tid; e < U * U; e += nt) P[e] = An[e];
+      } else {
+        // [2 A - (H_c a_j)^H (H_c a_j) - rho a_j^H a_j]_jj for column a_j of A~
+        // (thread j reads and writes column j only).
+        for (int j = tid; j < U; j += nt) {
+          float2 d1 = make_float2(0.f, 0.f), d2 = make_float2(0.f, 0.f);
+          for (int b = 0; b < S; ++b) d1 = cfma_conj(Va[j * SS + b], Va[j * SS + b], d1);
+          for (int v = 0; v < U; ++v) d2 = cfma_conj(P[j * U + v], P[j * U + v], d2);
+          const float2 a = P[j * U + j];
+          P[j * U + j] = make_float2(fmaf(-rho, d2.x, 2.f * a.x - d1.x), fmaf(-rho, d2.y, 2.f * a.y - d1.y));
+        }
+      }
       __syncthreads();
       continue;
     }
