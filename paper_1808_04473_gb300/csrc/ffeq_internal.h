@@ -138,7 +138,7 @@ struct RefineParams {
   const float2* H;      // [n_sc][U][B]
   const float2* y;      // [n_sc][n_sym][B]
   const float2* D;      // contraction output (for G_uu)
-  float2* As;           // [n_sc][Ceff][U][U] inverses, transposed (refined in place)
+  float2* As;           // [n_sc][Ceff][U][U] inverses, transposed (the diagonal refined in place)
   float2* Xs;           // [n_sc][Ceff][n_sym][U] (refined in place)
   const int* fails;     // [n_sc][Ceff]
   float2* z;

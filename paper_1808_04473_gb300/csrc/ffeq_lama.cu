@@ -10,7 +10,8 @@
 // kappa = 1/S_c, with N0 kappa and beta_c = U kappa.  Each iteration
 //     z   = y^MRC + (I - G) s + v                (the matrix-vector product reads s
 //                                                 from the group's shared-memory copy,
-//                                                 two entries per 128-bit broadcast load)
+//                                                 real and imaginary planes, four entries
+//                                                 per 128-bit broadcast load, paired FMAs)
 //     tau = N0 + beta phi
 //     s'  = F(z, tau),  phi' = <G(z, tau)>      (posterior mean / variance of the
 //                                                 equiprobable square-QAM prior, Eq. F;
@@ -34,35 +35,45 @@
 namespace ffeq {
 namespace {
 
-// Posterior mean and variance of one PAM axis (levels a_m = (2m - L + 1) d,
-// L = 2^HB, equiprobable) under Gaussian noise of variance tau/2:
+// Posterior mean and variance of both PAM axes of a square-QAM symbol at once
+// (x = (re, im); levels a_m = (2m - L + 1) d, L = 2^HB, equiprobable) under
+// Gaussian noise of variance tau/2 per axis:
 // p(a_m | x) ~ exp(-(x - a_m)^2 / tau) = 2^(-(x - a_m)^2 log2(e) / tau).
 // Exponents are taken relative to the nearest level a0, and the moments about
 // a0, so that a sharp posterior on an outer level keeps its small variance.
+// The two axes run as the halves of paired FP32 operations (__ffma2_rn and
+// friends, sm_100+), each half rounding as the scalar operation would.
 // inv_d = 1/d; l2t = log2(e) / tau (both once per call site, not per level).
 template <int HB>
-__device__ __forceinline__ void pam_posterior(float x, float l2t, float d, float inv_d, float& mean, float& var) {
+__device__ __forceinline__ void pam_posterior2(float2 x, float l2t, float d, float inv_d, float2& mean, float2& var) {
   constexpr int L = 1 << HB;
   // Nearest level index: round((x/d + L - 1) / 2), clamped to [0, L).
-  float q = rintf(fmaf(x, inv_d, static_cast<float>(L - 1)) * 0.5f);
-  q = fminf(fmaxf(q, 0.f), static_cast<float>(L - 1));
-  const float a0 = (2.f * q - static_cast<float>(L - 1)) * d;
-  const float e0 = (x - a0) * (x - a0);
-  float sw = 0.f, s1 = 0.f, s2 = 0.f;
+  const float2 t = __fmul2_rn(__ffma2_rn(x, make_float2(inv_d, inv_d), make_float2(L - 1.f, L - 1.f)),
+                              make_float2(0.5f, 0.5f));
+  const float2 q = make_float2(fminf(fmaxf(rintf(t.x), 0.f), L - 1.f), fminf(fmaxf(rintf(t.y), 0.f), L - 1.f));
+  const float2 a0 = __fmul2_rn(__ffma2_rn(q, make_float2(2.f, 2.f), make_float2(1.f - L, 1.f - L)),
+                               make_float2(d, d));
+  const float2 r0 = __ffma2_rn(a0, make_float2(-1.f, -1.f), x);          // x - a0
+  const float2 ne0 = __fmul2_rn(r0, make_float2(-r0.x, -r0.y));           // -(x - a0)^2
+  const float2 nl2t = make_float2(-l2t, -l2t);
+  const float2 na0 = make_float2(-a0.x, -a0.y);
+  float2 sw = make_float2(0.f, 0.f), s1 = sw, s2 = sw;
 #pragma unroll
   for (int m = 0; m < L; ++m) {
     const float a = (2.f * static_cast<float>(m) - static_cast<float>(L - 1)) * d;
-    const float e = x - a;
-    const float w = exp2f(fmaf(-e, e, e0) * l2t);   // <= 1; exactly 1 at a0
-    const float da = a - a0;
-    sw += w;
-    s1 = fmaf(w, da, s1);
-    s2 = fmaf(w * da, da, s2);
+    const float2 e = __fadd2_rn(x, make_float2(-a, -a));                  // x - a
+    const float2 u = __fmul2_rn(__ffma2_rn(e, e, ne0), nl2t);             // ((x-a0)^2 - e^2) l2t <= 0
+    const float2 w = make_float2(exp2f(u.x), exp2f(u.y));                 // exactly 1 at a0
+    const float2 da = __fadd2_rn(make_float2(a, a), na0);
+    sw = __fadd2_rn(sw, w);
+    s1 = __ffma2_rn(w, da, s1);
+    s2 = __ffma2_rn(__fmul2_rn(w, da), da, s2);
   }
-  const float r = 1.f / sw;
-  const float m1 = s1 * r;
-  mean = a0 + m1;
-  var = fmaxf(fmaf(-m1, m1, s2 * r), 0.f);
+  const float2 r = make_float2(__frcp_rn(sw.x), __frcp_rn(sw.y));
+  const float2 m1 = __fmul2_rn(s1, r);
+  mean = __fadd2_rn(a0, m1);
+  const float2 v2 = __ffma2_rn(make_float2(-m1.x, -m1.y), m1, __fmul2_rn(s2, r));
+  var = make_float2(fmaxf(v2.x, 0.f), fmaxf(v2.y, 0.f));
 }
 
 template <int UP, int HB>
@@ -84,12 +95,13 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
   const bool real = i < U;
   const int ic = real ? i : 0;
 
-  // s of every group, double-buffered by iteration parity: [2][ngroups_pad][UP]
-  float2* sbuf = reinterpret_cast<float2*>(smem);
-  float2* Fz = sbuf + 2 * ngroups_pad * UP;                      // [ngroups][UP]
-  float* Wt = reinterpret_cast<float*>(Fz + ngroups * UP);       // [ngroups]
-  float2* const sb0 = sbuf + g * UP;
-  float2* const sb1 = sbuf + (ngroups_pad + g) * UP;
+  // s of every group, double-buffered by iteration parity, as planes of real
+  // and imaginary parts: [2][ngroups_pad][2][UP] floats.
+  float* sbuf = reinterpret_cast<float*>(smem);
+  float2* Fz = reinterpret_cast<float2*>(sbuf + 4 * ngroups_pad * UP);   // [ngroups][UP]
+  float* Wt = reinterpret_cast<float*>(Fz + ngroups * UP);               // [ngroups]
+  float* const sb0 = sbuf + 2 * g * UP;
+  float* const sb1 = sbuf + 2 * (ngroups_pad + g) * UP;
 
   // Wait for the contraction grid (programmatic dependent launch).
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -99,11 +111,15 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
   const float beta = static_cast<float>(U) * kap;
   const float n0n = S > 0 ? p.N0 * kap : 1.f;     // an empty cluster: any tau > 0, weight 0 below
   const float2* Dg = p.D + (static_cast<size_t>(scc) * Ceff + cc) * static_cast<size_t>(U + NS) * U;
-  float2 grow[UP];
+  // Row i of kappa G_c as pairs of adjacent columns: (re j, re j+1), (im j, im j+1).
+  float2 gre[UP / 2], gim[UP / 2];
 #pragma unroll
-  for (int j = 0; j < UP; ++j) {
-    const float2 v = Dg[(j < U ? j : 0) * U + ic];
-    grow[j] = (real && j < U) ? cscale(v, kap) : make_float2(0.f, 0.f);
+  for (int j = 0; j < UP; j += 2) {
+    const float2 v0 = Dg[(j < U ? j : 0) * U + ic], v1 = Dg[(j + 1 < U ? j + 1 : 0) * U + ic];
+    const float2 g0 = (real && j < U) ? cscale(v0, kap) : make_float2(0.f, 0.f);
+    const float2 g1 = (real && j + 1 < U) ? cscale(v1, kap) : make_float2(0.f, 0.f);
+    gre[j / 2] = make_float2(g0.x, g1.x);
+    gim[j / 2] = make_float2(g0.y, g1.y);
   }
   const float2 yv = real ? cscale(Dg[(U + nc) * U + ic], kap) : make_float2(0.f, 0.f);
   const float d = p.llr_scale;
@@ -118,30 +134,42 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
     // iteration's stores before the loads, and the buffer written next iteration
     // is the other one (the one after that is only written once every lane has
     // passed the next __syncwarp, i.e. finished these loads).
-    float2* cur = (t & 1) ? sb1 : sb0;
-    cur[i] = s;
+    float* cur = (t & 1) ? sb1 : sb0;
+    cur[i] = s.x;
+    cur[UP + i] = s.y;
     __syncwarp();
-    float2 gs = make_float2(0.f, 0.f);
+    // (G s)_i = sum_j G_ij s_j: four paired partial sums over even / odd j,
+    // Re = sum g_re s_re - sum g_im s_im, Im = sum g_re s_im + sum g_im s_re.
+    float2 rr = make_float2(0.f, 0.f), ii = rr, ri = rr, ir = rr;
 #pragma unroll
-    for (int j = 0; j < UP; j += 2) {
-      const float4 q = *reinterpret_cast<const float4*>(cur + j);
-      gs = cfma(grow[j], make_float2(q.x, q.y), gs);
-      gs = cfma(grow[j + 1], make_float2(q.z, q.w), gs);
+    for (int j = 0; j < UP; j += 4) {
+      const float4 sr = *reinterpret_cast<const float4*>(cur + j);
+      const float4 si = *reinterpret_cast<const float4*>(cur + UP + j);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 sr2 = h ? make_float2(sr.z, sr.w) : make_float2(sr.x, sr.y);
+        const float2 si2 = h ? make_float2(si.z, si.w) : make_float2(si.x, si.y);
+        rr = __ffma2_rn(gre[j / 2 + h], sr2, rr);
+        ii = __ffma2_rn(gim[j / 2 + h], si2, ii);
+        ri = __ffma2_rn(gre[j / 2 + h], si2, ri);
+        ir = __ffma2_rn(gim[j / 2 + h], sr2, ir);
+      }
     }
-    z = cadd(csub(cadd(yv, s), gs), v);
+    const float2 gs = make_float2((rr.x + rr.y) - (ii.x + ii.y), (ri.x + ri.y) + (ir.x + ir.y));
+    z = __fadd2_rn(__fadd2_rn(__fadd2_rn(yv, s), make_float2(-gs.x, -gs.y)), v);
     tau = fmaf(beta, phi, n0n);
     if (t >= p.lama_iters) break;
-    const float inv_tau = 1.f / tau;
+    const float inv_tau = __frcp_rn(tau);
     const float l2t = kLog2e * inv_tau;
-    float mr, vr, mi, vi;
-    pam_posterior<HB>(z.x, l2t, d, inv_d, mr, vr);
-    pam_posterior<HB>(z.y, l2t, d, inv_d, mi, vi);
-    float gsum = real ? vr + vi : 0.f;
+    float2 mean, var;
+    pam_posterior2<HB>(z, l2t, d, inv_d, mean, var);
+    float gsum = real ? var.x + var.y : 0.f;
 #pragma unroll
     for (int o = UP / 2; o > 0; o >>= 1) gsum += __shfl_xor_sync(kFullMask, gsum, o, UP);
     const float phin = gsum * invU;
-    v = cscale(csub(z, s), beta * phin * inv_tau);
-    s = make_float2(mr, mi);
+    const float f = beta * phin * inv_tau;
+    v = __fmul2_rn(__fadd2_rn(z, make_float2(-s.x, -s.y)), make_float2(f, f));
+    s = mean;
     phi = phin;
   }
 
@@ -184,8 +212,8 @@ cudaError_t launch_lama_up(const SolveParams& p, cudaStream_t stream) {
   const int ngroups = p.Ceff * p.spc;
   const int threads = ((ngroups * UP + 31) / 32) * 32;
   const int ngroups_pad = threads / UP;
-  const size_t smem = static_cast<size_t>(2 * ngroups_pad + ngroups) * UP * sizeof(float2) +
-                      static_cast<size_t>(ngroups) * 4;
+  const size_t smem = static_cast<size_t>(4 * ngroups_pad) * UP * sizeof(float) +
+                      static_cast<size_t>(ngroups) * UP * sizeof(float2) + static_cast<size_t>(ngroups) * 4;
   const int nblk = (p.n_sym + p.spc - 1) / p.spc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(p.n_sc) * nblk);

@@ -291,11 +291,11 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
     for (int e = tid; e < U * U; e += nt) P[e] = Ae[e];
     __syncthreads();
   }
-  // Refined estimates and inverse back to the workspace (same layouts).
-  for (int e = tid; e < W * U; e += nt) {
-    const int j = e / U, i = e - j * U;
-    if (j < U) p.As[(sys * U + j) * U + i] = P[e];
-    else p.Xs[(sys * NS + (j - U)) * U + i] = P[e];
+  // Refined estimates and the diagonal of the refined inverse (all that the
+  // fusion kernel reads) back to the workspace, in the same layouts.
+  for (int e = tid; e < U + NS * U; e += nt) {
+    if (e < U) p.As[(sys * U + e) * U + e] = P[e * U + e];
+    else p.Xs[sys * NS * U + (e - U)] = P[U * U + (e - U)];
   }
   // Let the fusion kernel start its launch while this grid drains.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
