@@ -398,7 +398,7 @@ def soak(replay, seconds: float, torch):
         torch.cuda.synchronize()
 
 
-STEP_SHAPES = ((6, 0), (5, 0), (4, 0), (2, 0), (1, 0))   # launch shapes tried together for a whole step
+STEP_SHAPES = ((7, 0), (6, 0), (5, 0), (4, 0), (2, 0), (1, 0))   # launch shapes tried together for a whole step
 FUSED_SHAPE = 6          # the contraction and the solve in one launch (include/ffeq.h tuning)
 
 

@@ -304,10 +304,13 @@ ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const
  *                  shape 5 with ring depth 2; ffeq_local_preprocess runs shape 5
  *                  with ring depth 2 (16-byte aligned H and y, else the separate
  *                  kernels of shape 1 run);
+ *              7 = shape 5 in half-size CTAs (8 MMA warps, two CTAs per SM, half
+ *                  the subcarriers in flight per CTA; the same results), so
+ *                  that a kernel on another stream can share every SM;
  *   values[1]  shapes 1-4: subcarriers staged ahead per CTA, 1..3, or 0 = as
- *              many as fit; shape 5: ring depth per subcarrier (32-antenna
- *              slices), 2 or 3, 0 = 3; shape 6: 2 or 0 (= 2).
- * FP16X3 runs on shapes 1 and 5 only.
+ *              many as fit; shapes 5 and 7: ring depth per subcarrier
+ *              (32-antenna slices), 2 or 3, 0 = 3; shape 6: 2 or 0 (= 2).
+ * FP16X3 runs on shapes 1, 5, 6 and 7 only.
  * ffeq_plan_set_tuning takes exactly 2 values and returns FFEQ_ERR_UNSUPPORTED
  * when the shape does not apply to or fit the problem (plan unchanged);
  * ffeq_plan_get_tuning writes min(n, 2) values.  ffeq_plan_autotune times every

@@ -627,7 +627,7 @@ ffeq_status ffeq_plan_get_tuning(const ffeq_plan* plan, int* values, int n) {
 ffeq_status ffeq_plan_set_tuning(ffeq_plan* plan, const int* values, int n) {
   if (!plan || n != 2 || !values) return FFEQ_ERR_INVALID_ARG;
   if (values[0] < ffeq::kGramAuto || values[0] > ffeq::kGramVariantMax || values[1] < 0 ||
-      values[1] > (values[0] == ffeq::kGramStream ? ffeq::kGramStreamRing : 3))
+      values[1] > ((values[0] == ffeq::kGramStream || values[0] == ffeq::kGramStreamHalf) ? ffeq::kGramStreamRing : 3))
     return FFEQ_ERR_INVALID_ARG;
   // The shape must fit the problem with 16-byte aligned rows (the bulk-staged case).
   ffeq::GramParams gp{};

@@ -152,15 +152,16 @@ bool gram_configure(GramParams& p, int precision, int variant, int stages) {
     stages = kGramFusedRing;
   }
   if (variant == kGram4x3 && precision == FFEQ_FP32) return false;   // CUDA-core shapes: 16 (8 warps) and 8x2
-  if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream) return false;
+  if (precision == FFEQ_FP16X3 && variant != kGram16 && variant != kGramStream && variant != kGramStreamHalf)
+    return false;
   if (variant == kGramPresplit && (!p.cl_uniform || !gram_presplit_eligible(precision, p.B, p.Ceff))) return false;
-  if (variant == kGramStream && !stream_ok) return false;
-  if (variant != kGramStream && stages > kGramMaxStages) return false;
+  if ((variant == kGramStream || variant == kGramStreamHalf) && !stream_ok) return false;
+  if (variant != kGramStream && variant != kGramStreamHalf && stages > kGramMaxStages) return false;
   if (!p.bulk) {              // plain-load staging: one stage, no pre-split planes, no tensor maps
-    if (variant == kGramPresplit || variant == kGramStream) variant = kGram16;
+    if (variant == kGramPresplit || variant == kGramStream || variant == kGramStreamHalf) variant = kGram16;
     stages = 0;
   }
-  if (variant == kGramStream) {
+  if (variant == kGramStream || variant == kGramStreamHalf) {
     if (stages == 1) return false;          // the streamed shape converts one slice ahead
     p.stage_elems = p.slot_elems = p.n_slots = p.plane_bytes = 0;
     p.stages = stages > 0 ? stages : kGramStreamRing;

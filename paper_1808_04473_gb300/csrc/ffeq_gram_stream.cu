@@ -73,19 +73,20 @@
 namespace ffeq {
 namespace {
 
-constexpr int kStreamWarps = 16;
+constexpr int kStreamWarps = 16;         // MMA warps of the full-size CTA (one CTA per SM)
+constexpr int kStreamWarpsHalf = 8;      // MMA warps of the half-size CTA (two CTAs per SM)
 constexpr int kStreamKsb = 2;            // 16-antenna blocks per slice (one per half-row conversion step)
 constexpr int kStreamMaxRing = 3;
 static_assert(kStreamKsb == 2, "one half-row conversion step per k-step of a slice");
 
-template <int UP>
+template <int UP, int MW = kStreamWarps>
 struct StreamShape {
   static constexpr int MT = UP <= 16 ? 1 : 2;       // 16-user m-tiles
   static constexpr int HR = 16 * MT;                // user row slots per block
   static constexpr int BR = HR + 16;                // rows per block (then n_sym <= 16 symbol slots)
   static constexpr int BLOCK = BR * 128;            // bytes per 16-antenna block (multiple of 1024)
   static constexpr int WPU = 2 * MT;                // warps per subcarrier
-  static constexpr int UPC = kStreamWarps / WPU;    // subcarriers in flight per CTA
+  static constexpr int UPC = MW / WPU;              // subcarriers in flight per CTA
   static constexpr int NTH = UP <= 16 ? 2 : 3;      // 8-row n-tiles of W per warp
   static constexpr int SLICE = kStreamKsb * BLOCK;
 };
@@ -120,9 +121,9 @@ struct FusedShape {
   static_assert(UP <= 16, "the fused form holds one 8- or 16-lane group per team");
 };
 
-template <int UP, bool FUSED>
+template <int UP, bool FUSED, int MW>
 constexpr size_t stream_smem_bytes(int ring) {
-  using Sh = StreamShape<UP>;
+  using Sh = StreamShape<UP, MW>;
   size_t b = 1024 + static_cast<size_t>(Sh::UPC) * ring * Sh::SLICE + 3 * Sh::UPC * kStreamMaxRing * 8;
   if constexpr (FUSED) b += 4 * Sh::UPC * 8 + 16 + Sh::UPC * FusedShape<UP>::TEAM;
   return b;
@@ -308,8 +309,8 @@ struct SliceCursor {
   }
 };
 
-// Warp-specialized form.  kStreamWarps MMA warps (teams as above) and
-// kConvWarps converter warps per CTA.  A converter warp owns UPC / kConvWarps
+// Warp-specialized form.  MW MMA warps (teams as above; 16, or 8 for the
+// half-size CTA of which two share an SM) and kConvWarps converter warps per CTA.  A converter warp owns UPC / kConvWarps
 // teams: it issues their copies (producer), and as soon as a slice has landed
 // it converts it in place to planes and signals the team (conv barrier, one
 // arrival); the MMA warps only wait for converted slices, run ldmatrix and the
@@ -317,16 +318,16 @@ struct SliceCursor {
 // converter polls its teams without blocking (a slice is converted only after
 // it has been issued, a refill only after its gate has completed), so no wait
 // depends on the order in which the teams progress; every wait is bounded.
-template <int UP>
-__host__ __device__ constexpr int conv_warps() { return UP <= 16 ? 8 : 4; }   // one team per converter warp
+template <int UP, int MW>
+__host__ __device__ constexpr int conv_warps() { return StreamShape<UP, MW>::UPC; }   // one team per converter warp
 template <int UP, bool FUSED>
 __host__ __device__ constexpr int solve_warps() {
   if constexpr (FUSED) return FusedShape<UP>::WARPS;
   return 0;
 }
-template <int UP, bool FUSED>
+template <int UP, bool FUSED, int MW>
 __host__ __device__ constexpr int ws_threads() {
-  return (kStreamWarps + conv_warps<UP>() + solve_warps<UP, FUSED>()) * 32;
+  return (MW + conv_warps<UP, MW>() + solve_warps<UP, FUSED>()) * 32;
 }
 constexpr long kConvPollLimit = 1L << 24;   // converter passes without progress before it gives up
 
@@ -420,16 +421,17 @@ __device__ __forceinline__ void fused_solve(const StreamParams& p, unsigned char
   }
 }
 
-template <int UP, int MODE, bool FUSED>
-__global__ void __launch_bounds__(ws_threads<UP, FUSED>(), 1) gram_ws_kernel(const __grid_constant__ StreamParams p) {
-  using Sh = StreamShape<UP>;
+template <int UP, int MODE, bool FUSED, int MW>
+__global__ void __launch_bounds__(ws_threads<UP, FUSED, MW>(), (MW == kStreamWarps ? 1 : 2))
+    gram_ws_kernel(const __grid_constant__ StreamParams p) {
+  using Sh = StreamShape<UP, MW>;
   using FS = FusedShape<UP <= 16 ? UP : 16>;
   constexpr int NTH = Sh::NTH;
-  constexpr int kConvWarps = conv_warps<UP>();
-  constexpr int kWsThreads = ws_threads<UP, FUSED>();
+  constexpr int kConvWarps = conv_warps<UP, MW>();
+  constexpr int kWsThreads = ws_threads<UP, FUSED, MW>();
   constexpr int TPC = Sh::UPC / kConvWarps;       // teams per converter warp
   static_assert(Sh::UPC % kConvWarps == 0, "teams split evenly over the converter warps");
-  static_assert(!FUSED || UP <= 16, "fused form: 8 or 16 users");
+  static_assert(!FUSED || (UP <= 16 && MW == kStreamWarps), "fused form: 8 or 16 users, full-size CTA");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t ring0 = (raw + 1023u) & ~1023u;
@@ -475,11 +477,11 @@ __global__ void __launch_bounds__(ws_threads<UP, FUSED>(), 1) gram_ws_kernel(con
     __syncthreads();
   }
 
-  if (FUSED && warp >= kStreamWarps + kConvWarps) {
-    if constexpr (FUSED) fused_solve<UP>(p, team_area, hfull, hfree, warp - kStreamWarps - kConvWarps, lane);
-  } else if (warp >= kStreamWarps) {
+  if (FUSED && warp >= MW + kConvWarps) {
+    if constexpr (FUSED) fused_solve<UP>(p, team_area, hfull, hfree, warp - MW - kConvWarps, lane);
+  } else if (warp >= MW) {
     // ---------------- converter / producer warp
-    const int cw = warp - kStreamWarps;
+    const int cw = warp - MW;
     const uint64_t pol = l2_evict_first_policy();
     const uint32_t tx_full = static_cast<uint32_t>(kStreamKsb * 128 * Mrows);
     const uint32_t tx_last = static_cast<uint32_t>(nkb_last * 128 * Mrows);
@@ -704,28 +706,31 @@ bool encode_rows(CUtensorMap* map, const void* base, long long rows, int B, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int UP, int MODE, bool FUSED>
+template <int UP, int MODE, bool FUSED, int MW = kStreamWarps>
 cudaError_t launch_stream_up(const StreamParams& sp, cudaStream_t stream) {
   static int configured[64] = {0};
   static int num_sms[64] = {0};
   constexpr int kMaxRing = FUSED ? kGramFusedRing : kStreamMaxRing;
-  static_assert(stream_smem_bytes<UP, FUSED>(kMaxRing) <= 227 * 1024, "shared memory of one CTA");
+  constexpr int kPerSm = MW == kStreamWarps ? 1 : 2;   // CTAs that share an SM
+  static_assert(kPerSm * stream_smem_bytes<UP, FUSED, MW>(kMaxRing) <= 227 * 1024, "shared memory of an SM");
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 64 && !configured[dev]) {
-    err = cudaFuncSetAttribute(gram_ws_kernel<UP, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(stream_smem_bytes<UP, FUSED>(kMaxRing)));
+    err = cudaFuncSetAttribute(gram_ws_kernel<UP, MODE, FUSED, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(stream_smem_bytes<UP, FUSED, MW>(kMaxRing)));
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     configured[dev] = 1;
   }
   if (sp.ring < 2 || sp.ring > kMaxRing) return cudaErrorInvalidValue;
-  const int sms = dev < 64 ? num_sms[dev] : 152;
-  const int need = (sp.n_sc + StreamShape<UP>::UPC - 1) / StreamShape<UP>::UPC;
-  const int grid = need < sms ? need : sms;
-  gram_ws_kernel<UP, MODE, FUSED><<<grid, ws_threads<UP, FUSED>(), stream_smem_bytes<UP, FUSED>(sp.ring), stream>>>(sp);
+  const int slots = (dev < 64 ? num_sms[dev] : 152) * kPerSm;
+  constexpr int UPC = StreamShape<UP, MW>::UPC;
+  const int need = (sp.n_sc + UPC - 1) / UPC;
+  const int grid = need < slots ? need : slots;
+  gram_ws_kernel<UP, MODE, FUSED, MW>
+      <<<grid, ws_threads<UP, FUSED, MW>(), stream_smem_bytes<UP, FUSED, MW>(sp.ring), stream>>>(sp);
   return cudaGetLastError();
 }
 
@@ -789,10 +794,27 @@ static bool stream_params(const GramParams& p, StreamParams& sp) {
   return true;
 }
 
+template <int MW>
+cudaError_t launch_stream_mw(const StreamParams& sp, int precision, int UP, cudaStream_t stream) {
+  const bool f16 = precision == FFEQ_FP16X3;
+  switch (UP) {
+    case 8:
+      return f16 ? launch_stream_up<8, kFp16x3, false, MW>(sp, stream)
+                 : launch_stream_up<8, kBf16x3, false, MW>(sp, stream);
+    case 16:
+      return f16 ? launch_stream_up<16, kFp16x3, false, MW>(sp, stream)
+                 : launch_stream_up<16, kBf16x3, false, MW>(sp, stream);
+    default:
+      return f16 ? launch_stream_up<32, kFp16x3, false, MW>(sp, stream)
+                 : launch_stream_up<32, kBf16x3, false, MW>(sp, stream);
+  }
+}
+
 cudaError_t launch_gram_stream(const GramParams& p, int precision, cudaStream_t stream) {
   if (p.n_sc == 0) return cudaSuccess;
   StreamParams sp{};
   if (!stream_params(p, sp)) return cudaErrorInvalidValue;
+  if (p.variant == kGramStreamHalf) return launch_stream_mw<kStreamWarpsHalf>(sp, precision, padded_users(p.U), stream);
   const bool f16 = precision == FFEQ_FP16X3;
   switch (padded_users(p.U)) {
     case 8:

@@ -359,7 +359,7 @@ GramCaps gram_tc_caps(int B, int U, int n_sym, int Ceff, int variant) {
 }
 
 cudaError_t launch_gram_tc(const GramParams& p, int precision, cudaStream_t stream) {
-  if (p.variant == kGramStream) return launch_gram_stream(p, precision, stream);
+  if (p.variant == kGramStream || p.variant == kGramStreamHalf) return launch_gram_stream(p, precision, stream);
   const size_t smem = gram_smem_bytes(p);
   if (precision == FFEQ_FP16X3) return launch_mode<kFp16x3, 16, 1>(p, smem, stream);   // the 16-warp shape only
   if (precision == FFEQ_BF16X3 && p.variant == kGramPresplit && p.plane_bytes > 0) {

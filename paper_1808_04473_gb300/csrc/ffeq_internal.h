@@ -76,10 +76,12 @@ struct GramParams {
 // CTA moved by tensor-map copies, each warp owning its output tiles over the
 // whole antenna range; `stages` is then the depth of each subcarrier's ring);
 // fused (the streamed contraction with the solve, fusion and soft outputs in the
-// same launch when a whole equalization runs; ring depth 2).
+// same launch when a whole equalization runs; ring depth 2); streamed with
+// half-size CTAs (8 MMA warps, two CTAs per SM, so that another kernel's CTA can
+// share each SM).
 constexpr int kGramAuto = 0, kGram16 = 1, kGram8x2 = 2, kGramPresplit = 3, kGram4x3 = 4, kGramStream = 5,
-              kGramFused = 6;
-constexpr int kGramVariantMax = kGramFused;
+              kGramFused = 6, kGramStreamHalf = 7;
+constexpr int kGramVariantMax = kGramStreamHalf;
 constexpr int kGramFusedRing = 2;       // ring depth of the fused shape (its solve areas take the rest)
 constexpr int kGramStreamRing = 3;      // default (and largest) ring depth of the streamed shape (least 2)
 

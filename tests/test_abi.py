@@ -115,7 +115,8 @@ def test_plan_tuning_validation(built):
     plan = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP32)
     assert ff.ffeq_plan_get_tuning(plan) == (0, 0)
     # out of range; pre-split, the 4-warp and the streamed shapes need a tensor-core precision
-    for bad, status in (((7, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2), ((5, 0), 2), ((6, 0), 2)):
+    for bad, status in (((8, 0), 1), ((-1, 0), 1), ((1, 4), 1), ((3, 0), 2), ((4, 0), 2), ((5, 0), 2), ((6, 0), 2),
+                        ((7, 0), 2)):
         with pytest.raises(ff.FfeqError) as e:
             ff.ffeq_plan_set_tuning(plan, bad)
         assert e.value.status == status, bad
@@ -130,15 +131,17 @@ def test_plan_tuning_validation(built):
     ff.ffeq_plan_set_tuning(big, (3, 0))
     # The streamed shape: BF16x3 or FP16x3 with whole 16-antenna clusters (FD);
     # its second value is the depth of each subcarrier's ring (0: 3).
+    # The half-size streamed shape (7) takes the same problems with the same depths.
     for prec in (ff.BF16X3, ff.FP16X3):
         fd = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=prec)
-        for st in (0, 2, 3):
-            ff.ffeq_plan_set_tuning(fd, (5, st))
-            assert ff.ffeq_plan_get_tuning(fd) == (5, st)
-        for st, status in ((4, 1), (1, 2)):        # depth 1 cannot convert one slice ahead
-            with pytest.raises(ff.FfeqError) as e:
-                ff.ffeq_plan_set_tuning(fd, (5, st))
-            assert e.value.status == status
+        for v in (5, 7):
+            for st in (0, 2, 3):
+                ff.ffeq_plan_set_tuning(fd, (v, st))
+                assert ff.ffeq_plan_get_tuning(fd) == (v, st)
+            for st, status in ((4, 1), (1, 2)):        # depth 1 cannot convert one slice ahead
+                with pytest.raises(ff.FfeqError) as e:
+                    ff.ffeq_plan_set_tuning(fd, (v, st))
+                assert e.value.status == status
     # The fused shape: the streamed shape's conditions, U = 8 or 16, L-MMSE or ZF
     # without refinement; ring depth 2 (0 means 2).
     for prec in (ff.BF16X3, ff.FP16X3):
@@ -159,15 +162,16 @@ def test_plan_tuning_validation(built):
             ff.ffeq_plan_set_tuning(pl, (6, 2))
         assert e.value.status == 2, kw
     odd = ff.ffeq_plan_create(96, 8, 8, 10, 2, arch=ff.FD, precision=ff.BF16X3)      # S = 12
-    with pytest.raises(ff.FfeqError) as e:
-        ff.ffeq_plan_set_tuning(odd, (5, 0))
-    assert e.value.status == 2
+    for v in (5, 6, 7):
+        with pytest.raises(ff.FfeqError) as e:
+            ff.ffeq_plan_set_tuning(odd, (v, 0))
+        assert e.value.status == 2
     ff.ffeq_plan_set_tuning(ff.ffeq_plan_create(96, 8, 8, 10, 2, arch=ff.PD, precision=ff.BF16X3), (5, 0))
     tf = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.TF32X3)
     with pytest.raises(ff.FfeqError) as e:
         ff.ffeq_plan_set_tuning(tf, (5, 0))
     assert e.value.status == 2
-    # FP16x3 runs on the 16-warp and the streamed shapes only.
+    # FP16x3 runs on the 16-warp, streamed, fused and half-size streamed shapes only.
     h = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.FP16X3)
     for v in (2, 3, 4):
         with pytest.raises(ff.FfeqError) as e:

@@ -1,5 +1,5 @@
 """GPU parity of every launch shape of the uniform plan (include/ffeq.h tuning),
-the fused shape 6 included.
+the fused shape 6 and the half-size streamed shape 7 included.
 
 Each contraction shape and pipeline depth that fits is run on the same inputs
 and checked against the FP64 oracle with the bounds of test_gpu_parity (1e-5
@@ -53,7 +53,7 @@ def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
     f = lmmse.equalize_pd if arch == 0 else lmmse.equalize_fd
     o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, C, "unbiased")
     results = {}
-    for variant in (1, 2, 3, 4, 5, 6):
+    for variant in (1, 2, 3, 4, 5, 6, 7):
         for stages in (0, 1, 2, 3):
             try:
                 ff.ffeq_plan_set_tuning(plan, (variant, stages))
@@ -70,15 +70,17 @@ def test_every_shape_matches_the_oracle(ff, arch, precision, shape):
     assert any(k[0] == 1 for k in results)          # the default shape always fits
     t = ff.ffeq_plan_autotune_sets(plan, [H, H.clone()], [y, y.clone()], p.N0, p.Es, z, s2, None, None, ws, nb,
                                    reps=2)
-    assert t[0] in (1, 2, 3, 4, 5, 6) and 1 <= t[1] <= 3
+    assert t[0] in (1, 2, 3, 4, 5, 6, 7) and 1 <= t[1] <= 3
     t = ff.ffeq_plan_autotune(plan, H, y, p.N0, p.Es, z, s2, None, None, ws, nb, reps=2)
-    assert t[0] in (1, 2, 3, 4, 5, 6) and 1 <= t[1] <= 3
+    assert t[0] in (1, 2, 3, 4, 5, 6, 7) and 1 <= t[1] <= 3
     if precision != 0 and (arch == 0 or C == 1 or (B // C) % 16 == 0):   # one cluster: no boundaries
         assert (5, 2) in results and (5, 3) in results   # the streamed shape takes every such problem
+        assert (7, 2) in results and (7, 3) in results   # and its half-size CTA form (the same sums per warp)
+        assert np.array_equal(results[(7, 3)].view(np.int32), results[(5, 3)].view(np.int32))
         # the fused one where the users fill a lane group (the same bits as shape 5, ring 2)
         assert ((6, 2) in results) == (U in (8, 16))
         if (6, 2) in results:
             assert np.array_equal(results[(6, 2)].view(np.int32), results[(5, 2)].view(np.int32))
     else:
-        assert not any(k[0] in (5, 6) for k in results)
+        assert not any(k[0] in (5, 6, 7) for k in results)
     assert ff.ffeq_plan_get_tuning(plan) == t
