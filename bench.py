@@ -861,7 +861,8 @@ def main():
     ap.add_argument("--impl", default="ffeq", choices=["ffeq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="headline step only (no equalizer variants, correlated, training or uneven lines)")
+                    help="headline step only (no FP32 comparison, equalizer variants, correlated, training or "
+                         "uneven lines)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--concurrent", type=int, default=0,
                     help="1: PD and FD as two concurrent branches of each captured step")
@@ -929,7 +930,7 @@ def main():
     del head
 
     fp32_cmp = None
-    if args.precision != "fp32":
+    if args.precision != "fp32" and not args.no_extras:
         Kc = max(5, K // 4)
         r32 = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision="fp32", bits=bits, K=Kc, warmup=args.warmup,
                              breakdown=True, tune_step=True)
