@@ -563,8 +563,22 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
             items += [(f"{tag}_local", a, "local"), (f"{tag}_fuse", a, "fuse")]
             if fused[a]:
                 items.append((f"{tag}_fused", a, "step"))
+        def both_locals(i):
+            # The two contractions as the concurrent step runs them (two graph
+            # branches), without the solves: the Gram stage of the step.
+            fork, join = torch.cuda.Event(), torch.cuda.Event()
+            fork.record(cap)
+            cap2.wait_event(fork)
+            launch(archs[0], i, "local")
+            launch(archs[1], i, "local", cap2)
+            join.record(cap2)
+            cap.wait_event(join)
+
+        if concurrent:
+            items.append(("gram_stage_concurrent", None, "both"))
         for name, a, which in items:
-            gs = [capture(lambda i=i: launch(a, i, which)) for i in range(n_sets)]
+            gs = [capture(lambda i=i: both_locals(i) if which == "both" else launch(a, i, which))
+                  for i in range(n_sets)]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(cap):
                 for i in range(n_sets):
@@ -1025,6 +1039,17 @@ def main():
     dom = max(step_kernels, key=kern.get)
     roof = solve_roof(dom) if dom.endswith("_fuse") else gram_roof(dom)
 
+    gram_stage = {"pd": gram_roof("pd_local"), "fd": gram_roof("fd_local")}
+    if "gram_stage_concurrent" in kern:
+        # Both contractions together, as the step's two branches run them.
+        alg2 = 2 * input_bytes(B, U, n_sc, n_sym)
+        ach2 = alg2 / (kern["gram_stage_concurrent"] * 1e-3) / 1e9
+        gram_stage["pd+fd concurrent"] = {
+            "kernels": "PD and FD contractions as two graph branches (the step without its solves)",
+            "bound": "hbm", "achieved": ach2, "peak": hbm_peak, "peak_source": f"{peak_src} (STREAM-style copy)",
+            "unit": "GB/s", "frac": ach2 / hbm_peak, "algorithmic_bytes": alg2,
+            "ms": kern["gram_stage_concurrent"]}
+
     def arch_ms(tag, a):
         return kern[f"{tag}_fused"] if fused[a] else kern[f"{tag}_local"] + kern[f"{tag}_fuse"]
     line = {
@@ -1042,7 +1067,7 @@ def main():
         "per_arch_symbols_per_s": {"pd": U * n_sc * n_sym / (arch_ms("pd", ffeq.PD) * 1e-3),
                                    "fd": U * n_sc * n_sym / (arch_ms("fd", ffeq.FD) * 1e-3)},
         "roofline": roof,
-        "roofline_gram_stage": {"pd": gram_roof("pd_local"), "fd": gram_roof("fd_local")},
+        "roofline_gram_stage": gram_stage,
         "roofline_solve_stage": {"pd": solve_roof("pd_fuse"), "fd": solve_roof("fd_fuse")},
         "fp32_same_gpu": fp32_cmp,
         "equalizers": variants or None,
