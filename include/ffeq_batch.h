@@ -4,8 +4,9 @@
  * Each instance is the problem of ffeq.h (Sec. II-A..D, III-A, IV-A of the
  * paper: PD central L-MMSE from the summed local Gram matrices and MRC
  * outputs, or FD local L-MMSE with optimal fusion, Eq. fusionrule, Lemma 1,
- * Thm. 3) with its own sizes and noise level; the architecture, precision,
- * estimate and LLR width are shared by the batch.  The paper treats one system
+ * Thm. 3; or the ZF or MRC equalizer in place of L-MMSE) with its own sizes
+ * and noise level; the architecture, precision, equalizer, estimate and LLR
+ * width are shared by the batch.  The paper treats one system
  * at a time; batching instances is this library's addition for receivers that
  * serve several cells or carriers with one GPU.
  *
@@ -46,10 +47,15 @@ typedef struct {
 typedef struct {
   int arch;        /* ffeq_arch, shared by the batch */
   int precision;   /* ffeq_precision */
-  int estimate;    /* ffeq_estimate */
+  int estimate;    /* ffeq_estimate, read for L-MMSE only: ZF and MRC fuse their own pairs */
   int llr_bits;    /* 0, 2, 4, 6 or 8 */
   /* element counts of the flat buffers (info_elems = 0: info never passed) */
   long long h_elems, y_elems, z_elems, sigma2_elems, llr_elems, info_elems;
+  /* ffeq_equalizer, shared by the batch: FFEQ_LMMSE (0, zero-initialized
+   * configs), FFEQ_ZF or FFEQ_MRC with the meanings of ffeq.h (Sec. III-A; FD
+   * fusion by Lemma 1 with the same readings, including the N0 -> 0 limit
+   * weights of MRC); FFEQ_LAMA is FFEQ_ERR_UNSUPPORTED here. */
+  int equalizer;
 } ffeq_batch_config;
 
 typedef struct ffeq_batch ffeq_batch;

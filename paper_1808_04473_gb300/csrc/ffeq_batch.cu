@@ -78,18 +78,23 @@ struct ffeq_batch {
 
 namespace {
 
-int lanes_per_row_default(int arch, int UP) { return (arch == FFEQ_PD && UP == 16) ? 2 : 1; }
+// MRC runs one lane per row (no sweep); L-MMSE and ZF may split a row over two lanes.
+int lanes_per_row_default(int arch, int UP, int equalizer) {
+  return (equalizer != FFEQ_MRC && arch == FFEQ_PD && UP == 16) ? 2 : 1;
+}
 
-bool lpr_allowed(int UP, int lpr) { return lpr == 1 || (lpr == 2 && UP <= 16); }
+bool lpr_allowed(int UP, int lpr, int equalizer) {
+  return lpr == 1 || (lpr == 2 && UP <= 16 && equalizer != FFEQ_MRC);
+}
 
 // Smallest CTA width that holds the widest unit of the group.
 int min_threads(const Group& g) { return ((g.max_ceff * g.UP * g.lpr + 31) / 32) * 32; }
 
-bool threads_allowed(const Group& g, int threads, int lpr) {
+bool threads_allowed(const Group& g, int threads, int lpr, int equalizer) {
   if (threads < 32 || threads > 512 || threads % 32 != 0) return false;
   const int slots = threads / (g.UP * lpr);   // UP * lpr divides 32
   if (slots < g.max_ceff || slots > ffeq::kTileSlots) return false;
-  return ffeq::solve_batch_smem_bytes(g.UP, lpr, threads) <= kSolveSmemLimit;
+  return ffeq::solve_batch_smem_bytes(g.UP, lpr, threads, equalizer) <= kSolveSmemLimit;
 }
 
 // Tile packing of one group into the table image (next fit over the solve order).
@@ -182,6 +187,9 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       cfg->precision != FFEQ_FP16X3)
     return FFEQ_ERR_INVALID_ARG;
   if (cfg->estimate != FFEQ_UNBIASED && cfg->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
+  if (cfg->equalizer == FFEQ_LAMA) return FFEQ_ERR_UNSUPPORTED;
+  if (cfg->equalizer != FFEQ_LMMSE && cfg->equalizer != FFEQ_ZF && cfg->equalizer != FFEQ_MRC)
+    return FFEQ_ERR_INVALID_ARG;
   if (cfg->llr_bits != 0 && cfg->llr_bits != 2 && cfg->llr_bits != 4 && cfg->llr_bits != 6 && cfg->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
   if (cfg->h_elems < 0 || cfg->y_elems < 0 || cfg->z_elems < 0 || cfg->sigma2_elems < 0 || cfg->llr_elems < 0 ||
@@ -225,7 +233,10 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       d.Ceff = Ceff;
       d.n_sym = in.n_sym;
       d.N0 = in.N0;
-      d.rho = static_cast<float>(static_cast<double>(in.N0) / static_cast<double>(in.Es));
+      // Zero forcing is the L-MMSE sweep with rho = 0 (and the literal pairs).
+      d.rho = cfg->equalizer == FFEQ_ZF ? 0.f
+                                         : static_cast<float>(static_cast<double>(in.N0) / static_cast<double>(in.Es));
+      d.Es = in.Es;
       d.llr_scale = static_cast<float>(scale);
       d.inst = i;
       b->units.push_back(d);
@@ -300,9 +311,9 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       b->gram_order.insert(b->gram_order.end(), go.begin(), go.end());
       b->solve_order.insert(b->solve_order.end(), so.begin(), so.end());
       g.stages = g.max_stages < 3 ? g.max_stages : 3;
-      g.lpr = lanes_per_row_default(cfg->arch, UP);
+      g.lpr = lanes_per_row_default(cfg->arch, UP, cfg->equalizer);
       g.threads = std::max(128, min_threads(g));
-      if (!threads_allowed(g, g.threads, g.lpr)) g.threads = min_threads(g);
+      if (!threads_allowed(g, g.threads, g.lpr, cfg->equalizer)) g.threads = min_threads(g);
       b->groups.push_back(g);
     }
   }
@@ -396,10 +407,11 @@ ffeq_status ffeq_batch_set_tuning(ffeq_batch* b, const int* values, int n) {
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     const Group& g = b->groups[gi];
     const int* v = values + 4 * gi;
-    if (v[0] != g.UP || v[1] < 1 || v[1] > g.max_stages || !lpr_allowed(g.UP, v[3])) return FFEQ_ERR_INVALID_ARG;
+    if (v[0] != g.UP || v[1] < 1 || v[1] > g.max_stages || !lpr_allowed(g.UP, v[3], b->cfg.equalizer))
+      return FFEQ_ERR_INVALID_ARG;
     Group t = g;
     t.lpr = v[3];
-    if (!threads_allowed(t, v[2], v[3])) return FFEQ_ERR_INVALID_ARG;
+    if (!threads_allowed(t, v[2], v[3], b->cfg.equalizer)) return FFEQ_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(b->mu);
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
@@ -512,7 +524,8 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
     sp.info = info;
     sp.U = g.UP;
     sp.spc = 1;
-    sp.unbiased = b->cfg.estimate == FFEQ_UNBIASED;
+    sp.unbiased = b->cfg.equalizer == FFEQ_LMMSE && b->cfg.estimate == FFEQ_UNBIASED;
+    sp.equalizer = b->cfg.equalizer;
     sp.llr_bits = b->cfg.llr_bits;
     sp.desc = sdesc + g.first;
     sp.tiles = tiles + g.tile_first;
@@ -601,12 +614,12 @@ ffeq_status ffeq_batch_autotune(ffeq_batch* b, const void* H, const void* y, voi
     }
     // Lanes per row and solve CTA width (tiles are rebuilt for each).
     for (int lpr = 1; s == FFEQ_OK && lpr <= 2; ++lpr) {
-      if (!lpr_allowed(g.UP, lpr)) continue;
+      if (!lpr_allowed(g.UP, lpr, b->cfg.equalizer)) continue;
       for (int th : {64, 128, 256, 512}) {
         if (s != FFEQ_OK) break;
         Group cand = g;
         cand.lpr = lpr;
-        if ((lpr == g.lpr && th == g.threads) || !threads_allowed(cand, th, lpr)) continue;
+        if ((lpr == g.lpr && th == g.threads) || !threads_allowed(cand, th, lpr, b->cfg.equalizer)) continue;
         const int old_l = g.lpr, old_t = g.threads;
         g.lpr = lpr;
         g.threads = th;

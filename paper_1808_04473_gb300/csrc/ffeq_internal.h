@@ -20,6 +20,7 @@ struct BatchDesc {
   int B, U, Ceff, n_sym;
   float N0, rho, llr_scale;
   int inst;             // index of the instance (diagnostics)
+  float Es;             // symbol energy (the MRC variance scale)
 };
 
 // Element counts of the batch buffers (for the device-side bounds checks).
@@ -221,9 +222,10 @@ size_t solve_smem_bytes(int U, int Ceff);
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream);
 cudaError_t launch_lama(const SolveParams& p, cudaStream_t stream);
 int lama_symbols_per_cta(int U, int Ceff, int n_sym);
-// Uneven batch: p.U holds the group's padded users (8/16/32), lpr its lanes per row.
+// Uneven batch: p.U holds the group's padded users (8/16/32), lpr its lanes per row
+// (1 for MRC, p.equalizer); ZF runs the L-MMSE kernel with rho = 0 per descriptor.
 cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream);
-size_t solve_batch_smem_bytes(int UP, int lpr, int threads);
+size_t solve_batch_smem_bytes(int UP, int lpr, int threads, int equalizer);
 
 // Device addresses of a __device__ symbol, one per CUDA context (a context's
 // module holds its own copy; a context destroyed by cudaDeviceReset and the one

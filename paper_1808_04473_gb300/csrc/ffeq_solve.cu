@@ -54,7 +54,7 @@ struct SolveLayout {
 struct EpiDesc {
   long long z_off, s2_off, llr_off;
   int U, NS, Ceff, out0, slot0;
-  float N0, llr_scale;
+  float s2s, llr_scale;   // variance scale (N0; Es for MRC, whose denominators are Es / sigma_c^2)
   int pad;
 };
 constexpr int kEpiCacheBytes = kTileSlots * static_cast<int>(sizeof(EpiDesc));
@@ -63,10 +63,11 @@ constexpr int kEpiCacheBytes = kTileSlots * static_cast<int>(sizeof(EpiDesc));
 // shared memory (in parallel) with the prefix sums of their outputs and matrix
 // slots, then every output (descriptor j, symbol n, user u) is one work item:
 // sum descriptor j's Ceff slots (contiguous, in tile order) and write z, sigma^2
-// and LLRs at its offsets.
+// and LLRs at its offsets.  zflag [kTileSlots][UP] (MRC, or nullptr): users of
+// descriptor j fused with the N0 -> 0 limit weights, whose variance is 0.
 template <int UP>
 __device__ void batch_epilogue(const SolveParams& p, const float2* base, const int* fail, int nslot,
-                               EpiDesc* cache, int* ndesc) {
+                               EpiDesc* cache, int* ndesc, const int* zflag = nullptr) {
   using Lay = SolveLayout<UP>;
   const SolveTile tile = p.tiles[blockIdx.x];
   const int bits = p.llr_bits, hb = bits / 2;
@@ -82,7 +83,7 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
       e.U = d.U;
       e.NS = d.n_sym;
       e.Ceff = d.Ceff;
-      e.N0 = d.N0;
+      e.s2s = p.equalizer == FFEQ_MRC ? d.Es : d.N0;
       e.llr_scale = d.llr_scale;
     }
     cache[j] = e;
@@ -134,7 +135,7 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
     } else if (dn > 0.f) {
       const float rr = 1.f / dn;
       zz = cscale(nm, rr);
-      s2 = d.N0 * rr;
+      s2 = (zflag && zflag[j * UP + u]) ? 0.f : d.s2s * rr;
     } else {
       zz = make_float2(0.f, 0.f);
       s2 = INFINITY;
@@ -814,6 +815,107 @@ cudaError_t launch_mrc_up(const SolveParams& p, cudaStream_t stream) {
   return cudaLaunchKernelEx(&cfg, mrc_fuse_kernel<UP>, p);
 }
 
+// Maximum-ratio combining (Sec. III-A) for the tiles of an uneven batch: one
+// group of UP lanes per local system, the descriptor and cluster of each slot
+// decoded and checked as in solve_fuse_kernel's batch mode, the per-lane
+// arithmetic of mrc_fuse_kernel (weight w = Es / sigma_c^2, numerators
+// w y^MRC_i(n) / G_ii, the N0 -> 0 limit weights per descriptor with N0 = 0),
+// and the batch epilogue with sigma^2 = Es / sum w (0 for the limit-weight users).
+template <int UP>
+__global__ void __launch_bounds__(512) mrc_batch_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = SolveLayout<UP>;
+  int* fail_sc = reinterpret_cast<int*>(smem);                        // [tile count]: MRC never fails
+  float2* base = reinterpret_cast<float2*>(smem + 256 + kEpiCacheBytes + 16);
+  const int nmat = static_cast<int>(blockDim.x) / UP;
+  int* zflag = reinterpret_cast<int*>(base + nmat * Lay::kMat);       // [kTileSlots][UP]
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  if (threadIdx.x < 64) fail_sc[threadIdx.x] = 0;
+  for (int t = threadIdx.x; t < kTileSlots * UP; t += blockDim.x) zflag[t] = 0;
+  __syncthreads();
+  // Wait for the contraction grid (programmatic dependent launch).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  const SolveTile tile = p.tiles[blockIdx.x];
+  const unsigned m = g < kTileSlots ? p.slot_map[static_cast<size_t>(blockIdx.x) * kTileSlots + g] : 0xffffu;
+  const int j = static_cast<int>(m >> 8);
+  const int c = static_cast<int>(m & 0xffu);
+  const int dj = tile.first + j;
+  bool valid = m != 0xffffu && j < tile.count && j < kTileSlots && tile.first >= 0 && dj < p.n_desc;
+  const BatchDesc* d = valid ? p.desc + dj : p.desc;
+  const int U = d->U, NS = d->n_sym, Ceff = d->Ceff;
+  valid = valid && U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kTileSlots && c < Ceff;
+  const long long matSize = valid ? static_cast<long long>(U + NS) * U : 0;
+  valid = valid && span_ok(d->d_off, Ceff * matSize, p.lim.d) &&
+          (!p.info || span_ok(d->info_off, Ceff, p.lim.info));
+  if (!valid && m != 0xffffu && i == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+  const float2* Dg = p.D + (valid ? d->d_off + c * matSize : 0);
+  const bool live = valid && i < U;
+  const bool noiseless = valid && d->N0 == 0.f;
+  const float rho = valid ? d->rho : 0.f;
+  float gii = 0.f, intf = 0.f;
+  if (live) {
+    for (int jj = 0; jj < U; ++jj) {
+      const float2 v = Dg[jj * U + i];   // G_i,jj (conjugate symmetric)
+      if (jj == i) {
+        gii = v.x;
+      } else {
+        intf = fmaf(v.x, v.x, fmaf(v.y, v.y, intf));
+      }
+    }
+    if (noiseless && gii > 0.f && intf == 0.f) atomicOr(&zflag[j * UP + i], 1);
+  }
+  __syncthreads();
+  if (g < nmat) {
+    float2* Fz = base + g * Lay::kMat + Lay::kRow;
+    float* Dn = reinterpret_cast<float*>(Fz + Lay::kNum);
+    float w = 0.f;
+    if (live) {
+      float zs = 0.f;
+      if (gii > 0.f) {
+        if (noiseless && zflag[j * UP + i]) {
+          w = intf == 0.f ? gii : 0.f;          // the N0 -> 0 limit weights
+        } else {
+          const float den = fmaf(rho, gii, intf);
+          w = den > 0.f ? gii * gii / den : 0.f;
+        }
+        zs = w / gii;
+      }
+      for (int n = 0; n < NS; ++n) Fz[n * UP + i] = cscale(Dg[(U + n) * U + i], zs);
+      if (i == 0 && p.info) p.info[d->info_off + c] = 0;
+    }
+    Dn[i] = w;
+  }
+  __syncthreads();
+  batch_epilogue<UP>(p, base, fail_sc, nmat, reinterpret_cast<EpiDesc*>(smem + 256),
+                     reinterpret_cast<int*>(smem + 256 + kEpiCacheBytes), zflag);
+}
+
+template <int UP>
+cudaError_t launch_mrc_batch(const SolveParams& p, cudaStream_t stream) {
+  const size_t smem = solve_batch_smem_bytes(UP, 1, p.threads, FFEQ_MRC);
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 64 && !configured[dev]) {
+    err = cudaFuncSetAttribute(mrc_batch_kernel<UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    configured[dev] = 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.n_tiles);
+  cfg.blockDim = dim3(p.threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mrc_batch_kernel<UP>, p);
+}
+
 }  // namespace
 
 // PD (one system per subcarrier) with 8 < U < 16: a full warp per system (two
@@ -866,6 +968,14 @@ cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream) {
 }
 
 cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t stream) {
+  if (p.equalizer == FFEQ_MRC) {
+    if (lpr != 1) return cudaErrorInvalidValue;
+    switch (p.U) {
+      case 8: return launch_mrc_batch<8>(p, stream);
+      case 16: return launch_mrc_batch<16>(p, stream);
+      default: return launch_mrc_batch<32>(p, stream);
+    }
+  }
   switch (p.U) {
     case 8: return lpr == 2 ? launch_up<8, 2, true>(p, stream) : launch_up<8, 1, true>(p, stream);
     case 16: return lpr == 2 ? launch_up<16, 2, true>(p, stream) : launch_up<16, 1, true>(p, stream);
@@ -873,10 +983,11 @@ cudaError_t launch_solve_batch(const SolveParams& p, int lpr, cudaStream_t strea
   }
 }
 
-size_t solve_batch_smem_bytes(int UP, int lpr, int threads) {
+size_t solve_batch_smem_bytes(int UP, int lpr, int threads, int equalizer) {
   const int nmat = threads / (UP * lpr);
   size_t per = UP == 8 ? SolveLayout<8>::kMat : (UP == 16 ? SolveLayout<16>::kMat : SolveLayout<32>::kMat);
-  return 256 + kEpiCacheBytes + 16 + static_cast<size_t>(nmat) * per * sizeof(float2);
+  const size_t zflags = equalizer == FFEQ_MRC ? static_cast<size_t>(kTileSlots) * UP * sizeof(int) : 0;
+  return 256 + kEpiCacheBytes + 16 + static_cast<size_t>(nmat) * per * sizeof(float2) + zflags;
 }
 
 }  // namespace ffeq

@@ -55,7 +55,7 @@ class ffeq_batch_config(ctypes.Structure):
     _fields_ = [("arch", ctypes.c_int), ("precision", ctypes.c_int), ("estimate", ctypes.c_int),
                 ("llr_bits", ctypes.c_int), ("h_elems", ctypes.c_longlong), ("y_elems", ctypes.c_longlong),
                 ("z_elems", ctypes.c_longlong), ("sigma2_elems", ctypes.c_longlong),
-                ("llr_elems", ctypes.c_longlong), ("info_elems", ctypes.c_longlong)]
+                ("llr_elems", ctypes.c_longlong), ("info_elems", ctypes.c_longlong), ("equalizer", ctypes.c_int)]
 
 
 _lib = None
@@ -376,7 +376,7 @@ def ffeq_batch_set_tuning(batch: Batch, tuning) -> None:
 
 
 def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNBIASED, llr_bits: int = 0,
-               with_info: bool = True):
+               with_info: bool = True, equalizer: int = LMMSE):
     """Lay instances out back to back in flat buffers.
 
     ``specs``: sequence of ``(B, U, C, n_sc, n_sym, N0, Es)``.  Offsets of the
@@ -398,7 +398,7 @@ def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNB
         offs["llr"] += n_sc * n_sym * U * llr_bits
         offs["info"] += n_sc * Ceff
     cfg = ffeq_batch_config(arch, precision, estimate, llr_bits, offs["h"], offs["y"], offs["z"], offs["s2"],
-                            offs["llr"], offs["info"] if with_info else 0)
+                            offs["llr"], offs["info"] if with_info else 0, equalizer)
     return cfg, inst
 
 

@@ -42,7 +42,7 @@ def test_groups_by_padded_users_and_workspace_size(lib):
             assert 1 <= stages <= 3 and threads % 32 == 0 and 32 <= threads <= 512 and lpr in (1, 2)
             assert lpr == (2 if (arch == ffeq.PD and UP == 16) else 1)
         d_bytes = sum(p.n_sc * (p.C if arch == ffeq.FD else 1) * (p.U + p.n_sym) * p.U * 8 for p in ps)
-        tables = 256 + len(ps) * (2 * 88 + 8 + 64 * 2)
+        tables = 256 + len(ps) * (2 * 96 + 8 + 64 * 2)
         ws = ffeq.ffeq_batch_workspace_size(b)
         assert d_bytes + tables <= ws <= d_bytes + tables + 5 * 256
 
@@ -120,3 +120,21 @@ def test_tuning_roundtrip_and_validation(lib):
         t = [list(x) for x in tun]
         t[0][3] = 2                                                  # two lanes per row needs UP <= 16
         assert _status(ffeq.ffeq_batch_set_tuning, b, t) == 1
+
+
+def test_equalizer_choice(lib):
+    """ZF and MRC batches plan like L-MMSE ones (MRC: one lane per row, no sweep);
+    LAMA is not offered for batches and an unknown equalizer is an argument error."""
+    ps = synth.make_uneven(64, seed=5)
+    for eq, status in ((ffeq.LMMSE, 0), (ffeq.ZF, 0), (ffeq.MRC, 0), (ffeq.LAMA, 2), (7, 1), (-1, 1)):
+        cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.PD, llr_bits=4, equalizer=eq)
+        assert _status(ffeq.ffeq_batch_create, cfg, inst) == status, eq
+    cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.PD, llr_bits=4, equalizer=ffeq.MRC)
+    b = ffeq.ffeq_batch_create(cfg, inst)
+    tun = ffeq.ffeq_batch_get_tuning(b)
+    assert all(t[3] == 1 for t in tun)
+    for gi, (UP, st, th, lpr) in enumerate(tun):
+        if UP <= 16:
+            t = [list(x) for x in tun]
+            t[gi][3] = 2                                    # MRC has no row sweep to split
+            assert _status(ffeq.ffeq_batch_set_tuning, b, t) == 1

@@ -32,6 +32,7 @@ import numpy as np
 import pytest
 
 import parity
+from oracle import linear as olinear
 from oracle import llr as ollr
 from oracle import lmmse
 from paper_1808_04473_gb300 import synth
@@ -79,11 +80,11 @@ def _specs(ps):
 class Run:
     """Device buffers of one packed batch and its plan."""
 
-    def __init__(self, ff, ps, arch, precision=0, estimate=0, llr_bits=4, with_info=True, specs=None):
+    def __init__(self, ff, ps, arch, precision=0, estimate=0, llr_bits=4, with_info=True, specs=None, equalizer=0):
         dev = torch.device("cuda:0")
         self.ff, self.ps, self.arch, self.bits = ff, ps, arch, llr_bits
         cfg, inst = ff.pack_batch(specs or _specs(ps), arch=arch, precision=precision, estimate=estimate,
-                                  llr_bits=llr_bits, with_info=with_info)
+                                  llr_bits=llr_bits, with_info=with_info, equalizer=equalizer)
         self.cfg, self.inst = cfg, inst
         H, y = _flat(ps, cfg, inst)
         self.H = torch.from_numpy(H).to(dev)
@@ -307,3 +308,69 @@ def test_tuning_cache_roundtrip(ff, uneven, tmp_path):
     assert cached2 and t2 == t1
     b.equalize()
     _check(b, b.host(), precision=2)
+
+
+def _linear_instances(eq, seed):
+    """Random instances for the ZF / MRC batches: ZF with every inverted Gram
+    matrix well posed (B >= 2U for PD, clusters of at least 2U antennas for FD);
+    MRC over the whole uneven range plus noiseless instances (one user alone, and
+    users on disjoint antennas: the N0 -> 0 limit weights, sigma^2 = 0)."""
+    rng = np.random.default_rng(seed)
+    ps = []
+    for k in range(48):
+        B = int(rng.choice([64, 128, 256]))
+        if eq == 1:
+            U = int(rng.integers(2, 17))
+            Cs = [c for c in (1, 2, 4, 8) if B // c >= 2 * U]
+        else:
+            U = int(rng.integers(1, 33))
+            Cs = [c for c in (1, 2, 4, 8, 16) if B // c >= 4]
+        C = int(rng.choice(Cs))
+        ps.append(synth.make_problem(B, U, C, int(rng.integers(1, 4)), int(rng.integers(1, 15)),
+                                     snr_db=float(rng.uniform(5, 20)), bits=4, seed=seed * 1000 + k))
+    if eq == 2:
+        ps.append(synth.make_problem(64, 1, 4, 3, 5, snr_db=10.0, bits=4, seed=seed + 1, noiseless=True))
+        q = synth.make_problem(64, 4, 4, 2, 6, snr_db=10.0, bits=4, seed=seed + 2, noiseless=True)
+        for u in range(4):                     # user u only on antennas 16u .. 16u + 15
+            mask = np.zeros(64, bool)
+            mask[16 * u:16 * u + 16] = True
+            q.H[:, u, ~mask] = 0
+        q.y[:] = np.einsum("kub,kn u->knb".replace(" ", ""), q.H, np.ones((q.n_sc, q.n_sym, 4), np.complex64))
+        ps.append(q)
+    return ps
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+@pytest.mark.parametrize("eq", [1, 2], ids=["ZF", "MRC"])
+def test_zf_and_mrc_batches_match_the_oracle(ff, arch, eq):
+    """ZF and MRC in the uneven batch (``ffeq_batch_config.equalizer``) against
+    ``oracle.linear`` per instance: z, sigma^2 and the LLRs (4x) within the BF16x3
+    bound, or the kappa-aware bound for ZF (rho = 0)."""
+    ps = _linear_instances(eq, seed=7 + arch)
+    run = Run(ff, ps, arch, precision=2, llr_bits=4, equalizer=eq)
+    run.equalize()
+    out = run.host()
+    assert ff.ffeq_device_status(clear=True) == 0
+    name = "zf" if eq == 1 else "mrc"
+    f = olinear.equalize_pd_linear if arch == 0 else olinear.equalize_fd_linear
+    for idx, (p, it) in enumerate(zip(ps, run.inst)):
+        o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, name)
+        tol = PREC_TOL[2]
+        if eq == 1:
+            parts = lmmse.partition(p.B, p.C) if arch == 1 else [(0, p.B)]
+            kap = max(np.linalg.cond(p.H[k].astype(np.complex128).T[b0:b1].conj().T
+                                     @ p.H[k].astype(np.complex128).T[b0:b1])
+                      for k in range(p.n_sc) for b0, b1 in parts)
+            tol = max(tol, 2.0 * UNIT[2] * kap)
+        n, U, NS = p.n_sc, p.U, p.n_sym
+        z = out["z"][it.z_off:it.z_off + n * NS * U].reshape(n, NS, U)
+        s2 = out["s2"][it.sigma2_off:it.sigma2_off + n * U].reshape(n, U)
+        parity.check(f"z[{idx}]", z, o["z"], tol)
+        if p.N0 == 0 and eq == 2:
+            assert np.array_equal(s2 == 0, o["sigma2"] == 0), idx
+        parity.check(f"sigma2[{idx}]", s2, o["sigma2"], tol)
+        L = out["llr"][it.llr_off:it.llr_off + n * NS * U * 4].reshape(n, NS, U, 4)
+        if p.N0 > 0:
+            parity.check(f"llr[{idx}]", L, ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es), 4 * tol)
+        Ceff = p.C if arch == 1 else 1
+        assert (out["info"][it.info_off:it.info_off + n * Ceff] == 0).all(), idx
