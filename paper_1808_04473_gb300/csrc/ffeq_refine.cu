@@ -36,11 +36,14 @@ constexpr int kRefineThreadsMax = 512;   // per system: 2 S threads, 128..512
 constexpr int kFuseThreads = 256;
 constexpr float kCondFp64 = 1e4f;        // condition estimate above which the residual is FP64
 
-// Shared memory of one system (cluster c of subcarrier k; S antennas).
+// Shared memory of one system (cluster c of subcarrier k; S antennas).  The two
+// U x U scratch areas serve the steps before the last one (the full next
+// inverse) only: with one step (full = false) they are left out, so that more
+// systems share an SM.
 struct RefineLayout {
   int U, NS, S, SS, W;
   size_t hs, pm, va, rb, rr, an, ae, cn, total;   // offsets in bytes
-  __host__ __device__ RefineLayout(int U_, int NS_, int S_)
+  __host__ __device__ RefineLayout(int U_, int NS_, int S_, bool full = true)
       : U(U_), NS(NS_), S(S_), SS(S_ + 1), W(U_ + NS_) {
     size_t o = 0;
     hs = o;  o += static_cast<size_t>(U) * SS * 8;      // H_c rows (stride S + 1 complex)
@@ -48,8 +51,8 @@ struct RefineLayout {
     va = o;  o += static_cast<size_t>(U) * SS * 8;      // V = H_c a_j per antenna
     rb = o;  o += static_cast<size_t>(NS) * SS * 8;     // y_c - H_c x per antenna
     rr = o;  o += static_cast<size_t>(NS) * U * 8;      // residual
-    an = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse (FP64 residual: E)
-    ae = o;  o += static_cast<size_t>(U) * U * 8;       // next inverse with the FP64 residual
+    an = o;  o += full ? static_cast<size_t>(U) * U * 8 : 0;   // next inverse (FP64 residual: E)
+    ae = o;  o += full ? static_cast<size_t>(U) * U * 8 : 0;   // next inverse with the FP64 residual
     cn = o;  o += static_cast<size_t>(2) * U * 4;       // column norms for the condition estimate
     total = o;
   }
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
   const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, B = p.B;
   const int k = static_cast<int>(sys / Ceff), c = static_cast<int>(sys % Ceff);
   const int S = p.cl_off[c + 1] - p.cl_off[c];   // antennas of this cluster
-  const RefineLayout L(U, NS, S);
+  const RefineLayout L(U, NS, S, p.steps > 1);
   const int SS = L.SS, W = L.W;
   float2* Hs = reinterpret_cast<float2*>(smem + L.hs);
   float2* P = reinterpret_cast<float2*>(smem + L.pm);
@@ -259,21 +262,23 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
       Rr[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(x.x), sum.x)),
                           static_cast<float>(fma(-r, static_cast<double>(x.y), sum.y)));
     }
-    // The residual of the inverse, E = I - M_c A~ = I - H_c^H V - rho A~ (entry
-    // (i, j) at j U + i).
-    for (int e = tid; e < U * U; e += nt) {
-      const int j = e / U, i = e - j * U;   // entry (i, j)
-      const float2* aj = P + j * U;
-      double2 hv = make_double2(0.0, 0.0);
-      for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[i * SS + b], Va[j * SS + b], hv);
-      const double r = static_cast<double>(rho);
-      const double id = i == j ? 1.0 : 0.0;
-      An[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(aj[i].x), id - hv.x)),
-                          static_cast<float>(fma(-r, static_cast<double>(aj[i].y), -hv.y)));
+    const bool last = step + 1 == p.steps;
+    if (!last) {
+      // The residual of the inverse, E = I - M_c A~ = I - H_c^H V - rho A~ (entry
+      // (i, j) at j U + i).
+      for (int e = tid; e < U * U; e += nt) {
+        const int j = e / U, i = e - j * U;   // entry (i, j)
+        const float2* aj = P + j * U;
+        double2 hv = make_double2(0.0, 0.0);
+        for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[i * SS + b], Va[j * SS + b], hv);
+        const double r = static_cast<double>(rho);
+        const double id = i == j ? 1.0 : 0.0;
+        An[e] = make_float2(static_cast<float>(fma(-r, static_cast<double>(aj[i].x), id - hv.x)),
+                            static_cast<float>(fma(-r, static_cast<double>(aj[i].y), -hv.y)));
+      }
     }
     __syncthreads();
-    // x += A~ r   (A~[u][v] = column v of A~ at row u); the next inverse
-    // A~ + A~ E (Newton-Schulz in residual form) into Ae.
+    // x += A~ r   (A~[u][v] = column v of A~ at row u).
     for (int e = tid; e < NS * U; e += nt) {
       const int n = e / U, u = e - n * U;
       float2 d = make_float2(0.f, 0.f);
@@ -281,17 +286,49 @@ __global__ void __launch_bounds__(kRefineThreadsMax) refine_system_kernel(const 
       float2* x = P + (U + n) * U + u;
       *x = cadd(*x, d);
     }
-    for (int e = tid; e < U * U; e += nt) {
-      const int j = e / U, i = e - j * U;
+    if (!last) {
+      // The next inverse A~ + A~ E (Newton-Schulz in residual form) into Ae.
+      for (int e = tid; e < U * U; e += nt) {
+        const int j = e / U, i = e - j * U;
+        float2 d = make_float2(0.f, 0.f);
+        for (int v = 0; v < U; ++v) d = cfma(P[v * U + i], An[j * U + v], d);
+        Ae[e] = cadd(P[e], d);
+      }
+      __syncthreads();
+      for (int e = tid; e < U * U; e += nt) P[e] = Ae[e];
+      __syncthreads();
+      continue;
+    }
+    // Last step: only the diagonal of A~ + A~ E is read afterwards,
+    // [A~ + A~ E]_jj = A~_jj + sum_v A~_jv E_vj with column j of E formed on the
+    // fly (E_vj rounded to FP32 as above); four lanes per column j split the v
+    // sum (v = part, part + 4, ...) and add their parts in a fixed butterfly.
+    // The x update above reads only the estimates' rows of P besides A~, and
+    // column j's diagonal is written by its own lanes after they have read it.
+    __syncthreads();
+    for (int t = tid; t < ((4 * U + 31) / 32) * 32; t += nt) {
+      const int j = t >> 2, part = t & 3;
       float2 d = make_float2(0.f, 0.f);
-      for (int v = 0; v < U; ++v) d = cfma(P[v * U + i], An[j * U + v], d);
-      Ae[e] = cadd(P[e], d);
+      if (j < U) {
+        const double r = static_cast<double>(rho);
+        for (int v = part; v < U; v += 4) {
+          double2 hv = make_double2(0.0, 0.0);
+          for (int b = 0; b < S; ++b) hv = dcfma_conj(Hs[v * SS + b], Va[j * SS + b], hv);
+          const float2 a_vj = P[j * U + v];
+          const double id = v == j ? 1.0 : 0.0;
+          const float2 ev = make_float2(static_cast<float>(fma(-r, static_cast<double>(a_vj.x), id - hv.x)),
+                                        static_cast<float>(fma(-r, static_cast<double>(a_vj.y), -hv.y)));
+          d = cfma(P[v * U + j], ev, d);
+        }
+      }
+      d.x += __shfl_xor_sync(kFullMask, d.x, 1);
+      d.y += __shfl_xor_sync(kFullMask, d.y, 1);
+      d.x += __shfl_xor_sync(kFullMask, d.x, 2);
+      d.y += __shfl_xor_sync(kFullMask, d.y, 2);
+      if (j < U && part == 0) P[j * U + j] = cadd(P[j * U + j], d);
     }
     __syncthreads();
-    for (int e = tid; e < U * U; e += nt) P[e] = Ae[e];
-    __syncthreads();
-  }
-  // Refined estimates and the diagonal of the refined inverse (all that the
+  }  // Refined estimates and the diagonal of the refined inverse (all that the
   // fusion kernel reads) back to the workspace, in the same layouts.
   for (int e = tid; e < U + NS * U; e += nt) {
     if (e < U) p.As[(sys * U + e) * U + e] = P[e * U + e];
@@ -395,7 +432,7 @@ cudaError_t launch_refine(const RefineParams& p, cudaStream_t stream) {
   const int S = p.max_S;   // shared memory and threads for the largest cluster
   const int threads = 2 * S < 128 ? 128 : (2 * S > kRefineThreadsMax ? kRefineThreadsMax : ((2 * S + 31) / 32) * 32);
   err = launch_pdl(reinterpret_cast<const void*>(refine_system_kernel), dim3(static_cast<unsigned>(nsys)),
-                   dim3(threads), RefineLayout(p.U, p.n_sym, S).total, stream, p);
+                   dim3(threads), RefineLayout(p.U, p.n_sym, S, p.steps > 1).total, stream, p);
   if (err != cudaSuccess) return err;
   const size_t fsmem = static_cast<size_t>(p.Ceff) * p.n_sym * p.U * 8 + static_cast<size_t>(p.Ceff) * p.U * 4 + 16;
   return launch_pdl(reinterpret_cast<const void*>(refine_fuse_kernel), dim3(p.n_sc), dim3(kFuseThreads), fsmem,
