@@ -575,6 +575,17 @@ ffeq_status ffeq_fd_train_workspace_size(const ffeq_plan* plan, size_t* bytes) {
   return FFEQ_OK;
 }
 
+namespace {
+// The training pair runs fused (Gram matrices formed in the solving CTA) for
+// FP32 plans whose subcarrier fits in one CTA's shared memory; the same choice
+// for both passes, so the backward never looks for a workspace D the forward
+// did not write.
+bool train_fused(const ffeq_plan* plan) {
+  const ffeq_problem& p = plan->p;
+  return p.precision == FFEQ_FP32 && ffeq::train_fused_fits(p.U, p.n_sym, p.B, p.C);
+}
+}  // namespace
+
 ffeq_status ffeq_fd_train_forward(const ffeq_plan* plan, const void* H, const void* y, const float* rho_c,
                                   const float* nu, void* z, void* workspace, size_t workspace_bytes, void* stream) {
   ffeq::TrainParams tp;
@@ -583,6 +594,10 @@ ffeq_status ffeq_fd_train_forward(const ffeq_plan* plan, const void* H, const vo
   if (!z || !aligned(z, 8)) return FFEQ_ERR_INVALID_ARG;
   tp.z = static_cast<float2*>(z);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (train_fused(plan)) {
+    const cudaError_t e = ffeq::launch_train_forward_fused(tp, st);
+    return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
+  }
   r = local_preprocess(plan, H, y, workspace, st);
   if (r != FFEQ_OK) return r;
   const cudaError_t e = ffeq::launch_train_forward(tp, st);
@@ -603,7 +618,8 @@ ffeq_status ffeq_fd_train_backward(const ffeq_plan* plan, const void* H, const v
   tp.gy = static_cast<float2*>(gy);
   tp.grho = grho;
   tp.gnu = gnu;
-  const cudaError_t e = ffeq::launch_train_backward(tp, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = train_fused(plan) ? ffeq::launch_train_backward_fused(tp, static_cast<cudaStream_t>(stream))
+                                          : ffeq::launch_train_backward(tp, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
 }
 

@@ -186,6 +186,13 @@ struct TrainParams {
 size_t train_smem_bytes(int U, int C);
 cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t stream);
 cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t stream);
+// Fused forms (the local Gram matrices formed in the solving CTA, from H and Y
+// staged in shared memory; the gradients of H and Y in the backward CTA): for
+// FP32 plans whose subcarrier fits, ffeq_fd_train_forward / _backward run these
+// instead (forward: no contraction launch, no workspace D; backward: no W, G_b).
+bool train_fused_fits(int U, int n_sym, int B, int C);
+cudaError_t launch_train_forward_fused(const TrainParams& p, cudaStream_t stream);
+cudaError_t launch_train_backward_fused(const TrainParams& p, cudaStream_t stream);
 // Shared memory of the optimal-weight backward solve (one CTA per subcarrier).
 size_t train_optimal_smem_bytes(int U, int C);
 cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t stream);

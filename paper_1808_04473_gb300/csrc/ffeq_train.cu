@@ -348,6 +348,307 @@ __global__ void __launch_bounds__(512) train_optimal_solve_kernel(const TrainPar
   }
 }
 
+// Fused forms for FP32 plans whose subcarrier fits in shared memory: one CTA per
+// subcarrier stages H_k and Y_k antenna by antenna, each antenna's row laid out
+// like a row of the sweep, W = UP + NR columns (H[0..U)[b], zeros up to UP,
+// Y[0..n_sym)[b], zeros up to W) held as a plane of real parts then a plane of
+// imaginary parts, and lane i of group c forms row i of [G_c + rho_c I | R]
+// itself, in the sweep's column pairs, with two paired FMAs per complex
+// product and no column guards:
+//   G_c[i][j] = sum_{b in c} conj(H[i][b]) H[j][b],   B_c[i][n] = sum_{b in c} conj(H[i][b]) Y[n][b]
+// (Sec. II-C, the contraction of the separate path in antenna order), so the
+// local Gram matrices never go through the workspace: the forward pass forms
+// them for its sweep, the backward pass forms them again (the factorization is
+// recomputed, not stored) and, with H and Y still staged, forms the gradients
+// of H and Y in the same CTA from the low-rank form of W:
+//   sum_v H[v][b] W[v][u] = sum_n (H X)_n[b] conj(G_b[n][u]) + (H G_b)_n[b] conj(X[n][u]),
+//   dL/dH[u][b] = sum_n (Y[n][b] - (H X)_n[b]) conj(G_b[n][u]) - dL/dY[n][b] conj(X[n][u]),
+//   dL/dY[n][b] = (H G_b)_n[b] = sum_u H[u][b] G_b[n][u],
+// which needs neither W nor G_b in the workspace.
+template <int UP, int NR>
+struct FusedTrainLayout {
+  static constexpr int kW = UP + NR;   // columns of a staged row (a multiple of 4)
+  // Bytes: flags, the staged rows (B rows of 2 kW floats), the groups.
+  __host__ __device__ static size_t staged(int B) { return static_cast<size_t>(B) * 2 * kW * sizeof(float); }
+  __host__ __device__ static size_t bytes(int B, int C) {
+    return 16 + staged(B) + static_cast<size_t>(C) * TrainLayout<UP, NR>::kGroup * sizeof(float2);
+  }
+};
+
+// Stage H_k [U][B] and Y_k [NS][B] into the planar rows (every thread): 4-byte
+// asynchronous copies, coalesced on the global side and all in flight at once,
+// and zeros in the padding columns; completed (and made visible to the CTA) by
+// the caller's stage_wait.
+template <int UP, int NR>
+__device__ __forceinline__ void stage_rows(const float2* Hk, const float2* Yk, int U, int NS, int B, float* Wf) {
+  constexpr int W = UP + NR;
+  for (int r = 0; r < U + NS; ++r) {
+    const float2* src = r < U ? Hk + static_cast<size_t>(r) * B : Yk + static_cast<size_t>(r - U) * B;
+    const int col = r < U ? r : UP + (r - U);
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+      float* dst = Wf + b * 2 * W + col;
+      const float* s = reinterpret_cast<const float*>(src + b);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(s) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + W)), "l"(s + 1) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const int pad = (UP - U) + (NR - NS);   // zero columns [U, UP) and [UP + NS, W)
+  for (int e = threadIdx.x; e < B * pad; e += blockDim.x) {
+    const int b = e / pad, q = e - b * pad;
+    const int col = q < UP - U ? U + q : UP + NS + (q - (UP - U));
+    Wf[b * 2 * W + col] = 0.f;
+    Wf[b * 2 * W + W + col] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+}
+
+// Antennas [b0, b1) of cluster c.
+__device__ __forceinline__ void cluster_range(const TrainParams& p, int c, int& b0, int& b1) {
+  if (p.cl_uniform) {
+    const int S = p.B / p.C;
+    b0 = c * S;
+    b1 = b0 + S;
+  } else {
+    b0 = p.cl_off[c];
+    b1 = p.cl_off[c + 1];
+  }
+}
+
+// Row i of [G_c + rho I | R] formed from the staged rows in the sweep's column
+// pairs (rp[m]: real parts of columns 2m, 2m + 1; ip[m]: imaginary parts):
+// columns [0, MC) accumulate conj(H[i][b]) times the staged row of every
+// antenna b of the cluster, MC = W with the right-hand sides B_c (WITH_Y), else
+// MC = UP and R[i][n] = rhs(n).  Each half of a pair rounds as cfma_conj would.
+// Padding rows and groups past the clusters are identity rows with zero
+// right-hand sides.
+template <int UP, int NR, bool WITH_Y, typename Rhs>
+__device__ __forceinline__ void form_row(float2 (&rp)[(UP + NR) / 2], float2 (&ip)[(UP + NR) / 2], const float* Wf,
+                                         int U, int NS, int b0, int b1, int i, bool valid, float rho, Rhs rhs) {
+  constexpr int W = UP + NR;
+  constexpr int MC = WITH_Y ? W : UP;
+#pragma unroll
+  for (int m = 0; m < W / 2; ++m) rp[m] = ip[m] = make_float2(0.f, 0.f);
+  const bool live = valid && i < U;
+  if (live) {
+    for (int b = b0; b < b1; ++b) {
+      const float* wr = Wf + b * 2 * W;   // real parts, then imaginary parts
+      const float hr = wr[i], hi = wr[W + i];
+      const float2 hr2 = make_float2(hr, hr), hi2 = make_float2(hi, hi), nhi2 = make_float2(-hi, -hi);
+#pragma unroll
+      for (int c4 = 0; c4 < MC; c4 += 4) {
+        const float4 re = *reinterpret_cast<const float4*>(wr + c4);
+        const float4 im = *reinterpret_cast<const float4*>(wr + W + c4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int m = c4 / 2 + h;
+          const float2 r2 = h ? make_float2(re.z, re.w) : make_float2(re.x, re.y);
+          const float2 i2 = h ? make_float2(im.z, im.w) : make_float2(im.x, im.y);
+          rp[m] = __ffma2_rn(hr2, r2, rp[m]);    // Re conj(h) w = h_re w_re + h_im w_im
+          rp[m] = __ffma2_rn(hi2, i2, rp[m]);
+          ip[m] = __ffma2_rn(hr2, i2, ip[m]);    // Im conj(h) w = h_re w_im - h_im w_re
+          ip[m] = __ffma2_rn(nhi2, r2, ip[m]);
+        }
+      }
+    }
+  }
+  // The diagonal (G_ii real, plus rho); identity rows for padding lanes.
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    float re = j % 2 ? rp[j / 2].y : rp[j / 2].x;
+    float im = j % 2 ? ip[j / 2].y : ip[j / 2].x;
+    if (!live) {
+      re = i == j ? 1.f : 0.f;
+      im = 0.f;
+    } else if (j == i) {
+      re += rho;
+      im = 0.f;
+    }
+    if (j % 2) {
+      rp[j / 2].y = re;
+      ip[j / 2].y = im;
+    } else {
+      rp[j / 2].x = re;
+      ip[j / 2].x = im;
+    }
+  }
+  if constexpr (!WITH_Y) {
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+      const float2 v = (live && n < NS) ? rhs(n) : make_float2(0.f, 0.f);
+      const int j = UP + n;
+      if (j % 2) {
+        rp[j / 2].y = v.x;
+        ip[j / 2].y = v.y;
+      } else {
+        rp[j / 2].x = v.x;
+        ip[j / 2].x = v.y;
+      }
+    }
+  }
+}
+
+// Fused forward: the local Gram matrices, the sweep, X_c to the workspace and
+// z = sum_c nu_c X_c (fixed cluster order).
+template <int UP, int NR>
+__global__ void __launch_bounds__(512) train_forward_fused_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = TrainLayout<UP, NR>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C, B = p.B;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  int* fail_any = reinterpret_cast<int*>(smem);
+  float* Wf = reinterpret_cast<float*>(smem + 16);
+  float2* groups = reinterpret_cast<float2*>(smem + 16 + FusedTrainLayout<UP, NR>::staged(B));
+  float2* rowbuf = groups + gm * Lay::kGroup;
+  float2* F = rowbuf + Lay::kRow;              // [NR][UP]: nu * X of this cluster
+  if (threadIdx.x == 0) *fail_any = 0;
+  stage_rows<UP, NR>(p.H + static_cast<size_t>(k) * U * B, p.y + static_cast<size_t>(k) * NS * B, U, NS, B, Wf);
+  stage_wait();
+
+  int b0, b1;
+  cluster_range(p, gm, b0, b1);
+  float2 rp[W / 2], ip[W / 2];
+  form_row<UP, NR, true>(rp, ip, Wf, U, NS, b0, b1, i, valid, p.rho_c[gm], [](int) { return make_float2(0.f, 0.f); });
+  float rs = 1.f;
+  const int fail = gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
+  if (valid && i == 0 && fail) atomicOr(fail_any, 1);
+
+  const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
+  if (valid && i < U) {
+    float2* Xk = p.X + (static_cast<size_t>(k) * C + gm) * NS * U;
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+      if (n < NS) {
+        const float2 x = swept<W>(rp, ip, n, rs);
+        Xk[n * U + i] = x;
+        F[n * UP + i] = cscale(x, w);
+      }
+    }
+  }
+  __syncthreads();
+  const bool bad = *fail_any != 0;
+  for (int e = threadIdx.x; e < U * NS; e += blockDim.x) {
+    const int u = e % U, n = e / U;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < C; ++c) acc = cadd(acc, (groups + c * Lay::kGroup + Lay::kRow)[n * UP + u]);
+    p.z[(static_cast<size_t>(k) * NS + n) * U + u] = bad ? make_float2(NAN, NAN) : acc;
+  }
+}
+
+// Fused backward: G_b from the recomputed factorization of [G_c + rho_c I |
+// diag(nu_c) G_z], the partial sums of dL/drho_c and dL/dnu[c][.] (X_c from the
+// forward pass), then the gradients of H and Y per antenna from the staged rows
+// (the low-rank form above; sums over users and symbols in a fixed order).
+template <int UP, int NR>
+__global__ void __launch_bounds__(512) train_backward_fused_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = TrainLayout<UP, NR>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C, B = p.B;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  float* Wf = reinterpret_cast<float*>(smem + 16);
+  float2* groups = reinterpret_cast<float2*>(smem + 16 + FusedTrainLayout<UP, NR>::staged(B));
+  float2* rowbuf = groups + gm * Lay::kGroup;
+  float2* Gs = rowbuf + Lay::kRow;              // [NR][UP]  G_b of this cluster
+  float2* Xs = Gs + NR * UP;                    // [NR][UP]  X of this cluster
+  stage_rows<UP, NR>(p.H + static_cast<size_t>(k) * U * B, p.y + static_cast<size_t>(k) * NS * B, U, NS, B, Wf);
+  stage_wait();
+
+  int b0, b1;
+  cluster_range(p, gm, b0, b1);
+  const float2* gz = p.gz + static_cast<size_t>(k) * NS * U;
+  const float w = (valid && i < U) ? p.nu[gm * U + i] : 0.f;
+  float2 rp[W / 2], ip[W / 2];
+  form_row<UP, NR, false>(rp, ip, Wf, U, NS, b0, b1, i, valid, p.rho_c[gm],
+                          [&](int n) { return cscale(gz[n * U + i], w); });
+  float rs = 1.f;
+  gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
+
+  const bool live = valid && i < U;
+  const size_t off = (static_cast<size_t>(k) * C + gm) * NS * U;
+  float prho = 0.f, pnu = 0.f;
+#pragma unroll
+  for (int n = 0; n < NR; ++n) {
+    if (n < NS) {
+      const float2 gb = live ? swept<W>(rp, ip, n, rs) : make_float2(0.f, 0.f);
+      const float2 x = live ? p.X[off + n * U + i] : make_float2(0.f, 0.f);
+      const float2 gzv = live ? gz[n * U + i] : make_float2(0.f, 0.f);
+      prho -= gb.x * x.x + gb.y * x.y;          // Re(conj(G_b) X)
+      pnu += gzv.x * x.x + gzv.y * x.y;         // Re(conj(g_z) X)
+      if (valid) {
+        Gs[n * UP + i] = gb;
+        Xs[n * UP + i] = x;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = UP / 2; o > 0; o >>= 1) prho += __shfl_xor_sync(kFullMask, prho, o, UP);
+  float* P = p.P + (static_cast<size_t>(k) * C + gm) * (1 + U);
+  if (valid) {
+    if (i == 0) P[0] = prho;
+    if (i < U) P[1 + i] = pnu;
+  }
+  __syncthreads();
+
+  // Per antenna b of cluster c: (H X)_n, (H G_b)_n = dL/dY[n][b], then dL/dH[.][b].
+  float2* gHk = p.gH + static_cast<size_t>(k) * U * B;
+  float2* gyk = p.gy + static_cast<size_t>(k) * NS * B;
+  const int S = p.cl_uniform ? B / C : 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int c = 0;
+    if (p.cl_uniform) {
+      c = b / S;
+    } else {
+      while (c + 1 < C && b >= p.cl_off[c + 1]) ++c;
+    }
+    const float2* Gc = groups + c * Lay::kGroup + Lay::kRow;
+    const float2* Xc = Gc + NR * UP;
+    const float* wr = Wf + b * 2 * W;
+    float2 hx[NR], hg[NR];
+#pragma unroll
+    for (int n = 0; n < NR; ++n) hx[n] = hg[n] = make_float2(0.f, 0.f);
+    for (int v = 0; v < U; ++v) {
+      const float2 h = make_float2(wr[v], wr[W + v]);
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        if (n < NS) {
+          hx[n] = cfma(h, Xc[n * UP + v], hx[n]);
+          hg[n] = cfma(h, Gc[n * UP + v], hg[n]);
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+      if (n < NS) {
+        hx[n] = csub(make_float2(wr[UP + n], wr[W + UP + n]), hx[n]);   // Y[n][b] - (H X)_n[b]
+        gyk[static_cast<size_t>(n) * B + b] = hg[n];
+      }
+    }
+    for (int u = 0; u < U; ++u) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        if (n < NS) {
+          acc = cfma_conj(Gc[n * UP + u], hx[n], acc);    // conj(G_b[n][u]) (Y - H X)_n
+          acc = cfms_bconj(hg[n], Xc[n * UP + u], acc);   // - dL/dY[n][b] conj(X[n][u])
+        }
+      }
+      gHk[static_cast<size_t>(u) * B + b] = acc;
+    }
+  }
+}
+
 // Backward contraction, per subcarrier (G_b and W of its clusters staged in
 // shared memory):
 //   dL/dH[u][b] = sum_n Y[n][b] conj(G_b[n][u]) - sum_v H[v][b] W[v][u]
@@ -496,6 +797,28 @@ cudaError_t launch_backward_up(const TrainParams& p, cudaStream_t st) {
 }
 
 template <int UP, int NR>
+cudaError_t launch_forward_fused_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = FusedTrainLayout<UP, NR>::bytes(p.B, p.C);
+  cudaError_t e = set_smem(train_forward_fused_kernel<UP, NR>, smem);
+  if (e != cudaSuccess) return e;
+  train_forward_fused_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int UP, int NR>
+cudaError_t launch_backward_fused_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = FusedTrainLayout<UP, NR>::bytes(p.B, p.C);
+  cudaError_t e = set_smem(train_backward_fused_kernel<UP, NR>, smem);
+  if (e != cudaSuccess) return e;
+  train_backward_fused_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_reduce_kernel<<<p.C * (1 + p.U), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int UP, int NR>
 size_t optimal_smem_up(int C) {
   return 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16 +
          static_cast<size_t>(C) * OptimalLayout<UP, NR>::kGroup * sizeof(float2);
@@ -537,6 +860,25 @@ size_t train_smem_bytes(int U, int C) {
 cudaError_t launch_train_forward(const TrainParams& p, cudaStream_t st) { FFEQ_TRAIN_DISPATCH(launch_forward_up) }
 
 cudaError_t launch_train_backward(const TrainParams& p, cudaStream_t st) { FFEQ_TRAIN_DISPATCH(launch_backward_up) }
+
+bool train_fused_fits(int U, int n_sym, int B, int C) {
+  const bool wide = rhs_columns(n_sym) > 4;
+  size_t bytes;
+  switch (padded_users(U)) {
+    case 8: bytes = wide ? FusedTrainLayout<8, kNsymMax>::bytes(B, C) : FusedTrainLayout<8, 4>::bytes(B, C); break;
+    case 16: bytes = wide ? FusedTrainLayout<16, kNsymMax>::bytes(B, C) : FusedTrainLayout<16, 4>::bytes(B, C); break;
+    default: bytes = wide ? FusedTrainLayout<32, kNsymMax>::bytes(B, C) : FusedTrainLayout<32, 4>::bytes(B, C); break;
+  }
+  return bytes <= 227 * 1024;
+}
+
+cudaError_t launch_train_forward_fused(const TrainParams& p, cudaStream_t st) {
+  FFEQ_TRAIN_DISPATCH(launch_forward_fused_up)
+}
+
+cudaError_t launch_train_backward_fused(const TrainParams& p, cudaStream_t st) {
+  FFEQ_TRAIN_DISPATCH(launch_backward_fused_up)
+}
 
 size_t train_optimal_smem_bytes(int U, int C) {
   switch (padded_users(U)) {
