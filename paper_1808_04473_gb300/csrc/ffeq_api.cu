@@ -544,8 +544,11 @@ ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const
       !aligned(workspace, 256))
     return FFEQ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  r = local_preprocess(plan, H, y, workspace, st);
-  if (r != FFEQ_OK) return r;
+  const bool fused = p.precision == FFEQ_FP32 && ffeq::train_optimal_fused_fits(p.U, p.n_sym, p.B, p.C);
+  if (!fused) {
+    r = local_preprocess(plan, H, y, workspace, st);
+    if (r != FFEQ_OK) return r;
+  }
   char* base = static_cast<char*>(workspace);
   ffeq::TrainParams tp{};
   tp.H = static_cast<const float2*>(H);
@@ -565,7 +568,8 @@ ffeq_status ffeq_fd_optimal_backward(const ffeq_plan* plan, const void* H, const
   tp.status = ffeq::device_status_ptr();
   tp.cl_uniform = plan->cl_uniform ? 1 : 0;
   for (int c = 0; c <= p.C && !plan->cl_uniform; ++c) tp.cl_off[c] = plan->cl_off[c];
-  const cudaError_t e = ffeq::launch_train_optimal_backward(tp, st);
+  const cudaError_t e = fused ? ffeq::launch_train_optimal_backward_fused(tp, st)
+                              : ffeq::launch_train_optimal_backward(tp, st);
   return e == cudaSuccess ? FFEQ_OK : cuda_fail(e);
 }
 

@@ -196,6 +196,9 @@ cudaError_t launch_train_backward_fused(const TrainParams& p, cudaStream_t strea
 // Shared memory of the optimal-weight backward solve (one CTA per subcarrier).
 size_t train_optimal_smem_bytes(int U, int C);
 cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t stream);
+// Its fused form (FP32 plans whose subcarrier fits; no contraction launch, no D, W, G_b).
+bool train_optimal_fused_fits(int U, int n_sym, int B, int C);
+cudaError_t launch_train_optimal_backward_fused(const TrainParams& p, cudaStream_t stream);
 
 // Padded user count (8, 16 or 32) used for register tiles.
 int padded_users(int U);

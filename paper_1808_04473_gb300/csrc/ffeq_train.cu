@@ -649,6 +649,179 @@ __global__ void __launch_bounds__(512) train_backward_fused_kernel(const TrainPa
   }
 }
 
+// Fused adjoint through the optimal weights (FP32 plans whose subcarrier fits):
+// the rows of [M_c | B_c] formed from the staged H and Y as in the fused
+// training kernels, the sweep's rows of X_c and A_c, the weights, z, q, G_x and
+// G_b of train_optimal_solve_kernel, row i of A_c kept in shared memory, and the
+// gradients per antenna from the low-rank part of W_c and its full-rank term:
+//   sum_v H[v][b] W_c[v][u] = sum_n (H X)_n conj(G_b[n][u]) + (H G_b)_n conj(X[n][u])
+//                             + 2 sum_w (H A)_w q_w A[w][u],  (H A)_w = sum_v H[v][b] A[v][w],
+// so neither D nor W_c nor G_b goes through the workspace.
+template <int UP, int NR>
+struct OptimalFusedLayout {
+  static constexpr int kG = OptimalLayout<UP, NR>::kGroup + UP * UP;   // per group, + A [UP][UP]
+  __host__ __device__ static size_t wv_bytes(int C) { return ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16; }
+  __host__ __device__ static size_t bytes(int B, int C) {
+    return 16 + wv_bytes(C) + FusedTrainLayout<UP, NR>::staged(B) + static_cast<size_t>(C) * kG * sizeof(float2);
+  }
+};
+
+template <int UP, int NR>
+__global__ void __launch_bounds__(512) train_optimal_fused_kernel(const TrainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Lay = OptimalLayout<UP, NR>;
+  using FL = OptimalFusedLayout<UP, NR>;
+  constexpr int W = Lay::kW;
+  const int U = p.U, NS = p.n_sym, C = p.C, B = p.B;
+  const int g = threadIdx.x / UP, i = threadIdx.x % UP;
+  const int k = blockIdx.x;
+  const int gm = g < C ? g : C - 1;
+  const bool valid = g < C;
+  int* fail_any = reinterpret_cast<int*>(smem);
+  float* wv = reinterpret_cast<float*>(smem + 16);                       // [C][UP]: w_{c,u}
+  float* Wf = reinterpret_cast<float*>(smem + 16 + FL::wv_bytes(C));
+  float2* grp = reinterpret_cast<float2*>(smem + 16 + FL::wv_bytes(C) + FusedTrainLayout<UP, NR>::staged(B));
+  float2* rowbuf = grp + gm * FL::kG;
+  float2* Xs = rowbuf + Lay::kRow;            // [NR][UP]
+  float2* Gs = Xs + NR * UP;                  // [NR][UP]
+  float* qv = reinterpret_cast<float*>(Gs + NR * UP);   // [UP]
+  float2* As = rowbuf + Lay::kGroup;          // [UP][UP]: row v of A_c at v UP
+  if (threadIdx.x == 0) *fail_any = 0;
+  stage_rows<UP, NR>(p.H + static_cast<size_t>(k) * U * B, p.y + static_cast<size_t>(k) * NS * B, U, NS, B, Wf);
+  stage_wait();
+
+  int b0, b1;
+  cluster_range(p, gm, b0, b1);
+  const float rho = p.rho;
+  float2 rp[W / 2], ip[W / 2];
+  form_row<UP, NR, true>(rp, ip, Wf, U, NS, b0, b1, i, valid, rho, [](int) { return make_float2(0.f, 0.f); });
+  float rs = 1.f;
+  const int fail = gj_sweep_pairs<UP, W>(rp, ip, reinterpret_cast<float*>(rowbuf), i, valid, rs);
+  if (valid && i == 0 && fail) atomicOr(fail_any, 1);
+  // Row i of X_c and of A_c.
+  float2 xr[NR], ar[UP];
+#pragma unroll
+  for (int n = 0; n < NR; ++n) xr[n] = swept<W>(rp, ip, n, rs);
+#pragma unroll
+  for (int j = 0; j < UP; ++j) ar[j] = swept<W>(rp, ip, NR + j, rs);
+  float a = 1.f;
+#pragma unroll
+  for (int j = 0; j < UP; ++j)
+    if (j == i) a = ar[j].x;
+  const bool real = valid && i < U;
+  const float w = real ? 1.f / a : 0.f;
+  if (valid) {
+    wv[gm * UP + i] = real ? w : rho;         // padding users: w - rho = 0
+#pragma unroll
+    for (int n = 0; n < NR; ++n) Xs[n * UP + i] = (real && n < NS) ? xr[n] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < UP; ++j) As[i * UP + j] = ar[j];
+  }
+  __syncthreads();
+  const bool bad = *fail_any != 0;
+  // D_u and z_u over the clusters in a fixed order (every group for its own users).
+  float Du = 0.f;
+  for (int cc = 0; cc < C; ++cc) Du += wv[cc * UP + i] - rho;
+  const bool seen = Du > 0.f;
+  const float invD = seen ? 1.f / Du : 0.f;
+  const float2* gzk = p.gz + static_cast<size_t>(k) * NS * U;
+  float qn = 0.f;                                 // sum_n Re(conj(g_z) (X - z))
+#pragma unroll
+  for (int n = 0; n < NR; ++n) {
+    if (n < NS) {
+      float2 num = make_float2(0.f, 0.f);
+      for (int cc = 0; cc < C; ++cc) {
+        const float2 xc = (grp + cc * FL::kG + Lay::kRow)[n * UP + i];
+        const float wc = wv[cc * UP + i];
+        num = make_float2(fmaf(wc, xc.x, num.x), fmaf(wc, xc.y, num.y));
+      }
+      const float2 zn = cscale(num, invD);
+      const float2 gzv = real ? gzk[n * U + i] : make_float2(0.f, 0.f);
+      qn = fmaf(gzv.x, xr[n].x - zn.x, fmaf(gzv.y, xr[n].y - zn.y, qn));
+      if (valid) Gs[n * UP + i] = cscale(gzv, w * invD);   // G_x
+    }
+  }
+  if (valid) qv[i] = (real && seen) ? -qn * invD * w * w : 0.f;   // 1 / a^2 = w^2
+  __syncwarp();
+  // G_b row i = sum_j A_ij G_x[j].
+  float2 gb[NR];
+#pragma unroll
+  for (int n = 0; n < NR; ++n) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (n < NS) {
+#pragma unroll
+      for (int j = 0; j < UP; ++j) acc = cfma(ar[j], Gs[n * UP + j], acc);
+    }
+    gb[n] = bad ? make_float2(NAN, NAN) : acc;
+  }
+  __syncwarp();
+  if (valid) {
+#pragma unroll
+    for (int n = 0; n < NR; ++n)
+      if (n < NS) Gs[n * UP + i] = real ? gb[n] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+
+  // Per antenna b of cluster c: (H X)_n, (H G_b)_n = dL/dY[n][b], (H A)_w, then dL/dH[.][b].
+  float2* gHk = p.gH + static_cast<size_t>(k) * U * B;
+  float2* gyk = p.gy + static_cast<size_t>(k) * NS * B;
+  const int S = p.cl_uniform ? B / C : 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int c = 0;
+    if (p.cl_uniform) {
+      c = b / S;
+    } else {
+      while (c + 1 < C && b >= p.cl_off[c + 1]) ++c;
+    }
+    const float2* base = grp + c * FL::kG;
+    const float2* Xc = base + Lay::kRow;
+    const float2* Gc = Xc + NR * UP;
+    const float* qc = reinterpret_cast<const float*>(Gc + NR * UP);
+    const float2* Ac = base + Lay::kGroup;
+    const float* wr = Wf + b * 2 * W;
+    float2 hx[NR], hg[NR], ha[UP];
+#pragma unroll
+    for (int n = 0; n < NR; ++n) hx[n] = hg[n] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < UP; ++j) ha[j] = make_float2(0.f, 0.f);
+    for (int v = 0; v < U; ++v) {
+      const float2 h = make_float2(wr[v], wr[W + v]);
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        if (n < NS) {
+          hx[n] = cfma(h, Xc[n * UP + v], hx[n]);
+          hg[n] = cfma(h, Gc[n * UP + v], hg[n]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < UP; ++j) ha[j] = cfma(h, Ac[v * UP + j], ha[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < UP; ++j) ha[j] = cscale(ha[j], 2.f * qc[j]);   // 2 q_w (H A)_w
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+      if (n < NS) {
+        hx[n] = csub(make_float2(wr[UP + n], wr[W + UP + n]), hx[n]);   // Y[n][b] - (H X)_n[b]
+        gyk[static_cast<size_t>(n) * B + b] = hg[n];
+      }
+    }
+    for (int u = 0; u < U; ++u) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n = 0; n < NR; ++n) {
+        if (n < NS) {
+          acc = cfma_conj(Gc[n * UP + u], hx[n], acc);    // conj(G_b[n][u]) (Y - H X)_n
+          acc = cfms_bconj(hg[n], Xc[n * UP + u], acc);   // - dL/dY[n][b] conj(X[n][u])
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < UP; ++j)
+        if (j < U) acc = cfms(ha[j], Ac[j * UP + u], acc);   // - 2 sum_w (H A)_w q_w A[w][u]
+      gHk[static_cast<size_t>(u) * B + b] = acc;
+    }
+  }
+}
+
 // Backward contraction, per subcarrier (G_b and W of its clusters staged in
 // shared memory):
 //   dL/dH[u][b] = sum_n Y[n][b] conj(G_b[n][u]) - sum_v H[v][b] W[v][u]
@@ -819,6 +992,16 @@ cudaError_t launch_backward_fused_up(const TrainParams& p, cudaStream_t st) {
 }
 
 template <int UP, int NR>
+cudaError_t launch_optimal_fused_up(const TrainParams& p, cudaStream_t st) {
+  const int threads = ((p.C * UP + 31) / 32) * 32;
+  const size_t smem = OptimalFusedLayout<UP, NR>::bytes(p.B, p.C);
+  cudaError_t e = set_smem(train_optimal_fused_kernel<UP, NR>, smem);
+  if (e != cudaSuccess) return e;
+  train_optimal_fused_kernel<UP, NR><<<p.n_sc, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int UP, int NR>
 size_t optimal_smem_up(int C) {
   return 16 + ((static_cast<size_t>(C) * UP * 4 + 15) / 16) * 16 +
          static_cast<size_t>(C) * OptimalLayout<UP, NR>::kGroup * sizeof(float2);
@@ -890,6 +1073,21 @@ size_t train_optimal_smem_bytes(int U, int C) {
 
 cudaError_t launch_train_optimal_backward(const TrainParams& p, cudaStream_t st) {
   FFEQ_TRAIN_DISPATCH(launch_optimal_up)
+}
+
+bool train_optimal_fused_fits(int U, int n_sym, int B, int C) {
+  const bool wide = rhs_columns(n_sym) > 4;
+  size_t bytes;
+  switch (padded_users(U)) {
+    case 8: bytes = wide ? OptimalFusedLayout<8, kNsymMax>::bytes(B, C) : OptimalFusedLayout<8, 4>::bytes(B, C); break;
+    case 16: bytes = wide ? OptimalFusedLayout<16, kNsymMax>::bytes(B, C) : OptimalFusedLayout<16, 4>::bytes(B, C); break;
+    default: bytes = wide ? OptimalFusedLayout<32, kNsymMax>::bytes(B, C) : OptimalFusedLayout<32, 4>::bytes(B, C); break;
+  }
+  return bytes <= 227 * 1024;
+}
+
+cudaError_t launch_train_optimal_backward_fused(const TrainParams& p, cudaStream_t st) {
+  FFEQ_TRAIN_DISPATCH(launch_optimal_fused_up)
 }
 
 #undef FFEQ_TRAIN_DISPATCH
