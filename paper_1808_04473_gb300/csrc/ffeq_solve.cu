@@ -557,9 +557,13 @@ cudaError_t launch_up(const SolveParams& p, cudaStream_t stream) {
 // offsets from one column pointer (no padding rows, no clamped or selected
 // addresses), the right-hand sides reach shared memory by asynchronous copies
 // that overlap the sweep, and the epilogue walks (symbol, user) outputs with
-// shifts and masks instead of runtime divisions.
+// shifts and masks instead of runtime divisions.  Registers are not capped for
+// occupancy: 96 per thread without spills, five 128-thread CTAs per SM (the FD
+// throughput workload's 1200 CTAs in 1.6 waves) ran faster than a cap of 64
+// with spills and one wave (FD 24.7 -> 23.1 us alone, and the concurrent
+// PD + FD step 75.2 -> 70.7 us).
 template <int UP>
-__global__ void __launch_bounds__(512, (UP <= 16 ? 2 : 1)) solve_full_kernel(const SolveParams p) {
+__global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   using Lay = SolveLayout<UP>;
   constexpr int U = UP;
