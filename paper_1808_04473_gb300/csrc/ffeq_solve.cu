@@ -616,18 +616,24 @@ __global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p)
   const size_t sys = static_cast<size_t>(sc) * Ceff + c;
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncwarp();
-  // z_n = sum_j A[i][j] y^MRC_j(n) in j order; after every lane of the warp has
-  // read row n, the fusion term z_n / A_ii replaces it ([n][u]).
+  // z_n = sum_j A[i][j] y^MRC_j(n) in j order, two right-hand sides per round
+  // (two independent FMA chains per lane); after every lane of the warp has read
+  // rows n and n + 1, the fusion terms z_n / A_ii replace them ([n][u]).
 #pragma unroll
-  for (int n = 0; n < kNsymMax; ++n) {
+  for (int n = 0; n < kNsymMax; n += 2) {
     if (n < NS) {
-      const float2 zn = gj_row_dot<UP>(arow, Fz + n * UP);
+      const float2 z0 = gj_row_dot<UP>(arow, Fz + n * UP);
+      const float2 z1 = n + 1 < NS ? gj_row_dot<UP>(arow, Fz + (n + 1) * UP) : make_float2(0.f, 0.f);
       __syncwarp();
       if (g < nmat) {
         if (store) {
-          if (live) p.Xs[(sys * NS + n) * U + i] = zn;
+          if (live) {
+            p.Xs[(sys * NS + n) * U + i] = z0;
+            if (n + 1 < NS) p.Xs[(sys * NS + n + 1) * U + i] = z1;
+          }
         } else {
-          Fz[n * UP + i] = cscale(zn, invA);
+          Fz[n * UP + i] = cscale(z0, invA);
+          if (n + 1 < NS) Fz[(n + 1) * UP + i] = cscale(z1, invA);
         }
       }
     }
