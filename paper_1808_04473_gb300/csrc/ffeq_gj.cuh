@@ -400,18 +400,58 @@ __device__ __forceinline__ int gj_solve_row(float2 (&mrow)[UP], float rho, float
   return fail;
 }
 
-// z = sum_j arow[j] rhs[j] over j = 0 .. UP-1 in j order (rhs 16-byte aligned):
-// one right-hand side of the solved system.
+// z = sum_j arow[j] rhs[j] over j = 0 .. UP-1 (rhs 16-byte aligned): one
+// right-hand side of the solved system, as four real FMA chains in j order,
+//   P = (sum a_re y_re, sum a_re y_im),  Q = (sum a_im y_re, sum a_im y_im),
+//   z = (P.re - Q.im, P.im + Q.re).
+// gj_row_dot_pairs computes the same chains two at a time with paired FMAs and
+// gives the same bits.
 template <int UP>
 __device__ __forceinline__ float2 gj_row_dot(const float2 (&arow)[UP], const float2* rhs) {
-  float2 zn = make_float2(0.f, 0.f);
+  float2 P = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < UP; j += 2) {
     const float4 y2 = *reinterpret_cast<const float4*>(rhs + j);
-    zn = cfma(arow[j], make_float2(y2.x, y2.y), zn);
-    zn = cfma(arow[j + 1], make_float2(y2.z, y2.w), zn);
+    P.x = fmaf(arow[j].x, y2.x, P.x);
+    P.y = fmaf(arow[j].x, y2.y, P.y);
+    Q.x = fmaf(arow[j].y, y2.x, Q.x);
+    Q.y = fmaf(arow[j].y, y2.y, Q.y);
+    P.x = fmaf(arow[j + 1].x, y2.z, P.x);
+    P.y = fmaf(arow[j + 1].x, y2.w, P.y);
+    Q.x = fmaf(arow[j + 1].y, y2.z, Q.x);
+    Q.y = fmaf(arow[j + 1].y, y2.w, Q.y);
   }
-  return zn;
+  return make_float2(__fsub_rn(P.x, Q.y), __fadd_rn(P.y, Q.x));
+}
+
+// The row of A held as duplicated pairs for gj_row_dot_pairs: are[j] =
+// (Re a_j, Re a_j), aim[j] = (Im a_j, Im a_j).
+template <int UP>
+__device__ __forceinline__ void gj_row_split(const float2 (&arow)[UP], float2 (&are)[UP], float2 (&aim)[UP]) {
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    are[j] = make_float2(arow[j].x, arow[j].x);
+    aim[j] = make_float2(arow[j].y, arow[j].y);
+  }
+}
+
+// gj_row_dot on the duplicated pairs: P += (a_re, a_re) * (y_re, y_im) and
+// Q += (a_im, a_im) * (y_re, y_im) are one paired FMA each (__ffma2_rn rounds
+// each half as fmaf would), half the FMA instructions of the scalar form.
+template <int UP>
+__device__ __forceinline__ float2 gj_row_dot_pairs(const float2 (&are)[UP], const float2 (&aim)[UP],
+                                                   const float2* rhs) {
+  float2 P = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < UP; j += 2) {
+    const float4 y2 = *reinterpret_cast<const float4*>(rhs + j);
+    const float2 y0 = make_float2(y2.x, y2.y), y1 = make_float2(y2.z, y2.w);
+    P = __ffma2_rn(are[j], y0, P);
+    Q = __ffma2_rn(aim[j], y0, Q);
+    P = __ffma2_rn(are[j + 1], y1, P);
+    Q = __ffma2_rn(aim[j + 1], y1, Q);
+  }
+  return make_float2(__fsub_rn(P.x, Q.y), __fadd_rn(P.y, Q.x));
 }
 
 }  // namespace ffeq

@@ -614,16 +614,18 @@ __global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p)
   const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
   const bool store = p.Xs != nullptr;   // refinement follows: keep estimates and inverses
   const size_t sys = static_cast<size_t>(sc) * Ceff + c;
+  float2 are[UP], aim[UP];
+  gj_row_split<UP>(arow, are, aim);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncwarp();
   // z_n = sum_j A[i][j] y^MRC_j(n) in j order, two right-hand sides per round
-  // (two independent FMA chains per lane); after every lane of the warp has read
-  // rows n and n + 1, the fusion terms z_n / A_ii replace them ([n][u]).
+  // (four independent paired-FMA chains per lane); after every lane of the warp
+  // has read rows n and n + 1, the fusion terms z_n / A_ii replace them ([n][u]).
 #pragma unroll
   for (int n = 0; n < kNsymMax; n += 2) {
     if (n < NS) {
-      const float2 z0 = gj_row_dot<UP>(arow, Fz + n * UP);
-      const float2 z1 = n + 1 < NS ? gj_row_dot<UP>(arow, Fz + (n + 1) * UP) : make_float2(0.f, 0.f);
+      const float2 z0 = gj_row_dot_pairs<UP>(are, aim, Fz + n * UP);
+      const float2 z1 = n + 1 < NS ? gj_row_dot_pairs<UP>(are, aim, Fz + (n + 1) * UP) : make_float2(0.f, 0.f);
       __syncwarp();
       if (g < nmat) {
         if (store) {
@@ -642,7 +644,7 @@ __global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p)
     // Inverse stored transposed (row j = column j of A, coalesced over the lanes i).
     if (live) {
 #pragma unroll
-      for (int j = 0; j < UP; ++j) p.As[(sys * U + j) * U + i] = arow[j];
+      for (int j = 0; j < UP; ++j) p.As[(sys * U + j) * U + i] = make_float2(are[j].x, aim[j].x);
       if (i == 0) {
         p.fails[sys] = fail;
         if (p.info) p.info[sys] = fail;
