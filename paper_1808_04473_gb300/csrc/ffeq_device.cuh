@@ -22,6 +22,21 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// The hardware's approximate base-2 exponential and reciprocal (PTX
+// ex2.approx.ftz.f32, rcp.approx.ftz.f32: one special-function instruction each;
+// subnormal inputs and results flush to zero).  For iterations whose result is
+// held to a tolerance rather than to the correctly rounded value.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------- complex (float2)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

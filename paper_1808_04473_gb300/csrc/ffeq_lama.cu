@@ -63,13 +63,13 @@ __device__ __forceinline__ void pam_posterior2(float2 x, float l2t, float d, flo
     const float a = (2.f * static_cast<float>(m) - static_cast<float>(L - 1)) * d;
     const float2 e = __fadd2_rn(x, make_float2(-a, -a));                  // x - a
     const float2 u = __fmul2_rn(__ffma2_rn(e, e, ne0), nl2t);             // ((x-a0)^2 - e^2) l2t <= 0
-    const float2 w = make_float2(exp2f(u.x), exp2f(u.y));                 // exactly 1 at a0
+    const float2 w = make_float2(ex2_approx(u.x), ex2_approx(u.y));       // 1 at a0
     const float2 da = __fadd2_rn(make_float2(a, a), na0);
     sw = __fadd2_rn(sw, w);
     s1 = __ffma2_rn(w, da, s1);
     s2 = __ffma2_rn(__fmul2_rn(w, da), da, s2);
   }
-  const float2 r = make_float2(__frcp_rn(sw.x), __frcp_rn(sw.y));
+  const float2 r = make_float2(rcp_approx(sw.x), rcp_approx(sw.y));   // sw >= 1
   const float2 m1 = __fmul2_rn(s1, r);
   mean = __fadd2_rn(a0, m1);
   const float2 v2 = __ffma2_rn(make_float2(-m1.x, -m1.y), m1, __fmul2_rn(s2, r));
@@ -159,7 +159,7 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p
     z = __fadd2_rn(__fadd2_rn(__fadd2_rn(yv, s), make_float2(-gs.x, -gs.y)), v);
     tau = fmaf(beta, phi, n0n);
     if (t >= p.lama_iters) break;
-    const float inv_tau = __frcp_rn(tau);
+    const float inv_tau = rcp_approx(tau);
     const float l2t = kLog2e * inv_tau;
     float2 mean, var;
     pam_posterior2<HB>(z, l2t, d, inv_d, mean, var);
