@@ -77,7 +77,7 @@ __device__ __forceinline__ void pam_posterior2(float2 x, float l2t, float d, flo
 }
 
 template <int UP, int HB>
-__global__ void __maxnreg__(UP == 32 ? 128 : 72) lama_kernel(const SolveParams p) {
+__global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, NB = p.spc;   // spc: received vectors per CTA
   const int nblk = (NS + NB - 1) / NB;
