@@ -37,7 +37,7 @@ __device__ __forceinline__ void axis_llr(float x, float inv_s2, float scale, flo
 }
 
 __device__ __forceinline__ void symbol_llr(float2 z, float s2, float scale, int h, float* out) {
-  const float inv = isinf(s2) ? 0.f : 1.f / s2;   // s2 = 0: +inf; NaN stays NaN
+  const float inv = isinf(s2) ? 0.f : rcp_approx(s2);   // s2 = 0: +inf; NaN stays NaN
   switch (h) {
     case 1: axis_llr<1>(z.x, inv, scale, out); axis_llr<1>(z.y, inv, scale, out + 1); break;
     case 2: axis_llr<2>(z.x, inv, scale, out); axis_llr<2>(z.y, inv, scale, out + 2); break;

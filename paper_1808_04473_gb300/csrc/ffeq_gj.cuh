@@ -122,7 +122,7 @@ __device__ __forceinline__ int gj_sweep_pairs(float2 (&rp)[W / 2], float2 (&ip)[
       const float piv = buf[2 * W];
       const bool ok = piv > 0.f;
       if (!ok && fail == 0) fail = kk + 1;
-      const float r = __frcp_rn(ok ? piv : 1.f);
+      const float r = rcp_approx(ok ? piv : 1.f);
       if (me) my_r = r;
       const float gr = me ? 0.f : fr * r;
       const float gi = me ? 0.f : fi * r;
@@ -227,11 +227,11 @@ __device__ __forceinline__ int gj_sweep_block2(float2 (&rp)[W / 2], float2 (&ip)
     const float2 P01 = make_float2(b0.z, b0.w), P10 = make_float2(b1.x, b1.y), P11 = make_float2(b1.z, b1.w);
     const float pa = b0.x;
     const bool oka = pa > 0.f;
-    const float ra = __frcp_rn(oka ? pa : 1.f);
+    const float ra = rcp_approx(oka ? pa : 1.f);
     const float2 h = make_float2(P10.x * ra, P10.y * ra);
     const float pb = P11.x - (h.x * P01.x - h.y * P01.y);
     const bool okb = pb > 0.f;
-    const float rb = __frcp_rn(okb ? pb : 1.f);
+    const float rb = rcp_approx(okb ? pb : 1.f);
     if (fail == 0) {
       if (!oka) fail = k + 1;
       else if (!okb) fail = k + 2;
@@ -335,7 +335,7 @@ __device__ __forceinline__ int gj_sweep_deferred(float2 (&aug)[W], float* rowbuf
       const float piv = buf[2 * W];
       const bool ok = piv > 0.f;
       if (!ok && fail == 0) fail = kk + 1;
-      const float r = __frcp_rn(ok ? piv : 1.f);
+      const float r = rcp_approx(ok ? piv : 1.f);
       if (me) my_r = r;
       const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(aug[s].x * r, aug[s].y * r);
       const float dlt = me ? 1.f : 0.f;

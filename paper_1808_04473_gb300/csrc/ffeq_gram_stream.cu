@@ -375,7 +375,7 @@ __device__ __forceinline__ void fused_solve(const StreamParams& p, unsigned char
       float2 arow[UP];
       float Ai, gii;
       const int fail = gj_solve_row<UP>(mrow, rho, rowbuf, i, true, arow, Ai, gii);
-      const float invA = 1.f / Ai;
+      const float invA = rcp_approx(Ai);
       const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
 #pragma unroll
       for (int n = 0; n < kNsymMax; ++n) {
@@ -399,7 +399,7 @@ __device__ __forceinline__ void fused_solve(const StreamParams& p, unsigned char
       failed = failed || fail != 0;
     }
     if (!live) continue;
-    const float rr = 1.f / dn;
+    const float rr = rcp_approx(dn);
     for (int n = 0; n < NS; ++n) {
       float2 zz;
       float s2;

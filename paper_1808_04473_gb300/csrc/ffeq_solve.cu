@@ -133,7 +133,7 @@ __device__ void batch_epilogue(const SolveParams& p, const float2* base, const i
       zz = make_float2(NAN, NAN);
       s2 = NAN;
     } else if (dn > 0.f) {
-      const float rr = 1.f / dn;
+      const float rr = rcp_approx(dn);
       zz = cscale(nm, rr);
       s2 = (zflag && zflag[j * UP + u]) ? 0.f : d.s2s * rr;
     } else {
@@ -178,7 +178,7 @@ __device__ __forceinline__ void uniform_epilogue(const SolveParams& p, const flo
       zz = make_float2(NAN, NAN);
       s2 = NAN;
     } else if (dn > 0.f) {
-      const float rr = 1.f / dn;
+      const float rr = rcp_approx(dn);
       zz = cscale(nm, rr);
       s2 = (zflag && zflag[s * UP + u]) ? 0.f : s2_scale * rr;
     } else {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(512, (solve_min_blocks<UP, LPR, BATCH>())) sol
       arow[j] = cscale(make_float2(j % 2 ? rp[j / 2].y : rp[j / 2].x, j % 2 ? ip[j / 2].y : ip[j / 2].x), rs);
       if (j == i) Ai = arow[j].x;
     }
-    const float invA = 1.f / Ai;
+    const float invA = rcp_approx(Ai);
     // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
     // mu = 0 exactly, which the subtraction would only reach up to rounding.
     const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(512, (solve_min_blocks<UP, LPR, BATCH>())) sol
         const float2 f = make_float2(__shfl_sync(kFullMask, aug[k].x, i, GS), __shfl_sync(kFullMask, aug[k].y, i, GS));
         const bool ok = piv > 0.f;
         if (!ok && fail == 0) fail = k + 1;
-        const float r = __frcp_rn(ok ? piv : 1.f);
+        const float r = rcp_approx(ok ? piv : 1.f);
         const bool me = i == k;
         if (me) my_r = r;
         const float2 gg = me ? make_float2(0.f, 0.f) : make_float2(f.x * r, f.y * r);
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(512, (solve_min_blocks<UP, LPR, BATCH>())) sol
     for (int j = 0; j < UP; ++j)
       if (j == i) Ai = aug[kA + j].x;
     Ai = __shfl_sync(kFullMask, Ai, i, GS);
-    const float invA = 1.f / Ai;
+    const float invA = rcp_approx(Ai);
     // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
     // mu = 0 exactly, which the subtraction would only reach up to rounding.
     const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p)
   float2 arow[UP];
   float Ai, gii;
   const int fail = gj_solve_row<UP>(mrow, rho, reinterpret_cast<float*>(rowbuf), i, g < nmat, arow, Ai, gii);
-  const float invA = 1.f / Ai;
+  const float invA = rcp_approx(Ai);
   // mu = [A G]_ii = 1 - rho A_ii; a user the cluster cannot see (G_ii = 0) has
   // mu = 0 exactly, which the subtraction would only reach up to rounding.
   const float mu = gii == 0.f ? 0.f : fmaxf(1.f - rho * Ai, 0.f);
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(512, 1) solve_full_kernel(const SolveParams p)
         zz = make_float2(NAN, NAN);
         s2 = NAN;
       } else if (dn > 0.f) {
-        const float rr = 1.f / dn;
+        const float rr = rcp_approx(dn);
         zz = cscale(nm, rr);
         s2 = p.N0 * rr;
       } else {
