@@ -810,6 +810,56 @@ def run_correlated(R, K, warmup):
             "arms": arms}
 
 
+def lama_flops(U, bits, T):
+    """Algorithmic FP32 flops of LAMA per received vector and cluster: T products
+    G s of 8 U^2 flops and T - 1 denoiser steps of U (2 * 2^(b/2) * 6 + 10) flops
+    (per PAM level and axis: distance, exponent scaling, weight sums, first and
+    second moments; then the moments and the update)."""
+    levels = 2 ** (bits // 2)
+    return T * 8 * U * U + (T - 1) * U * (2 * levels * 6 + 10)
+
+
+def lama_roofline(kern, U, C, n_sc, n_sym, bits):
+    """FP32 ALU roofline of the PD and FD LAMA kernels from their breakdown times."""
+    roof = {}
+    for tag, Ceff in (("pd", 1), ("fd", C)):
+        flops = lama_flops(U, bits, LAMA_ITERS) * n_sc * Ceff * n_sym
+        ach = flops / (kern[f"{tag}_fuse"] * 1e-3) / 1e12
+        roof[tag] = {"kernel": f"lama_kernel ({tag.upper()}, T = {LAMA_ITERS})", "bound": "alu", "achieved": ach,
+                     "peak": FP32_ALU_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "unit": "TFLOP/s", "frac": ach / FP32_ALU_TFLOPS, "algorithmic_flops_per_launch": flops,
+                     "kernel_ms": kern[f"{tag}_fuse"]}
+    return roof
+
+
+def run_lama(R, K, warmup, pinned):
+    """The headline shape with LAMA (Sec. III-B, LAMA_ITERS iterations) in place
+    of L-MMSE: the step the default line's `equalizers.lama` key times, as a line
+    of its own with the LAMA kernels' FP32 ALU roofline (a profiling target)."""
+    import numpy as np
+    from paper_1808_04473_gb300 import synth
+    ffeq = R.ffeq
+    w = WORKLOAD
+    B, U, C, n_sc, n_sym, bits = w["B"], w["U"], w["C"], w["n_sc"], w["n_sym"], w["bits"]
+    shape = (B, U, C, n_sc, n_sym)
+    p = synth.make_problem(B, U, C, n_sc, n_sym, snr_db=w["snr_db"], bits=bits, seed=12345 + R.rank)
+    (Hs, ys), n_sets, in_bytes = R.rotating_sets(p.H, p.y)
+    r = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision="bf16x3", bits=bits, K=K, warmup=warmup,
+                       equalizer=ffeq.LAMA, pinned=pinned, breakdown=True, concurrent=True,
+                       tune_step=pinned is None)
+    kern = r["kern"]
+    roof = lama_roofline(kern, U, C, n_sc, n_sym, bits)
+    symbols = 2 * U * n_sc * n_sym
+    return {"workload": f"B={B} U={U} C={C} {n_sc}sc x {n_sym}sym 16-QAM Rayleigh 10dB, PD+FD LAMA "
+                        f"(T = {LAMA_ITERS}), LLRs",
+            "value": job_rate(symbols, R.world, K, r["ms"]), "unit": UNIT, "ms_per_step": r["ms"] / K,
+            "steps": K, "l2": f"rotating {n_sets} input sets ({n_sets * in_bytes / 2**20:.0f} MiB > L2)",
+            "kernels_ms": kern, "schedule": r["schedule"],
+            "tuning": {("pd" if a == ffeq.PD else "fd"): list(ffeq.ffeq_plan_get_tuning(pl))
+                       for a, pl in r["plans"].items()},
+            "roofline": roof}
+
+
 def run_training(R, K, warmup):
     """One training step of the differentiable FD form: ffeq_fd_train_forward and
     ffeq_fd_train_backward on B=128, U=16, C=8, 8 draws x 1024 subcarriers, QPSK,
@@ -966,9 +1016,9 @@ def main():
     ap.add_argument("--tuning", default=None,
                     help="pin the contraction shapes instead of autotuning: PD_SHAPE,PD_STAGES,FD_SHAPE,FD_STAGES "
                          "(values of ffeq_plan_set_tuning; for reproducible profiles)")
-    ap.add_argument("--workload", default="ofdm", choices=["ofdm", "uneven", "correlated", "training"],
+    ap.add_argument("--workload", default="ofdm", choices=["ofdm", "uneven", "correlated", "training", "lama"],
                     help="ofdm: the headline B=256 U=16 C=8 1200x14 step (other workloads as extra keys); "
-                         "uneven / correlated / training: that workload's line alone")
+                         "uneven / correlated / training / lama: that workload's line alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -986,6 +1036,9 @@ def main():
             line = uneven_line(R, args.steps, args.warmup, args.precision, ClockSampler(local_rank))
         elif args.workload == "correlated":
             line = run_correlated(R, args.steps, args.warmup)
+        elif args.workload == "lama":
+            line = run_lama(R, args.steps, args.warmup,
+                            [int(v) for v in args.tuning.split(",")] if args.tuning else None)
         else:
             line = run_training(R, args.steps, args.warmup)
         if rank == 0:
@@ -1046,6 +1099,8 @@ def main():
                                 warmup=args.warmup, equalizer=eq, breakdown=True, tune_step=True)
             variants[name] = {"value": job_rate(symbols_per_step, world, Kv, rv["ms"]), "ms_per_step": rv["ms"] / Kv,
                               "steps": Kv, "kernels_ms": rv["kern"], "schedule": rv["schedule"]}
+            if eq == ffeq.LAMA:
+                variants[name]["roofline"] = lama_roofline(rv["kern"], U, C, n_sc, n_sym, bits)
             del rv
 
     # ---- end to end from pinned host memory (the headline e2e number), and through

@@ -25,3 +25,13 @@ def test_error_measures():
     g[1, 2] += 1e-3
     nrm, ent = bench._errors(g, o)
     assert abs(ent - 1e-3) < 1e-12 and abs(nrm - 1e-3 / 2) < 1e-12
+
+
+def test_lama_flop_count():
+    # Per received vector and cluster, U = 16, 16-QAM (two bits per PAM axis),
+    # T = 8: eight products of 8 U^2 = 2048 flops and seven denoiser steps of
+    # U (2 * 4 * 6 + 10) = 928 flops: 16 384 + 6 496.
+    import bench
+    assert bench.lama_flops(16, 4, 8) == 16384 + 6496 == 22880
+    # T = 1: one product, no denoiser step.
+    assert bench.lama_flops(8, 2, 1) == 8 * 64
