@@ -38,12 +38,15 @@ def _blocks(H, y, k, bounds):
     return [(Hm[b0:b1], Ym[b0:b1]) for (b0, b1) in bounds]
 
 
-def fd_train_forward(H, y, rho, nu):
-    """Return ``z`` ``[n_sc][n_sym][U]`` and the local estimates ``x`` ``[n_sc][C][n_sym][U]``."""
+def fd_train_forward(H, y, rho, nu, cluster_sizes=None):
+    """Return ``z`` ``[n_sc][n_sym][U]`` and the local estimates ``x`` ``[n_sc][C][n_sym][U]``.
+
+    ``cluster_sizes``: the antennas of each cluster (Sec. II-B, contiguous, summing
+    to B); ``None`` for C clusters of B / C."""
     n_sc, U, B = H.shape
     n_sym = y.shape[1]
     C = len(rho)
-    bounds = partition(B, C)
+    bounds = partition(B, C, cluster_sizes)
     z = np.zeros((n_sc, n_sym, U), np.complex128)
     xs = np.zeros((n_sc, C, n_sym, U), np.complex128)
     for k in range(n_sc):
@@ -55,15 +58,16 @@ def fd_train_forward(H, y, rho, nu):
     return z, xs
 
 
-def fd_train_backward(H, y, rho, nu, gz):
+def fd_train_backward(H, y, rho, nu, gz, cluster_sizes=None):
     """Gradients of a real loss with ``dL/dz = gz`` (``[n_sc][n_sym][U]``, dL/dRe + i dL/dIm).
 
-    Returns ``(gH [n_sc][U][B], gy [n_sc][n_sym][B], grho [C], gnu [C][U])``.
+    Returns ``(gH [n_sc][U][B], gy [n_sc][n_sym][B], grho [C], gnu [C][U])``;
+    ``cluster_sizes`` as for ``fd_train_forward``.
     """
     n_sc, U, B = H.shape
     n_sym = y.shape[1]
     C = len(rho)
-    bounds = partition(B, C)
+    bounds = partition(B, C, cluster_sizes)
     gH = np.zeros((n_sc, U, B), np.complex128)
     gy = np.zeros((n_sc, n_sym, B), np.complex128)
     grho = np.zeros(C)

@@ -50,6 +50,40 @@ def test_gradients_match_finite_differences(seed):
         assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("sizes", [[2, 9, 5], [0, 7, 9]])
+def test_unequal_clusters_match_finite_differences(sizes):
+    """Clusters of given sizes (Sec. II-B; an empty one included): every gradient
+    equals central differences of the forward on the same partition, and the
+    forward's local estimates are each cluster's own L-MMSE solve."""
+    p, H, y, rho, nu = _problem(7, B=16, U=3, C=3)
+    s = p.s
+    z, xs = adjoint.fd_train_forward(H, y, rho, nu, cluster_sizes=sizes)
+    gz = 2.0 * (z - s)
+    gH, gy, grho, gnu = adjoint.fd_train_backward(H, y, rho, nu, gz, cluster_sizes=sizes)
+
+    def f(h, t, r, w):
+        return _loss(adjoint.fd_train_forward(h, t, r, w, cluster_sizes=sizes)[0], s)
+
+    fH = adjoint.finite_difference(lambda h: f(h, y, rho, nu), H)
+    fy = adjoint.finite_difference(lambda t: f(H, t, rho, nu), y)
+    fr = adjoint.finite_difference(lambda r: f(H, y, r, nu), rho)
+    fn = adjoint.finite_difference(lambda w: f(H, y, rho, w), nu)
+    for got, ref in ((gH, fH), (gy, fy), (grho, fr), (gnu, fn)):
+        assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+    # Local estimates: the regularized least-squares solution of each cluster alone,
+    # through an SVD (no normal equations), and zero for an empty cluster.
+    b0 = 0
+    for c, bc in enumerate(sizes):
+        for k in range(H.shape[0]):
+            Hc = H[k].T[b0:b0 + bc]
+            Yc = y[k].T[b0:b0 + bc]
+            A = np.vstack([Hc, np.sqrt(rho[c]) * np.eye(H.shape[1])])
+            R = np.vstack([Yc, np.zeros((H.shape[1], Yc.shape[1]))])
+            X = np.linalg.lstsq(A, R, rcond=None)[0]
+            np.testing.assert_allclose(xs[k, c], X.T, rtol=1e-10, atol=1e-12)
+        b0 += bc
+
+
 def test_gradient_of_a_wrong_formula_is_caught():
     """Sanity of the pin itself: dropping the H G_b X^H term breaks the H gradient."""
     p, H, y, rho, nu = _problem(5)
