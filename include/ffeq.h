@@ -182,9 +182,8 @@ ffeq_status ffeq_plan_create(ffeq_plan** out, const ffeq_problem* p);
  * enter the result (the local results are summed, Eq. fullMRC).  FD with
  * unequal sizes runs the contraction on shapes 1-4 (the streamed and pre-split
  * shapes need equal clusters) and at most 64 clusters; the training entry
- * points (ffeq_fd_train_*) need equal clusters and return
- * FFEQ_ERR_UNSUPPORTED otherwise.  FFEQ_ERR_INVALID_ARG for a negative size or
- * sizes that do not sum to B. */
+ * points (ffeq_fd_train_*, ffeq_fd_optimal_backward) follow the plan's clusters.
+ * FFEQ_ERR_INVALID_ARG for a negative size or sizes that do not sum to B. */
 ffeq_status ffeq_plan_create_clusters(ffeq_plan** out, const ffeq_problem* p, const int* cluster_sizes);
 
 /* Destroy a plan (NULL is ignored). */

@@ -21,12 +21,13 @@ from . import ffeq
 
 class FDEqualize(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, H, y, rho_c, nu, C: int, precision: int = ffeq.FP32):
+    def forward(ctx, H, y, rho_c, nu, C: int, precision: int = ffeq.FP32, cluster_sizes=None):
         H, y = H.contiguous(), y.contiguous()
         rho_c, nu = rho_c.contiguous().float(), nu.contiguous().float()
         n_sc, U, B = H.shape
         n_sym = y.shape[1]
-        plan = ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=ffeq.FD, precision=precision)
+        plan = ffeq.ffeq_plan_create(B, U, C, n_sc, n_sym, arch=ffeq.FD, precision=precision,
+                                     cluster_sizes=cluster_sizes)
         nb = ffeq.ffeq_fd_train_workspace_size(plan)
         ws = torch.empty(nb, dtype=torch.uint8, device=H.device)
         z = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=H.device)
@@ -44,12 +45,13 @@ class FDEqualize(torch.autograd.Function):
         grho = torch.empty_like(rho_c)
         gnu = torch.empty_like(nu)
         ffeq.ffeq_fd_train_backward(ctx.plan, H, y, rho_c, nu, gz, gH, gy, grho, gnu, ctx.ws, ctx.nb)
-        return gH, gy, grho, gnu, None, None
+        return gH, gy, grho, gnu, None, None, None
 
 
-def fd_equalize(H, y, rho_c, nu, C: int, precision: int = ffeq.FP32):
-    """Differentiable FD equalization (see ``FDEqualize``)."""
-    return FDEqualize.apply(H, y, rho_c, nu, C, precision)
+def fd_equalize(H, y, rho_c, nu, C: int, precision: int = ffeq.FP32, cluster_sizes=None):
+    """Differentiable FD equalization (see ``FDEqualize``); ``cluster_sizes``: antennas
+    per cluster (Sec. II-B), ``None`` for B / C each."""
+    return FDEqualize.apply(H, y, rho_c, nu, C, precision, cluster_sizes)
 
 
 class FDEqualizeOptimal(torch.autograd.Function):

@@ -464,7 +464,6 @@ ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, co
   if (!plan) return FFEQ_ERR_INVALID_ARG;
   const ffeq_problem& p = plan->p;
   if (p.arch != FFEQ_FD) return FFEQ_ERR_INVALID_ARG;
-  if (!plan->cl_uniform) return FFEQ_ERR_UNSUPPORTED;   // the training kernels take clusters of B / C antennas
   if (p.equalizer != FFEQ_LMMSE) return FFEQ_ERR_UNSUPPORTED;   // the differentiable form is L-MMSE
   if (ffeq::padded_users(p.U) * p.C > 512 || ffeq::train_smem_bytes(p.U, p.C) > kSolveSmemLimit)
     return FFEQ_ERR_UNSUPPORTED;
@@ -489,7 +488,8 @@ ffeq_status train_params(const ffeq_plan* plan, const void* H, const void* y, co
   tp.C = p.C;
   tp.n_sc = p.n_sc;
   tp.n_sym = p.n_sym;
-  tp.cl_uniform = 1;
+  tp.cl_uniform = plan->cl_uniform ? 1 : 0;   // else cluster c holds antennas [cl_off[c], cl_off[c + 1])
+  for (int c = 0; c <= p.C && !plan->cl_uniform; ++c) tp.cl_off[c] = plan->cl_off[c];
   return FFEQ_OK;
 }
 

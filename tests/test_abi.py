@@ -234,10 +234,11 @@ def test_cluster_sizes_validation(built):
     # Equal sizes given explicitly are the uniform plan (the streamed shape applies).
     eq = ff.ffeq_plan_create(256, 16, 8, 10, 14, arch=ff.FD, precision=ff.BF16X3, cluster_sizes=[32] * 8)
     ff.ffeq_plan_set_tuning(eq, (5, 0))
-    # The training kernels need equal clusters (checked before any device call).
+    # The training entry points take the plan's clusters; their argument checks
+    # come before any device call (a workspace below ffeq_fd_train_workspace_size).
     L = ff.lib()
-    st = L.ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 1 << 30, None)
-    assert st == 2
+    st = L.ffeq_fd_train_forward(fd.handle, 256, 256, 256, 256, 256, 256, 16, None)
+    assert st == 1
 
 
 def test_equalizer_validation(built):

@@ -38,13 +38,13 @@ def _setup(B, U, C, n_sc, n_sym, seed, snr=10.0):
     return p, rho.astype(np.float32), nu.astype(np.float32)
 
 
-def _run(ff, p, rho, nu, C, gz=None):
+def _run(ff, p, rho, nu, C, gz=None, sizes=None):
     dev = torch.device("cuda:0")
     H = torch.from_numpy(p.H).to(dev)
     y = torch.from_numpy(p.y).to(dev)
     r = torch.from_numpy(rho).to(dev)
     w = torch.from_numpy(nu).to(dev)
-    plan = ff.ffeq_plan_create(p.B, p.U, C, p.n_sc, p.n_sym, arch=ff.FD)
+    plan = ff.ffeq_plan_create(p.B, p.U, C, p.n_sc, p.n_sym, arch=ff.FD, cluster_sizes=sizes)
     nb = ff.ffeq_fd_train_workspace_size(plan)
     ws = torch.empty(nb, dtype=torch.uint8, device=dev)
     z = torch.empty((p.n_sc, p.n_sym, p.U), dtype=torch.complex64, device=dev)
@@ -72,6 +72,33 @@ def test_forward_and_backward_match_the_oracle(ff, B, U, C, n_sc, n_sym):
     parity.check("z", g["z"], z0, 1e-5)
     gH, gy, grho, gnu = adjoint.fd_train_backward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64),
                                                   gz.astype(np.complex64).astype(np.complex128))
+    parity.check("gH", g["gH"], gH, 1e-3)
+    parity.check("gy", g["gy"], gy, 1e-3)
+    for name, ref in (("grho", grho), ("gnu", gnu)):
+        assert _relmax(g[name], ref) <= 1e-3, (name, _relmax(g[name], ref))
+
+
+TRAIN_UNEQUAL = [  # B, U, C, n_sc, n_sym, sizes (Sec. II-B: clusters of given sizes)
+    (20, 4, 3, 9, 2, [0, 13, 7]),            # an empty cluster; B % C != 0
+    (96, 12, 3, 10, 5, [40, 24, 32]),
+    (256, 32, 16, 5, 14, [8, 24, 16, 16, 12, 20, 16, 16, 16, 16, 10, 22, 16, 16, 16, 16]),
+]
+
+
+@pytest.mark.parametrize("B,U,C,n_sc,n_sym,sizes", TRAIN_UNEQUAL)
+def test_unequal_clusters_match_the_oracle(ff, B, U, C, n_sc, n_sym, sizes):
+    """The free-weight form on clusters of given sizes: forward and every gradient
+    against the oracle on the same partition (bounds as for equal clusters)."""
+    p = synth.make_problem(B, U, 1, n_sc, n_sym, snr_db=10.0, bits=2, seed=B + C)
+    rng = np.random.default_rng(B + C + 7)
+    rho = ((p.N0 / p.Es) * rng.uniform(0.5, 2.0, C)).astype(np.float32)
+    nu = (rng.uniform(0.5, 1.5, (C, U)) / C).astype(np.float32)
+    z0, _ = adjoint.fd_train_forward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64), cluster_sizes=sizes)
+    gz = 2.0 * (z0 - p.s) / z0.size
+    g = _run(ff, p, rho, nu, C, gz, sizes)
+    parity.check("z", g["z"], z0, 1e-5)
+    gH, gy, grho, gnu = adjoint.fd_train_backward(p.H, p.y, rho.astype(np.float64), nu.astype(np.float64),
+                                                  gz.astype(np.complex64).astype(np.complex128), cluster_sizes=sizes)
     parity.check("gH", g["gH"], gH, 1e-3)
     parity.check("gy", g["gy"], gy, 1e-3)
     for name, ref in (("grho", grho), ("gnu", gnu)):
