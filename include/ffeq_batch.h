@@ -14,7 +14,7 @@
  *   H      cf32  [n_sc][U][B]            at h_off       (complex elements)
  *   y      cf32  [n_sc][n_sym][B]        at y_off
  *   z      cf32  [n_sc][n_sym][U]        at z_off
- *   sigma2 f32   [n_sc][U]               at sigma2_off  (float elements)
+ *   sigma2 f32   [n_sc][U]               at sigma2_off  (float elements; [n_sc][n_sym][U] for LAMA)
  *   llr    f32   [n_sc][n_sym][U][bits]  at llr_off     (only when llr_bits > 0)
  *   info   i32   [n_sc][Ceff]            at info_off    (only when info is passed)
  * with Ceff = C (FD) or 1 (PD), and the layouts and meanings of ffeq.h.  The
@@ -54,8 +54,12 @@ typedef struct {
   /* ffeq_equalizer, shared by the batch: FFEQ_LMMSE (0, zero-initialized
    * configs), FFEQ_ZF or FFEQ_MRC with the meanings of ffeq.h (Sec. III-A; FD
    * fusion by Lemma 1 with the same readings, including the N0 -> 0 limit
-   * weights of MRC); FFEQ_LAMA is FFEQ_ERR_UNSUPPORTED here. */
+   * weights of MRC), or FFEQ_LAMA (Sec. III-B, Algorithm 1, FD fused by
+   * Lemma 1 as in ffeq.h: needs llr_bits > 0, the prior's constellation, and
+   * N0 > 0 in every instance; sigma^2 per received vector). */
   int equalizer;
+  /* LAMA iterations T (1..64) for FFEQ_LAMA, else 0 (FFEQ_ERR_INVALID_ARG). */
+  int lama_iters;
 } ffeq_batch_config;
 
 typedef struct ffeq_batch ffeq_batch;

@@ -80,11 +80,11 @@ namespace {
 
 // MRC runs one lane per row (no sweep); L-MMSE and ZF may split a row over two lanes.
 int lanes_per_row_default(int arch, int UP, int equalizer) {
-  return (equalizer != FFEQ_MRC && arch == FFEQ_PD && UP == 16) ? 2 : 1;
+  return (equalizer != FFEQ_MRC && equalizer != FFEQ_LAMA && arch == FFEQ_PD && UP == 16) ? 2 : 1;
 }
 
 bool lpr_allowed(int UP, int lpr, int equalizer) {
-  return lpr == 1 || (lpr == 2 && UP <= 16 && equalizer != FFEQ_MRC);
+  return lpr == 1 || (lpr == 2 && UP <= 16 && equalizer != FFEQ_MRC && equalizer != FFEQ_LAMA);
 }
 
 // Smallest CTA width that holds the widest unit of the group.
@@ -148,6 +148,8 @@ ffeq_status validate_instance(const ffeq_batch_config& cfg, const ffeq_instance&
   if (in.B % in.C != 0) return FFEQ_ERR_INVALID_ARG;
   if (!(in.N0 >= 0.f) || !std::isfinite(in.N0) || !(in.Es > 0.f) || !std::isfinite(in.Es))
     return FFEQ_ERR_INVALID_ARG;
+  const bool lama = cfg.equalizer == FFEQ_LAMA;
+  if (lama && !(in.N0 > 0.f)) return FFEQ_ERR_INVALID_ARG;   // the LAMA denoiser needs tau > 0
   if (in.U > 32 || in.n_sym > ffeq::kNsymMax) return FFEQ_ERR_UNSUPPORTED;
   const long long nsc = in.n_sc, U = in.U, B = in.B, NS = in.n_sym;
   const long long Ceff = cfg.arch == FFEQ_FD ? in.C : 1;
@@ -155,7 +157,8 @@ ffeq_status validate_instance(const ffeq_batch_config& cfg, const ffeq_instance&
     return off >= 0 && n >= 0 && off <= extent && n <= extent - off;
   };
   if (!in_range(in.h_off, nsc * U * B, cfg.h_elems) || !in_range(in.y_off, nsc * NS * B, cfg.y_elems) ||
-      !in_range(in.z_off, nsc * NS * U, cfg.z_elems) || !in_range(in.sigma2_off, nsc * U, cfg.sigma2_elems))
+      !in_range(in.z_off, nsc * NS * U, cfg.z_elems) ||
+      !in_range(in.sigma2_off, nsc * U * (lama ? NS : 1), cfg.sigma2_elems))   // LAMA: per received vector
     return FFEQ_ERR_INVALID_ARG;
   if (cfg.llr_bits && !in_range(in.llr_off, nsc * NS * U * cfg.llr_bits, cfg.llr_elems))
     return FFEQ_ERR_INVALID_ARG;
@@ -187,9 +190,12 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       cfg->precision != FFEQ_FP16X3)
     return FFEQ_ERR_INVALID_ARG;
   if (cfg->estimate != FFEQ_UNBIASED && cfg->estimate != FFEQ_LITERAL) return FFEQ_ERR_INVALID_ARG;
-  if (cfg->equalizer == FFEQ_LAMA) return FFEQ_ERR_UNSUPPORTED;
-  if (cfg->equalizer != FFEQ_LMMSE && cfg->equalizer != FFEQ_ZF && cfg->equalizer != FFEQ_MRC)
+  if (cfg->equalizer != FFEQ_LMMSE && cfg->equalizer != FFEQ_ZF && cfg->equalizer != FFEQ_MRC &&
+      cfg->equalizer != FFEQ_LAMA)
     return FFEQ_ERR_INVALID_ARG;
+  if (cfg->equalizer == FFEQ_LAMA ? (cfg->lama_iters < 1 || cfg->lama_iters > 64 || cfg->llr_bits == 0)
+                                  : cfg->lama_iters != 0)
+    return FFEQ_ERR_INVALID_ARG;   // LAMA's prior is the LLR constellation
   if (cfg->llr_bits != 0 && cfg->llr_bits != 2 && cfg->llr_bits != 4 && cfg->llr_bits != 6 && cfg->llr_bits != 8)
     return FFEQ_ERR_INVALID_ARG;
   if (cfg->h_elems < 0 || cfg->y_elems < 0 || cfg->z_elems < 0 || cfg->sigma2_elems < 0 || cfg->llr_elems < 0 ||
@@ -222,7 +228,7 @@ ffeq_status ffeq_batch_create(ffeq_batch** out, const ffeq_batch_config* cfg, co
       d.h_off = in.h_off + k * U * B;
       d.y_off = in.y_off + k * NS * B;
       d.z_off = in.z_off + k * NS * U;
-      d.s2_off = in.sigma2_off + k * U;
+      d.s2_off = in.sigma2_off + k * U * (cfg->equalizer == FFEQ_LAMA ? NS : 1);
       d.llr_off = cfg->llr_bits ? in.llr_off + k * NS * U * cfg->llr_bits : 0;
       d.info_off = cfg->info_elems > 0 ? in.info_off + k * Ceff : 0;
       d.d_off = d_off;
@@ -535,7 +541,16 @@ ffeq_status equalize_locked(ffeq_batch* b, const void* H, const void* y, void* z
     sp.threads = g.threads;
     sp.lim = lim;
     sp.status = status;
-    e = ffeq::launch_solve_batch(sp, g.lpr, gs);
+    if (b->cfg.equalizer == FFEQ_LAMA) {
+      // One CTA per unit in contraction order, its received vectors a few at a time.
+      sp.desc = gdesc + g.first;
+      sp.lama_iters = b->cfg.lama_iters;
+      const int lanes = ((g.max_ceff * g.UP + 31) / 32) * 32;
+      sp.threads = lanes > 256 ? lanes : 256;
+      e = ffeq::launch_lama_batch(sp, gs);
+    } else {
+      e = ffeq::launch_solve_batch(sp, g.lpr, gs);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
   for (int j = 0; j < n_side; ++j) {
@@ -612,8 +627,9 @@ ffeq_status ffeq_batch_autotune(ffeq_batch* b, const void* H, const void* y, voi
       if (s == FFEQ_OK && t < best) best = t;
       else g.stages = old;
     }
-    // Lanes per row and solve CTA width (tiles are rebuilt for each).
-    for (int lpr = 1; s == FFEQ_OK && lpr <= 2; ++lpr) {
+    // Lanes per row and solve CTA width (tiles are rebuilt for each); LAMA
+    // sizes its CTAs by the group's units instead.
+    for (int lpr = 1; s == FFEQ_OK && lpr <= 2 && b->cfg.equalizer != FFEQ_LAMA; ++lpr) {
       if (!lpr_allowed(g.UP, lpr, b->cfg.equalizer)) continue;
       for (int th : {64, 128, 256, 512}) {
         if (s != FFEQ_OK) break;

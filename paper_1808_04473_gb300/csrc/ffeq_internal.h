@@ -231,6 +231,7 @@ int solve_subcarriers_per_cta(int U, int Ceff);
 size_t solve_smem_bytes(int U, int Ceff);
 cudaError_t launch_solve(const SolveParams& p, cudaStream_t stream);
 cudaError_t launch_lama(const SolveParams& p, cudaStream_t stream);
+cudaError_t launch_lama_batch(const SolveParams& p, cudaStream_t stream);
 int lama_symbols_per_cta(int U, int Ceff, int n_sym);
 // Uneven batch: p.U holds the group's padded users (8/16/32), lpr its lanes per row
 // (1 for MRC, p.equalizer); ZF runs the L-MMSE kernel with rho = 0 per descriptor.

@@ -76,22 +76,33 @@ __device__ __forceinline__ void pam_posterior2(float2 x, float l2t, float d, flo
   var = make_float2(fmaxf(v2.x, 0.f), fmaxf(v2.y, 0.f));
 }
 
+// One CTA's share of a subcarrier: NB received vectors from n0 on, every
+// cluster.  Pointers are this subcarrier's (D [Ceff][U + NS][U], z and sigma^2
+// [NS][U], LLRs [NS][U][bits], info [Ceff]); S is the antennas of the calling
+// thread's cluster.  live = false: the CTA's subcarrier is past the end (inputs
+// clamped in bounds, nothing written).
+struct LamaUnit {
+  const float2* D;
+  float2* z;
+  float* s2;
+  float* llr;
+  int* info;
+  int U, NS, Ceff, NB, n0, S, iters, bits;
+  float N0, Es, d;
+  bool live;
+};
+
 template <int UP, int HB>
-__global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int U = p.U, NS = p.n_sym, Ceff = p.Ceff, NB = p.spc;   // spc: received vectors per CTA
-  const int nblk = (NS + NB - 1) / NB;
-  const int sc = blockIdx.x / nblk;
-  const int n0 = (blockIdx.x - sc * nblk) * NB;
+__device__ __forceinline__ void lama_block(const LamaUnit& w, unsigned char* smem) {
+  const int U = w.U, NS = w.NS, Ceff = w.Ceff, NB = w.NB, n0 = w.n0;
   const int g = threadIdx.x / UP, i = threadIdx.x % UP;
   const int ngroups = Ceff * NB;
   const int ngroups_pad = static_cast<int>(blockDim.x) / UP;   // groups of the last warp's padding lanes included
   const int c = g % Ceff, nb = g / Ceff;
   const int n = n0 + nb;
-  const bool valid = g < ngroups && n < NS && sc < p.n_sc;
+  const bool valid = g < ngroups && n < NS && w.live;
   const int cc = g < ngroups ? c : 0;
   const int nc = valid ? n : n0;
-  const int scc = sc < p.n_sc ? sc : p.n_sc - 1;
   const bool real = i < U;
   const int ic = real ? i : 0;
 
@@ -103,14 +114,11 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p
   float* const sb0 = sbuf + 2 * g * UP;
   float* const sb1 = sbuf + 2 * (ngroups_pad + g) * UP;
 
-  // Wait for the contraction grid (programmatic dependent launch).
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-
-  const int S = p.cl_size[cc];
+  const int S = w.S;
   const float kap = S > 0 ? 1.f / static_cast<float>(S) : 0.f;
   const float beta = static_cast<float>(U) * kap;
-  const float n0n = S > 0 ? p.N0 * kap : 1.f;     // an empty cluster: any tau > 0, weight 0 below
-  const float2* Dg = p.D + (static_cast<size_t>(scc) * Ceff + cc) * static_cast<size_t>(U + NS) * U;
+  const float n0n = S > 0 ? w.N0 * kap : 1.f;     // an empty cluster: any tau > 0, weight 0 below
+  const float2* Dg = w.D + static_cast<size_t>(cc) * static_cast<size_t>(U + NS) * U;
   // Row i of kappa G_c as pairs of adjacent columns: (re j, re j+1), (im j, im j+1).
   float2 gre[UP / 2], gim[UP / 2];
 #pragma unroll
@@ -122,13 +130,13 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p
     gim[j / 2] = make_float2(g0.y, g1.y);
   }
   const float2 yv = real ? cscale(Dg[(U + nc) * U + ic], kap) : make_float2(0.f, 0.f);
-  const float d = p.llr_scale;
+  const float d = w.d;
   const float inv_d = 1.f / d;
   const float invU = 1.f / static_cast<float>(U);
   constexpr float kLog2e = 1.4426950408889634f;
 
   float2 s = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f), z;
-  float phi = p.Es, tau;
+  float phi = w.Es, tau;
   for (int t = 1;; ++t) {
     // z = y + s - G s + v.  A group lies within one warp: __syncwarp orders this
     // iteration's stores before the loads, and the buffer written next iteration
@@ -158,7 +166,7 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p
     const float2 gs = make_float2((rr.x + rr.y) - (ii.x + ii.y), (ri.x + ri.y) + (ir.x + ir.y));
     z = __fadd2_rn(__fadd2_rn(__fadd2_rn(yv, s), make_float2(-gs.x, -gs.y)), v);
     tau = fmaf(beta, phi, n0n);
-    if (t >= p.lama_iters) break;
+    if (t >= w.iters) break;
     const float inv_tau = rcp_approx(tau);
     const float l2t = kLog2e * inv_tau;
     float2 mean, var;
@@ -174,19 +182,19 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p
   }
 
   if (g < ngroups) {
-    const float w = S > 0 ? 1.f / tau : 0.f;
-    Fz[g * UP + i] = cscale(z, w);
-    if (i == 0) Wt[g] = w;
-    if (valid && i == 0 && p.info) p.info[static_cast<size_t>(sc) * Ceff + c] = 0;
+    const float wc = S > 0 ? 1.f / tau : 0.f;
+    Fz[g * UP + i] = cscale(z, wc);
+    if (i == 0) Wt[g] = wc;
+    if (valid && i == 0 && w.info) w.info[c] = 0;
   }
   __syncthreads();
 
   // ---- per (symbol, user) of this CTA: fuse over the clusters, write the outputs
-  const int hb = p.llr_bits / 2;
+  const int hb = w.bits / 2;
   for (int e = threadIdx.x; e < NB * U; e += blockDim.x) {
     const int b = e / U, u = e - b * U;
     const int nn = n0 + b;
-    if (nn >= NS || sc >= p.n_sc) break;
+    if (nn >= NS || !w.live) break;
     float2 nm = make_float2(0.f, 0.f);
     float dn = 0.f;
     for (int k = 0; k < Ceff; ++k) {
@@ -200,10 +208,93 @@ __global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p
       zz = cscale(nm, rr);
       s2 = rr;
     }
-    const size_t zi = (static_cast<size_t>(sc) * NS + nn) * U + u;
-    p.z[zi] = zz;
-    p.sigma2[zi] = s2;
-    if (p.llr_bits) symbol_llr(zz, s2, p.llr_scale, hb, p.llr + zi * p.llr_bits);
+    const size_t zi = static_cast<size_t>(nn) * U + u;
+    w.z[zi] = zz;
+    w.s2[zi] = s2;
+    if (w.bits) symbol_llr(zz, s2, w.d, hb, w.llr + zi * w.bits);
+  }
+}
+
+template <int UP, int HB>
+__global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int NS = p.n_sym, NB = p.spc;   // spc: received vectors per CTA
+  const int nblk = (NS + NB - 1) / NB;
+  const int sc = blockIdx.x / nblk;
+  const int scc = sc < p.n_sc ? sc : p.n_sc - 1;
+  const int g = threadIdx.x / UP;
+  const int cc = g < p.Ceff * NB ? g % p.Ceff : 0;
+  LamaUnit w;
+  w.D = p.D + static_cast<size_t>(scc) * p.Ceff * static_cast<size_t>(p.U + NS) * p.U;
+  w.z = p.z + static_cast<size_t>(scc) * NS * p.U;
+  w.s2 = p.sigma2 + static_cast<size_t>(scc) * NS * p.U;
+  w.llr = p.llr_bits ? p.llr + static_cast<size_t>(scc) * NS * p.U * p.llr_bits : nullptr;
+  w.info = p.info ? p.info + static_cast<size_t>(scc) * p.Ceff : nullptr;
+  w.U = p.U;
+  w.NS = NS;
+  w.Ceff = p.Ceff;
+  w.NB = NB;
+  w.n0 = (blockIdx.x - sc * nblk) * NB;
+  w.S = p.cl_size[cc];
+  w.iters = p.lama_iters;
+  w.bits = p.llr_bits;
+  w.N0 = p.N0;
+  w.Es = p.Es;
+  w.d = p.llr_scale;
+  w.live = sc < p.n_sc;
+  // Wait for the contraction grid (programmatic dependent launch).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  lama_block<UP, HB>(w, smem);
+}
+
+// Uneven batch: one CTA per unit (subcarrier of an instance), whose descriptor
+// gives the sizes, scalars and offsets (each checked against the batch's
+// extents; a unit that fails is skipped and sets FFEQ_ERR_INVALID_ARG in the
+// status word).  The CTA takes the unit's received vectors NB at a time, NB =
+// threads / (Ceff UP), clusters of B / Ceff antennas; sigma^2 per received
+// vector ([NS][U] at s2_off).
+template <int UP, int HB>
+__global__ void __maxnreg__(UP == 32 ? 128 : 64) lama_batch_kernel(const SolveParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int j = blockIdx.x;
+  if (j >= p.n_desc) return;
+  const BatchDesc d = p.desc[j];
+  const int U = d.U, NS = d.n_sym, Ceff = d.Ceff, B = d.B;
+  const long long lanes = static_cast<long long>(Ceff) * UP;
+  bool ok = U >= 1 && U <= UP && NS >= 1 && NS <= kNsymMax && Ceff >= 1 && Ceff <= kMaxClusters && B >= Ceff &&
+            B % Ceff == 0 && lanes <= static_cast<long long>(blockDim.x) && d.N0 > 0.f && d.Es > 0.f &&
+            d.llr_scale > 0.f && p.llr_bits > 0;
+  if (ok) {
+    const long long mat = static_cast<long long>(U + NS) * U, per = static_cast<long long>(NS) * U;
+    ok = span_ok(d.d_off, Ceff * mat, p.lim.d) && span_ok(d.z_off, per, p.lim.z) && span_ok(d.s2_off, per, p.lim.s2) &&
+         span_ok(d.llr_off, per * p.llr_bits, p.lim.llr) && (!p.info || span_ok(d.info_off, Ceff, p.lim.info));
+  }
+  if (!ok) {
+    if (threadIdx.x == 0 && p.status) atomicExch(p.status, FFEQ_ERR_INVALID_ARG);
+    return;
+  }
+  LamaUnit w;
+  w.D = p.D + d.d_off;
+  w.z = p.z + d.z_off;
+  w.s2 = p.sigma2 + d.s2_off;
+  w.llr = p.llr + d.llr_off;
+  w.info = p.info ? p.info + d.info_off : nullptr;
+  w.U = U;
+  w.NS = NS;
+  w.Ceff = Ceff;
+  w.NB = static_cast<int>(blockDim.x / lanes);
+  w.S = B / Ceff;
+  w.iters = p.lama_iters;
+  w.bits = p.llr_bits;
+  w.N0 = d.N0;
+  w.Es = d.Es;
+  w.d = d.llr_scale;
+  w.live = true;
+  for (int n0 = 0; n0 < NS; n0 += w.NB) {
+    w.n0 = n0;
+    lama_block<UP, HB>(w, smem);
+    __syncthreads();   // the next vectors reuse the shared areas
   }
 }
 
@@ -238,7 +329,48 @@ cudaError_t launch_lama_bits(const SolveParams& p, cudaStream_t stream) {
   }
 }
 
+template <int UP, int HB>
+cudaError_t launch_lama_batch_up(const SolveParams& p, cudaStream_t stream) {
+  const int ngp = p.threads / UP;   // lane groups of a CTA (each unit uses Ceff * NB of them)
+  const size_t smem = static_cast<size_t>(4 * ngp) * UP * sizeof(float) +
+                      static_cast<size_t>(ngp) * UP * sizeof(float2) + static_cast<size_t>(ngp) * 4;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(p.n_desc));
+  cfg.blockDim = dim3(p.threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lama_batch_kernel<UP, HB>, p);
+}
+
+template <int UP>
+cudaError_t launch_lama_batch_bits(const SolveParams& p, cudaStream_t stream) {
+  switch (p.llr_bits) {
+    case 2: return launch_lama_batch_up<UP, 1>(p, stream);
+    case 4: return launch_lama_batch_up<UP, 2>(p, stream);
+    case 6: return launch_lama_batch_up<UP, 3>(p, stream);
+    default: return launch_lama_batch_up<UP, 4>(p, stream);
+  }
+}
+
 }  // namespace
+
+// Uneven batch (p.U = the group's users padding, p.threads a multiple of 32 of
+// at least Ceff * UP for every unit, p.desc / p.n_desc the group's units).
+cudaError_t launch_lama_batch(const SolveParams& p, cudaStream_t stream) {
+  if (p.n_desc <= 0) return cudaSuccess;
+  if (p.threads < 32 || p.threads > 512 || p.threads % 32 || p.threads % p.U) return cudaErrorInvalidValue;
+  switch (p.U) {
+    case 8: return launch_lama_batch_bits<8>(p, stream);
+    case 16: return launch_lama_batch_bits<16>(p, stream);
+    case 32: return launch_lama_batch_bits<32>(p, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 // Received vectors per CTA: the groups of all clusters of NB vectors, at most
 // 256 lanes, with NB chosen so that the blocks of one subcarrier split n_sym evenly.

@@ -55,7 +55,8 @@ class ffeq_batch_config(ctypes.Structure):
     _fields_ = [("arch", ctypes.c_int), ("precision", ctypes.c_int), ("estimate", ctypes.c_int),
                 ("llr_bits", ctypes.c_int), ("h_elems", ctypes.c_longlong), ("y_elems", ctypes.c_longlong),
                 ("z_elems", ctypes.c_longlong), ("sigma2_elems", ctypes.c_longlong),
-                ("llr_elems", ctypes.c_longlong), ("info_elems", ctypes.c_longlong), ("equalizer", ctypes.c_int)]
+                ("llr_elems", ctypes.c_longlong), ("info_elems", ctypes.c_longlong), ("equalizer", ctypes.c_int),
+                ("lama_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -376,11 +377,12 @@ def ffeq_batch_set_tuning(batch: Batch, tuning) -> None:
 
 
 def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNBIASED, llr_bits: int = 0,
-               with_info: bool = True, equalizer: int = LMMSE):
+               with_info: bool = True, equalizer: int = LMMSE, lama_iters: int = 0):
     """Lay instances out back to back in flat buffers.
 
     ``specs``: sequence of ``(B, U, C, n_sc, n_sym, N0, Es)``.  Offsets of the
-    complex arrays are kept even (16-byte aligned rows when B is even).
+    complex arrays are kept even (16-byte aligned rows when B is even); sigma^2
+    is ``[n_sc][n_sym][U]`` per instance for LAMA, else ``[n_sc][U]``.
     Returns ``(config, instances)``.
     """
     def even(x):
@@ -394,11 +396,11 @@ def pack_batch(specs, arch: int = PD, precision: int = FP32, estimate: int = UNB
         offs["h"] = even(offs["h"] + n_sc * U * B)
         offs["y"] = even(offs["y"] + n_sc * n_sym * B)
         offs["z"] = even(offs["z"] + n_sc * n_sym * U)
-        offs["s2"] += n_sc * U
+        offs["s2"] += n_sc * U * (n_sym if equalizer == LAMA else 1)
         offs["llr"] += n_sc * n_sym * U * llr_bits
         offs["info"] += n_sc * Ceff
     cfg = ffeq_batch_config(arch, precision, estimate, llr_bits, offs["h"], offs["y"], offs["z"], offs["s2"],
-                            offs["llr"], offs["info"] if with_info else 0, equalizer)
+                            offs["llr"], offs["info"] if with_info else 0, equalizer, lama_iters)
     return cfg, inst
 
 

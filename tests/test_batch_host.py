@@ -123,12 +123,22 @@ def test_tuning_roundtrip_and_validation(lib):
 
 
 def test_equalizer_choice(lib):
-    """ZF and MRC batches plan like L-MMSE ones (MRC: one lane per row, no sweep);
-    LAMA is not offered for batches and an unknown equalizer is an argument error."""
+    """ZF, MRC and LAMA batches plan like L-MMSE ones (MRC and LAMA: one lane per
+    row); LAMA takes 1..64 iterations, the others none; an unknown equalizer is an
+    argument error."""
     ps = synth.make_uneven(64, seed=5)
-    for eq, status in ((ffeq.LMMSE, 0), (ffeq.ZF, 0), (ffeq.MRC, 0), (ffeq.LAMA, 2), (7, 1), (-1, 1)):
-        cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.PD, llr_bits=4, equalizer=eq)
-        assert _status(ffeq.ffeq_batch_create, cfg, inst) == status, eq
+    for eq, iters, status in ((ffeq.LMMSE, 0, 0), (ffeq.ZF, 0, 0), (ffeq.MRC, 0, 0), (ffeq.LAMA, 6, 0),
+                              (ffeq.LAMA, 0, 1), (ffeq.LAMA, 65, 1), (ffeq.ZF, 2, 1), (7, 0, 1), (-1, 0, 1)):
+        cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.PD, llr_bits=4, equalizer=eq, lama_iters=iters)
+        assert _status(ffeq.ffeq_batch_create, cfg, inst) == status, (eq, iters)
+    cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.FD, llr_bits=4, equalizer=ffeq.LAMA, lama_iters=6)
+    assert all(t[3] == 1 for t in ffeq.ffeq_batch_get_tuning(ffeq.ffeq_batch_create(cfg, inst)))
+    # LAMA's prior is the LLR constellation, and its denoiser needs N0 > 0 in every instance.
+    cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.FD, llr_bits=0, equalizer=ffeq.LAMA, lama_iters=6)
+    assert _status(ffeq.ffeq_batch_create, cfg, inst) == 1
+    q = synth.make_problem(64, 4, 2, 2, 3, snr_db=10.0, bits=4, seed=2, noiseless=True)
+    cfg, inst = ffeq.pack_batch(_specs(ps + [q]), arch=ffeq.FD, llr_bits=4, equalizer=ffeq.LAMA, lama_iters=6)
+    assert _status(ffeq.ffeq_batch_create, cfg, inst) == 1
     cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.PD, llr_bits=4, equalizer=ffeq.MRC)
     b = ffeq.ffeq_batch_create(cfg, inst)
     tun = ffeq.ffeq_batch_get_tuning(b)

@@ -32,6 +32,7 @@ import numpy as np
 import pytest
 
 import parity
+from oracle import lama as olama
 from oracle import linear as olinear
 from oracle import llr as ollr
 from oracle import lmmse
@@ -80,11 +81,12 @@ def _specs(ps):
 class Run:
     """Device buffers of one packed batch and its plan."""
 
-    def __init__(self, ff, ps, arch, precision=0, estimate=0, llr_bits=4, with_info=True, specs=None, equalizer=0):
+    def __init__(self, ff, ps, arch, precision=0, estimate=0, llr_bits=4, with_info=True, specs=None, equalizer=0,
+                 lama_iters=0):
         dev = torch.device("cuda:0")
         self.ff, self.ps, self.arch, self.bits = ff, ps, arch, llr_bits
         cfg, inst = ff.pack_batch(specs or _specs(ps), arch=arch, precision=precision, estimate=estimate,
-                                  llr_bits=llr_bits, with_info=with_info, equalizer=equalizer)
+                                  llr_bits=llr_bits, with_info=with_info, equalizer=equalizer, lama_iters=lama_iters)
         self.cfg, self.inst = cfg, inst
         H, y = _flat(ps, cfg, inst)
         self.H = torch.from_numpy(H).to(dev)
@@ -372,5 +374,43 @@ def test_zf_and_mrc_batches_match_the_oracle(ff, arch, eq):
         L = out["llr"][it.llr_off:it.llr_off + n * NS * U * 4].reshape(n, NS, U, 4)
         if p.N0 > 0:
             parity.check(f"llr[{idx}]", L, ollr.maxlog_llr(o["z"], o["sigma2"][:, None, :], 4, p.Es), 4 * tol)
+        Ceff = p.C if arch == 1 else 1
+        assert (out["info"][it.info_off:it.info_off + n * Ceff] == 0).all(), idx
+
+
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+def test_lama_batch_matches_the_oracle(ff, arch):
+    """LAMA (Sec. III-B, Algorithm 1, T = 6) in the uneven batch against
+    ``oracle.lama`` per instance: z, sigma^2 per received vector and the LLRs (4x),
+    FP32 preprocessing, within the uniform LAMA path's bound (2e-5) on instances
+    whose every cluster has beta_c = U / S_c <= 1/2 (as the uniform LAMA cases)."""
+    rng = np.random.default_rng(11 + arch)
+    ps = []
+    for k in range(40):
+        B = int(rng.choice([64, 128, 256]))
+        U = int(rng.integers(1, 33))
+        Cs = [c for c in (1, 2, 4, 8, 16) if B // c >= 2 * U]
+        if not Cs:
+            U = B // 2
+            Cs = [1]
+        C = int(rng.choice(Cs))
+        ps.append(synth.make_problem(B, U, C, int(rng.integers(1, 4)), int(rng.integers(1, 15)),
+                                     snr_db=float(rng.uniform(5, 20)), bits=4, seed=9000 + 100 * arch + k,
+                                     Es=float(rng.choice([1.0, 2.0]))))
+    run = Run(ff, ps, arch, precision=0, llr_bits=4, equalizer=ff.LAMA, lama_iters=6)
+    run.equalize()
+    out = run.host()
+    assert ff.ffeq_device_status(clear=True) == 0
+    f = olama.equalize_pd_lama if arch == 0 else olama.equalize_fd_lama
+    tol = 2e-5
+    for idx, (p, it) in enumerate(zip(ps, run.inst)):
+        o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, 4, 6)
+        n, U, NS = p.n_sc, p.U, p.n_sym
+        z = out["z"][it.z_off:it.z_off + n * NS * U].reshape(n, NS, U)
+        s2 = out["s2"][it.sigma2_off:it.sigma2_off + n * NS * U].reshape(n, NS, U)
+        parity.check(f"z[{idx}]", z, o["z"], tol)
+        parity.check(f"sigma2[{idx}]", s2, o["sigma2"], tol)
+        L = out["llr"][it.llr_off:it.llr_off + n * NS * U * 4].reshape(n, NS, U, 4)
+        parity.check(f"llr[{idx}]", L, ollr.maxlog_llr(o["z"], o["sigma2"], 4, p.Es), 4 * tol)
         Ceff = p.C if arch == 1 else 1
         assert (out["info"][it.info_off:it.info_off + n * Ceff] == 0).all(), idx
