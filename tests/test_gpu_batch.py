@@ -378,12 +378,17 @@ def test_zf_and_mrc_batches_match_the_oracle(ff, arch, eq):
         assert (out["info"][it.info_off:it.info_off + n * Ceff] == 0).all(), idx
 
 
+LAMA_TOL = {0: 2e-5, 2: 3e-4, 3: 5e-5}      # the uniform LAMA path's bounds (FP32, BF16x3, FP16x3)
+
+
+@pytest.mark.parametrize("precision", [0, 2, 3], ids=["fp32", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
-def test_lama_batch_matches_the_oracle(ff, arch):
+def test_lama_batch_matches_the_oracle(ff, arch, precision):
     """LAMA (Sec. III-B, Algorithm 1, T = 6) in the uneven batch against
     ``oracle.lama`` per instance: z, sigma^2 per received vector and the LLRs (4x),
-    FP32 preprocessing, within the uniform LAMA path's bound (2e-5) on instances
-    whose every cluster has beta_c = U / S_c <= 1/2 (as the uniform LAMA cases)."""
+    within the uniform LAMA path's bound for the preprocessing precision, on
+    instances whose every cluster has beta_c = U / S_c <= 1/2 (as the uniform
+    LAMA cases)."""
     rng = np.random.default_rng(11 + arch)
     ps = []
     for k in range(40):
@@ -397,12 +402,12 @@ def test_lama_batch_matches_the_oracle(ff, arch):
         ps.append(synth.make_problem(B, U, C, int(rng.integers(1, 4)), int(rng.integers(1, 15)),
                                      snr_db=float(rng.uniform(5, 20)), bits=4, seed=9000 + 100 * arch + k,
                                      Es=float(rng.choice([1.0, 2.0]))))
-    run = Run(ff, ps, arch, precision=0, llr_bits=4, equalizer=ff.LAMA, lama_iters=6)
+    run = Run(ff, ps, arch, precision=precision, llr_bits=4, equalizer=ff.LAMA, lama_iters=6)
     run.equalize()
     out = run.host()
     assert ff.ffeq_device_status(clear=True) == 0
     f = olama.equalize_pd_lama if arch == 0 else olama.equalize_fd_lama
-    tol = 2e-5
+    tol = LAMA_TOL[precision]
     for idx, (p, it) in enumerate(zip(ps, run.inst)):
         o = f(p.H, p.y, float(np.float32(p.N0)), p.Es, p.C, 4, 6)
         n, U, NS = p.n_sc, p.U, p.n_sym
