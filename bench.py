@@ -404,7 +404,7 @@ FUSED_SHAPE = 6          # the contraction and the solve in one launch (include/
 
 def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equalizer=0, refine=0,
                    refine_fp64=0, pinned=None, breakdown=False, sampler=None, soak_s=0.0, concurrent=False,
-                   tune_step=False):
+                   tune_step=False, tune_schedule=False):
     """K steps of PD then FD equalization; each step is captured once per rotating
     input set as a CUDA graph (what a serving loop replays per frame) and the
     timed region replays K graphs, bracketed by CUDA events on the replay stream.
@@ -420,6 +420,8 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
     every pair of contraction shapes in STEP_SHAPES, sequential and concurrent,
     and keep the fastest (setup, outside the timed region): the best shape of a
     plan alone is not always the best one next to the other plan's kernels.
+    tune_schedule: keep each plan's own tuning and choose only between the
+    sequential and the concurrent step by timing both.
     Leaves the outputs of input set 0 in `outs`."""
     torch, ffeq, dev = R.torch, R.ffeq, R.dev
     B, U, C, n_sc, n_sym = shape
@@ -527,6 +529,17 @@ def equalize_steps(R, shape, Hs, ys, N0, Es, *, precision, bits, K, warmup, equa
             for a in archs:
                 launch(a, 0, "step")
         cap.synchronize()
+    elif tune_schedule and not pinned:
+        best = None
+        for conc in (False, True):
+            concurrent = conc
+            gs = [capture(lambda i=i: whole_step(i)) for i in range(n_sets)]
+            t = time_steps(gs, 2 * n_sets)
+            del gs
+            if best is None or t < best[0]:
+                best = (t, conc)
+        concurrent = best[1]
+        schedule = {"concurrent": concurrent, "chosen_by": "whole-step timing, sequential against concurrent"}
     steps = [capture(lambda i=i: whole_step(i)) for i in range(n_sets)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if sampler is not None:          # clocks: sampled from the load phase through the timed region
@@ -841,8 +854,9 @@ def run_correlated(R, K, warmup):
     for name, prec, refine in (("fp32", "fp32", 0), ("fp16x3", "fp16x3", 0),
                                ("fp32+refine1(fp64>1e4)", "fp32", 1), ("fp16x3+refine1(fp64>1e4)", "fp16x3", 1)):
         r = equalize_steps(R, shape, Hs, ys, p.N0, p.Es, precision=prec, bits=w["bits"], K=K, warmup=warmup,
-                           refine=refine, refine_fp64=1 if refine else 0)
+                           refine=refine, refine_fp64=1 if refine else 0, tune_schedule=True)
         arms[name] = {"value": job_rate(symbols, R.world, K, r["ms"]), "ms_per_step": r["ms"] / K, "steps": K,
+                      "schedule": r["schedule"],
                       "error_vs_oracle": _accuracy(p, r["outs"], idx, (0, 1)) if R.rank == 0 else None}
         del r
     return {"workload": "B=256 U=32 C=16 3300sc x 14sym 64-QAM, exponential correlation r=0.7, 15dB, PD+FD, LLRs",
