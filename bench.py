@@ -1201,7 +1201,7 @@ def main():
         extras["training"] = run_training(R, max(5, min(K // 10, 200)), args.warmup)
         u = uneven_line(R, max(5, min(K // 10, 200)), args.warmup, args.precision)
         extras["uneven"] = {k: u[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "roofline",
-                                              "tuning")}
+                                              "tuning", "schedule")}
 
     # ---- roofline of the dominant kernel (and of the Gram stage)
     hbm_peak, peak_src = _peaks()
