@@ -4,8 +4,9 @@
 the plan; this module stores the result in a JSON file keyed by the GPU name,
 the batch configuration and the multiset of instance shapes, so that a later
 process with the same batch skips the timing and restores the tuning with
-``ffeq_batch_set_tuning``.  Only launch shapes are cached: every tuning gives
-bit-identical results.
+``ffeq_batch_set_tuning``.  Only launch shapes are cached: pipeline depth and
+CTA width give bit-identical results, lanes per row changes only the rounding
+order of the solve.
 """
 from __future__ import annotations
 
@@ -26,7 +27,7 @@ def default_cache_path() -> str:
 def batch_key(batch: ffeq.Batch, device_name: str) -> str:
     c = batch.config
     shapes = sorted((i.B, i.U, i.C, i.n_sc, i.n_sym) for i in batch.instances)
-    text = json.dumps([device_name, c.arch, c.precision, c.estimate, c.llr_bits, shapes])
+    text = json.dumps([device_name, c.arch, c.precision, c.estimate, c.llr_bits, c.equalizer, c.lama_iters, shapes])
     return hashlib.sha256(text.encode()).hexdigest()[:32]
 
 

@@ -148,3 +148,18 @@ def test_equalizer_choice(lib):
             t = [list(x) for x in tun]
             t[gi][3] = 2                                    # MRC has no row sweep to split
             assert _status(ffeq.ffeq_batch_set_tuning, b, t) == 1
+
+
+def test_tuning_cache_key_separates_equalizers(lib):
+    """The cached launch shapes of a batch are keyed by everything the plan's
+    groups and kernels depend on: the same shapes with another equalizer or
+    iteration count take another entry."""
+    from paper_1808_04473_gb300 import tuning
+    ps = synth.make_uneven(32, seed=8)
+    keys = {}
+    for eq, iters in ((ffeq.LMMSE, 0), (ffeq.ZF, 0), (ffeq.MRC, 0), (ffeq.LAMA, 4), (ffeq.LAMA, 8)):
+        cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.FD, llr_bits=4, equalizer=eq, lama_iters=iters)
+        keys[(eq, iters)] = tuning.batch_key(ffeq.ffeq_batch_create(cfg, inst), "GPU")
+    assert len(set(keys.values())) == len(keys)
+    cfg, inst = ffeq.pack_batch(_specs(ps), arch=ffeq.FD, llr_bits=4)
+    assert tuning.batch_key(ffeq.ffeq_batch_create(cfg, inst), "GPU") == keys[(ffeq.LMMSE, 0)]
