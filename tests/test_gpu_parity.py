@@ -247,6 +247,20 @@ def test_host_entry_point_both_paths(ff, arch, pinned):
     assert np.array_equal(L.numpy(), g["llr"]) and (info.numpy() == 0).all()
 
 
+@pytest.mark.parametrize("snr", [float(v) for v in range(0, 22, 2)])
+@pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp32", "bf16x3"])
+def test_snr_sweep_of_the_throughput_shape(ff, snr, arch, precision):
+    """The per-subcarrier shape of the throughput workload (B=256, U=16, C=8, 14
+    symbols, 16-QAM) over its SNR sweep, 0..20 dB in 2 dB steps, FP32 and BF16x3
+    contractions: every subcarrier of 96 against the oracle, z, sigma^2 and LLRs,
+    within the precision's bound (kappa-aware)."""
+    p = synth.make_problem(256, 16, 8, 96, 14, snr_db=snr, bits=4, seed=4000 + int(snr))
+    g = _gpu(ff, p, arch, 0, llr_bits=4, precision=precision)
+    _check(g, _oracle(p, arch, 0), p, 4, tol=_bound(p, arch, precision))
+    assert (g["info"] == 0).all()
+
+
 @pytest.mark.parametrize("arch", [0, 1], ids=["PD", "FD"])
 @pytest.mark.parametrize("precision", [0, 1, 2, 3], ids=["fp32", "tf32x3", "bf16x3", "fp16x3"])
 def test_full_size_throughput_workload_sampled(ff, arch, precision):
